@@ -1,0 +1,179 @@
+/*
+ * hpmxp.h -- C interface of the HPL-MxP solver library (libhpmxp.so).
+ *
+ * The library solves A x = b for a dense n x n system to the fp64 accuracy
+ * HPL demands, by a low-precision LU factorization without pivoting followed
+ * by fp64 GMRES-based iterative refinement (Dongarra & Luszczek, "HPL-MxP
+ * Benchmark: Mixed-Precision Algorithms, Iterative Refinement, and Scalable
+ * Data Generation", arXiv 2509.19618, section "Algorithmic Framework").  It
+ * runs on one GB300 GPU (sm_103a).
+ *
+ * Conventions shared by every entry point:
+ *  - Every array argument is DEVICE memory owned by the caller.  The library
+ *    never allocates, frees or retains caller memory; scratch space is passed
+ *    in as `ws` / `ws_bytes` (size from the matching *_workspace function,
+ *    256-byte aligned).  Host-side outputs are marked "host".
+ *  - Matrices are column major with an explicit leading dimension.
+ *  - Every call is ordered on the caller's CUDA stream (`stream`, a
+ *    cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
+ *    that return host values synchronize that stream before returning.
+ *  - Every call returns an hpmxp_status and never aborts, exits or traps.
+ *    HPMXP_EINVAL leaves every output untouched.  Device waits inside the
+ *    library's kernels are bounded; a wait that runs out returns
+ *    HPMXP_ETIMEOUT and leaves the outputs unspecified.
+ *  - The library is thread compatible: concurrent calls must use distinct
+ *    workspaces.
+ */
+#ifndef HPMXP_H_
+#define HPMXP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HPMXP_OK = 0,
+  HPMXP_EINVAL = 1,      /* bad argument (size, leading dimension, alignment, NULL) */
+  HPMXP_ENOMEM = 2,      /* workspace too small */
+  HPMXP_ECUDA = 3,       /* a CUDA runtime/driver call failed */
+  HPMXP_ENOCONV = 4,     /* refinement needed more than max_iters iterations */
+  HPMXP_EBREAKDOWN = 5,  /* zero or non-finite pivot, or non-finite value in the refinement */
+  HPMXP_ETIMEOUT = 6,    /* a bounded device-side wait ran out */
+  HPMXP_EINVALID = 7     /* final scaled residual >= the acceptance threshold */
+} hpmxp_status;
+
+/* Low-precision format of the factorization (section "Algorithmic Framework":
+ * the factors must be at least FP16-accurate; BF16 has FP32's exponent range).
+ * HPMXP_FP8_E4M3 keeps BF16 factors and runs only the trailing-matrix (Schur)
+ * update on OCP E4M3 operands with fp32 per-128x128-tile scales. */
+typedef enum { HPMXP_BF16 = 0, HPMXP_FP16 = 1, HPMXP_FP8_E4M3 = 2 } hpmxp_prec;
+
+/* Diagonal of the generated matrix (section "Matrix Generation" and the
+ * diagonal-scaling discussion of section "Experimental Results"). */
+typedef enum {
+  HPMXP_DIAG_DOMINANT = 0, /* a_ii = sum_{j!=i} |a_ij| + margin: strictly row diagonally dominant */
+  HPMXP_DIAG_SQRTN = 1,    /* a_ii = r_ii + sign(r_ii) sqrt(n): the sqrt(n) scaling the paper recommends */
+  HPMXP_DIAG_NONE = 2      /* raw uniform entries, no diagonal scaling */
+} hpmxp_diag;
+
+/* Human-readable name of a status code (static storage; never NULL). */
+const char* hpmxp_status_string(hpmxp_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int hpmxp_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Generation (section "Matrix Generation": a scalable generator for which any
+ * entry is computable independently; the matrix admits LU without pivoting).
+ *
+ * Entries come from the 64-bit LCG s' = 6364136223846793005 s +
+ * 1442695040888963407 (mod 2^64) seeded with `seed`; draw t uses the state
+ * after t+1 steps, reached by skip-ahead.  The top 52 bits u of a state give
+ * the value (2u + 1 - 2^52) 2^-53, uniform in (-0.5, 0.5) and never 0.
+ * Entry A(i,j) is draw i + j*n, b(i,r) is draw n*n + i + r*n.  The diagonal is
+ * then replaced as `diag_mode` says; for DOMINANT the off-diagonal magnitudes
+ * are summed exactly in 128-bit integer arithmetic and a_ii =
+ * fl(fl(S_i) 2^-53 + margin), so the result is bit-for-bit reproducible.
+ *
+ *   n        1 <= n <= 131072
+ *   A        out, n x n fp64, column major, lda >= n
+ *   b        out, n x nrhs fp64, ldb >= n (may be NULL when nrhs == 0)
+ *   ws       scratch of hpmxp_generate_workspace(n) bytes
+ * Generation is not part of the timed solve (section "Algorithmic Framework",
+ * figure-of-merit paragraph). */
+size_t hpmxp_generate_workspace(int64_t n);
+hpmxp_status hpmxp_generate(int64_t n, uint64_t seed, double margin, int diag_mode, double* A,
+                            int64_t lda, double* b, int64_t ldb, int64_t nrhs, void* ws,
+                            size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Low-precision LU without pivoting (section "Algorithmic Framework", Fig. 1).
+ *
+ * Casts A (fp64) to the factor format (round to nearest even) and factors it
+ * in place, right-looking, with Schur-update depth `nb` (128, 256 or 512):
+ * the diagonal block is factored in fp32 arithmetic (recursively at depth 128),
+ * the panels are formed by multiplying with fp32-inverted 128x128 diagonal
+ * blocks, and the trailing update A22 <- A22 - L21 U12 is a tensor-core product
+ * of low-precision operands accumulated in fp32 and rounded once into storage.
+ *
+ *   A        in, n x n fp64, lda >= n (not modified)
+ *   prec     hpmxp_prec
+ *   LU       out, n x n 16-bit (BF16 for HPMXP_BF16 and HPMXP_FP8_E4M3, FP16 for
+ *            HPMXP_FP16), column major; unit-lower L below the diagonal, U on
+ *            and above it.  ldlu >= n, ldlu % 8 == 0, LU 16-byte aligned.
+ *   ws       scratch of hpmxp_factor_workspace(n, prec, nb) bytes
+ * Returns HPMXP_EBREAKDOWN when a pivot is zero or not finite (the factors are
+ * then unusable). */
+size_t hpmxp_factor_workspace(int64_t n, int prec, int nb);
+hpmxp_status hpmxp_factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU,
+                          int64_t ldlu, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* GMRES-based iterative refinement (section "Algorithmic Framework").
+ *
+ * x0 = U^{-1} L^{-1} b from the low-precision factors, then repeatedly
+ * r = b - A x in fp64; stop when the HPL scaled residual
+ * ||r||_inf / ((||A||_inf ||x||_inf + ||b||_inf) n 2^-53) < accept; otherwise run
+ * restarted GMRES(restart) on M^{-1} A d = M^{-1} r with M = LU as a LEFT
+ * preconditioner (modified Gram-Schmidt Arnoldi, Givens rotations, fp64) and
+ * update x += d.  More than max_iters inner iterations in total is a failure
+ * (the paper's 50-iteration rule).  An inner cycle stops once the
+ * least-squares residual estimate |g_{j+1}| <= beta * max(inner_tol,
+ * theta * accept / sr0), sr0 being the scaled residual when the cycle starts. */
+typedef struct {
+  int32_t restart;       /* GMRES restart length m, 1..64 (default 30) */
+  int32_t max_iters;     /* cap on inner iterations summed over restarts (default 50) */
+  double inner_tol;      /* relative floor of the inner stopping test (default 1e-12) */
+  double theta;          /* adaptive inner-stopping factor, 0 disables (default 0.1) */
+  double accept;         /* acceptance threshold of the scaled residual (default 16) */
+  int32_t precond_fp32;  /* 1: apply M^{-1} in fp32 arithmetic, 0: fp64 (default 0) */
+  int32_t reserved;
+} hpmxp_ir_params;
+
+typedef struct {
+  int32_t iters;         /* inner (Arnoldi) iterations, summed over restarts */
+  int32_t outer;         /* restart cycles started */
+  double scaled_resid;   /* scaled residual of the returned x */
+  int32_t status;        /* hpmxp_status of this right-hand side */
+  int32_t reserved;
+} hpmxp_ir_info;
+
+/* Fills *p with the defaults listed above. */
+void hpmxp_ir_params_default(hpmxp_ir_params* p);
+
+/*   A        in, n x n fp64, lda >= n
+ *   LU       in, factors from hpmxp_factor with the same n and prec, ldlu as there
+ *   b        in, n x nrhs fp64, ldb >= n
+ *   x        out, n x nrhs fp64, ldx >= n; holds the last iterate even on failure
+ *   nrhs     1..8 right-hand sides, refined together (one pass over A and LU per
+ *            iteration serves all of them)
+ *   prm      host, NULL for the defaults
+ *   info     host, nrhs entries (may be NULL)
+ *   ws       scratch of hpmxp_solve_workspace(n, nrhs, restart) bytes
+ * Synchronizes `stream`.  Returns HPMXP_OK when every right-hand side met the
+ * threshold, else the worst per-column status (ENOCONV, EBREAKDOWN). */
+size_t hpmxp_solve_workspace(int64_t n, int64_t nrhs, int restart);
+hpmxp_status hpmxp_solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu,
+                            int prec, const double* b, int64_t ldb, double* x, int64_t ldx,
+                            int64_t nrhs, const hpmxp_ir_params* prm, hpmxp_ir_info* info,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Backward-error check (section "Algorithmic Framework"): for every column c,
+ * scaled_resid[c] = ||A x_c - b_c||_inf / ((||A||_inf ||x_c||_inf + ||b_c||_inf) n eps)
+ * with eps = 2^-53, all in fp64.  The solution is valid when it is < 16.
+ *   scaled_resid  host, nrhs entries
+ *   ws            scratch of hpmxp_residual_workspace(n, nrhs) bytes
+ * Synchronizes `stream`. */
+size_t hpmxp_residual_workspace(int64_t n, int64_t nrhs);
+hpmxp_status hpmxp_residual(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
+                            const double* b, int64_t ldb, int64_t nrhs, double* scaled_resid,
+                            void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPMXP_H_ */

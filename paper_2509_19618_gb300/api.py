@@ -1,0 +1,162 @@
+"""PyTorch-facing wrappers over the C interface: device memory and streams
+come from torch, every step of the solve runs in libhpmxp.so.
+
+Matrices are column major: a ``ColMajor`` keeps a (cols x ld) torch tensor
+whose row j is column j of the matrix, so element (i, j) lives at
+``storage[j, i]`` and ``ColMajor.view()`` is the (rows x cols) matrix.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+def _round_up(a: int, b: int) -> int:
+    return (a + b - 1) // b * b
+
+
+def stream_handle(stream: torch.cuda.Stream | None = None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclass
+class ColMajor:
+    storage: torch.Tensor   # (cols, ld)
+    rows: int
+    cols: int
+
+    @property
+    def ld(self) -> int:
+        return self.storage.shape[1]
+
+    @property
+    def ptr(self) -> int:
+        return self.storage.data_ptr()
+
+    def view(self) -> torch.Tensor:
+        return self.storage[:, : self.rows].t()
+
+    @staticmethod
+    def empty(rows: int, cols: int, dtype, device, ld: int | None = None, align: int = 8) -> "ColMajor":
+        ld = ld if ld is not None else _round_up(max(rows, 1), align)
+        return ColMajor(torch.empty((cols, ld), dtype=dtype, device=device), rows, cols)
+
+    @staticmethod
+    def from_tensor(t: torch.Tensor, device, dtype=torch.float64, align: int = 8) -> "ColMajor":
+        t = torch.as_tensor(t)
+        if t.dim() == 1:
+            t = t[:, None]
+        m = ColMajor.empty(t.shape[0], t.shape[1], dtype, device, align=align)
+        m.view().copy_(t.to(device=device, dtype=dtype))
+        return m
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _check(fn: str, status: int):
+    if status != capi.OK:
+        raise capi.HpmxpError(fn, status)
+
+
+def generate(n: int, seed: int = 1, margin: float = 1.0, diag: int = capi.DIAG_DOMINANT, nrhs: int = 1,
+             device="cuda", stream=None) -> tuple[ColMajor, ColMajor]:
+    """The benchmark's system A (n x n fp64) and b (n x nrhs fp64), generated on the device."""
+    A = ColMajor.empty(n, n, torch.float64, device)
+    b = ColMajor.empty(n, max(nrhs, 1), torch.float64, device)
+    ws = workspace(capi.hpmxp_generate_workspace(n), device)
+    st = capi.hpmxp_generate(n, seed, margin, diag, A.ptr, A.ld, b.ptr, b.ld, nrhs, ws.data_ptr(), ws.numel(),
+                             stream_handle(stream))
+    _check("hpmxp_generate", st)
+    return A, b
+
+
+def factor_storage_dtype(prec: int):
+    return torch.float16 if prec == capi.FP16 else torch.bfloat16
+
+
+def factor(A: ColMajor, prec: int = capi.BF16, nb: int = 128, LU: ColMajor | None = None, ws=None,
+           stream=None) -> ColMajor:
+    """Low-precision LU without pivoting of A; returns the packed factors."""
+    n = A.rows
+    if LU is None:
+        LU = ColMajor.empty(n, n, factor_storage_dtype(prec), A.storage.device)
+    if ws is None:
+        ws = workspace(capi.hpmxp_factor_workspace(n, prec, nb), A.storage.device)
+    st = capi.hpmxp_factor(n, A.ptr, A.ld, prec, nb, LU.ptr, LU.ld, ws.data_ptr(), ws.numel(),
+                           stream_handle(stream))
+    _check("hpmxp_factor", st)
+    return LU
+
+
+def ir_params(**kw) -> capi.IRParams:
+    p = capi.hpmxp_ir_params_default()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def solve_ir(A: ColMajor, LU: ColMajor, b: ColMajor, prec: int = capi.BF16, params: capi.IRParams | None = None,
+             x: ColMajor | None = None, ws=None, stream=None, check: bool = True):
+    """GMRES-IR; returns (x, [info dicts], status)."""
+    n, k = A.rows, b.cols
+    if x is None:
+        x = ColMajor.empty(n, k, torch.float64, A.storage.device)
+    restart = params.restart if params is not None else 30
+    if ws is None:
+        ws = workspace(capi.hpmxp_solve_workspace(n, k, restart), A.storage.device)
+    info = (capi.IRInfo * k)()
+    st = capi.hpmxp_solve_ir(n, A.ptr, A.ld, LU.ptr, LU.ld, prec, b.ptr, b.ld, x.ptr, x.ld, k, params, info,
+                             ws.data_ptr(), ws.numel(), stream_handle(stream))
+    infos = [dict(iters=i.iters, outer=i.outer, scaled_resid=i.scaled_resid, status=i.status) for i in info]
+    if check and st not in (capi.OK, capi.ENOCONV, capi.EBREAKDOWN):
+        _check("hpmxp_solve_ir", st)
+    return x, infos, st
+
+
+def residual(A: ColMajor, x: ColMajor, b: ColMajor, stream=None) -> np.ndarray:
+    """HPL scaled residual of every column (fp64, on the device)."""
+    n, k = A.rows, x.cols
+    out = (ctypes.c_double * k)()
+    ws = workspace(capi.hpmxp_residual_workspace(n, k), A.storage.device)
+    st = capi.hpmxp_residual(n, A.ptr, A.ld, x.ptr, x.ld, b.ptr, b.ld, k, ctypes.addressof(out), ws.data_ptr(),
+                             ws.numel(), stream_handle(stream))
+    _check("hpmxp_residual", st)
+    return np.array(out[:], dtype=np.float64)
+
+
+def hpl_mxp_ops(n: int, nrhs: int = 1) -> float:
+    """Canonical operation count (section "Algorithmic Framework"): 2/3 n^3 + 3/2 n^2
+    for one right-hand side; with k right-hand sides the solves count 2 k n^2."""
+    return 2.0 / 3.0 * n**3 - 0.5 * n**2 + 2.0 * nrhs * n**2
+
+
+class Solver:
+    """Reusable device buffers for repeated solves of one shape (bench, serving)."""
+
+    def __init__(self, n: int, nrhs: int = 1, prec: int = capi.BF16, nb: int = 128, device="cuda",
+                 params: capi.IRParams | None = None):
+        self.n, self.nrhs, self.prec, self.nb = n, nrhs, prec, nb
+        self.params = params if params is not None else capi.hpmxp_ir_params_default()
+        self.device = torch.device(device)
+        self.LU = ColMajor.empty(n, n, factor_storage_dtype(prec), self.device)
+        self.x = ColMajor.empty(n, nrhs, torch.float64, self.device)
+        self.fws = workspace(capi.hpmxp_factor_workspace(n, prec, nb), self.device)
+        self.sws = workspace(capi.hpmxp_solve_workspace(n, nrhs, self.params.restart), self.device)
+
+    def factor(self, A: ColMajor, stream=None) -> ColMajor:
+        return factor(A, self.prec, self.nb, LU=self.LU, ws=self.fws, stream=stream)
+
+    def solve(self, A: ColMajor, b: ColMajor, stream=None):
+        return solve_ir(A, self.LU, b, self.prec, self.params, x=self.x, ws=self.sws, stream=stream)
+
+    def __call__(self, A: ColMajor, b: ColMajor, stream=None):
+        self.factor(A, stream)
+        return self.solve(A, b, stream)

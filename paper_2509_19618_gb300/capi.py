@@ -1,0 +1,154 @@
+"""ctypes binding of libhpmxp.so (include/hpmxp.h, include/hpmxp_testing.h).
+
+The ``hpmxp_*`` functions here have the C names and take raw pointers (ints),
+sizes and a stream handle; they only marshal arguments.  PyTorch is used by
+the friendlier wrappers in ``api.py`` for device memory and streams.  There is
+no fallback: importing this module on a machine where the library cannot be
+built or loaded raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ETIMEOUT, EINVALID = range(8)
+BF16, FP16, FP8_E4M3 = 0, 1, 2
+DIAG_DOMINANT, DIAG_SQRTN, DIAG_NONE = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN",
+                6: "ETIMEOUT", 7: "EINVALID"}
+
+
+class IRParams(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("theta", ctypes.c_double), ("accept", ctypes.c_double), ("precond_fp32", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class IRInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("scaled_resid", ctypes.c_double),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class HpmxpError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn}: {STATUS_NAMES.get(status, status)} ({status_string(status)})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load (building first if stale) libhpmxp.so and declare its signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if _build.stale():
+            _build.build()
+        L = ctypes.CDLL(_build.LIB)
+        i64, u64, i32, d, sz, P = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
+                                   ctypes.c_size_t, ctypes.c_void_p)
+        sig = {
+            "hpmxp_status_string": ([i32], ctypes.c_char_p),
+            "hpmxp_version": ([], i32),
+            "hpmxp_generate_workspace": ([i64], sz),
+            "hpmxp_generate": ([i64, u64, d, i32, P, i64, P, i64, i64, P, sz, P], i32),
+            "hpmxp_factor_workspace": ([i64, i32, i32], sz),
+            "hpmxp_factor": ([i64, P, i64, i32, i32, P, i64, P, sz, P], i32),
+            "hpmxp_ir_params_default": ([ctypes.POINTER(IRParams)], None),
+            "hpmxp_solve_workspace": ([i64, i64, i32], sz),
+            "hpmxp_solve_ir": ([i64, P, i64, P, i64, i32, P, i64, P, i64, i64, ctypes.POINTER(IRParams),
+                                ctypes.POINTER(IRInfo), P, sz, P], i32),
+            "hpmxp_residual_workspace": ([i64, i64], sz),
+            "hpmxp_residual": ([i64, P, i64, P, i64, P, i64, i64, P, P, sz, P], i32),
+            "hpmxp_test_gemm": ([i32, i32, i32, P, i64, P, i64, P, i64, P, i64, i32, ctypes.c_float, i32, i32,
+                                 P, i32, P, i32, i32, P, P], i32),
+            "hpmxp_test_cast": ([i64, P, i64, i32, P, i64, P], i32),
+            "hpmxp_test_precond": ([i64, P, i64, i32, P, i64, P, i64, i64, i32, P, sz, P], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return load().hpmxp_status_string(s).decode()
+
+
+def declared_symbols() -> list[str]:
+    """Every function declared in include/*.h."""
+    names = []
+    inc = os.path.join(_build.ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            text = open(os.path.join(inc, h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(hpmxp_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def _call(name: str, *args) -> int:
+    return getattr(load(), name)(*args)
+
+
+def hpmxp_generate_workspace(n):
+    return _call("hpmxp_generate_workspace", n)
+
+
+def hpmxp_generate(n, seed, margin, diag_mode, A, lda, b, ldb, nrhs, ws, ws_bytes, stream):
+    return _call("hpmxp_generate", n, seed, margin, diag_mode, A, lda, b, ldb, nrhs, ws, ws_bytes, stream)
+
+
+def hpmxp_factor_workspace(n, prec, nb):
+    return _call("hpmxp_factor_workspace", n, prec, nb)
+
+
+def hpmxp_factor(n, A, lda, prec, nb, LU, ldlu, ws, ws_bytes, stream):
+    return _call("hpmxp_factor", n, A, lda, prec, nb, LU, ldlu, ws, ws_bytes, stream)
+
+
+def hpmxp_ir_params_default() -> IRParams:
+    p = IRParams()
+    load().hpmxp_ir_params_default(ctypes.byref(p))
+    return p
+
+
+def hpmxp_solve_workspace(n, nrhs, restart):
+    return _call("hpmxp_solve_workspace", n, nrhs, restart)
+
+
+def hpmxp_solve_ir(n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs, params, info, ws, ws_bytes, stream):
+    return _call("hpmxp_solve_ir", n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs,
+                 None if params is None else ctypes.byref(params), info, ws, ws_bytes, stream)
+
+
+def hpmxp_residual_workspace(n, nrhs):
+    return _call("hpmxp_residual_workspace", n, nrhs)
+
+
+def hpmxp_residual(n, A, lda, x, ldx, b, ldb, nrhs, out, ws, ws_bytes, stream):
+    return _call("hpmxp_residual", n, A, lda, x, ldx, b, ldb, nrhs, out, ws, ws_bytes, stream)
+
+
+def hpmxp_test_gemm(*args):
+    return _call("hpmxp_test_gemm", *args)
+
+
+def hpmxp_test_cast(*args):
+    return _call("hpmxp_test_cast", *args)
+
+
+def hpmxp_test_precond(*args):
+    return _call("hpmxp_test_precond", *args)

@@ -1,0 +1,167 @@
+// C interface of libhpmxp.so (declared in include/hpmxp.h): argument
+// validation, workspace sizing and status mapping around the kernels.
+#include "internal.h"
+#include "../../include/hpmxp_testing.h"
+
+namespace hpmxp {
+
+hpmxp_status status_from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return HPMXP_OK;
+  if (e == cudaErrorInvalidValue) return HPMXP_EINVAL;
+  return HPMXP_ECUDA;
+}
+
+hpmxp_status status_from_word(uint32_t w) {
+  if (w & kErrTimeout) return HPMXP_ETIMEOUT;
+  if (w & kErrBounds) return HPMXP_EINVAL;
+  if (w & (kErrPivot | kErrNonFinite)) return HPMXP_EBREAKDOWN;
+  return HPMXP_OK;
+}
+
+hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu, int prec,
+                      const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs,
+                      const hpmxp_ir_params& prm, hpmxp_ir_info* info, void* ws, cudaStream_t st);
+hpmxp_status residual_check(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
+                            const double* b, int64_t ldb, int64_t nrhs, double* out, void* ws, cudaStream_t st);
+
+}  // namespace hpmxp
+
+using namespace hpmxp;
+
+namespace {
+constexpr int64_t kMaxN = int64_t(1) << 17;
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+bool prec_ok(int p) { return p == HPMXP_BF16 || p == HPMXP_FP16 || p == HPMXP_FP8_E4M3; }
+}  // namespace
+
+extern "C" {
+
+const char* hpmxp_status_string(hpmxp_status s) {
+  switch (s) {
+    case HPMXP_OK: return "ok";
+    case HPMXP_EINVAL: return "invalid argument";
+    case HPMXP_ENOMEM: return "workspace too small";
+    case HPMXP_ECUDA: return "CUDA error";
+    case HPMXP_ENOCONV: return "refinement did not converge within max_iters";
+    case HPMXP_EBREAKDOWN: return "breakdown: zero or non-finite pivot or value";
+    case HPMXP_ETIMEOUT: return "a bounded device wait ran out";
+    case HPMXP_EINVALID: return "scaled residual above the acceptance threshold";
+    default: return "unknown status";
+  }
+}
+
+int hpmxp_version(void) { return 10000; }
+
+size_t hpmxp_generate_workspace(int64_t n) { return n > 0 ? round_up<size_t>(16 * (size_t)n, 256) : 0; }
+
+hpmxp_status hpmxp_generate(int64_t n, uint64_t seed, double margin, int diag_mode, double* A, int64_t lda,
+                            double* b, int64_t ldb, int64_t nrhs, void* ws, size_t ws_bytes, void* stream) {
+  if (n < 1 || n > kMaxN || !A || lda < n || nrhs < 0 || (nrhs > 0 && (!b || ldb < n)) || !ws)
+    return HPMXP_EINVAL;
+  if (diag_mode < HPMXP_DIAG_DOMINANT || diag_mode > HPMXP_DIAG_NONE) return HPMXP_EINVAL;
+  if (!aligned(ws, 16)) return HPMXP_EINVAL;
+  if (ws_bytes < hpmxp_generate_workspace(n)) return HPMXP_ENOMEM;
+  cudaError_t e = launch_generate(n, seed, margin, diag_mode, A, lda, b, ldb, nrhs, (unsigned long long*)ws,
+                                  (cudaStream_t)stream);
+  return status_from_cuda(e);
+}
+
+size_t hpmxp_factor_workspace(int64_t n, int prec, int nb) {
+  if (n < 1 || !prec_ok(prec) || !(nb == 128 || nb == 256 || nb == 512)) return 0;
+  return factor_ws_bytes(n, prec, nb);
+}
+
+hpmxp_status hpmxp_factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU, int64_t ldlu,
+                          void* ws, size_t ws_bytes, void* stream) {
+  if (n < 1 || n > kMaxN || !A || lda < n || !LU || ldlu < n || (ldlu % 8) != 0 || !aligned(LU, 16) || !ws ||
+      !aligned(ws, 256) || !prec_ok(prec) || !(nb == 128 || nb == 256 || nb == 512))
+    return HPMXP_EINVAL;
+  if (ws_bytes < factor_ws_bytes(n, prec, nb)) return HPMXP_ENOMEM;
+  return factor(n, A, lda, prec, nb, LU, ldlu, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+void hpmxp_ir_params_default(hpmxp_ir_params* p) {
+  if (!p) return;
+  p->restart = 30;
+  p->max_iters = 50;
+  p->inner_tol = 1e-12;
+  p->theta = 0.1;
+  p->accept = 16.0;
+  p->precond_fp32 = 0;
+  p->reserved = 0;
+}
+
+size_t hpmxp_solve_workspace(int64_t n, int64_t nrhs, int restart) {
+  if (n < 1 || nrhs < 1 || nrhs > 8 || restart < 1 || restart > 64) return 0;
+  return solve_ws_bytes(n, nrhs, restart);
+}
+
+hpmxp_status hpmxp_solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu, int prec,
+                            const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs,
+                            const hpmxp_ir_params* prm, hpmxp_ir_info* info, void* ws, size_t ws_bytes,
+                            void* stream) {
+  hpmxp_ir_params p;
+  hpmxp_ir_params_default(&p);
+  if (prm) p = *prm;
+  if (n < 1 || n > kMaxN || !A || lda < n || !LU || ldlu < n || !b || ldb < n || !x || ldx < n || nrhs < 1 ||
+      nrhs > 8 || !ws || !aligned(ws, 256) || !prec_ok(prec) || p.restart < 1 || p.restart > 64 ||
+      p.max_iters < 0 || !(p.accept > 0.0) || p.inner_tol < 0.0 || p.theta < 0.0)
+    return HPMXP_EINVAL;
+  if (ws_bytes < solve_ws_bytes(n, nrhs, p.restart)) return HPMXP_ENOMEM;
+  return solve_ir(n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs, p, info, ws, (cudaStream_t)stream);
+}
+
+size_t hpmxp_residual_workspace(int64_t n, int64_t nrhs) {
+  if (n < 1 || nrhs < 1 || nrhs > 8) return 0;
+  return residual_ws_bytes(n, nrhs);
+}
+
+hpmxp_status hpmxp_residual(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
+                            const double* b, int64_t ldb, int64_t nrhs, double* scaled_resid, void* ws,
+                            size_t ws_bytes, void* stream) {
+  if (n < 1 || n > kMaxN || !A || lda < n || !x || ldx < n || !b || ldb < n || nrhs < 1 || nrhs > 8 ||
+      !scaled_resid || !ws || !aligned(ws, 256))
+    return HPMXP_EINVAL;
+  if (ws_bytes < residual_ws_bytes(n, nrhs)) return HPMXP_ENOMEM;
+  return residual_check(n, A, lda, x, ldx, b, ldb, nrhs, scaled_resid, ws, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Test hooks (include/hpmxp_testing.h)
+// ---------------------------------------------------------------------------
+hpmxp_status hpmxp_test_gemm(int M, int N, int K, const void* A, int64_t lda, const void* B, int64_t ldb,
+                             void* C, int64_t ldc, void* R, int64_t ldr, int mode, float sign, int fmt,
+                             int fp8, const float* sA, int sa_ld, const float* sB, int sb_ld, int engine,
+                             uint32_t* status, void* stream) {
+  if (M < 0 || N < 0 || K <= 0 || (K % 128) || !A || !B || !status || (mode == kEpiSub && !C) ||
+      (mode != kEpiSub && mode != kEpiStore) || (fmt != kBF16 && fmt != kFP16) ||
+      (fp8 && (!sA || !sB || K > 512)) || (!C && !R))
+    return HPMXP_EINVAL;
+  GemmArgs g{};
+  g.M = M; g.N = N; g.K = K; g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+  g.R = R; g.ldr = ldr; g.mode = mode; g.sign = sign; g.fmt = fmt; g.fp8 = fp8;
+  g.sA = sA; g.sa_ld = sa_ld; g.sB = sB; g.sb_ld = sb_ld; g.status = status;
+  cudaError_t e = engine == 1 ? gemm_simt(g, (cudaStream_t)stream) : gemm_tc(g, (cudaStream_t)stream);
+  return status_from_cuda(e);
+}
+
+hpmxp_status hpmxp_test_cast(int64_t n, const double* A, int64_t lda, int prec, void* out, int64_t ldo,
+                             void* stream) {
+  if (n < 1 || !A || lda < n || !out || ldo < n || (ldo % 8) || !aligned(out, 16) || !prec_ok(prec))
+    return HPMXP_EINVAL;
+  return status_from_cuda(launch_cast(n, A, lda, out, ldo, prec == HPMXP_FP16 ? kFP16 : kBF16,
+                                      (cudaStream_t)stream));
+}
+
+hpmxp_status hpmxp_test_precond(int64_t n, const void* LU, int64_t ldlu, int prec, const double* v,
+                                int64_t ldv, double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws,
+                                size_t ws_bytes, void* stream) {
+  if (n < 1 || n > kMaxN || !LU || ldlu < n || !v || ldv < n || !z || ldz < n || nrhs < 1 || nrhs > 8 ||
+      !ws || !aligned(ws, 256) || !prec_ok(prec))
+    return HPMXP_EINVAL;
+  if (ws_bytes < solve_ws_bytes(n, nrhs, 1)) return HPMXP_ENOMEM;
+  return precond_apply(n, LU, ldlu, prec == HPMXP_FP16 ? kFP16 : kBF16, v, ldv, z, ldz, nrhs, fp32, ws,
+                       (cudaStream_t)stream);
+}
+
+}  // extern "C"

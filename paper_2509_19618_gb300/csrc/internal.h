@@ -1,0 +1,121 @@
+// Internal declarations shared by the translation units of libhpmxp.so.
+// Not part of the public interface (include/hpmxp.h is).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/hpmxp.h"
+
+namespace hpmxp {
+
+// ---------------------------------------------------------------------------
+// Device status word.  Kernels never trap: a failed check or a bounded wait
+// that runs out ORs a bit into a status word in the caller's workspace, and
+// the host maps it to an hpmxp_status after synchronizing.
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+  kErrTimeout = 1u,     // a bounded device wait ran out
+  kErrPivot = 2u,       // zero or non-finite pivot in a diagonal block
+  kErrNonFinite = 4u,   // non-finite value in the refinement
+  kErrBounds = 8u,      // a device-side bounds/shape check failed
+};
+
+// Bounds of every device-side wait: at most kSpinLimit polls and at most
+// kWaitNs nanoseconds of the global timer (checked every 256 polls).  A
+// legitimate wait here lasts microseconds to milliseconds.
+constexpr long long kSpinLimit = 1ll << 28;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Round up / ceil division helpers.
+template <class T>
+__host__ __device__ inline T cdiv(T a, T b) { return (a + b - 1) / b; }
+template <class T>
+__host__ __device__ inline T round_up(T a, T b) { return cdiv(a, b) * b; }
+
+// 16-bit storage formats of the factors.
+enum Fmt16 { kBF16 = 0, kFP16 = 1 };
+
+__device__ inline float ld16(const uint16_t* p, int fmt) {
+  const uint16_t h = *p;
+  if (fmt == kBF16) return __uint_as_float((uint32_t)h << 16);
+  return __half2float(__ushort_as_half(h));
+}
+__device__ inline float u16_to_f32(uint16_t h, int fmt) {
+  if (fmt == kBF16) return __uint_as_float((uint32_t)h << 16);
+  return __half2float(__ushort_as_half(h));
+}
+__device__ inline uint16_t f32_to_u16(float v, int fmt) {
+  if (fmt == kBF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  return __half_as_ushort(__float2half_rn(v));
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers implemented in the .cu files.
+// ---------------------------------------------------------------------------
+
+// gen.cu
+cudaError_t launch_generate(int64_t n, uint64_t seed, double margin, int mode, double* A,
+                            int64_t lda, double* b, int64_t ldb, int64_t nrhs,
+                            unsigned long long* sums, cudaStream_t st);
+
+// GEMM engines (gemm_tc.cu: tcgen05 tensor cores; lu.cu: a SIMT validation
+// engine that accumulates with one fp32 FMA per term in ascending k).
+//
+// D(i, j) for i < M, j < N is acc(i, j) = sum_{k < K} A(i, k) B(j, k), both
+// operands K-major 16-bit (A(i,k) at A[i*lda + k], B(j,k) at B[j*ldb + k]),
+// K a multiple of 128 (128-deep fp8 slices for the E4M3 kind).
+// Epilogue (`mode`):
+//   kEpiSub    C(i,j) = st(C(i,j) - acc)    C column major 16-bit, in place
+//   kEpiStore  C(i,j) = st(sign * acc)      C column major (C may be NULL)
+//              and, if R != NULL, R(i,j) = same value, R row major (R[i*ldr + j])
+enum EpiMode { kEpiSub = 0, kEpiStore = 1 };
+struct GemmArgs {
+  int M, N, K;
+  const void* A; int64_t lda;
+  const void* B; int64_t ldb;
+  void* C; int64_t ldc;
+  void* R; int64_t ldr;
+  int mode;
+  float sign;
+  int fmt;              // kBF16 / kFP16 operands and outputs
+  // E4M3 variant (operands are 8-bit, K-major, lda/ldb in elements=bytes):
+  // scales sA[(i/128) * sa_ld + kb], sB[(j/128) * sb_ld + kb] per 128-deep slice kb.
+  int fp8;
+  const float* sA; int sa_ld;
+  const float* sB; int sb_ld;
+  uint32_t* status;
+};
+cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st);
+cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st);
+// Returns the engine selected for the factorization (0 = tcgen05, 1 = SIMT
+// validation engine, chosen by HPMXP_GEMM_ENGINE=simt for parity tests).
+int gemm_engine();
+
+// lu.cu
+cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st);
+size_t factor_ws_bytes(int64_t n, int prec, int nb);
+hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU,
+                    int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st);
+
+// ir.cu
+size_t solve_ws_bytes(int64_t n, int64_t nrhs, int restart);
+size_t residual_ws_bytes(int64_t n, int64_t nrhs);
+hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, const double* v, int64_t ldv,
+                           double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws, cudaStream_t st);
+
+hpmxp_status status_from_cuda(cudaError_t e);
+hpmxp_status status_from_word(uint32_t w);
+
+}  // namespace hpmxp

@@ -1,0 +1,907 @@
+// fp64 GMRES-based iterative refinement (section "Algorithmic Framework":
+// x0 from the low-precision factors, then GMRES with the factors as a left
+// preconditioner, fp64 working precision, at most 50 iterations, HPL
+// backward-error criterion below 16).
+//
+// Kernels:
+//   gemv_partial / gemv_finish  r = b - A x for up to 8 columns; A (fp64,
+//       column major) is read once for all columns, coalesced 16-byte loads,
+//       split over column chunks with a deterministic second pass.  The
+//       first pass can also accumulate |A| row sums (||A||_inf).
+//   precond_kernel  z = U^{-1} L^{-1} v with the 16-bit factors, both sweeps
+//       in one cooperative launch: block rows of 64 are owned round-robin by
+//       the CTAs; the owner of a block solves its diagonal block as soon as
+//       every earlier block has been applied and publishes it behind a
+//       release flag; others wait (bounded) with acquire loads.
+//   mgs_step / vec_norm / givens / cycle_start / cycle_finish / update:
+//       modified Gram-Schmidt Arnoldi, Givens least squares, x += V y.
+// All control decisions are taken on the device; the host reads a few
+// words per Arnoldi step to decide whether to launch the next one.
+#include "internal.h"
+
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+namespace hpmxp {
+namespace {
+
+constexpr int kMaxM = 64;     // largest restart length
+constexpr int kMaxK = 8;      // right-hand sides refined together
+constexpr int kTB = 64;       // preconditioner block rows
+constexpr int kRedBlocks = 304;
+
+__device__ inline unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ inline double bits_d(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// |a| as an fp32 lower bound from the top word of the fp64 pattern (exponent
+// rebias, 20 mantissa bits, tiny values flushed to 0): integer ops only, so
+// the ||A||_inf estimate of the stopping test costs no fp64 instructions.
+__device__ inline float abs_f32_est(double a) {
+  const int hi = __double2hiint(a) & 0x7fffffff;
+  const int t = hi - (896 << 20);
+  return t > 0 ? __int_as_float(min(t, 0x7f7fffff >> 3) << 3) : 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Per right-hand-side state of the refinement (device memory).
+// ---------------------------------------------------------------------------
+struct RhsState {
+  double H[(kMaxM + 1) * kMaxM];   // Hessenberg, column major (m+1) x m
+  double cs[kMaxM], sn[kMaxM], g[kMaxM + 1], y[kMaxM];
+  double beta, tol, sr, hn;
+  double anorm, bnorm;
+  unsigned long long rn_bits, xn_bits, bn_bits, an_bits;   // max-reductions (non-negative doubles)
+  int outer_active;   // refinement still running
+  int cycle_active;   // inside a GMRES cycle, Arnoldi steps still wanted
+  int k;              // Arnoldi steps done in the current cycle
+  int iters, outer, status;
+};
+
+struct Brief {          // copied to the host after each control kernel
+  int outer_active, cycle_active, iters, outer, status;
+  int pad;
+  double sr;
+};
+
+struct SolveParams {
+  int n_rhs, m, max_iters;
+  double inner_tol, theta, accept;
+  int64_t n;
+};
+
+// ---------------------------------------------------------------------------
+// GEMV: P[c][i + r*n] = sum_{j in chunk c} A(i, j) X(j, r); optional |A| row
+// sums (fp32 estimate or exact fp64) into RS[c][i].
+// 128 threads x 2 rows = 256 rows per CTA, columns of the chunk in order.
+// ---------------------------------------------------------------------------
+constexpr int kGemvRows = 256;
+
+template <int K, int kAbs>   // kAbs: 0 none, 1 fp32 estimate, 2 fp64 exact
+__global__ void __launch_bounds__(128) gemv_partial_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
+                                                           const double* __restrict__ X, int64_t ldx,
+                                                           int64_t chunk, double* __restrict__ P,
+                                                           void* __restrict__ RS) {
+  __shared__ double xs[64 * K];
+  const int64_t i = (int64_t)blockIdx.x * kGemvRows + 2 * threadIdx.x;
+  const int64_t j0 = (int64_t)blockIdx.y * chunk, j1 = min(j0 + chunk, n);
+  double acc0[K], acc1[K];
+#pragma unroll
+  for (int r = 0; r < K; ++r) { acc0[r] = 0.0; acc1[r] = 0.0; }
+  float s0 = 0.0f, s1 = 0.0f;
+  double d0 = 0.0, d1 = 0.0;
+  const bool two = i + 1 < n;
+  const bool vec = two && ((((uintptr_t)(A + i)) & 15) == 0) && ((lda & 1) == 0);
+  for (int64_t jb = j0; jb < j1; jb += 64) {
+    const int cnt = (int)min((int64_t)64, j1 - jb);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt * K; t += 128) {
+      const int jj = t % cnt, r = t / cnt;
+      xs[r * 64 + jj] = X[jb + jj + r * ldx];
+    }
+    __syncthreads();
+    if (i < n) {
+      const double* col = A + i + jb * lda;
+#pragma unroll 4
+      for (int jj = 0; jj < cnt; ++jj) {
+        double a0, a1;
+        if (vec) {
+          const double2 v = *reinterpret_cast<const double2*>(col);
+          a0 = v.x; a1 = v.y;
+        } else {
+          a0 = col[0];
+          a1 = two ? col[1] : 0.0;
+        }
+        col += lda;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const double xv = xs[r * 64 + jj];
+          acc0[r] = __fma_rn(a0, xv, acc0[r]);
+          acc1[r] = __fma_rn(a1, xv, acc1[r]);
+        }
+        if (kAbs == 1) { s0 += abs_f32_est(a0); s1 += abs_f32_est(a1); }
+        if (kAbs == 2) { d0 += fabs(a0); d1 += fabs(a1); }
+      }
+    }
+  }
+  if (i >= n) return;
+  double* Pc = P + (int64_t)blockIdx.y * n * K;
+#pragma unroll
+  for (int r = 0; r < K; ++r) {
+    Pc[i + r * n] = acc0[r];
+    if (two) Pc[i + 1 + r * n] = acc1[r];
+  }
+  if (kAbs == 1) {
+    float* R = (float*)RS + (int64_t)blockIdx.y * n;
+    R[i] = s0;
+    if (two) R[i + 1] = s1;
+  } else if (kAbs == 2) {
+    double* R = (double*)RS + (int64_t)blockIdx.y * n;
+    R[i] = d0;
+    if (two) R[i + 1] = d1;
+  }
+}
+
+// out(i, r) = B(i, r) - sum_c P[c](i, r), or + sum_c P[c](i, r) when B is NULL
+// (chunks in order); max-reduces
+// |out|, |X| (when xn) and the row sums (when abs_mode) into the states.
+__global__ void gemv_finish_kernel(int64_t n, int K, int nchunk, const double* __restrict__ P,
+                                   const double* __restrict__ B, int64_t ldb, double* __restrict__ out,
+                                   int64_t ldo, const double* __restrict__ X, int64_t ldx, int abs_mode,
+                                   const void* __restrict__ RS, RhsState* st, int track_norms) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ unsigned long long smax[3 * kMaxK + 1];
+  if (threadIdx.x < 3 * kMaxK + 1) smax[threadIdx.x] = 0;
+  __syncthreads();
+  if (i < n) {
+    for (int r = 0; r < K; ++r) {
+      double s = 0.0;
+      for (int c = 0; c < nchunk; ++c) s += P[(int64_t)c * n * K + i + r * n];
+      const double v = B ? B[i + r * ldb] - s : s;
+      out[i + r * ldo] = v;
+      if (track_norms) {
+        atomicMax(&smax[r], dbits(fabs(v)));
+        atomicMax(&smax[kMaxK + r], dbits(fabs(X[i + r * ldx])));
+        if (B) atomicMax(&smax[2 * kMaxK + r], dbits(fabs(B[i + r * ldb])));
+      }
+    }
+    if (abs_mode == 1) {
+      float s = 0.0f;
+      for (int c = 0; c < nchunk; ++c) s += ((const float*)RS)[(int64_t)c * n + i];
+      atomicMax(&smax[3 * kMaxK], dbits((double)s));
+    } else if (abs_mode == 2) {
+      double s = 0.0;
+      for (int c = 0; c < nchunk; ++c) s += ((const double*)RS)[(int64_t)c * n + i];
+      atomicMax(&smax[3 * kMaxK], dbits(s));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < K && track_norms) {
+    const int r = threadIdx.x;
+    atomicMax(&st[r].rn_bits, smax[r]);
+    atomicMax(&st[r].xn_bits, smax[kMaxK + r]);
+    if (B) atomicMax(&st[r].bn_bits, smax[2 * kMaxK + r]);
+    if (abs_mode) atomicMax(&st[r].an_bits, smax[3 * kMaxK]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioner z = U^{-1} L^{-1} v, arithmetic T (double or float).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ inline T as_t(float f) { return (T)f; }
+
+template <class T>
+__device__ inline void spin_until(const int* flag, int epoch, uint32_t* status, int* abort_flag) {
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = global_ns();
+    for (long long i = 0;; ++i) {
+      int v;
+      asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+      if (v == epoch) break;
+      if (i > kSpinLimit || ((i & 63) == 0 && global_ns() - t0 > kWaitNs)) {
+        atomicOr(status, kErrTimeout);
+        *abort_flag = 1;
+        break;
+      }
+      if (i > 64) __nanosleep(32);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ inline void publish_flag(int* flag, int epoch) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(flag), "r"(epoch) : "memory");
+}
+
+template <class T, int K>
+__global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
+                                                      int fmt, const double* __restrict__ v, int64_t ldv,
+                                                      double* __restrict__ z, int64_t ldz, T* __restrict__ pub,
+                                                      int* __restrict__ flags, int epoch, uint32_t* status) {
+  extern __shared__ unsigned char smraw[];
+  const int nb = (int)cdiv<int64_t>(n, kTB);
+  const int G = gridDim.x, me = blockIdx.x;
+  const int nown = (nb - me + G - 1) / G;      // blocks me, me+G, ...
+  T* acc = reinterpret_cast<T*>(smraw);        // [nown][kTB][K]
+  T* zc = acc + (size_t)nown * kTB * K;        // [kTB][K] current published block
+  float* tile = reinterpret_cast<float*>(zc + kTB * K);   // [kTB][kTB + 1] diagonal block
+  T* part = reinterpret_cast<T*>(tile + kTB * (kTB + 1)); // [4][kTB][K] partial sums
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  if (tid == 0) abort_flag = 0;
+  int* fflags = flags;          // forward sweep
+  int* bflags = flags + nb;     // backward sweep
+  T* fpub = pub;
+  T* bpub = pub + (size_t)nb * kTB * K;
+
+  // initialize accumulators with v
+  for (int o = 0; o < nown; ++o) {
+    const int blk = me + o * G;
+    for (int t = tid; t < kTB * K; t += 256) {
+      const int ii = t % kTB, r = t / kTB;
+      const int64_t i = (int64_t)blk * kTB + ii;
+      acc[((size_t)o * kTB + ii) * K + r] = i < n ? (T)v[i + r * ldv] : (T)0;
+    }
+  }
+  __syncthreads();
+
+  // acc_o -= Tile(row block of o, column block c) * zc ; tile from LU
+  auto apply_tile = [&](int o, int c) {
+    const int blk = me + o * G;
+    const int ii = tid % kTB, jg = tid / kTB;     // 4 column groups of 16
+    const int64_t i = (int64_t)blk * kTB + ii;
+    T s[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) s[r] = (T)0;
+    if (i < n) {
+      for (int jj = jg * 16; jj < jg * 16 + 16; ++jj) {
+        const int64_t j = (int64_t)c * kTB + jj;
+        if (j >= n) break;
+        const T l = (T)u16_to_f32(LU[i + j * ld], fmt);
+#pragma unroll
+        for (int r = 0; r < K; ++r) s[r] = l * zc[jj * K + r] + s[r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) part[(jg * kTB + ii) * K + r] = s[r];
+    __syncthreads();
+    for (int t = tid; t < kTB * K; t += 256) {
+      const int i2 = t / K, r = t % K;
+      T tot = part[(0 * kTB + i2) * K + r] + part[(1 * kTB + i2) * K + r];
+      tot = tot + part[(2 * kTB + i2) * K + r];
+      tot = tot + part[(3 * kTB + i2) * K + r];
+      acc[((size_t)o * kTB + i2) * K + r] -= tot;
+    }
+    __syncthreads();
+  };
+
+  // load diagonal block c into the shared tile
+  auto load_diag = [&](int c) {
+    for (int t = tid; t < kTB * kTB; t += 256) {
+      const int ii = t % kTB, jj = t / kTB;
+      const int64_t i = (int64_t)c * kTB + ii, j = (int64_t)c * kTB + jj;
+      tile[ii * (kTB + 1) + jj] = (i < n && j < n) ? u16_to_f32(LU[i + j * ld], fmt) : (i == j ? 1.0f : 0.0f);
+    }
+    __syncthreads();
+  };
+
+  // ---------------- forward sweep: unit lower L ----------------
+  for (int c = 0; c < nb; ++c) {
+    if (abort_flag) break;
+    const int owner = c % G;
+    if (owner == me) {
+      const int o = c / G;
+      load_diag(c);
+      if (tid < 32) {   // one warp: substitution in order, rows lane, lane+32
+        T* a = acc + (size_t)o * kTB * K;
+        for (int p = 0; p < kTB; ++p) {
+          T zp[K];
+#pragma unroll
+          for (int r = 0; r < K; ++r) zp[r] = a[p * K + r];
+          __syncwarp();
+          for (int ii = tid; ii < kTB; ii += 32)
+            if (ii > p) {
+              const T l = (T)tile[ii * (kTB + 1) + p];
+#pragma unroll
+              for (int r = 0; r < K; ++r) a[ii * K + r] = a[ii * K + r] - l * zp[r];
+            }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      for (int t = tid; t < kTB * K; t += 256) {
+        const T val = acc[(size_t)o * kTB * K + t];
+        zc[t] = val;
+        fpub[(size_t)c * kTB * K + t] = val;
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) publish_flag(&fflags[c], epoch);
+    } else {
+      // only needed if this CTA owns a block after c
+      const int last = me + (nown - 1) * G;
+      if (nown == 0 || last <= c) continue;
+      spin_until<T>(&fflags[c], epoch, status, &abort_flag);
+      if (abort_flag) break;
+      for (int t = tid; t < kTB * K; t += 256) zc[t] = fpub[(size_t)c * kTB * K + t];
+      __syncthreads();
+    }
+    for (int o = 0; o < nown; ++o)
+      if (me + o * G > c) apply_tile(o, c);
+  }
+  __syncthreads();
+  // acc now holds y = L^{-1} v for the owned blocks
+
+  // ---------------- backward sweep: upper U ----------------
+  for (int c = nb - 1; c >= 0; --c) {
+    if (abort_flag) break;
+    const int owner = c % G;
+    if (owner == me) {
+      const int o = c / G;
+      load_diag(c);
+      if (tid < 32) {
+        T* a = acc + (size_t)o * kTB * K;
+        for (int p = kTB - 1; p >= 0; --p) {
+          const T u = (T)tile[p * (kTB + 1) + p];
+          __syncwarp();
+          T zp[K];
+#pragma unroll
+          for (int r = 0; r < K; ++r) zp[r] = a[p * K + r] / u;
+          __syncwarp();
+          if (tid == 0) {
+#pragma unroll
+            for (int r = 0; r < K; ++r) a[p * K + r] = zp[r];
+          }
+          for (int ii = tid; ii < p; ii += 32) {
+            const T uu = (T)tile[ii * (kTB + 1) + p];
+#pragma unroll
+            for (int r = 0; r < K; ++r) a[ii * K + r] = a[ii * K + r] - uu * zp[r];
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      for (int t = tid; t < kTB * K; t += 256) {
+        const T val = acc[(size_t)o * kTB * K + t];
+        zc[t] = val;
+        bpub[(size_t)c * kTB * K + t] = val;
+        const int ii = t / K, r = t % K;
+        const int64_t i = (int64_t)c * kTB + ii;
+        if (i < n) z[i + r * ldz] = (double)val;
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) publish_flag(&bflags[c], epoch);
+    } else {
+      if (nown == 0 || me >= c) continue;   // owned blocks are me, me+G, ...; some must be < c
+      spin_until<T>(&bflags[c], epoch, status, &abort_flag);
+      if (abort_flag) break;
+      for (int t = tid; t < kTB * K; t += 256) zc[t] = bpub[(size_t)c * kTB * K + t];
+      __syncthreads();
+    }
+    for (int o = 0; o < nown; ++o)
+      if (me + o * G < c) apply_tile(o, c);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Vector kernels.  Deterministic reductions: per-thread strided partials,
+// fixed-shape block tree, per-block partials summed in order by the last CTA.
+// ---------------------------------------------------------------------------
+__device__ inline double block_sum(double v, double* sh) {
+  const int tid = threadIdx.x;
+  sh[tid] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) sh[tid] += sh[tid + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// For every rhs r that is in an active cycle: optionally w -= h_prev v_prev
+// (h_prev = H(i-1, j)), then reduce either <w, v_i> (into H(i, j)) or <w, w>
+// (into hn, as a square root) when i == j + 1.
+__global__ void __launch_bounds__(256) mgs_kernel(int64_t n, int K, int m, int j, int i, double* W, int64_t ldw,
+                                                  const double* V, int64_t ldv_col, int64_t ldv_rhs,
+                                                  RhsState* st, double* partials, unsigned int* counter) {
+  __shared__ double sh[256];
+  __shared__ bool last;
+  for (int r = 0; r < K; ++r) {
+    const bool act = st[r].cycle_active != 0;
+    double part = 0.0;
+    if (act) {
+      double* w = W + r * ldw;
+      const double* vprev = i > 0 ? V + r * ldv_rhs + (int64_t)(i - 1) * ldv_col : nullptr;
+      const double hprev = i > 0 ? st[r].H[(i - 1) + j * (m + 1)] : 0.0;
+      const double* vi = i <= j ? V + r * ldv_rhs + (int64_t)i * ldv_col : nullptr;
+      for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        double wt = w[t];
+        if (vprev) { wt = __fma_rn(-hprev, vprev[t], wt); w[t] = wt; }
+        part = vi ? __fma_rn(wt, vi[t], part) : __fma_rn(wt, wt, part);
+      }
+    }
+    const double bs = block_sum(part, sh);
+    if (threadIdx.x == 0) partials[(int64_t)r * kRedBlocks + blockIdx.x] = bs;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < K) {
+    const int r = threadIdx.x;
+    if (st[r].cycle_active) {
+      double s = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) s += partials[(int64_t)r * kRedBlocks + b];
+      if (i <= j) st[r].H[i + j * (m + 1)] = s;
+      else st[r].hn = sqrt(s);
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0;
+}
+
+// ||z||_2 for cycle start (beta), into st[r].beta, for rhs with outer_active.
+__global__ void __launch_bounds__(256) norm2_kernel(int64_t n, int K, const double* Z, int64_t ldz, RhsState* st,
+                                                    double* partials, unsigned int* counter) {
+  __shared__ double sh[256];
+  __shared__ bool last;
+  for (int r = 0; r < K; ++r) {
+    double part = 0.0;
+    if (st[r].outer_active) {
+      const double* z = Z + r * ldz;
+      for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        part = __fma_rn(z[t], z[t], part);
+    }
+    const double bs = block_sum(part, sh);
+    if (threadIdx.x == 0) partials[(int64_t)r * kRedBlocks + blockIdx.x] = bs;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < K) {
+    const int r = threadIdx.x;
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[(int64_t)r * kRedBlocks + b];
+    st[r].beta = sqrt(s);
+  }
+  if (threadIdx.x == 0) *counter = 0;
+}
+
+// dst(:, r) = src(:, r) / d_r with d_r = st[r].beta (which == 0) or st[r].hn (which == 1),
+// for rhs whose flag (cycle_active or outer_active) is set.
+__global__ void scale_kernel(int64_t n, int K, const double* src, int64_t lds, double* dst, int64_t ldd,
+                             const RhsState* st, int which) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  for (int r = 0; r < K; ++r) {
+    const bool act = which == 0 ? st[r].outer_active != 0 : st[r].cycle_active != 0;
+    if (!act) continue;
+    const double d = which == 0 ? st[r].beta : st[r].hn;
+    dst[t + r * ldd] = src[t + r * lds] / d;
+  }
+}
+
+__global__ void init_kernel(int K, RhsState* st) {
+  if ((int)threadIdx.x < K) st[threadIdx.x].outer_active = 1;
+}
+
+// Outer check: scaled residual from the max-reductions; decide per rhs.
+__global__ void check_kernel(SolveParams sp, RhsState* st, Brief* brief, int first) {
+  const int r = threadIdx.x;
+  if (r >= sp.n_rhs) return;
+  RhsState& s = st[r];
+  if (first) {
+    s.anorm = bits_d(s.an_bits);
+    s.bnorm = bits_d(s.bn_bits);
+  }
+  if (s.outer_active) {
+    const double rn = bits_d(s.rn_bits), xn = bits_d(s.xn_bits);
+    const double sr = rn / ((s.anorm * xn + s.bnorm) * ((double)sp.n * 0x1p-53));
+    s.sr = sr;
+    if (!isfinite(sr)) { s.status = HPMXP_EBREAKDOWN; s.outer_active = 0; }
+    else if (sr < sp.accept) { s.status = HPMXP_OK; s.outer_active = 0; }
+    else if (s.iters >= sp.max_iters) { s.status = HPMXP_ENOCONV; s.outer_active = 0; }
+  }
+  s.rn_bits = 0; s.xn_bits = 0;
+  s.cycle_active = 0;
+  brief[r].outer_active = s.outer_active; brief[r].cycle_active = 0;
+  brief[r].iters = s.iters; brief[r].outer = s.outer; brief[r].status = s.status; brief[r].sr = s.sr;
+}
+
+// Cycle start (after beta = ||M^{-1} r||): g = beta e1, tolerance.
+__global__ void cycle_start_kernel(SolveParams sp, RhsState* st, Brief* brief) {
+  const int r = threadIdx.x;
+  if (r >= sp.n_rhs) return;
+  RhsState& s = st[r];
+  s.cycle_active = 0;
+  if (s.outer_active) {
+    if (!(isfinite(s.beta) && s.beta > 0.0)) {
+      s.status = HPMXP_EBREAKDOWN; s.outer_active = 0;
+    } else {
+      s.outer += 1;
+      s.k = 0;
+      for (int t = 0; t <= sp.m; ++t) s.g[t] = 0.0;
+      s.g[0] = s.beta;
+      const double adapt = sp.theta > 0.0 ? sp.theta * sp.accept / s.sr : 0.0;
+      s.tol = s.beta * fmax(sp.inner_tol, adapt);
+      s.cycle_active = s.iters < sp.max_iters ? 1 : 0;
+    }
+  }
+  brief[r].outer_active = s.outer_active; brief[r].cycle_active = s.cycle_active;
+  brief[r].status = s.status; brief[r].iters = s.iters; brief[r].outer = s.outer; brief[r].sr = s.sr;
+}
+
+// Givens update of column j (after MGS filled H(0..j, j) and hn).
+__global__ void givens_kernel(SolveParams sp, int j, RhsState* st, Brief* brief) {
+  const int r = threadIdx.x;
+  if (r >= sp.n_rhs) return;
+  RhsState& s = st[r];
+  if (s.cycle_active) {
+    const int ld = sp.m + 1;
+    double* h = s.H + j * ld;
+    const double hn = s.hn;
+    h[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a0 = h[i], a1 = h[i + 1];
+      h[i] = s.cs[i] * a0 + s.sn[i] * a1;
+      h[i + 1] = -s.sn[i] * a0 + s.cs[i] * a1;
+    }
+    const double hj = h[j];
+    const double den = hypot(hj, hn);
+    if (!(isfinite(den) && den != 0.0)) {
+      s.status = HPMXP_EBREAKDOWN; s.outer_active = 0; s.cycle_active = 0;
+    } else {
+      s.cs[j] = hj / den;
+      s.sn[j] = hn / den;
+      h[j] = den;
+      h[j + 1] = 0.0;
+      s.g[j + 1] = -s.sn[j] * s.g[j];
+      s.g[j] = s.cs[j] * s.g[j];
+      s.iters += 1;
+      s.k = j + 1;
+      if (hn == 0.0 || fabs(s.g[j + 1]) <= s.tol || s.k >= sp.m || s.iters >= sp.max_iters) s.cycle_active = 0;
+      if (!isfinite(s.g[j + 1])) { s.status = HPMXP_EBREAKDOWN; s.outer_active = 0; s.cycle_active = 0; }
+    }
+  }
+  brief[r].cycle_active = s.cycle_active; brief[r].outer_active = s.outer_active;
+  brief[r].iters = s.iters; brief[r].status = s.status;
+}
+
+// y = H(0:k, 0:k)^{-1} g(0:k) by back substitution.
+__global__ void cycle_finish_kernel(SolveParams sp, RhsState* st) {
+  const int r = threadIdx.x;
+  if (r >= sp.n_rhs) return;
+  RhsState& s = st[r];
+  if (!s.outer_active) { s.k = 0; return; }
+  const int ld = sp.m + 1;
+  for (int i = s.k - 1; i >= 0; --i) {
+    double acc = s.g[i];
+    for (int t = i + 1; t < s.k; ++t) acc = __fma_rn(-s.H[i + t * ld], s.y[t], acc);
+    s.y[i] = acc / s.H[i + i * ld];
+  }
+}
+
+// x(:, r) += V_r(:, 0:k) y_r
+__global__ void update_kernel(int64_t n, int K, double* X, int64_t ldx, const double* V, int64_t ldv_col,
+                              int64_t ldv_rhs, const RhsState* st) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  for (int r = 0; r < K; ++r) {
+    const int k = st[r].outer_active ? st[r].k : 0;
+    double xv = X[t + r * ldx];
+    for (int i = 0; i < k; ++i) xv = __fma_rn(V[r * ldv_rhs + (int64_t)i * ldv_col + t], st[r].y[i], xv);
+    X[t + r * ldx] = xv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct SolveWs {
+  uint32_t* status;
+  RhsState* st;
+  Brief* brief;
+  unsigned int* counter;
+  int* flags;        // 2 * nb
+  double* partials;  // kMaxK * kRedBlocks
+  double* r;         // n x K
+  double* w;         // n x K
+  double* tmp;       // n x K
+  double* V;         // K x (m+1) x n
+  double* P;         // nchunk x n x K
+  void* RS;          // nchunk x n (fp64 size)
+  void* pub;         // 2 x nb x kTB x K doubles
+  size_t bytes;
+};
+
+int gemv_chunks(int64_t n) {
+  const int64_t rb = cdiv<int64_t>(n, kGemvRows);
+  int64_t c = cdiv<int64_t>(4 * 152, rb);
+  c = std::max<int64_t>(1, std::min<int64_t>(c, cdiv<int64_t>(n, 64)));
+  return (int)std::min<int64_t>(c, 64);
+}
+
+SolveWs carve_solve(void* base, int64_t n, int64_t K, int m) {
+  SolveWs w{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? (char*)base + off : nullptr;
+    off += round_up<size_t>(bytes, 256);
+    return p;
+  };
+  const int64_t nb = cdiv<int64_t>(n, kTB);
+  const int nchunk = gemv_chunks(n);
+  w.status = (uint32_t*)take(256);
+  w.st = (RhsState*)take(sizeof(RhsState) * kMaxK);
+  w.brief = (Brief*)take(sizeof(Brief) * kMaxK);
+  w.counter = (unsigned int*)take(256);
+  w.flags = (int*)take(sizeof(int) * 2 * nb);
+  w.partials = (double*)take(sizeof(double) * kMaxK * kRedBlocks);
+  w.r = (double*)take(sizeof(double) * n * K);
+  w.w = (double*)take(sizeof(double) * n * K);
+  w.tmp = (double*)take(sizeof(double) * n * K);
+  w.V = (double*)take(sizeof(double) * n * (m + 1) * K);
+  w.P = (double*)take(sizeof(double) * nchunk * n * K);
+  w.RS = take(sizeof(double) * nchunk * n);
+  w.pub = take(sizeof(double) * 2 * nb * kTB * K);
+  w.bytes = off;
+  return w;
+}
+
+template <int K>
+cudaError_t gemv_k(int64_t n, const double* A, int64_t lda, const double* X, int64_t ldx, int abs_mode,
+                   double* P, void* RS, int nchunk, cudaStream_t st) {
+  const int64_t chunk = cdiv<int64_t>(n, nchunk);
+  dim3 grid((unsigned)cdiv<int64_t>(n, kGemvRows), (unsigned)nchunk);
+  if (abs_mode == 0) gemv_partial_kernel<K, 0><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  else if (abs_mode == 1) gemv_partial_kernel<K, 1><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  else gemv_partial_kernel<K, 2><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  return cudaGetLastError();
+}
+
+// out = b - A X (b may be NULL: out = -A X), with optional norm tracking.
+cudaError_t residual(int64_t n, int K, const double* A, int64_t lda, const double* X, int64_t ldx,
+                     const double* B, int64_t ldb, double* out, int64_t ldo, int abs_mode, int track,
+                     const SolveWs& w, cudaStream_t st) {
+  const int nchunk = gemv_chunks(n);
+  cudaError_t e;
+  switch (K) {
+    case 1: e = gemv_k<1>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
+    case 2: e = gemv_k<2>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
+    case 3: e = gemv_k<3>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
+    case 4: e = gemv_k<4>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
+    case 5: e = gemv_k<5>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
+    case 6: e = gemv_k<6>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
+    case 7: e = gemv_k<7>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
+    default: e = gemv_k<8>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  gemv_finish_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, nchunk, w.P, B, ldb, out, ldo, X, ldx,
+                                                                      abs_mode, w.RS, w.st, track);
+  return cudaGetLastError();
+}
+
+size_t precond_smem(int64_t n, int K, int G, bool fp32) {
+  const int nb = (int)cdiv<int64_t>(n, kTB);
+  const int nown = cdiv(nb, G);
+  const size_t ts = fp32 ? 4 : 8;
+  return ts * ((size_t)nown * kTB * K + kTB * K + 4 * kTB * K) + sizeof(float) * kTB * (kTB + 1) + 64;
+}
+
+template <class T, int K>
+cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt, const double* v, int64_t ldv,
+                             double* z, int64_t ldz, const SolveWs& w, int epoch, int G, size_t smem,
+                             cudaStream_t st) {
+  auto kern = precond_kernel<T, K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  T* pub = (T*)w.pub;
+  int* flags = w.flags;
+  uint32_t* status = w.status;
+  void* args[] = {&n, (void*)&LU, &ld, &fmt, (void*)&v, &ldv, &z, &ldz, &pub, &flags, &epoch, &status};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(256), args, smem, st);
+}
+
+template <class T>
+cudaError_t precond_launch_t(int K, int64_t n, const uint16_t* LU, int64_t ld, int fmt, const double* v,
+                             int64_t ldv, double* z, int64_t ldz, const SolveWs& w, int epoch, int G, size_t smem,
+                             cudaStream_t st) {
+  switch (K) {
+    case 1: return precond_launch_k<T, 1>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
+    case 2: return precond_launch_k<T, 2>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
+    case 3: return precond_launch_k<T, 3>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
+    case 4: return precond_launch_k<T, 4>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
+    case 5: return precond_launch_k<T, 5>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
+    case 6: return precond_launch_k<T, 6>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
+    case 7: return precond_launch_k<T, 7>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
+    default: return precond_launch_k<T, 8>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
+  }
+}
+
+struct Solver {
+  int64_t n;
+  int K, m;
+  const double* A; int64_t lda;
+  const uint16_t* LU; int64_t ldlu; int fmt;
+  const double* B; int64_t ldb;
+  double* X; int64_t ldx;
+  hpmxp_ir_params prm;
+  SolveWs w;
+  cudaStream_t st;
+  int epoch = 0;
+  int G = 0;
+  size_t psmem = 0;
+  Brief brief[kMaxK];
+
+  int64_t ldv_rhs() const { return n * (m + 1); }
+
+  cudaError_t precond(const double* v, int64_t ldv, double* z, int64_t ldz) {
+    ++epoch;
+    if (prm.precond_fp32)
+      return precond_launch_t<float>(K, n, LU, ldlu, fmt, v, ldv, z, ldz, w, epoch, G, psmem, st);
+    return precond_launch_t<double>(K, n, LU, ldlu, fmt, v, ldv, z, ldz, w, epoch, G, psmem, st);
+  }
+
+  cudaError_t read_brief() {
+    cudaError_t e = cudaMemcpyAsync(brief, w.brief, sizeof(Brief) * K, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  }
+  bool any(int Brief::*f) const {
+    for (int r = 0; r < K; ++r)
+      if (brief[r].*f) return true;
+    return false;
+  }
+
+  cudaError_t setup() {
+    cudaError_t e;
+    const int nb = (int)cdiv<int64_t>(n, kTB);
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    // one CTA per SM at most: a cooperative launch keeps all of them resident
+    G = std::max(1, std::min(nb, sms));
+    psmem = precond_smem(n, K, G, prm.precond_fp32 != 0);
+    if (psmem > 200 * 1024) return cudaErrorInvalidValue;
+    if ((e = cudaMemsetAsync(w.st, 0, sizeof(RhsState) * kMaxK, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.flags, 0, sizeof(int) * 2 * nb, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.counter, 0, 256, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.status, 0, 4, st)) != cudaSuccess) return e;
+    init_kernel<<<1, 32, 0, st>>>(K, w.st);
+    return cudaGetLastError();
+  }
+
+  cudaError_t run() {
+    cudaError_t e = setup();
+    if (e != cudaSuccess) return e;
+    SolveParams sp{K, m, prm.max_iters, prm.inner_tol, prm.theta, prm.accept, n};
+
+    // x0 = U^{-1} L^{-1} b
+    if ((e = precond(B, ldb, X, ldx)) != cudaSuccess) return e;
+    bool first = true;
+    for (;;) {
+      // r = b - A x, norms; decide
+      if ((e = residual(n, K, A, lda, X, ldx, B, ldb, w.r, n, first ? 1 : 0, 1, w, st)) != cudaSuccess) return e;
+      check_kernel<<<1, 32, 0, st>>>(sp, w.st, w.brief, first ? 1 : 0);
+      first = false;
+      if ((e = read_brief()) != cudaSuccess) return e;
+      if (!any(&Brief::outer_active)) break;
+      // cycle start: z = M^{-1} r, beta, v0 = z / beta
+      if ((e = precond(w.r, n, w.tmp, n)) != cudaSuccess) return e;
+      norm2_kernel<<<kRedBlocks, 256, 0, st>>>(n, K, w.tmp, n, w.st, w.partials, w.counter);
+      cycle_start_kernel<<<1, 32, 0, st>>>(sp, w.st, w.brief);
+      scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, w.tmp, n, w.V, ldv_rhs(), w.st, 0);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = read_brief()) != cudaSuccess) return e;
+      if (!any(&Brief::outer_active)) break;
+      for (int j = 0; j < m && any(&Brief::cycle_active); ++j) {
+        // w = M^{-1} (A v_j)
+        if ((e = residual(n, K, A, lda, w.V + (int64_t)j * n, ldv_rhs(), nullptr, 0, w.tmp, n, 0, 0, w, st)) !=
+            cudaSuccess)
+          return e;
+        if ((e = precond(w.tmp, n, w.w, n)) != cudaSuccess) return e;
+        for (int i = 0; i <= j + 1; ++i)
+          mgs_kernel<<<kRedBlocks, 256, 0, st>>>(n, K, m, j, i, w.w, n, w.V, n, ldv_rhs(), w.st, w.partials,
+                                                 w.counter);
+        givens_kernel<<<1, 32, 0, st>>>(sp, j, w.st, w.brief);
+        scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, w.w, n, w.V + (int64_t)(j + 1) * n,
+                                                                       ldv_rhs(), w.st, 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = read_brief()) != cudaSuccess) return e;
+      }
+      cycle_finish_kernel<<<1, 32, 0, st>>>(sp, w.st);
+      update_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, X, ldx, w.V, n, ldv_rhs(), w.st);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+};
+
+}  // namespace
+
+size_t solve_ws_bytes(int64_t n, int64_t nrhs, int restart) { return carve_solve(nullptr, n, nrhs, restart).bytes; }
+size_t residual_ws_bytes(int64_t n, int64_t nrhs) { return carve_solve(nullptr, n, nrhs, 1).bytes; }
+
+hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu, int prec,
+                      const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs,
+                      const hpmxp_ir_params& prm, hpmxp_ir_info* info, void* ws, cudaStream_t st) {
+  Solver s;
+  s.n = n; s.K = (int)nrhs; s.m = prm.restart;
+  s.A = A; s.lda = lda;
+  s.LU = (const uint16_t*)LU; s.ldlu = ldlu; s.fmt = prec == HPMXP_FP16 ? kFP16 : kBF16;
+  s.B = b; s.ldb = ldb; s.X = x; s.ldx = ldx;
+  s.prm = prm;
+  s.w = carve_solve(ws, n, nrhs, prm.restart);
+  s.st = st;
+  cudaError_t e = s.run();
+  if (e != cudaSuccess) return status_from_cuda(e);
+  uint32_t word = 0;
+  e = cudaMemcpyAsync(&word, s.w.status, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = s.read_brief();
+  if (e != cudaSuccess) return status_from_cuda(e);
+  if (word) return status_from_word(word);
+  int worst = HPMXP_OK;
+  for (int r = 0; r < s.K; ++r) {
+    if (info) {
+      info[r].iters = s.brief[r].iters;
+      info[r].outer = s.brief[r].outer;
+      info[r].scaled_resid = s.brief[r].sr;
+      info[r].status = s.brief[r].status;
+      info[r].reserved = 0;
+    }
+    if (s.brief[r].status != HPMXP_OK && worst == HPMXP_OK) worst = s.brief[r].status;
+  }
+  return (hpmxp_status)worst;
+}
+
+hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, const double* v, int64_t ldv,
+                           double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws, cudaStream_t st) {
+  Solver s;
+  s.n = n; s.K = (int)nrhs; s.m = 1;
+  s.LU = (const uint16_t*)LU; s.ldlu = ldlu; s.fmt = fmt;
+  hpmxp_ir_params_default(&s.prm);
+  s.prm.precond_fp32 = fp32;
+  s.w = carve_solve(ws, n, nrhs, 1);
+  s.st = st;
+  cudaError_t e = s.setup();
+  if (e == cudaSuccess) e = s.precond(v, ldv, z, ldz);
+  uint32_t word = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&word, s.w.status, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  return status_from_word(word);
+}
+
+hpmxp_status residual_check(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
+                            const double* b, int64_t ldb, int64_t nrhs, double* out, void* ws, cudaStream_t st) {
+  SolveWs w = carve_solve(ws, n, nrhs, 1);
+  cudaError_t e = cudaMemsetAsync(w.st, 0, sizeof(RhsState) * kMaxK, st);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  e = residual(n, (int)nrhs, A, lda, x, ldx, b, ldb, w.r, n, 2, 1, w, st);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  std::vector<RhsState> hs(nrhs);
+  for (int64_t r = 0; r < nrhs; ++r) {
+    e = cudaMemcpyAsync(&hs[r], w.st + r, sizeof(RhsState), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+  }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  for (int64_t r = 0; r < nrhs; ++r) {
+    double rn, xn, bn, an;
+    memcpy(&rn, &hs[r].rn_bits, 8); memcpy(&xn, &hs[r].xn_bits, 8);
+    memcpy(&bn, &hs[r].bn_bits, 8); memcpy(&an, &hs[r].an_bits, 8);
+    out[r] = rn / ((an * xn + bn) * ((double)n * 0x1p-53));
+  }
+  return HPMXP_OK;
+}
+
+}  // namespace hpmxp

@@ -1,0 +1,572 @@
+// Low-precision blocked right-looking LU without pivoting (section
+// "Algorithmic Framework", Fig. 1 and the paragraph after it).
+//
+// Schedule for update depth NB (128, 256 or 512), at every diagonal block
+// D = [k, k+b):
+//   (i)   factor D in fp32 arithmetic: a single-CTA shared-memory kernel for
+//         128-wide sub-blocks (getrf + fp32 inverses of its L and U factors),
+//         sub-blocks of a wider D chained by 128-deep panel/Schur products;
+//   (ii)  U12 = L_D^{-1} A12 and L21 = A21 U_D^{-1} by block substitution over
+//         the 128-wide sub-blocks s, each step ONE product with fp32
+//         accumulation against a concatenated operand [W_s | Linv_ss] or
+//         [Z_s ; Uinv_ss] (W_s = -Linv_ss L_{s,0:s}, Z_s = -U_{0:s,s} Uinv_ss);
+//   (iii) A22 <- st(A22 - L21 U12), one tensor-core product of depth b.
+// Every product runs on the GEMM engine (tcgen05 by default).  Operands are
+// kept K-major: U12 is K-major in the column-major factor array already, and
+// the column panel is packed row-major once per step.
+#include "internal.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+namespace hpmxp {
+namespace {
+
+constexpr int kB = 128;         // base (sub-)block width
+constexpr int kLd = kB + 1;     // padded shared-memory leading dimension
+
+// ---------------------------------------------------------------------------
+// fp64 -> 16-bit float, round to nearest even, written from the IEEE 754
+// definition on the bit pattern (exponent rebias, 45- or 42-bit round-off with
+// ties to even, subnormal quantum for tiny values, overflow to infinity).
+// ---------------------------------------------------------------------------
+template <int kMant, int kBias>
+__device__ inline uint16_t f64_to_f16bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(u >> 63) << 15;
+  const int e = (int)((u >> 52) & 0x7ff);
+  const unsigned long long m = u & ((1ull << 52) - 1);
+  constexpr int kExpBits = 15 - kMant;
+  constexpr uint32_t kInf = ((1u << kExpBits) - 1) << kMant;
+  if (e == 0x7ff) return (uint16_t)(sign | kInf | (m ? (1u << (kMant - 1)) : 0u));
+  const int E = e - 1023 + kBias;             // biased target exponent
+  if (E >= (1 << kExpBits) - 1) return (uint16_t)(sign | kInf);
+  if (E >= 1) {
+    constexpr int kDrop = 52 - kMant;
+    const unsigned long long keep = m >> kDrop, rem = m & ((1ull << kDrop) - 1);
+    const unsigned long long half = 1ull << (kDrop - 1);
+    uint32_t r = ((uint32_t)E << kMant) | (uint32_t)keep;
+    if (rem > half || (rem == half && (keep & 1))) r += 1;   // may carry into the exponent / infinity
+    return (uint16_t)(sign | r);
+  }
+  if (e == 0) return (uint16_t)sign;            // fp64 subnormals are far below the 16-bit ones
+  // target subnormal: value = mf 2^(e-1075) = k * 2^(1 - kBias - kMant)
+  const unsigned long long mf = m | (1ull << 52);
+  const int s = 1075 - e - (kBias - 1 + kMant);  // right shift taking mf to units of the quantum
+  if (s > 63) return (uint16_t)sign;
+  const unsigned long long k = mf >> s, rem = mf & ((1ull << s) - 1), half = 1ull << (s - 1);
+  uint32_t r = (uint32_t)k;
+  if (rem > half || (rem == half && (k & 1))) r += 1;
+  return (uint16_t)(sign | r);
+}
+
+__device__ inline uint16_t f64_to_u16(double x, int fmt) {
+  return fmt == kBF16 ? f64_to_f16bits<7, 127>(x) : f64_to_f16bits<10, 15>(x);
+}
+
+// A (fp64, column major) -> LU (16-bit, column major).  Each thread converts
+// two consecutive rows of one column with one 16-byte load when aligned.
+__global__ void cast_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
+                            uint16_t* __restrict__ LU, int64_t ldlu, int fmt) {
+  const int64_t pairs = (n + 1) / 2;
+  const int64_t total = pairs * n;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = g / pairs, i = (g % pairs) * 2;
+    const double* src = A + i + j * lda;
+    uint16_t* dst = LU + i + j * ldlu;
+    if (i + 1 < n) {
+      double2 v;
+      if ((((uintptr_t)src) & 15) == 0) v = *reinterpret_cast<const double2*>(src);
+      else { v.x = src[0]; v.y = src[1]; }
+      const uint32_t packed = (uint32_t)f64_to_u16(v.x, fmt) | ((uint32_t)f64_to_u16(v.y, fmt) << 16);
+      *reinterpret_cast<uint32_t*>(dst) = packed;   // ldlu even and LU 16-byte aligned
+    } else {
+      dst[0] = f64_to_u16(src[0], fmt);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (i) Diagonal block of width b <= 128, one CTA: right-looking unblocked
+// factorization in fp32 (l = a / pivot, then a -= l u by fused multiply-add,
+// pivots ascending), rounding into storage, then the fp32 inverses of the
+// stored unit-lower L and upper U:
+//   X = L^{-1}: X[r][c] = -sum_{t=c}^{r-1} L[r][t] X[t][c]   (t ascending)
+//   Y = U^{-1}: Y[c][c] = 1 / U[c][c];
+//               Y[r][c] = (-sum_{t=c}^{r+1} U[r][t] Y[t][c]) / U[r][r] (t descending)
+// evaluated column-parallel in the same per-entry operation order, rounded to
+// storage and written as the K-major GEMM operands Linv (Linv[p*ldl + t]) and
+// Uinv^T (UinvT[p*ldu + t] = Uinv[t][p]).  128 x 128 zero-padded.
+// ---------------------------------------------------------------------------
+constexpr int kGetrfThreads = 512;
+
+__global__ void __launch_bounds__(kGetrfThreads)
+getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_t* __restrict__ linv,
+                  int64_t ldl, uint16_t* __restrict__ uinvT, int64_t ldu, uint32_t* status) {
+  extern __shared__ float sm[];
+  float* a = sm;               // a[j * kLd + i] = D(i, j)
+  float* x = sm + kB * kLd;    // inverse work, x[c * kLd + r] = X(r, c)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kGetrfThreads / 32;
+
+  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    const int i = idx % kB, j = idx / kB;
+    a[j * kLd + i] = (i < b && j < b) ? u16_to_f32(D[i + (int64_t)j * ldd], fmt) : 0.0f;
+  }
+  __syncthreads();
+
+  bool bad = false;
+  for (int p = 0; p < b; ++p) {
+    const float piv = a[p * kLd + p];
+    if (!(isfinite(piv) && piv != 0.0f)) bad = true;
+    for (int i = p + 1 + tid; i < b; i += kGetrfThreads) a[p * kLd + i] = __fdiv_rn(a[p * kLd + i], piv);
+    __syncthreads();
+    for (int j = p + 1 + warp; j < b; j += nw) {
+      const float u = a[j * kLd + p];
+      for (int i = p + 1 + lane; i < b; i += 32)
+        a[j * kLd + i] = __fmaf_rn(-a[p * kLd + i], u, a[j * kLd + i]);
+    }
+    __syncthreads();
+  }
+  if (bad && tid == 0) atomicOr(status, kErrPivot);
+
+  // round into storage; keep the stored values for the inverses
+  for (int idx = tid; idx < b * b; idx += kGetrfThreads) {
+    const int i = idx % b, j = idx / b;
+    const uint16_t h = f32_to_u16(a[j * kLd + i], fmt);
+    D[i + (int64_t)j * ldd] = h;
+    a[j * kLd + i] = u16_to_f32(h, fmt);
+  }
+  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    const int r = idx % kB, c = idx / kB;
+    x[c * kLd + r] = (r == c && r < b) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+
+  // X = L^{-1}: step t updates rows r > t of every column c <= t
+  for (int t = 0; t < b; ++t) {
+    for (int c = warp; c <= t; c += nw) {
+      const float xt = x[c * kLd + t];
+      for (int r = t + 1 + lane; r < b; r += 32)
+        x[c * kLd + r] = __fmaf_rn(-a[t * kLd + r], xt, x[c * kLd + r]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    const int t = idx % kB, p = idx / kB;   // Linv[p][t] = X(p, t)
+    linv[(int64_t)p * ldl + t] = (p < b && t < b) ? f32_to_u16(x[t * kLd + p], fmt) : (uint16_t)0;
+  }
+  __syncthreads();
+
+  // Y = U^{-1}: x[c * kLd + r] holds the running sum for r < c, then Y(r, c)
+  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    const int r = idx % kB, c = idx / kB;
+    x[c * kLd + r] = (r == c && r < b) ? __fdiv_rn(1.0f, a[c * kLd + c]) : 0.0f;
+  }
+  __syncthreads();
+  for (int t = b - 1; t >= 0; --t) {
+    const float utt = a[t * kLd + t];
+    for (int c = t + 1 + tid; c < b; c += kGetrfThreads) x[c * kLd + t] = __fdiv_rn(-x[c * kLd + t], utt);
+    __syncthreads();
+    for (int c = t + warp; c < b; c += nw) {
+      const float yt = x[c * kLd + t];
+      for (int r = lane; r < t; r += 32) x[c * kLd + r] = __fmaf_rn(a[t * kLd + r], yt, x[c * kLd + r]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    const int t = idx % kB, p = idx / kB;   // UinvT[p][t] = Y(t, p)
+    uinvT[(int64_t)p * ldu + t] = (p < b && t < b) ? f32_to_u16(x[p * kLd + t], fmt) : (uint16_t)0;
+  }
+}
+
+// Column-major block (rows x cols at src, lds) -> row-major (dst[i*ldd + j]).
+__global__ void pack_rows_kernel(int64_t rows, int cols, const uint16_t* __restrict__ src, int64_t lds,
+                                 uint16_t* __restrict__ dst, int64_t ldd) {
+  __shared__ uint16_t t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = i0 + threadIdx.x;
+    const int j = j0 + k;
+    t[k][threadIdx.x] = (i < rows && j < cols) ? src[i + (int64_t)j * lds] : (uint16_t)0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = i0 + k;
+    const int j = j0 + threadIdx.x;
+    if (i < rows && j < cols) dst[i * ldd + j] = t[threadIdx.x][k];
+  }
+}
+
+// W_s = st(-Linv_ss L_{s,0:s}) into the first ws columns of the row-major
+// operand Aop (row p, column q), fp32 accumulation over t ascending:
+//   W[p][q] = -sum_t Linv[p][t] * L(s0 + t, k + q)
+// Linv is Aop[p * ld + ws + t]; L(s0+t, k+q) = Lsub[t + q * ldlu].
+__global__ void make_w_kernel(int ws, uint16_t* aop, int64_t ld, const uint16_t* __restrict__ Lsub,
+                              int64_t ldlu, int fmt) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+  if (q >= ws) return;
+  const uint16_t* li = aop + (int64_t)p * ld + ws;
+  const uint16_t* lc = Lsub + (int64_t)q * ldlu;
+  float acc = 0.0f;
+  for (int t = 0; t < kB; ++t) acc = __fmaf_rn(u16_to_f32(li[t], fmt), u16_to_f32(lc[t], fmt), acc);
+  aop[(int64_t)p * ld + q] = f32_to_u16(-acc, fmt);
+}
+
+// Z_s^T into the first zs columns of the row-major operand Bop (row p, column q):
+//   Z[q][p] = -sum_t U(k + q, s0 + t) * Uinv[t][p]
+// Uinv[t][p] = Bop[p * ld + zs + t]; U(k+q, s0+t) = Usub[q + t * ldlu].
+__global__ void make_z_kernel(int zs, uint16_t* bop, int64_t ld, const uint16_t* __restrict__ Usub,
+                              int64_t ldlu, int fmt) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+  if (q >= zs) return;
+  const uint16_t* ui = bop + (int64_t)p * ld + zs;
+  float acc = 0.0f;
+  for (int t = 0; t < kB; ++t)
+    acc = __fmaf_rn(u16_to_f32(Usub[q + (int64_t)t * ldlu], fmt), u16_to_f32(ui[t], fmt), acc);
+  bop[(int64_t)p * ld + q] = f32_to_u16(-acc, fmt);
+}
+
+// ---------------------------------------------------------------------------
+// SIMT validation engine: the same products as the tensor-core engine with
+// one fp32 fused multiply-add per term in ascending k (the oracle's order), so
+// a factorization run on it is bit-identical to the oracle.  64 x 64 tiles,
+// 256 threads, 4 x 4 outputs per thread.
+// ---------------------------------------------------------------------------
+__device__ inline float e4m3_to_f32(uint8_t v) {
+  const uint32_t s = (uint32_t)(v >> 7), e = (v >> 3) & 15, m = v & 7;
+  float f;
+  if (e == 0) f = (float)m * 0x1p-9f;                        // subnormal: m/8 * 2^-6
+  else if (e == 15 && m == 7) f = __uint_as_float(0x7fc00000u);
+  else f = __uint_as_float(((e + 120u) << 23) | (m << 20));  // (1 + m/8) 2^(e-7)
+  return s ? -f : f;
+}
+
+__global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs g) {
+  __shared__ float As[64][33], Bs[64][33];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+  float acc[4][4], accg[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
+  for (int k0 = 0; k0 < g.K; k0 += 32) {
+    if (g.fp8 && (k0 % 128) == 0) {
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c) accg[a][c] = 0.0f;
+    }
+    for (int idx = tid; idx < 64 * 32; idx += 256) {
+      const int r = idx / 32, kk = idx % 32;
+      const int64_t i = m0 + r, j = n0 + r;
+      float av = 0.0f, bv = 0.0f;
+      if (g.fp8) {
+        if (i < g.M) av = e4m3_to_f32(((const uint8_t*)g.A)[i * g.lda + k0 + kk]);
+        if (j < g.N) bv = e4m3_to_f32(((const uint8_t*)g.B)[j * g.ldb + k0 + kk]);
+      } else {
+        if (i < g.M) av = u16_to_f32(((const uint16_t*)g.A)[i * g.lda + k0 + kk], g.fmt);
+        if (j < g.N) bv = u16_to_f32(((const uint16_t*)g.B)[j * g.ldb + k0 + kk], g.fmt);
+      }
+      As[r][kk] = av;
+      Bs[r][kk] = bv;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < 32; ++kk)
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c) {
+          if (g.fp8) accg[a][c] = __fmaf_rn(As[ty * 4 + a][kk], Bs[tx * 4 + c][kk], accg[a][c]);
+          else acc[a][c] = __fmaf_rn(As[ty * 4 + a][kk], Bs[tx * 4 + c][kk], acc[a][c]);
+        }
+    __syncthreads();
+    if (g.fp8 && ((k0 + 32) % 128) == 0) {
+      const int kb = k0 / 128;
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c) {
+          const int64_t i = min(m0 + ty * 4 + a, (int64_t)g.M - 1), j = min(n0 + tx * 4 + c, (int64_t)g.N - 1);
+          const float sc = __fmul_rn(g.sA[(i / 128) * g.sa_ld + kb], g.sB[(j / 128) * g.sb_ld + kb]);
+          acc[a][c] = __fmaf_rn(accg[a][c], sc, acc[a][c]);
+        }
+    }
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c) {
+      const int64_t i = m0 + ty * 4 + a, j = n0 + tx * 4 + c;
+      if (i >= g.M || j >= g.N) continue;
+      uint16_t* cp = g.C ? (uint16_t*)g.C + i + j * g.ldc : nullptr;
+      float v;
+      if (g.mode == kEpiSub) v = __fsub_rn(u16_to_f32(*cp, g.fmt), acc[a][c]);
+      else v = g.sign * acc[a][c];
+      const uint16_t h = f32_to_u16(v, g.fmt);
+      if (cp) *cp = h;
+      if (g.R) ((uint16_t*)g.R)[i * g.ldr + j] = h;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP8 variant of the Schur update (config with E4M3 operands): quantize the
+// column panel (row-major, rows x b) and the row panel (column-major b x cols
+// in the factor array) per 128 x 128 tile: s = fl32(amax / 448) (1 when the
+// tile is zero), q = E4M3_satfinite(fl32(x / s)).  Outputs are K-major bytes:
+// Lq[i * ldq + p], Uq[j * ldq + p], scales sL[(i/128) * ng + g], sU[(j/128) * ng + g].
+// One CTA per tile.
+// ---------------------------------------------------------------------------
+__device__ inline uint8_t f32_to_e4m3_sat(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+__global__ void __launch_bounds__(256) quant_tile_kernel(const uint16_t* __restrict__ src, int64_t lds,
+                                                        int rowmajor, int64_t rows, int b, int fmt,
+                                                        uint8_t* __restrict__ q, int64_t ldq, float* scale,
+                                                        int ng) {
+  const int64_t a = blockIdx.x;   // 128-row (or column) tile of the long side
+  const int gk = blockIdx.y;      // 128-deep slice
+  const int tid = threadIdx.x;
+  __shared__ float red[256];
+  float amax = 0.0f;
+  for (int idx = tid; idx < kB * kB; idx += 256) {
+    const int64_t x = a * kB + idx / kB;
+    const int p = gk * kB + idx % kB;
+    if (x < rows && p < b) {
+      const uint16_t h = rowmajor ? src[x * lds + p] : src[p + x * lds];
+      amax = fmaxf(amax, fabsf(u16_to_f32(h, fmt)));
+    }
+  }
+  red[tid] = amax;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (tid < s) red[tid] = fmaxf(red[tid], red[tid + s]);
+    __syncthreads();
+  }
+  amax = red[0];
+  const float sc = amax == 0.0f ? 1.0f : __fdiv_rn(amax, 448.0f);
+  for (int idx = tid; idx < kB * kB; idx += 256) {
+    const int64_t x = a * kB + idx / kB;
+    const int p = gk * kB + idx % kB;
+    if (x < rows && p < b) {
+      const uint16_t h = rowmajor ? src[x * lds + p] : src[p + x * lds];
+      q[x * ldq + p] = f32_to_e4m3_sat(__fdiv_rn(u16_to_f32(h, fmt), sc));
+    }
+  }
+  if (tid == 0) scale[a * ng + gk] = sc;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout of the factorization (all offsets 256-byte aligned).
+// ---------------------------------------------------------------------------
+struct FactorWs {
+  uint32_t* status;
+  uint16_t* Lp;      // packed column panel, row major, n x NB
+  uint16_t* Li;      // packed inner column panel, row major, NB x 128
+  uint16_t* Aop;     // 4 row-panel operands [W_s | Linv_ss], 128 x NB each
+  uint16_t* Bop;     // 4 column-panel operands [Z_s^T | Uinv_ss^T], 128 x NB each
+  uint8_t* Lq;       // fp8 column panel, n x NB bytes
+  uint8_t* Uq;       // fp8 row panel, n x NB bytes (K-major per column)
+  float* sL;         // fp8 scales, (n/128) x 4
+  float* sU;
+  size_t bytes;
+};
+
+FactorWs carve(void* base, int64_t n, int prec, int NB) {
+  FactorWs w{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? (char*)base + off : nullptr;
+    off += round_up<size_t>(bytes, 256);
+    return p;
+  };
+  const int64_t nr = round_up<int64_t>(n, kB);
+  w.status = (uint32_t*)take(256);
+  w.Lp = (uint16_t*)take(sizeof(uint16_t) * nr * NB);
+  w.Li = (uint16_t*)take(sizeof(uint16_t) * (size_t)NB * kB);
+  w.Aop = (uint16_t*)take(sizeof(uint16_t) * 4 * kB * NB);
+  w.Bop = (uint16_t*)take(sizeof(uint16_t) * 4 * kB * NB);
+  if (prec == HPMXP_FP8_E4M3) {
+    w.Lq = (uint8_t*)take((size_t)nr * NB);
+    w.Uq = (uint8_t*)take((size_t)nr * NB);
+    w.sL = (float*)take(sizeof(float) * (nr / kB) * 4);
+    w.sU = (float*)take(sizeof(float) * (nr / kB) * 4);
+  }
+  w.bytes = off;
+  return w;
+}
+
+struct Factorizer {
+  int64_t n;
+  uint16_t* LU;
+  int64_t ld;
+  int fmt, prec, NB, engine;
+  FactorWs w;
+  cudaStream_t st;
+  cudaError_t err = cudaSuccess;
+
+  uint16_t* at(int64_t i, int64_t j) const { return LU + i + j * ld; }
+  uint16_t* aop(int s) const { return w.Aop + (size_t)s * kB * NB; }
+  uint16_t* bop(int s) const { return w.Bop + (size_t)s * kB * NB; }
+
+  void check(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
+
+  void gemm(GemmArgs g) {
+    if (g.M <= 0 || g.N <= 0) return;
+    g.fmt = fmt;
+    g.status = w.status;
+    check(engine == 1 ? gemm_simt(g, st) : gemm_tc(g, st));
+  }
+
+  void getrf_base(int64_t k, int b, int slot) {
+    getrf_base_kernel<<<1, kGetrfThreads, 2 * kB * kLd * sizeof(float), st>>>(
+        b, at(k, k), ld, fmt, aop(slot) + slot * kB, NB, bop(slot) + slot * kB, NB, w.status);
+    check(cudaGetLastError());
+  }
+
+  void pack(int64_t rows, int cols, const uint16_t* src, uint16_t* dst, int64_t ldd) {
+    if (rows <= 0) return;
+    dim3 grid((unsigned)cdiv<int64_t>(rows, 32), (unsigned)cdiv(cols, 32));
+    pack_rows_kernel<<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, ld, dst, ldd);
+    check(cudaGetLastError());
+  }
+
+  // Panels and Schur update of one sub-step inside a diagonal block wider than
+  // 128: sub-block at kk (width 128) of the block ending at e.
+  void inner_step(int64_t kk, int slot, int64_t e) {
+    const int64_t m = e - (kk + kB);
+    if (m <= 0) return;
+    GemmArgs u{};   // U12 = st(Linv A12), in place
+    u.M = kB; u.N = (int)m; u.K = kB;
+    u.A = aop(slot) + slot * kB; u.lda = NB;
+    u.B = at(kk, kk + kB); u.ldb = ld;
+    u.C = at(kk, kk + kB); u.ldc = ld;
+    u.mode = kEpiStore; u.sign = 1.0f;
+    gemm(u);
+    pack(m, kB, at(kk + kB, kk), w.Li, kB);
+    GemmArgs l{};   // L21 = st(A21 Uinv): column major into LU, row major over the packed copy
+    l.M = (int)m; l.N = kB; l.K = kB;
+    l.A = w.Li; l.lda = kB;
+    l.B = bop(slot) + slot * kB; l.ldb = NB;
+    l.C = at(kk + kB, kk); l.ldc = ld;
+    l.R = w.Li; l.ldr = kB;
+    l.mode = kEpiStore; l.sign = 1.0f;
+    gemm(l);
+    GemmArgs t{};   // A22 <- st(A22 - L21 U12)
+    t.M = (int)m; t.N = (int)m; t.K = kB;
+    t.A = w.Li; t.lda = kB;
+    t.B = at(kk, kk + kB); t.ldb = ld;
+    t.C = at(kk + kB, kk + kB); t.ldc = ld;
+    t.mode = kEpiSub;
+    gemm(t);
+  }
+
+  void run() {
+    for (int64_t k = 0; k < n && err == cudaSuccess; k += NB) {
+      const int64_t b = std::min<int64_t>(NB, n - k);
+      const int nsub = (int)cdiv<int64_t>(b, kB);
+      // (i) diagonal block
+      for (int s = 0; s < nsub; ++s) {
+        const int64_t kk = k + (int64_t)s * kB;
+        getrf_base(kk, (int)std::min<int64_t>(kB, k + b - kk), s);
+        if (nsub > 1) inner_step(kk, s, k + b);
+      }
+      const int64_t m = n - (k + b);
+      if (m <= 0) break;
+      // (ii) row panel U12 and column panel L21, block substitution over s
+      pack(m, (int)b, at(k + b, k), w.Lp, NB);
+      for (int s = 0; s < nsub; ++s) {
+        const int64_t s0 = k + (int64_t)s * kB;
+        if (s > 0) {
+          make_w_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(
+              s * kB, aop(s), NB, at(s0, k), ld, fmt);
+          make_z_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(
+              s * kB, bop(s), NB, at(k, s0), ld, fmt);
+          check(cudaGetLastError());
+        }
+        GemmArgs u{};
+        u.M = kB; u.N = (int)m; u.K = (s + 1) * kB;
+        u.A = aop(s); u.lda = NB;
+        u.B = at(k, k + b); u.ldb = ld;
+        u.C = at(s0, k + b); u.ldc = ld;
+        u.mode = kEpiStore; u.sign = 1.0f;
+        gemm(u);
+        GemmArgs l{};
+        l.M = (int)m; l.N = kB; l.K = (s + 1) * kB;
+        l.A = w.Lp; l.lda = NB;
+        l.B = bop(s); l.ldb = NB;
+        l.C = at(k + b, s0); l.ldc = ld;
+        l.R = w.Lp + s * kB; l.ldr = NB;
+        l.mode = kEpiStore; l.sign = 1.0f;
+        gemm(l);
+      }
+      // (iii) Schur update of depth b
+      GemmArgs t{};
+      t.M = (int)m; t.N = (int)m; t.K = (int)b;
+      t.C = at(k + b, k + b); t.ldc = ld;
+      t.mode = kEpiSub;
+      if (prec == HPMXP_FP8_E4M3) {
+        const int ng = nsub;
+        quant_tile_kernel<<<dim3((unsigned)cdiv<int64_t>(m, kB), ng), 256, 0, st>>>(
+            w.Lp, NB, 1, m, (int)b, fmt, w.Lq, NB, w.sL, 4);
+        quant_tile_kernel<<<dim3((unsigned)cdiv<int64_t>(m, kB), ng), 256, 0, st>>>(
+            at(k, k + b), ld, 0, m, (int)b, fmt, w.Uq, NB, w.sU, 4);
+        check(cudaGetLastError());
+        t.fp8 = 1;
+        t.A = w.Lq; t.lda = NB;
+        t.B = w.Uq; t.ldb = NB;
+        t.sA = w.sL; t.sa_ld = 4;
+        t.sB = w.sU; t.sb_ld = 4;
+      } else {
+        t.A = w.Lp; t.lda = NB;
+        t.B = at(k, k + b); t.ldb = ld;
+      }
+      gemm(t);
+    }
+  }
+};
+
+}  // namespace
+
+int gemm_engine() {
+  const char* e = getenv("HPMXP_GEMM_ENGINE");
+  return (e && strcmp(e, "simt") == 0) ? 1 : 0;
+}
+
+cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(g.N, 64), (unsigned)cdiv(g.M, 64));
+  gemm_simt_kernel<<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st) {
+  const int64_t work = (n + 1) / 2 * n;
+  const int blocks = (int)std::min<int64_t>(cdiv<int64_t>(work, 256), 152 * 16);
+  cast_kernel<<<blocks, 256, 0, st>>>(n, A, lda, (uint16_t*)out, ldo, fmt);
+  return cudaGetLastError();
+}
+
+size_t factor_ws_bytes(int64_t n, int prec, int nb) { return carve(nullptr, n, prec, nb).bytes; }
+
+hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU,
+                    int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(getrf_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * kB * kLd * (int)sizeof(float));
+    if (e != cudaSuccess) return status_from_cuda(e);
+    attr_set = true;
+  }
+  Factorizer f;
+  f.n = n; f.LU = (uint16_t*)LU; f.ld = ldlu;
+  f.prec = prec; f.fmt = prec == HPMXP_FP16 ? kFP16 : kBF16;
+  f.NB = nb; f.engine = gemm_engine();
+  f.w = carve(ws, n, prec, nb);
+  f.st = st;
+  f.check(cudaMemsetAsync(f.w.status, 0, sizeof(uint32_t), st));
+  f.check(launch_cast(n, A, lda, LU, ldlu, f.fmt, st));
+  f.run();
+  if (f.err != cudaSuccess) return status_from_cuda(f.err);
+  uint32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, f.w.status, sizeof(word), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  return status_from_word(word);
+}
+
+}  // namespace hpmxp

@@ -1,0 +1,369 @@
+"""GPU parity tests: every stage of the CUDA path against the CPU oracle, through
+the C interface.  Bit-exact where the work is integer or deterministic
+rounding (generator, cast, and the whole factorization on the SIMT reference
+engine); tolerance-based where tensor-core summation order differs (the
+default tcgen05 factorization, the refinement).
+
+Tolerances (derived in the design doc):
+  factors, tcgen05 engine:  ||LU_gpu - LU_orc||_F / ||LU_orc||_F <= 8 n u_low
+                            (asserted tighter too: <= u_low)
+  solution:                 scaled residual < 16, ||x_gpu - x_orc||_inf / ||x_orc||_inf <= 1e-10,
+                            |iters_gpu - iters_orc| <= 1
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from inputs import vectors  # noqa: E402
+from paper_2509_19618_gb300 import api, capi  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+U_LOW = {capi.BF16: 2.0**-8, capi.FP16: 2.0**-11, capi.FP8_E4M3: 2.0**-8}
+ORC_FMT = {capi.BF16: oracle.BF16, capi.FP16: oracle.FP16, capi.FP8_E4M3: oracle.BF16}
+
+
+def to_np(m: api.ColMajor) -> np.ndarray:
+    v = m.view()
+    if v.dtype in (torch.bfloat16, torch.float16):
+        v = v.float()
+    return v.double().cpu().numpy()
+
+
+class engine:
+    """Select the factorization's GEMM engine for the duration of a block."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        self.old = os.environ.get("HPMXP_GEMM_ENGINE")
+        if self.name == "simt":
+            os.environ["HPMXP_GEMM_ENGINE"] = "simt"
+        else:
+            os.environ.pop("HPMXP_GEMM_ENGINE", None)
+
+    def __exit__(self, *a):
+        if self.old is None:
+            os.environ.pop("HPMXP_GEMM_ENGINE", None)
+        else:
+            os.environ["HPMXP_GEMM_ENGINE"] = self.old
+
+
+# ---------------------------------------------------------------------------
+# generator: integer work, bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 3, 127, 128, 129, 600, 1000])
+@pytest.mark.parametrize("mode", [capi.DIAG_DOMINANT, capi.DIAG_SQRTN, capi.DIAG_NONE])
+def test_generator_bit_exact(n, mode):
+    A, b = api.generate(n, seed=1234 + n, margin=1.5, diag=mode, nrhs=3, device=DEV)
+    A_o, b_o = oracle.generate(n, 1234 + n, margin=1.5, mode=mode, nrhs=3)
+    assert np.array_equal(to_np(A), A_o)
+    assert np.array_equal(to_np(b), b_o)
+
+
+@pytest.mark.parametrize("n", [32768])
+def test_generator_full_size_sampled_rows(n):
+    A, b = api.generate(n, seed=1, device=DEV)
+    rows = [0, 1, 4095, 4096, 17000, n - 1]
+    R = oracle.generate_rows(n, 1, rows)
+    for k, i in enumerate(rows):
+        got = A.view()[i].cpu().numpy()
+        assert np.array_equal(got, R[k]), i
+    bi = b.view()[:, 0].cpu().numpy()
+    for i in [0, 77, n - 1]:
+        assert bi[i] == oracle.draw_value(1, n * n + i)
+    del A, b
+    torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# cast: deterministic rounding, bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [capi.BF16, capi.FP16])
+def test_cast_bit_exact(prec):
+    n = 300
+    A_o, _ = oracle.generate(n, 5)
+    special = np.array([0.0, -0.0, 1e-30, -1e-30, 2.0**-24, 3 * 2.0**-26, 65504.0, 65520.0, 1e6, -1e40,
+                        np.inf, -np.inf, 1.0 + 2.0**-8, 1.0 + 3 * 2.0**-9, 1.0 + 2.0**-11, 6e-8])
+    A_o[: len(special), 0] = special
+    A = api.ColMajor.from_tensor(torch.from_numpy(A_o), DEV)
+    out = api.ColMajor.empty(n, n, api.factor_storage_dtype(prec), DEV)
+    st = capi.hpmxp_test_cast(n, A.ptr, A.ld, prec, out.ptr, out.ld, api.stream_handle())
+    assert st == capi.OK
+    torch.cuda.synchronize()
+    want = oracle.round_to(A_o, ORC_FMT[prec])
+    got = to_np(out)
+    assert np.array_equal(np.signbit(got), np.signbit(want))
+    assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------------------
+# GEMM engines against the product's plain definition
+# ---------------------------------------------------------------------------
+def _bf16(x):
+    return oracle.round_to(x, oracle.BF16)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 128), (200, 333, 128), (384, 256, 256), (130, 520, 512)])
+@pytest.mark.parametrize("eng", [0, 1])
+def test_gemm_engines(M, N, K, eng):
+    g = np.random.default_rng(M * 7 + N + K)
+    A = _bf16(g.uniform(-1, 1, (M, K)))
+    B = _bf16(g.uniform(-1, 1, (N, K)))
+    C0 = _bf16(g.uniform(-64, 64, (M, N)))
+    tA = torch.from_numpy(A).to(DEV, torch.bfloat16).contiguous()
+    tB = torch.from_numpy(B).to(DEV, torch.bfloat16).contiguous()
+    C = api.ColMajor.from_tensor(torch.from_numpy(C0), DEV, dtype=torch.bfloat16)
+    R = torch.zeros((M, N), dtype=torch.bfloat16, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    exact = A @ B.T
+    # subtract mode, in place
+    st = capi.hpmxp_test_gemm(M, N, K, tA.data_ptr(), K, tB.data_ptr(), K, C.ptr, C.ld, None, 0, 0, 1.0, 0, 0,
+                              None, 0, None, 0, eng, status.data_ptr(), api.stream_handle())
+    assert st == capi.OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    got = to_np(C)
+    want = C0 - exact
+    ulp = np.spacing(np.abs(_bf16(want)).astype(np.float32)).astype(np.float64) * 2**16
+    assert np.all(np.abs(got - want) <= ulp + 1e-5 * np.abs(A).sum(1)[:, None].max())
+    # store mode, negated, into both column-major C and the row-major copy
+    C2 = api.ColMajor.empty(M, N, torch.bfloat16, DEV)
+    st = capi.hpmxp_test_gemm(M, N, K, tA.data_ptr(), K, tB.data_ptr(), K, C2.ptr, C2.ld, R.data_ptr(), N, 1, -1.0,
+                              0, 0, None, 0, None, 0, eng, status.data_ptr(), api.stream_handle())
+    assert st == capi.OK
+    torch.cuda.synchronize()
+    got2 = to_np(C2)
+    assert np.array_equal(got2, R.float().double().cpu().numpy())
+    assert np.allclose(got2, -exact, rtol=2.0**-8, atol=1e-4)
+
+
+def test_gemm_engines_agree_closely():
+    M, N, K = 256, 384, 512
+    g = np.random.default_rng(3)
+    A = _bf16(g.uniform(-1, 1, (M, K)))
+    B = _bf16(g.uniform(-1, 1, (N, K)))
+    tA = torch.from_numpy(A).to(DEV, torch.bfloat16).contiguous()
+    tB = torch.from_numpy(B).to(DEV, torch.bfloat16).contiguous()
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    outs = []
+    for eng in (0, 1):
+        R = torch.zeros((M, N), dtype=torch.bfloat16, device=DEV)
+        st = capi.hpmxp_test_gemm(M, N, K, tA.data_ptr(), K, tB.data_ptr(), K, None, 0, R.data_ptr(), N, 1, 1.0, 0,
+                                  0, None, 0, None, 0, eng, status.data_ptr(), api.stream_handle())
+        assert st == capi.OK
+        outs.append(R)
+    torch.cuda.synchronize()
+    a, b = outs[0].float(), outs[1].float()
+    assert bool(((a - b).abs() <= a.abs() * 2.0**-7 + 1e-6).all())
+
+
+@pytest.mark.parametrize("eng", [0, 1])
+def test_gemm_fp8(eng):
+    M, N, K = 256, 200, 256
+    g = np.random.default_rng(11)
+    qa = g.integers(0, 0x7e, size=(M, K), dtype=np.uint8) | (g.integers(0, 2, size=(M, K), dtype=np.uint8) << 7)
+    qb = g.integers(0, 0x7e, size=(N, K), dtype=np.uint8) | (g.integers(0, 2, size=(N, K), dtype=np.uint8) << 7)
+
+    def dec(c):
+        s = np.where(c >> 7, -1.0, 1.0)
+        e = (c >> 3) & 15
+        m = (c & 7).astype(np.float64)
+        return s * np.where(e == 0, m / 8 * 2.0**-6, (1 + m / 8) * np.exp2(e.astype(np.float64) - 7))
+
+    sa = g.uniform(0.5, 2, (2, 2)).astype(np.float32)
+    sb = g.uniform(0.5, 2, (2, 2)).astype(np.float32)
+    tA = torch.from_numpy(qa).to(DEV)
+    tB = torch.from_numpy(qb).to(DEV)
+    tsa = torch.from_numpy(sa).to(DEV)
+    tsb = torch.from_numpy(sb).to(DEV)
+    C0 = _bf16(g.uniform(-4000, 4000, (M, N)))
+    C = api.ColMajor.from_tensor(torch.from_numpy(C0), DEV, dtype=torch.bfloat16)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    st = capi.hpmxp_test_gemm(M, N, K, tA.data_ptr(), K, tB.data_ptr(), K, C.ptr, C.ld, None, 0, 0, 1.0, 0, 1,
+                              tsa.data_ptr(), 2, tsb.data_ptr(), 2, eng, status.data_ptr(), api.stream_handle())
+    assert st == capi.OK
+    torch.cuda.synchronize()
+    A, B = dec(qa), dec(qb)
+    want = C0.copy()
+    for gk in range(2):
+        sl = slice(128 * gk, 128 * gk + 128)
+        part = A[:, sl] @ B[:, sl].T
+        sc = (sa[np.arange(M) // 128, gk][:, None].astype(np.float64) * sb[np.arange(N) // 128, gk][None, :])
+        want -= part * sc
+    got = to_np(C)
+    assert np.all(np.abs(got - want) <= 2.0**-7 * np.abs(want) + 1e-2 * np.abs(C0 - want).max() * 2.0**-8 + 0.5)
+
+
+# ---------------------------------------------------------------------------
+# factorization
+# ---------------------------------------------------------------------------
+CASES = [(1, 128), (2, 128), (100, 128), (128, 128), (129, 128), (300, 128), (300, 256), (640, 256),
+         (700, 512), (1000, 512), (1031, 128)]
+
+
+@pytest.mark.parametrize("n,nb", CASES)
+@pytest.mark.parametrize("prec", [capi.BF16, capi.FP16])
+def test_factor_simt_engine_bit_exact(n, nb, prec):
+    A_o, _ = oracle.generate(n, 40 + n)
+    A = api.ColMajor.from_tensor(torch.from_numpy(A_o), DEV)
+    with engine("simt"):
+        LU = api.factor(A, prec, nb)
+    torch.cuda.synchronize()
+    LU_o, rc = oracle.factor(A_o, ORC_FMT[prec], nb)
+    assert rc == 0
+    got = to_np(LU)
+    bad = np.argwhere(got != LU_o)
+    assert bad.size == 0, (bad[:5], got[tuple(bad[0])], LU_o[tuple(bad[0])])
+
+
+@pytest.mark.parametrize("n,nb", [(300, 128), (700, 256), (1000, 512), (1500, 512)])
+def test_factor_fp8_simt_engine_bit_exact(n, nb):
+    A_o, _ = oracle.generate(n, 3)
+    A = api.ColMajor.from_tensor(torch.from_numpy(A_o), DEV)
+    with engine("simt"):
+        LU = api.factor(A, capi.FP8_E4M3, nb)
+    torch.cuda.synchronize()
+    LU_o, _ = oracle.factor(A_o, oracle.BF16, nb, fmt_update=oracle.E4M3)
+    assert np.array_equal(to_np(LU), LU_o)
+
+
+@pytest.mark.parametrize("n,nb", CASES + [(2048, 128), (2048, 512)])
+@pytest.mark.parametrize("prec", [capi.BF16, capi.FP16, capi.FP8_E4M3])
+def test_factor_tensor_cores_within_tolerance(n, nb, prec):
+    A_o, _ = oracle.generate(n, 40 + n)
+    A = api.ColMajor.from_tensor(torch.from_numpy(A_o), DEV)
+    LU = api.factor(A, prec, nb)
+    torch.cuda.synchronize()
+    LU_o, _ = oracle.factor(A_o, ORC_FMT[prec], nb,
+                            fmt_update=oracle.E4M3 if prec == capi.FP8_E4M3 else None)
+    got = to_np(LU)
+    rel = np.linalg.norm(got - LU_o) / np.linalg.norm(LU_o)
+    assert rel <= 8 * n * U_LOW[prec]
+    assert rel <= U_LOW[prec]
+    L, U = oracle.split_lu(got)
+    assert np.linalg.norm(L @ U - A_o) / np.linalg.norm(A_o) <= 2 * U_LOW[prec]
+
+
+def test_factor_zero_pivot_is_breakdown():
+    n = 200
+    A_o, _ = oracle.generate(n, 2, mode=oracle.NONE)
+    A_o[0, 0] = 0.0
+    A = api.ColMajor.from_tensor(torch.from_numpy(A_o), DEV)
+    with pytest.raises(capi.HpmxpError) as e:
+        api.factor(A, capi.BF16, 128)
+    assert e.value.status == capi.EBREAKDOWN
+
+
+# ---------------------------------------------------------------------------
+# preconditioner and refinement
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,k,fp32", [(1, 1, 0), (64, 1, 0), (65, 2, 0), (1000, 3, 0), (1000, 1, 1), (4099, 8, 0)])
+def test_precond_against_oracle(n, k, fp32):
+    A_o, _ = oracle.generate(n, 9)
+    LU_o, _ = oracle.factor(A_o, oracle.BF16, 128)
+    LU = api.ColMajor.from_tensor(torch.from_numpy(LU_o), DEV, dtype=torch.bfloat16)
+    V = vectors(n, k, 17)
+    v = api.ColMajor.from_tensor(torch.from_numpy(V), DEV)
+    z = api.ColMajor.empty(n, k, torch.float64, DEV)
+    ws = api.workspace(capi.hpmxp_solve_workspace(n, k, 1), DEV)
+    st = capi.hpmxp_test_precond(n, LU.ptr, LU.ld, capi.BF16, v.ptr, v.ld, z.ptr, z.ld, k, fp32, ws.data_ptr(),
+                                 ws.numel(), api.stream_handle())
+    assert st == capi.OK
+    torch.cuda.synchronize()
+    got = to_np(z)
+    for c in range(k):
+        want = oracle.precond(LU_o, V[:, c], prec=fp32)
+        tol = 1e-5 if fp32 else 1e-13
+        assert np.abs(got[:, c] - want).max() <= tol * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n,nb,prec,k", [(1, 128, capi.BF16, 1), (2, 128, capi.BF16, 1), (64, 128, capi.BF16, 1),
+                                         (300, 128, capi.BF16, 3), (1024, 128, capi.BF16, 1),
+                                         (1024, 256, capi.FP16, 2), (1500, 512, capi.FP8_E4M3, 1),
+                                         (2049, 512, capi.BF16, 8)])
+def test_solve_against_oracle(n, nb, prec, k):
+    A, b = api.generate(n, seed=n, nrhs=k, device=DEV)
+    LU = api.factor(A, prec, nb)
+    x, info, st = api.solve_ir(A, LU, b, prec)
+    torch.cuda.synchronize()
+    sr = api.residual(A, x, b)
+    assert st == capi.OK, info
+    A_o, b_o = oracle.generate(n, n, nrhs=k)
+    LU_o, _ = oracle.factor(A_o, ORC_FMT[prec], nb, fmt_update=oracle.E4M3 if prec == capi.FP8_E4M3 else None)
+    X_o, info_o, rc = oracle.solve_ir(A_o, LU_o, b_o)
+    sr_o = oracle.scaled_residual(A_o, to_np(x), b_o)
+    xg = to_np(x)
+    for c in range(k):
+        assert sr[c] < 16.0 and info[c]["status"] == capi.OK
+        assert sr[c] == pytest.approx(sr_o[c], rel=1e-6, abs=1e-3)
+        assert np.abs(xg[:, c] - X_o[:, c]).max() <= 1e-10 * np.abs(X_o[:, c]).max()
+        assert abs(info[c]["iters"] - info_o[c]["iters"]) <= 1
+        assert info[c]["iters"] <= 50
+
+
+def test_solve_fp32_preconditioner():
+    n = 2000
+    A, b = api.generate(n, seed=5, device=DEV)
+    LU = api.factor(A, capi.BF16, 256)
+    x, info, st = api.solve_ir(A, LU, b, capi.BF16, api.ir_params(precond_fp32=1))
+    sr = api.residual(A, x, b)
+    assert st == capi.OK and sr[0] < 16.0
+
+
+def test_solve_nan_rhs_is_breakdown():
+    n = 256
+    A, b = api.generate(n, seed=5, device=DEV)
+    LU = api.factor(A, capi.BF16, 128)
+    b.view()[3, 0] = float("nan")
+    x, info, st = api.solve_ir(A, LU, b, capi.BF16)
+    assert st == capi.EBREAKDOWN and info[0]["status"] == capi.EBREAKDOWN
+
+
+def test_solve_unscaled_matrix_reports_failure():
+    # no diagonal scaling and no pivoting: the refinement cannot recover
+    n = 400
+    A, b = api.generate(n, seed=1, diag=capi.DIAG_NONE, device=DEV)
+    LU = api.factor(A, capi.BF16, 128)
+    x, info, st = api.solve_ir(A, LU, b, capi.BF16)
+    assert st == capi.ENOCONV and info[0]["iters"] == 50
+
+
+def test_residual_against_oracle():
+    n, k = 777, 2
+    A, b = api.generate(n, seed=3, nrhs=k, device=DEV)
+    X = vectors(n, k, 5)
+    x = api.ColMajor.from_tensor(torch.from_numpy(X), DEV)
+    got = api.residual(A, x, b)
+    A_o, b_o = oracle.generate(n, 3, nrhs=k)
+    want = oracle.scaled_residual(A_o, X, b_o)
+    assert np.allclose(got, want, rtol=1e-9)
+
+
+def test_full_size_solve_n32768():
+    n = 32768
+    A, b = api.generate(n, seed=1, device=DEV)
+    s = api.Solver(n, 1, capi.BF16, nb=512, device=DEV)
+    x, info, st = s(A, b)
+    torch.cuda.synchronize()
+    sr = api.residual(A, x, b)
+    assert st == capi.OK and sr[0] < 16.0, (info, sr)
+    # independent check of sampled residual rows from skip-ahead rows on the CPU
+    rows = [0, 12345, n - 1]
+    R = oracle.generate_rows(n, 1, rows)
+    xv = x.view()[:, 0].cpu().numpy()
+    bv = b.view()[:, 0].cpu().numpy()
+    an = np.abs(R).sum(axis=1).max() * 1.05
+    for k, i in enumerate(rows):
+        r = bv[i] - R[k] @ xv
+        assert abs(r) <= 16 * n * 2.0**-53 * (an * np.abs(xv).max() + np.abs(bv).max())
+    del A, b, s
+    torch.cuda.empty_cache()
