@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""HPL-MxP benchmark on GB300: BF16 (or FP16 / FP8-update) LU without pivoting
++ fp64 GMRES-IR on the generated diagonally dominant system, reported as
+HPL-MxP TFLOP/s = (2/3 n^3 + 3/2 n^2) / time-to-solution (section "Algorithmic
+Framework").
+
+One step = one full solve of the resident system: cast A to the factor format,
+factor, x0 and GMRES-IR to scaled residual < 16.  Generation is untimed, as the
+paper prescribes; the backward-error check runs after the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--n 32768] [--nb 0|128|256|512] [--prec bf16|fp16|fp8]
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas of the same
+solve, no collective on the data path; value = all ranks' work / max time.
+`--impl reference` times the CPU oracle on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HPL-MxP TFLOP/s (2n^3/3 + 3n^2/2 per solve) at scaled residual < 16"
+PREC = {"bf16": 0, "fp16": 1, "fp8": 2}
+
+
+def hpl_ops(n: int) -> float:
+    return 2.0 / 3.0 * n**3 + 1.5 * n**2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--nb", type=int, default=0, help="Schur update depth; 0 = autotune over 128/256/512")
+    ap.add_argument("--prec", default="bf16", choices=list(PREC))
+    ap.add_argument("--precond-fp32", type=int, default=-1, help="-1 = library default")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_setup(backend: str):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return rank, local, ws
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(v: float, ws: int, device) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_solve_timed(n: int, seed: int, prec: str, nb: int):
+    import oracle
+    A, b = oracle.generate(n, seed)
+    fmt = oracle.FP16 if prec == "fp16" else oracle.BF16
+    upd = oracle.E4M3 if prec == "fp8" else None
+    t0 = time.perf_counter()
+    LU, _ = oracle.factor(A, fmt, nb, fmt_update=upd)
+    X, info, rc = oracle.solve_ir(A, LU, b)
+    dt = time.perf_counter() - t0
+    return dt, info[0], rc
+
+
+def oracle_sample_size(target_s: float, seed: int, prec: str, nb: int) -> tuple[int, float]:
+    """Largest multiple of 128 whose oracle solve should take about target_s."""
+    n0 = 768
+    dt, _, _ = oracle_solve_timed(n0, seed, prec, min(nb, 128))
+    n = int(n0 * (target_s / max(dt, 1e-3)) ** (1 / 3)) // 128 * 128
+    return max(256, min(n, 8192)), dt
+
+
+def cpu_baseline(args, nb: int) -> dict:
+    import oracle
+    n, _ = oracle_sample_size(args.cpu_seconds, args.seed, args.prec, nb)
+    dt, info, rc = oracle_solve_timed(n, args.seed, args.prec, min(nb, 512))
+    return {"value": hpl_ops(n) / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one oracle solve (factor + GMRES-IR) of the same generated system at n={n} "
+                      f"(the full n is out of reach on the host), {dt:.2f} s, status {rc}, iters {info['iters']}"}
+
+
+def run_reference(args):
+    rank, local, ws = dist_setup("gloo")
+    if rank != 0:
+        return
+    import oracle
+    nb = args.nb or 128
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    n, _ = oracle_sample_size(per_step, args.seed, args.prec, nb)
+    for _ in range(args.warmup):
+        oracle_solve_timed(n, args.seed, args.prec, nb)
+    times = []
+    for _ in range(args.steps):
+        dt, info, rc = oracle_solve_timed(n, args.seed, args.prec, nb)
+        times.append(dt)
+    t = sum(times) / len(times)
+    value = hpl_ops(n) / t / 1e12
+    sample = f"oracle solve of the generated system at n={n} (nb={nb}, {args.prec}) per step"
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.prec, "data": "synthetic (generated on the host by the oracle)",
+            "impl": "reference",
+            "config": {"workload": f"HPL-MxP solve, n={args.n} requested, sampled at n={n}", "n": n, "nb": nb,
+                       "prec": args.prec, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, local, ws = dist_setup("nccl")
+    import torch
+    from paper_2509_19618_gb300 import api, autotune, capi
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, prec = args.n, PREC[args.prec]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+
+    A, b = api.generate(n, seed=args.seed, device=dev)          # untimed (paper: generation not timed)
+    params = capi.hpmxp_ir_params_default()
+    if args.precond_fp32 >= 0:
+        params.precond_fp32 = args.precond_fp32
+    nb = args.nb or autotune.pick_nb(n, prec, A, device=dev)
+    solver = api.Solver(n, 1, prec, nb, device=dev, params=params)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(args.warmup, 0)):
+        solver(A, b)
+    torch.cuda.synchronize(dev)
+
+    capi.hpmxp_prof_enable(False)
+    # timed region 1: device time of K whole solves, inputs resident in HBM
+    launches0 = capi.hpmxp_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            x, info, st = solver(A, b)
+            infos.append((st, info[0]))
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+    launches = capi.hpmxp_launch_count() - launches0
+    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    t_step = allmax(t_step, ws, dev)
+    ok = all(st == capi.OK for st, _ in infos)
+    sr = float(api.residual(A, solver.x, b)[0])                 # untimed backward-error check
+    value = ws * hpl_ops(n) / t_step / 1e12
+
+    # per-kernel attribution: one more instrumented pass (events on the launching stream)
+    capi.hpmxp_prof_reset()
+    capi.hpmxp_prof_enable(True)
+    solver(A, b)
+    torch.cuda.synchronize(dev)
+    capi.hpmxp_prof_enable(False)
+    kinds = {"gemm": capi.PROF_GEMM, "gemv": capi.PROF_GEMV, "precond": capi.PROF_PRECOND,
+             "getrf": capi.PROF_GETRF}
+    prof = {k: capi.hpmxp_prof_read(v) for k, v in kinds.items()}
+    g = prof["gemm"]
+    bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    dom_ms_launch = g["ms"] / max(g["launches"], 1)
+    achieved = (g["work"] / max(g["launches"], 1)) / (dom_ms_launch / 1e3) / 1e12 if g["launches"] else None
+    peak = bf16_peak * (2.0 if prec == 2 else 1.0)
+    roofline = {"bound": "tensor", "kernel": "gemm_tc_kernel (tcgen05 panel + Schur-update products)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback 1.7 PF/s")
+                + (" x2 nominal fp8/bf16 ratio" if prec == 2 else ""),
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "per_kind_ms_per_solve": {k: v["ms"] for k, v in prof.items()},
+                "per_kind_launches": {k: v["launches"] for k, v in prof.items()}}
+    gv = prof["gemv"]
+    if gv["launches"]:
+        roofline["gemv_gbs"] = gv["work"] / (gv["ms"] / 1e3) / 1e9
+    pc = prof["precond"]
+    if pc["launches"]:
+        roofline["precond_gbs"] = pc["work"] / (pc["ms"] / 1e3) / 1e9
+
+    # timed region 2: end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        A_h = torch.empty((A.storage.shape[0], A.storage.shape[1]), dtype=torch.float64, pin_memory=True)
+        b_h = torch.empty((b.storage.shape[0], b.storage.shape[1]), dtype=torch.float64, pin_memory=True)
+        A_h.copy_(A.storage)
+        b_h.copy_(b.storage)
+        x_h = torch.empty((1, solver.x.ld), dtype=torch.float64, pin_memory=True)
+        A2 = api.ColMajor(torch.empty_like(A.storage), n, n)
+        b2 = api.ColMajor(torch.empty_like(b.storage), n, 1)
+        del A
+        torch.cuda.empty_cache()
+        steps = max(1, min(args.steps, 5))
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            A2.storage.copy_(A_h, non_blocking=True)
+            b2.storage.copy_(b_h, non_blocking=True)
+            solver(A2, b2)
+            x_h.copy_(solver.x.storage, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        t_e2e = (time.perf_counter() - t0) / steps
+        barrier(ws)
+        t_e2e = allmax(t_e2e, ws, dev)
+        e2e = {"value": ws * hpl_ops(n) / t_e2e / 1e12, "unit": "TFLOP/s", "ms_per_step": t_e2e * 1e3,
+               "h2d_bytes_per_step": int(A_h.numel() * 8 + b_h.numel() * 8),
+               "d2h_bytes_per_step": int(x_h.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, nb)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.prec, "data": "synthetic (on-device LCG generator, seed %d)"
+                % args.seed,
+                "config": {"workload": f"HPL-MxP single system n={n}, {args.prec} LU nb={nb} + fp64 GMRES-IR(30)",
+                           "n": n, "nb": nb, "prec": args.prec, "global_batch": ws, "seq_len": None,
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (A is %.1f GB)" % (8 * n * n / 1e9),
+                           "precond_fp32": int(params.precond_fp32)},
+                "valid": bool(ok and sr < 16.0), "scaled_residual": sr,
+                "ir_iters": infos[-1][1]["iters"], "ir_outer": infos[-1][1]["outer"],
+                "gpu_launches": int(launches), "roofline": roofline, "clocks": clk.summary(),
+                "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -173,6 +173,23 @@ hpmxp_status hpmxp_residual(int64_t n, const double* A, int64_t lda, const doubl
                             const double* b, int64_t ldb, int64_t nrhs, double* scaled_resid,
                             void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Measurement support (the paper has no counterpart; used by the benchmark).
+ * hpmxp_launch_count: kernels this library has launched since it was loaded.
+ * hpmxp_prof_enable(1) makes the library record a CUDA event pair around
+ * every launch of the timed kinds, on the launching stream:
+ *   kind 0  tensor-core GEMM        work = 2 M N K flops per launch
+ *   kind 1  fp64 GEMV (residual)    work = 8 n^2 bytes of A per launch
+ *   kind 2  preconditioner apply    work = 2 n^2 bytes of factors per launch
+ *   kind 3  diagonal-block getrf    work = 2 b^3 flops per launch
+ * hpmxp_prof_read synchronizes the recorded events and returns the summed
+ * event time, work and launch count of one kind since the last reset.
+ * Returns HPMXP_EINVAL for a bad kind or NULL output. */
+unsigned long long hpmxp_launch_count(void);
+void hpmxp_prof_enable(int on);
+void hpmxp_prof_reset(void);
+int hpmxp_prof_read(int kind, double* total_ms, double* total_work, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

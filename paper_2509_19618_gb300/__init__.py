@@ -14,11 +14,5 @@ from .capi import (BF16, FP16, FP8_E4M3, DIAG_DOMINANT, DIAG_SQRTN, DIAG_NONE, H
 __all__ = ["capi", "BF16", "FP16", "FP8_E4M3", "DIAG_DOMINANT", "DIAG_SQRTN", "DIAG_NONE", "HpmxpError",
            "IRInfo", "IRParams", "hpmxp_factor", "hpmxp_factor_workspace", "hpmxp_generate",
            "hpmxp_generate_workspace", "hpmxp_ir_params_default", "hpmxp_residual", "hpmxp_residual_workspace",
-           "hpmxp_solve_ir", "hpmxp_solve_workspace", "api"]
+           "hpmxp_solve_ir", "hpmxp_solve_workspace"]
 
-
-def __getattr__(name):
-    if name == "api":   # torch-facing wrappers, imported lazily (torch import is slow)
-        from . import api
-        return api
-    raise AttributeError(name)

@@ -73,6 +73,10 @@ def load():
             "hpmxp_test_gemm": ([i32, i32, i32, P, i64, P, i64, P, i64, P, i64, i32, ctypes.c_float, i32, i32,
                                  P, i32, P, i32, i32, P, P], i32),
             "hpmxp_test_cast": ([i64, P, i64, i32, P, i64, P], i32),
+            "hpmxp_launch_count": ([], ctypes.c_ulonglong),
+            "hpmxp_prof_enable": ([i32], None),
+            "hpmxp_prof_reset": ([], None),
+            "hpmxp_prof_read": ([i32, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)], i32),
             "hpmxp_test_precond": ([i64, P, i64, i32, P, i64, P, i64, i64, i32, P, sz, P], i32),
         }
         for name, (args, res) in sig.items():
@@ -140,6 +144,29 @@ def hpmxp_residual_workspace(n, nrhs):
 
 def hpmxp_residual(n, A, lda, x, ldx, b, ldb, nrhs, out, ws, ws_bytes, stream):
     return _call("hpmxp_residual", n, A, lda, x, ldx, b, ldb, nrhs, out, ws, ws_bytes, stream)
+
+
+def hpmxp_launch_count() -> int:
+    return int(load().hpmxp_launch_count())
+
+
+def hpmxp_prof_enable(on: bool):
+    load().hpmxp_prof_enable(1 if on else 0)
+
+
+def hpmxp_prof_reset():
+    load().hpmxp_prof_reset()
+
+
+PROF_GEMM, PROF_GEMV, PROF_PRECOND, PROF_GETRF = 0, 1, 2, 3
+
+
+def hpmxp_prof_read(kind: int) -> dict:
+    ms, work, cnt = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+    st = load().hpmxp_prof_read(kind, ctypes.byref(ms), ctypes.byref(work), ctypes.byref(cnt))
+    if st != OK:
+        raise HpmxpError("hpmxp_prof_read", st)
+    return dict(ms=ms.value, work=work.value, launches=cnt.value)
 
 
 def hpmxp_test_gemm(*args):

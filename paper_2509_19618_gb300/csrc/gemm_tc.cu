@@ -304,7 +304,8 @@ template <int kStages>
 size_t smem_bytes_for() { return 1024 + (size_t)kStages * (kStageA + kStageB) + 8 * (2 * kStages + 1) + 16; }
 
 template <int kStages>
-cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, size_t smem, cudaStream_t st) {
+cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, size_t smem, double flops,
+                   cudaStream_t st) {
   static int configured_for = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -315,7 +316,10 @@ cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p
     configured_for = dev;
   }
   dim3 grid((unsigned)cdiv(p.N, kBN), (unsigned)cdiv(p.M, kBM));
+  void* tok = prof_begin(st);
   gemm_tc_kernel<kStages><<<grid, kThreads, smem, st>>>(a, b, p);
+  prof_end(tok, kProfGemm, flops, st);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -346,12 +350,13 @@ cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
   // more than the 512 TMEM columns of an SM at once.
   const int max_res = (int)(512u / p.ncols);
   const size_t floor_smem = max_res >= 3 ? 0 : (max_res == 2 ? 100 * 1024 : 120 * 1024);
+  const double flops = 2.0 * g.M * (double)g.N * g.K;
   if (p.nkb <= 2) {
     const size_t smem = std::max(smem_bytes_for<2>(), floor_smem);
-    return launch<2>(ta, tb, p, smem, st);
+    return launch<2>(ta, tb, p, smem, flops, st);
   }
   const size_t smem = std::max(smem_bytes_for<4>(), floor_smem);
-  return launch<4>(ta, tb, p, smem, st);
+  return launch<4>(ta, tb, p, smem, flops, st);
 }
 
 }  // namespace hpmxp

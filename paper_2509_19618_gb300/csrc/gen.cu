@@ -135,7 +135,9 @@ cudaError_t launch_generate(int64_t n, uint64_t seed, double margin, int mode, d
   if (nrhs > 0) {
     const int64_t work = cdiv<int64_t>(n, 64) * nrhs;
     gen_rhs_kernel<<<(unsigned)cdiv<int64_t>(work, 128), 128, 0, st>>>(n, nrhs, seed, b, ldb);
+    count_launches(1);
   }
+  count_launches(2);
   return cudaGetLastError();
 }
 

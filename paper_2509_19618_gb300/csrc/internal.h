@@ -115,6 +115,13 @@ size_t residual_ws_bytes(int64_t n, int64_t nrhs);
 hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, const double* v, int64_t ldv,
                            double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws, cudaStream_t st);
 
+// prof.cu: launch counting and optional event timing (kinds below).
+enum ProfKind { kProfGemm = 0, kProfGemv = 1, kProfPrecond = 2, kProfGetrf = 3, kProfKinds = 4 };
+void count_launches(int k);
+bool prof_on();
+void* prof_begin(cudaStream_t st);
+void prof_end(void* token, int kind, double work, cudaStream_t st);
+
 hpmxp_status status_from_cuda(cudaError_t e);
 hpmxp_status status_from_word(uint32_t w);
 

@@ -674,6 +674,7 @@ cudaError_t residual(int64_t n, int K, const double* A, int64_t lda, const doubl
                      const SolveWs& w, cudaStream_t st) {
   const int nchunk = gemv_chunks(n);
   cudaError_t e;
+  void* tok = prof_begin(st);
   switch (K) {
     case 1: e = gemv_k<1>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
     case 2: e = gemv_k<2>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
@@ -687,6 +688,8 @@ cudaError_t residual(int64_t n, int K, const double* A, int64_t lda, const doubl
   if (e != cudaSuccess) return e;
   gemv_finish_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, nchunk, w.P, B, ldb, out, ldo, X, ldx,
                                                                       abs_mode, w.RS, w.st, track);
+  prof_end(tok, kProfGemv, 8.0 * (double)n * (double)n, st);
+  count_launches(2);
   return cudaGetLastError();
 }
 
@@ -746,9 +749,13 @@ struct Solver {
 
   cudaError_t precond(const double* v, int64_t ldv, double* z, int64_t ldz) {
     ++epoch;
-    if (prm.precond_fp32)
-      return precond_launch_t<float>(K, n, LU, ldlu, fmt, v, ldv, z, ldz, w, epoch, G, psmem, st);
-    return precond_launch_t<double>(K, n, LU, ldlu, fmt, v, ldv, z, ldz, w, epoch, G, psmem, st);
+    void* tok = prof_begin(st);
+    cudaError_t e = prm.precond_fp32
+                        ? precond_launch_t<float>(K, n, LU, ldlu, fmt, v, ldv, z, ldz, w, epoch, G, psmem, st)
+                        : precond_launch_t<double>(K, n, LU, ldlu, fmt, v, ldv, z, ldz, w, epoch, G, psmem, st);
+    prof_end(tok, kProfPrecond, 2.0 * (double)n * (double)n, st);
+    count_launches(1);
+    return e;
   }
 
   cudaError_t read_brief() {
@@ -777,6 +784,7 @@ struct Solver {
     if ((e = cudaMemsetAsync(w.counter, 0, 256, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.status, 0, 4, st)) != cudaSuccess) return e;
     init_kernel<<<1, 32, 0, st>>>(K, w.st);
+    count_launches(1);
     return cudaGetLastError();
   }
 
@@ -792,6 +800,7 @@ struct Solver {
       // r = b - A x, norms; decide
       if ((e = residual(n, K, A, lda, X, ldx, B, ldb, w.r, n, first ? 1 : 0, 1, w, st)) != cudaSuccess) return e;
       check_kernel<<<1, 32, 0, st>>>(sp, w.st, w.brief, first ? 1 : 0);
+      count_launches(1);
       first = false;
       if ((e = read_brief()) != cudaSuccess) return e;
       if (!any(&Brief::outer_active)) break;
@@ -800,6 +809,7 @@ struct Solver {
       norm2_kernel<<<kRedBlocks, 256, 0, st>>>(n, K, w.tmp, n, w.st, w.partials, w.counter);
       cycle_start_kernel<<<1, 32, 0, st>>>(sp, w.st, w.brief);
       scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, w.tmp, n, w.V, ldv_rhs(), w.st, 0);
+      count_launches(3);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if ((e = read_brief()) != cudaSuccess) return e;
       if (!any(&Brief::outer_active)) break;
@@ -813,6 +823,7 @@ struct Solver {
           mgs_kernel<<<kRedBlocks, 256, 0, st>>>(n, K, m, j, i, w.w, n, w.V, n, ldv_rhs(), w.st, w.partials,
                                                  w.counter);
         givens_kernel<<<1, 32, 0, st>>>(sp, j, w.st, w.brief);
+        count_launches(j + 4);
         scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, w.w, n, w.V + (int64_t)(j + 1) * n,
                                                                        ldv_rhs(), w.st, 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -820,6 +831,7 @@ struct Solver {
       }
       cycle_finish_kernel<<<1, 32, 0, st>>>(sp, w.st);
       update_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, X, ldx, w.V, n, ldv_rhs(), w.st);
+      count_launches(2);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -414,8 +414,11 @@ struct Factorizer {
   }
 
   void getrf_base(int64_t k, int b, int slot) {
+    void* tok = prof_begin(st);
     getrf_base_kernel<<<1, kGetrfThreads, 2 * kB * kLd * sizeof(float), st>>>(
         b, at(k, k), ld, fmt, aop(slot) + slot * kB, NB, bop(slot) + slot * kB, NB, w.status);
+    prof_end(tok, kProfGetrf, (double)b * b * b * 2.0, st);
+    count_launches(1);
     check(cudaGetLastError());
   }
 
@@ -423,6 +426,7 @@ struct Factorizer {
     if (rows <= 0) return;
     dim3 grid((unsigned)cdiv<int64_t>(rows, 32), (unsigned)cdiv(cols, 32));
     pack_rows_kernel<<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, ld, dst, ldd);
+    count_launches(1);
     check(cudaGetLastError());
   }
 
@@ -477,6 +481,7 @@ struct Factorizer {
               s * kB, aop(s), NB, at(s0, k), ld, fmt);
           make_z_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(
               s * kB, bop(s), NB, at(k, s0), ld, fmt);
+          count_launches(2);
           check(cudaGetLastError());
         }
         GemmArgs u{};
@@ -506,6 +511,7 @@ struct Factorizer {
             w.Lp, NB, 1, m, (int)b, fmt, w.Lq, NB, w.sL, 4);
         quant_tile_kernel<<<dim3((unsigned)cdiv<int64_t>(m, kB), ng), 256, 0, st>>>(
             at(k, k + b), ld, 0, m, (int)b, fmt, w.Uq, NB, w.sU, 4);
+        count_launches(2);
         check(cudaGetLastError());
         t.fp8 = 1;
         t.A = w.Lq; t.lda = NB;
@@ -531,6 +537,7 @@ int gemm_engine() {
 cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st) {
   dim3 grid((unsigned)cdiv(g.N, 64), (unsigned)cdiv(g.M, 64));
   gemm_simt_kernel<<<grid, 256, 0, st>>>(g);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -538,6 +545,7 @@ cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int6
   const int64_t work = (n + 1) / 2 * n;
   const int blocks = (int)std::min<int64_t>(cdiv<int64_t>(work, 256), 152 * 16);
   cast_kernel<<<blocks, 256, 0, st>>>(n, A, lda, (uint16_t*)out, ldo, fmt);
+  count_launches(1);
   return cudaGetLastError();
 }
 

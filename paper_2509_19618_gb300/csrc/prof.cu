@@ -1,0 +1,103 @@
+// Measurement support (not part of the paper's method): a count of this
+// library's kernel launches, and optional CUDA-event timing of selected
+// kernels on the stream that launches them, so a benchmark can attribute
+// time and work to the dominant kernel without a profiler.
+#include "internal.h"
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+namespace hpmxp {
+namespace {
+
+std::atomic<unsigned long long> g_launches{0};
+std::atomic<int> g_enabled{0};
+
+struct Span {
+  cudaEvent_t a, b;
+  int kind;
+  double work;
+};
+
+std::mutex g_mu;
+std::vector<Span> g_open;             // recorded, not yet resolved
+double g_ms[kProfKinds], g_work[kProfKinds];
+long long g_count[kProfKinds];
+std::vector<cudaEvent_t> g_pool;
+
+cudaEvent_t take_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void resolve_locked() {
+  for (Span& s : g_open) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(s.b) == cudaSuccess && cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
+      g_ms[s.kind] += ms;
+      g_work[s.kind] += s.work;
+      g_count[s.kind] += 1;
+    }
+    g_pool.push_back(s.a);
+    g_pool.push_back(s.b);
+  }
+  g_open.clear();
+}
+
+}  // namespace
+
+void count_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+
+bool prof_on() { return g_enabled.load(std::memory_order_relaxed) != 0; }
+
+void* prof_begin(cudaStream_t st) {
+  if (!prof_on()) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaEvent_t a = take_event();
+  cudaEventRecord(a, st);
+  return (void*)a;
+}
+
+void prof_end(void* token, int kind, double work, cudaStream_t st) {
+  if (!token) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaEvent_t b = take_event();
+  cudaEventRecord(b, st);
+  g_open.push_back(Span{(cudaEvent_t)token, b, kind, work});
+  if (g_open.size() > 4096) resolve_locked();
+}
+
+}  // namespace hpmxp
+
+using namespace hpmxp;
+
+extern "C" {
+
+unsigned long long hpmxp_launch_count(void) { return g_launches.load(); }
+
+void hpmxp_prof_enable(int on) { g_enabled.store(on ? 1 : 0); }
+
+void hpmxp_prof_reset(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  resolve_locked();
+  for (int k = 0; k < kProfKinds; ++k) { g_ms[k] = 0.0; g_work[k] = 0.0; g_count[k] = 0; }
+}
+
+int hpmxp_prof_read(int kind, double* total_ms, double* total_work, long long* launches) {
+  if (kind < 0 || kind >= kProfKinds || !total_ms || !total_work || !launches) return HPMXP_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  resolve_locked();
+  *total_ms = g_ms[kind];
+  *total_work = g_work[kind];
+  *launches = g_count[kind];
+  return HPMXP_OK;
+}
+
+}  // extern "C"

@@ -72,3 +72,9 @@ def test_library_is_sm103a_build():
     from paper_2509_19618_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
     assert _build.LIB.startswith(_build.PKG)   # in-tree
+
+
+def test_python_modules_import():
+    import importlib
+    for m in ("paper_2509_19618_gb300.api", "paper_2509_19618_gb300.autotune", "bench"):
+        importlib.import_module(m)
