@@ -304,7 +304,10 @@ def test_solve_against_oracle(n, nb, prec, k):
     xg = to_np(x)
     for c in range(k):
         assert sr[c] < 16.0 and info[c]["status"] == capi.OK
-        assert sr[c] == pytest.approx(sr_o[c], rel=1e-6, abs=1e-3)
+        # both evaluate the residual of the same x in fp64 with different
+        # summation orders; each has error <= n eps (|A||x| + |b|), i.e. <= 1 in
+        # scaled units, so they can differ by at most 2
+        assert abs(sr[c] - sr_o[c]) <= 2.0
         assert np.abs(xg[:, c] - X_o[:, c]).max() <= 1e-10 * np.abs(X_o[:, c]).max()
         assert abs(info[c]["iters"] - info_o[c]["iters"]) <= 1
         assert info[c]["iters"] <= 50
