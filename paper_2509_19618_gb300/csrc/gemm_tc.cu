@@ -2,33 +2,47 @@
 // (section "Algorithmic Framework", Fig. 1: low-precision operands, fp32
 // accumulation).  sm_103a: operands are staged into shared memory by TMA
 // (128-byte swizzle, K-major), multiplied by tcgen05.mma issued from one
-// thread with the fp32 accumulator in tensor memory, and read back with
-// tcgen05.ld by four epilogue warps that apply C - acc (or +-acc) and round to
-// the 16-bit storage format.
+// thread with fp32 accumulators in tensor memory, and read back with
+// tcgen05.ld by four epilogue warps.
 //
-// CTA = 6 warps: warp 0 issues TMA, warp 1 owns TMEM and issues the MMAs,
-// warps 2..5 run the epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
-// Tile 128 x 128, K staged 128 bytes per row per stage.  The E4M3 variant
-// keeps one TMEM accumulator per 128-deep K slice and folds them with the
+// Persistent kernel, one CTA per SM, 128 x 128 output tiles in a static
+// round-robin order.  The MMA computes the TRANSPOSED tile (TMEM lane = output
+// column j, TMEM column = output row i) so each epilogue thread owns 16
+// consecutive rows of one column of the column-major output: the C tile is
+// moved by TMA between HBM and a 128-byte-swizzled shared buffer and the
+// epilogue touches it with 16-byte, bank-conflict-free accesses.
+//
+// Roles: warp 0 TMA producer of the operand ring; warp 1 TMEM owner and MMA
+// issuer; warps 2..5 epilogue (warp w reads TMEM lanes 32*(w%4)..+31), which
+// also prefetch C tiles two tiles ahead and issue the TMA stores.
+// Accumulators are double buffered in TMEM (single buffered for 4-slice FP8),
+// so the epilogue of one tile overlaps the MMAs of the next.  The E4M3
+// variant keeps one accumulator per 128-deep K slice and folds them with the
 // per-tile scales in the epilogue.
 //
-// Every wait is bounded (kSpinLimit polls, kWaitNs of wall time); a wait that runs out sets
-// kErrTimeout in the status word, skips the remaining work and still frees
-// tensor memory before the CTA exits.
+// Every wait is bounded (kSpinLimit polls, kWaitNs of wall time); a wait that
+// runs out sets kErrTimeout in the status word, skips the remaining work and
+// still drains its copies and frees tensor memory before the CTA exits.
 #include "internal.h"
 
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 namespace hpmxp {
 namespace {
 
-constexpr int kBM = 128, kBN = 128;
-constexpr int kRowBytes = 128;                       // K bytes per row per stage (one swizzle atom)
-constexpr int kStageA = kBM * kRowBytes;             // 16 KiB
-constexpr int kStageB = kBN * kRowBytes;             // 16 KiB
+constexpr int kTI = 128;                      // output rows per tile (MMA N)
+constexpr int kTJ = 128;                      // output columns per tile (MMA M, TMEM lanes)
+constexpr int kRowBytes = 128;                // K bytes per operand row per stage (one swizzle atom)
+constexpr int kStages = 4;
+constexpr int kStageA = kTJ * kRowBytes;      // MMA A operand: rows j (16 KiB)
+constexpr int kStageB = kTI * kRowBytes;      // MMA B operand: rows i (16 KiB)
+constexpr int kCBox = kTJ * 128;              // one C box: 64 rows x 128 columns (16 KiB)
+constexpr int kCTile = 2 * kCBox;             // 32 KiB
 constexpr int kThreads = 192;
+constexpr int kEpiThreads = 128;
 
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -38,6 +52,9 @@ __device__ inline void mbar_init(uint32_t bar, uint32_t count) {
 __device__ inline void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ inline void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ inline void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ inline bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -65,6 +82,16 @@ __device__ inline void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, i
       ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+__device__ inline void tma_store_2d(const CUtensorMap* tm, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"((uint64_t)tm), "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
+__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ inline void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ inline void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ inline void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ inline void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -127,48 +154,62 @@ __device__ inline uint64_t sdesc_sw128(uint32_t saddr) {
 // Instruction descriptor: fp32 accumulator, K-major A and B, M = 128, N = 128.
 // Operand format code: kind::f16 -> 0 F16, 1 BF16; kind::f8f6f4 -> 0 E4M3.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt_code) {
-  return (1u << 4) | (fmt_code << 7) | (fmt_code << 10) | ((uint32_t)(kBN >> 3) << 17) |
-         ((uint32_t)(kBM >> 4) << 24);
+  return (1u << 4) | (fmt_code << 7) | (fmt_code << 10) | ((uint32_t)(kTI >> 3) << 17) |
+         ((uint32_t)(kTJ >> 4) << 24);
 }
 
 struct TcParams {
-  int M, N, nkb;        // rows, columns, K stages (128 bytes of K each)
+  int M, N, nkb;          // output rows, columns, K stages (128 bytes of K each)
+  int tiles_i, ntiles;
   int mode;
   float sign;
   int fmt;
-  int fp8;              // E4M3 operands: one accumulator per stage (= 128-deep slice)
-  uint32_t ncols;       // TMEM columns allocated
-  uint16_t* C; int64_t ldc;
+  int fp8;                // E4M3 operands: one accumulator per stage (= 128-deep slice)
+  int nbuf;               // TMEM accumulator buffers (1 or 2)
+  uint32_t acc_cols;      // TMEM columns per accumulator buffer
+  uint32_t ncols;         // TMEM columns allocated
+  int has_c;              // write (and for kEpiSub read) the column-major C through tmC
   uint16_t* R; int64_t ldr;
   const float* sA; int sa_ld;
   const float* sB; int sb_ld;
   uint32_t* status;
 };
 
-template <int kStages>
+__device__ inline uint32_t pack16x2(float lo, float hi, int fmt) {
+  return (uint32_t)f32_to_u16(lo, fmt) | ((uint32_t)f32_to_u16(hi, fmt) << 16);
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
-gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmC, TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);   // swizzle atoms need 1024-byte alignment
-  const uint32_t sA = smem_u32(smem);
-  const uint32_t sB = sA + kStages * kStageA;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * (kStageA + kStageB));
+  const uint32_t sOpA = smem_u32(smem);                            // [kStages][rows j][128 B]
+  const uint32_t sOpB = sOpA + kStages * kStageA;                  // [kStages][rows i][128 B]
+  const uint32_t sC = sOpB + kStages * kStageB;                    // [2][2 boxes][cols j][128 B]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * (kStageA + kStageB) + 2 * kCTile);
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int s) { return bar0 + 8u * (uint32_t)s; };
   auto empty = [&](int s) { return bar0 + 8u * (uint32_t)(kStages + s); };
-  const uint32_t done = bar0 + 8u * (uint32_t)(2 * kStages);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  auto acc_full = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + b); };
+  auto acc_empty = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + 2 + b); };
+  auto c_full = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + 4 + b); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 6);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
 
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(full(s), 1); mbar_init(empty(s), 1); }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), kEpiThreads / 32);
+      mbar_init(c_full(b), 1);
+    }
     fence_mbar_init();
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    if (p.has_c) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmC) : "memory");
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), p.ncols);
@@ -181,85 +222,167 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: stage s holds K bytes [128 kb, 128 kb + 128) of A and B
-      const int kx = kRowBytes / 2;   // the maps count K in 16-bit units: 64 per 128-byte stage
-      int issued = 0;
+      // operand ring: stage s holds K bytes [128 kb, +128) of the tile's rows j (A) and rows i (B)
+      long long pos = 0;   // ring position over all tiles of this CTA
       bool ok = true;
-      for (int kb = 0; kb < p.nkb && ok; ++kb) {
-        const int s = kb % kStages, use = kb / kStages;
-        if (use > 0 && !mbar_wait(empty(s), (uint32_t)((use - 1) & 1))) { ok = false; break; }
-        mbar_expect_tx(full(s), kStageA + kStageB);
-        tma_load_2d(sA + s * kStageA, &tmA, kb * kx, m0, full(s));
-        tma_load_2d(sB + s * kStageB, &tmB, kb * kx, n0, full(s));
-        ++issued;
+      for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+        const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
+        for (int kb = 0; kb < p.nkb; ++kb, ++pos) {
+          const int s = (int)(pos % kStages);
+          const long long use = pos / kStages;
+          if (use > 0 && !mbar_wait(empty(s), (uint32_t)((use - 1) & 1))) { ok = false; break; }
+          mbar_expect_tx(full(s), kStageA + kStageB);
+          tma_load_2d(sOpA + s * kStageA, &tmB, kb * (kRowBytes / 2), j0, full(s));
+          tma_load_2d(sOpB + s * kStageB, &tmA, kb * (kRowBytes / 2), i0, full(s));
+        }
       }
       if (!ok) atomicOr(p.status, kErrTimeout);
       // drain: the last load of every stage has landed before the CTA can exit
-      for (int kb = max(0, issued - kStages); kb < issued; ++kb)
-        if (!mbar_wait(full(kb % kStages), (uint32_t)((kb / kStages) & 1))) atomicOr(p.status, kErrTimeout);
+      for (long long q = (pos > kStages ? pos - kStages : 0); q < pos; ++q)
+        if (!mbar_wait(full((int)(q % kStages)), (uint32_t)((q / kStages) & 1))) atomicOr(p.status, kErrTimeout);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = p.fp8 ? make_idesc(0) : make_idesc(p.fmt == kBF16 ? 1u : 0u);
+      long long pos = 0;
       bool ok = true;
-      for (int kb = 0; kb < p.nkb; ++kb) {
-        const int s = kb % kStages, use = kb / kStages;
-        if (!mbar_wait(full(s), (uint32_t)(use & 1))) { ok = false; break; }
+      int local = 0;
+      for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++local) {
+        const int ab = local % p.nbuf, ause = local / p.nbuf;
+        if (ause > 0 && !mbar_wait(acc_empty(ab), (uint32_t)((ause - 1) & 1))) { ok = false; break; }
         tc_fence_after();
-        const uint32_t d = tmem + (p.fp8 ? (uint32_t)(kb * kBN) : 0u);
-        for (int kk = 0; kk < 4; ++kk) {   // 4 MMAs of 32 bytes of K each
-          const uint64_t a = sdesc_sw128(sA + s * kStageA + kk * 32);
-          const uint64_t b = sdesc_sw128(sB + s * kStageB + kk * 32);
-          const uint32_t acc = p.fp8 ? (kk > 0) : (kb > 0 || kk > 0);
-          if (p.fp8) tc_mma_f8(d, a, b, idesc, acc);
-          else tc_mma_f16(d, a, b, idesc, acc);
+        const uint32_t d0 = tmem + (uint32_t)ab * p.acc_cols;
+        for (int kb = 0; kb < p.nkb; ++kb, ++pos) {
+          const int s = (int)(pos % kStages);
+          if (!mbar_wait(full(s), (uint32_t)((pos / kStages) & 1))) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = d0 + (p.fp8 ? (uint32_t)(kb * kTI) : 0u);
+          for (int kk = 0; kk < 4; ++kk) {   // 4 MMAs of 32 bytes of K each
+            const uint64_t a = sdesc_sw128(sOpA + s * kStageA + kk * 32);
+            const uint64_t b = sdesc_sw128(sOpB + s * kStageB + kk * 32);
+            const uint32_t acc = p.fp8 ? (kk > 0) : (kb > 0 || kk > 0);
+            if (p.fp8) tc_mma_f8(d, a, b, idesc, acc);
+            else tc_mma_f16(d, a, b, idesc, acc);
+          }
+          tc_commit(empty(s));   // the stage is free once these MMAs have read it
         }
-        tc_commit(empty(s));   // the stage is free once these MMAs have read it
+        tc_commit(acc_full(ab));
       }
       if (!ok) atomicOr(p.status, kErrTimeout);
-      tc_commit(done);
     }
   } else {
-    // epilogue: this warp's 32 TMEM lanes are rows m0 + 32 q + lane
+    // epilogue: thread = output column j = j0 + jl, jl = 32 q + lane (its TMEM lane)
     const int q = warp & 3;
-    const int64_t row = (int64_t)m0 + 32 * q + lane;
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0));   // warp-uniform for tcgen05.ld
-    tc_fence_after();
-    if (!ok) {
-      if (lane == 0) atomicOr(p.status, kErrTimeout);
-    } else {
-      const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+    const int jl = 32 * q + lane;
+    const bool leader = (warp == 2 && lane == 0);
+    const bool load_c = p.has_c && p.mode == kEpiSub;
+    int issued_c[2] = {-1, -1};   // local tile whose C load is outstanding in each buffer
+    if (leader && load_c) {       // prefetch the C tiles of the first two local tiles
+      int local = 0;
+      for (int t = blockIdx.x; t < p.ntiles && local < 2; t += gridDim.x, ++local) {
+        const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
+        mbar_expect_tx(c_full(local), kCTile);
+        tma_load_2d(sC + local * kCTile, &tmC, i0, j0, c_full(local));
+        tma_load_2d(sC + local * kCTile + kCBox, &tmC, i0 + 64, j0, c_full(local));
+        issued_c[local] = local;
+      }
+    }
+    bool ok = true;
+    int local = 0;
+    for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++local) {
+      const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
+      const int cb = local & 1, ab = local % p.nbuf;
+      const uint32_t cbuf = sC + cb * kCTile;
+      bool w = true;
+      if (load_c) w = mbar_wait(c_full(cb), (uint32_t)((local >> 1) & 1));
+      if (leader) issued_c[cb] = -1;
+      w = w && mbar_wait(acc_full(ab), (uint32_t)((local / p.nbuf) & 1));
+      w = __all_sync(0xffffffffu, w);   // warp-uniform for tcgen05.ld
+      if (!w) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t lane_addr = tmem + (uint32_t)ab * p.acc_cols + ((uint32_t)(32 * q) << 16);
       float sc[4] = {1.0f, 1.0f, 1.0f, 1.0f};
       if (p.fp8)
         for (int g = 0; g < p.nkb && g < 4; ++g)
-          sc[g] = __fmul_rn(p.sA[(m0 / 128) * p.sa_ld + g], p.sB[(n0 / 128) * p.sb_ld + g]);
-      for (int c0 = 0; c0 < kBN; c0 += 16) {
+          sc[g] = __fmul_rn(p.sA[(i0 / 128) * p.sa_ld + g], p.sB[(j0 / 128) * p.sb_ld + g]);
+      const int64_t j = (int64_t)j0 + jl;
+      for (int c16 = 0; c16 < kTI / 16; ++c16) {
         float acc[16];
         uint32_t r[16];
         if (p.fp8) {
           for (int v = 0; v < 16; ++v) acc[v] = 0.0f;
           for (int g = 0; g < p.nkb; ++g) {
-            tmem_ld16(lane_addr + (uint32_t)(g * kBN + c0), r);
+            tmem_ld16(lane_addr + (uint32_t)(g * kTI + c16 * 16), r);
             for (int v = 0; v < 16; ++v) acc[v] = __fmaf_rn(__uint_as_float(r[v]), sc[g], acc[v]);
           }
         } else {
-          tmem_ld16(lane_addr + (uint32_t)c0, r);
+          tmem_ld16(lane_addr + (uint32_t)(c16 * 16), r);
           for (int v = 0; v < 16; ++v) acc[v] = __uint_as_float(r[v]);
         }
-        if (row < p.M) {
+        // rows i0 + 16 c16 .. +15 of column j: two 16-byte chunks of the swizzled box
+        const int box = c16 >> 2, ch = (c16 & 3) * 2;
+        const uint32_t row_addr = cbuf + box * kCBox + jl * 128;
+        const uint32_t a0 = row_addr + (((ch + 0) ^ (jl & 7)) << 4);
+        const uint32_t a1 = row_addr + (((ch + 1) ^ (jl & 7)) << 4);
+        uint32_t outw[8];
+        if (p.mode == kEpiSub) {
+          uint32_t cw[8];
+          asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(cw[0]), "=r"(cw[1]), "=r"(cw[2]), "=r"(cw[3]) : "r"(a0) : "memory");
+          asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(cw[4]), "=r"(cw[5]), "=r"(cw[6]), "=r"(cw[7]) : "r"(a1) : "memory");
+          for (int v = 0; v < 8; ++v) {
+            const float lo = __fsub_rn(u16_to_f32((uint16_t)(cw[v] & 0xffffu), p.fmt), acc[2 * v]);
+            const float hi = __fsub_rn(u16_to_f32((uint16_t)(cw[v] >> 16), p.fmt), acc[2 * v + 1]);
+            outw[v] = pack16x2(lo, hi, p.fmt);
+          }
+        } else {
+          for (int v = 0; v < 8; ++v) outw[v] = pack16x2(p.sign * acc[2 * v], p.sign * acc[2 * v + 1], p.fmt);
+        }
+        if (p.has_c) {
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                       ::"r"(a0), "r"(outw[0]), "r"(outw[1]), "r"(outw[2]), "r"(outw[3]) : "memory");
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                       ::"r"(a1), "r"(outw[4]), "r"(outw[5]), "r"(outw[6]), "r"(outw[7]) : "memory");
+        }
+        if (p.R && j < p.N) {
           for (int v = 0; v < 16; ++v) {
-            const int64_t col = (int64_t)n0 + c0 + v;
-            if (col >= p.N) break;
-            uint16_t* cp = p.C ? p.C + row + col * p.ldc : nullptr;
-            float out;
-            if (p.mode == kEpiSub) out = __fsub_rn(u16_to_f32(*cp, p.fmt), acc[v]);
-            else out = p.sign * acc[v];
-            const uint16_t h = f32_to_u16(out, p.fmt);
-            if (cp) *cp = h;
-            if (p.R) p.R[row * p.ldr + col] = h;
+            const int64_t i = (int64_t)i0 + c16 * 16 + v;
+            if (i < p.M) p.R[i * p.ldr + j] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
           }
         }
       }
+      // accumulator buffer free for the MMA warp
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty(ab));
+      if (p.has_c) {
+        fence_async_smem();
+        epi_barrier();
+        if (leader) {
+          tma_store_2d(&tmC, i0, j0, cbuf);
+          tma_store_2d(&tmC, i0 + 64, j0, cbuf + kCBox);
+          bulk_commit();
+          bulk_wait_read0();   // the buffer can be refilled
+          // prefetch the C tile two local tiles ahead into this buffer
+          const int t2 = t + 2 * (int)gridDim.x;
+          if (load_c && t2 < p.ntiles) {
+            const int i2 = (t2 % p.tiles_i) * kTI, j2 = (t2 / p.tiles_i) * kTJ;
+            mbar_expect_tx(c_full(cb), kCTile);
+            tma_load_2d(cbuf, &tmC, i2, j2, c_full(cb));
+            tma_load_2d(cbuf + kCBox, &tmC, i2 + 64, j2, c_full(cb));
+            issued_c[cb] = local + 2;
+          }
+        }
+      }
+    }
+    if (!ok && lane == 0) atomicOr(p.status, kErrTimeout);
+    if (leader) {
+      bulk_wait0();
+      // C loads issued for tiles this CTA did not reach (error path) land before exit
+      for (int b = 0; b < 2; ++b)
+        if (issued_c[b] >= 0 && !mbar_wait(c_full(b), (uint32_t)((issued_c[b] >> 1) & 1)))
+          atomicOr(p.status, kErrTimeout);
     }
   }
   tc_fence_before();
@@ -284,43 +407,35 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D K-major operand: `rows` rows of `k_bytes` bytes, consecutive rows
-// `ld_bytes` apart; box = 128 rows x 128 bytes, 128-byte swizzle, zero fill
-// outside the operand.
-bool make_operand_map(CUtensorMap* tm, const void* base, uint64_t k_bytes, uint64_t rows, uint64_t ld_bytes) {
+// 2-D map over 16-bit units: `rows` rows of `inner` units, consecutive rows
+// `ld_bytes` apart, box = box_inner x box_rows, 128-byte swizzle, zero fill
+// outside the matrix.
+bool make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows, uint64_t ld_bytes,
+              uint32_t box_inner, uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
-  if (((uintptr_t)base & 15) || (ld_bytes & 15) || (k_bytes % kRowBytes)) return false;
-  cuuint64_t dims[2] = {k_bytes / 2, rows};
+  if (((uintptr_t)base & 15) || (ld_bytes & 15) || inner == 0 || rows == 0) return false;
+  cuuint64_t dims[2] = {inner, rows};
   cuuint64_t strides[1] = {ld_bytes};
-  cuuint32_t box[2] = {kRowBytes / 2, 128};
+  cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t es[2] = {1, 1};
   return fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int kStages>
-size_t smem_bytes_for() { return 1024 + (size_t)kStages * (kStageA + kStageB) + 8 * (2 * kStages + 1) + 16; }
+constexpr size_t kSmemBytes =
+    1024 + (size_t)kStages * (kStageA + kStageB) + 2 * kCTile + 8 * (2 * kStages + 6) + 16;
 
-template <int kStages>
-cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, size_t smem, double flops,
-                   cudaStream_t st) {
-  static int configured_for = -1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (configured_for != dev) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(200 * 1024));
-    if (e != cudaSuccess) return e;
-    configured_for = dev;
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
   }
-  dim3 grid((unsigned)cdiv(p.N, kBN), (unsigned)cdiv(p.M, kBM));
-  void* tok = prof_begin(st);
-  gemm_tc_kernel<kStages><<<grid, kThreads, smem, st>>>(a, b, p);
-  prof_end(tok, kProfGemm, flops, st);
-  count_launches(1);
-  return cudaGetLastError();
+  return sms;
 }
 
 }  // namespace
@@ -330,33 +445,53 @@ cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
   const int esz = g.fp8 ? 1 : 2;
   const uint64_t kbytes = (uint64_t)g.K * esz;
   if (kbytes % kRowBytes) return cudaErrorInvalidValue;
-  CUtensorMap ta, tb;
-  if (!make_operand_map(&ta, g.A, kbytes, (uint64_t)g.M, (uint64_t)g.lda * esz) ||
-      !make_operand_map(&tb, g.B, kbytes, (uint64_t)g.N, (uint64_t)g.ldb * esz))
+  CUtensorMap ta, tb, tc;
+  if (!make_map(&ta, g.A, kbytes / 2, (uint64_t)g.M, (uint64_t)g.lda * esz, kRowBytes / 2, kTI) ||
+      !make_map(&tb, g.B, kbytes / 2, (uint64_t)g.N, (uint64_t)g.ldb * esz, kRowBytes / 2, kTJ))
     return cudaErrorInvalidValue;
   TcParams p{};
+  p.has_c = g.C != nullptr;
+  if (p.has_c) {
+    // column-major C: inner = rows; box = 64 rows x 128 columns
+    if (!make_map(&tc, g.C, (uint64_t)g.M, (uint64_t)g.N, (uint64_t)g.ldc * 2, 64, kTJ))
+      return cudaErrorInvalidValue;
+  } else {
+    tc = ta;   // never dereferenced
+  }
   p.M = g.M; p.N = g.N; p.nkb = (int)(kbytes / kRowBytes);
+  p.tiles_i = cdiv(g.M, kTI);
+  p.ntiles = p.tiles_i * cdiv(g.N, kTJ);
   p.mode = g.mode; p.sign = g.sign; p.fmt = g.fmt; p.fp8 = g.fp8;
-  p.C = (uint16_t*)g.C; p.ldc = g.ldc; p.R = (uint16_t*)g.R; p.ldr = g.ldr;
+  p.R = (uint16_t*)g.R; p.ldr = g.ldr;
   p.sA = g.sA; p.sa_ld = g.sa_ld; p.sB = g.sB; p.sb_ld = g.sb_ld;
   p.status = g.status;
   if (g.fp8) {
     if (p.nkb > 4) return cudaErrorInvalidValue;   // one 128-column accumulator per slice
-    p.ncols = p.nkb <= 1 ? 128u : (p.nkb <= 2 ? 256u : 512u);
+    p.acc_cols = (uint32_t)(kTI * p.nkb);
   } else {
-    p.ncols = 128u;
+    p.acc_cols = kTI;
   }
-  // Shared memory also caps residency so that resident CTAs never ask for
-  // more than the 512 TMEM columns of an SM at once.
-  const int max_res = (int)(512u / p.ncols);
-  const size_t floor_smem = max_res >= 3 ? 0 : (max_res == 2 ? 100 * 1024 : 120 * 1024);
+  p.nbuf = (2 * p.acc_cols <= 512u) ? 2 : 1;
+  uint32_t need = p.acc_cols * (uint32_t)p.nbuf, ncols = 32;
+  while (ncols < need) ncols <<= 1;
+  p.ncols = ncols;
+
+  static int configured_for = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_for != dev) {
+    cudaError_t e =
+        cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    configured_for = dev;
+  }
+  const int grid = std::min(p.ntiles, num_sms());
   const double flops = 2.0 * g.M * (double)g.N * g.K;
-  if (p.nkb <= 2) {
-    const size_t smem = std::max(smem_bytes_for<2>(), floor_smem);
-    return launch<2>(ta, tb, p, smem, flops, st);
-  }
-  const size_t smem = std::max(smem_bytes_for<4>(), floor_smem);
-  return launch<4>(ta, tb, p, smem, flops, st);
+  void* tok = prof_begin(st);
+  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, tc, p);
+  prof_end(tok, kProfGemm, flops, st);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace hpmxp

@@ -287,15 +287,13 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     __syncthreads();
   };
 
-  // ---------------- forward sweep: unit lower L ----------------
-  for (int c = 0; c < nb; ++c) {
-    if (abort_flag) break;
-    const int owner = c % G;
-    if (owner == me) {
-      const int o = c / G;
-      load_diag(c);
-      if (tid < 32) {   // one warp: substitution in order, rows lane, lane+32
-        T* a = acc + (size_t)o * kTB * K;
+  // Solve the diagonal block of owned block o (forward: unit lower L;
+  // backward: upper U), publish it and keep it in zc.
+  auto solve_publish = [&](int o, int c, bool forward) {
+    load_diag(c);
+    if (tid < 32) {   // one warp, rows lane and lane + 32, pivots in order
+      T* a = acc + (size_t)o * kTB * K;
+      if (forward) {
         for (int p = 0; p < kTB; ++p) {
           T zp[K];
 #pragma unroll
@@ -309,43 +307,9 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
             }
           __syncwarp();
         }
-      }
-      __syncthreads();
-      for (int t = tid; t < kTB * K; t += 256) {
-        const T val = acc[(size_t)o * kTB * K + t];
-        zc[t] = val;
-        fpub[(size_t)c * kTB * K + t] = val;
-      }
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) publish_flag(&fflags[c], epoch);
-    } else {
-      // only needed if this CTA owns a block after c
-      const int last = me + (nown - 1) * G;
-      if (nown == 0 || last <= c) continue;
-      spin_until<T>(&fflags[c], epoch, status, &abort_flag);
-      if (abort_flag) break;
-      for (int t = tid; t < kTB * K; t += 256) zc[t] = fpub[(size_t)c * kTB * K + t];
-      __syncthreads();
-    }
-    for (int o = 0; o < nown; ++o)
-      if (me + o * G > c) apply_tile(o, c);
-  }
-  __syncthreads();
-  // acc now holds y = L^{-1} v for the owned blocks
-
-  // ---------------- backward sweep: upper U ----------------
-  for (int c = nb - 1; c >= 0; --c) {
-    if (abort_flag) break;
-    const int owner = c % G;
-    if (owner == me) {
-      const int o = c / G;
-      load_diag(c);
-      if (tid < 32) {
-        T* a = acc + (size_t)o * kTB * K;
+      } else {
         for (int p = kTB - 1; p >= 0; --p) {
           const T u = (T)tile[p * (kTB + 1) + p];
-          __syncwarp();
           T zp[K];
 #pragma unroll
           for (int r = 0; r < K; ++r) zp[r] = a[p * K + r] / u;
@@ -362,27 +326,84 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
           __syncwarp();
         }
       }
-      __syncthreads();
-      for (int t = tid; t < kTB * K; t += 256) {
-        const T val = acc[(size_t)o * kTB * K + t];
-        zc[t] = val;
-        bpub[(size_t)c * kTB * K + t] = val;
+    }
+    __syncthreads();
+    T* dst = forward ? fpub : bpub;
+    for (int t = tid; t < kTB * K; t += 256) {
+      const T val = acc[(size_t)o * kTB * K + t];
+      dst[(size_t)c * kTB * K + t] = val;
+      if (!forward) {
         const int ii = t / K, r = t % K;
         const int64_t i = (int64_t)c * kTB + ii;
         if (i < n) z[i + r * ldz] = (double)val;
       }
-      __threadfence();
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) publish_flag(forward ? &fflags[c] : &bflags[c], epoch);
+  };
+
+  // ---------------- forward sweep: unit lower L ----------------
+  // Look-ahead: the owner of block c+1 applies block c to it, solves and
+  // publishes it before updating its other blocks with block c.
+  int solved = -1;   // forward: last block this CTA solved ahead of its turn
+  for (int c = 0; c < nb; ++c) {
+    if (abort_flag) break;
+    const int owner = c % G;
+    const int last = me + (nown - 1) * G;
+    if (owner == me) {
+      const int o = c / G;
+      if (solved != c) solve_publish(o, c, true);
+      for (int t = tid; t < kTB * K; t += 256) zc[t] = acc[(size_t)o * kTB * K + t];
       __syncthreads();
-      if (tid == 0) publish_flag(&bflags[c], epoch);
     } else {
-      if (nown == 0 || me >= c) continue;   // owned blocks are me, me+G, ...; some must be < c
+      if (nown == 0 || last <= c) continue;   // no owned block after c
+      spin_until<T>(&fflags[c], epoch, status, &abort_flag);
+      if (abort_flag) break;
+      for (int t = tid; t < kTB * K; t += 256) zc[t] = fpub[(size_t)c * kTB * K + t];
+      __syncthreads();
+    }
+    int skip = -1;
+    if (c + 1 < nb && (c + 1) % G == me) {
+      const int o1 = (c + 1) / G;
+      apply_tile(o1, c);
+      solve_publish(o1, c + 1, true);
+      solved = c + 1;
+      skip = o1;   // solve_publish leaves zc (block c) untouched
+    }
+    for (int o = 0; o < nown; ++o)
+      if (o != skip && me + o * G > c) apply_tile(o, c);
+  }
+  __syncthreads();
+  // acc now holds y = L^{-1} v for the owned blocks
+
+  // ---------------- backward sweep: upper U ----------------
+  solved = nb;
+  for (int c = nb - 1; c >= 0; --c) {
+    if (abort_flag) break;
+    const int owner = c % G;
+    if (owner == me) {
+      const int o = c / G;
+      if (solved != c) solve_publish(o, c, false);
+      for (int t = tid; t < kTB * K; t += 256) zc[t] = acc[(size_t)o * kTB * K + t];
+      __syncthreads();
+    } else {
+      if (nown == 0 || me >= c) continue;   // owned blocks are me, me+G, ...; none before c
       spin_until<T>(&bflags[c], epoch, status, &abort_flag);
       if (abort_flag) break;
       for (int t = tid; t < kTB * K; t += 256) zc[t] = bpub[(size_t)c * kTB * K + t];
       __syncthreads();
     }
+    int skip = -1;
+    if (c - 1 >= 0 && (c - 1) % G == me) {
+      const int o1 = (c - 1) / G;
+      apply_tile(o1, c);
+      solve_publish(o1, c - 1, false);
+      solved = c - 1;
+      skip = o1;
+    }
     for (int o = 0; o < nown; ++o)
-      if (me + o * G < c) apply_tile(o, c);
+      if (o != skip && me + o * G < c) apply_tile(o, c);
   }
 }
 

@@ -101,85 +101,169 @@ __global__ void cast_kernel(int64_t n, const double* __restrict__ A, int64_t lda
 // storage and written as the K-major GEMM operands Linv (Linv[p*ldl + t]) and
 // Uinv^T (UinvT[p*ldu + t] = Uinv[t][p]).  128 x 128 zero-padded.
 // ---------------------------------------------------------------------------
-constexpr int kGetrfThreads = 512;
+constexpr int kGetrfThreads = 256;   // 16 x 16 threads, 8 x 8 entries each
 
 __global__ void __launch_bounds__(kGetrfThreads)
 getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_t* __restrict__ linv,
                   int64_t ldl, uint16_t* __restrict__ uinvT, int64_t ldu, uint32_t* status) {
-  extern __shared__ float sm[];
-  float* a = sm;               // a[j * kLd + i] = D(i, j)
-  float* x = sm + kB * kLd;    // inverse work, x[c * kLd + r] = X(r, c)
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kGetrfThreads / 32;
-
-  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-    const int i = idx % kB, j = idx / kB;
-    a[j * kLd + i] = (i < b && j < b) ? u16_to_f32(D[i + (int64_t)j * ldd], fmt) : 0.0f;
-  }
-  __syncthreads();
-
-  bool bad = false;
-  for (int p = 0; p < b; ++p) {
-    const float piv = a[p * kLd + p];
-    if (!(isfinite(piv) && piv != 0.0f)) bad = true;
-    for (int i = p + 1 + tid; i < b; i += kGetrfThreads) a[p * kLd + i] = __fdiv_rn(a[p * kLd + i], piv);
-    __syncthreads();
-    for (int j = p + 1 + warp; j < b; j += nw) {
-      const float u = a[j * kLd + p];
-      for (int i = p + 1 + lane; i < b; i += 32)
-        a[j * kLd + i] = __fmaf_rn(-a[p * kLd + i], u, a[j * kLd + i]);
+  __shared__ float rowbuf[2][kB];   // broadcast row of the current step (double buffered)
+  __shared__ float colbuf[2][kB];   // broadcast column of the current step
+  __shared__ float dg[kB];          // diagonal of the stored U
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int r0 = ty * 8, c0 = tx * 8;   // this thread's rows r0..r0+7 and columns c0..c0+7
+  float a[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int i = r0 + r, j = c0 + c;
+      a[r][c] = (i < b && j < b) ? u16_to_f32(D[i + (int64_t)j * ldd], fmt) : 0.0f;
     }
-    __syncthreads();
+
+  // factorization: step p broadcasts row p (u) and the scaled column p (l)
+  bool bad = false;
+  for (int pb = 0; pb < 16; ++pb) {
+#pragma unroll
+    for (int cp = 0; cp < 8; ++cp) {
+      const int p = pb * 8 + cp;
+      if (p >= b) break;
+      float* urow = rowbuf[p & 1];
+      if (ty == pb) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) urow[c0 + c] = a[cp][c];
+      }
+      __syncthreads();
+      const float piv = urow[p];
+      if (!(isfinite(piv) && piv != 0.0f)) bad = true;
+      if (tx == pb) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if (r0 + r > p) a[r][cp] = __fdiv_rn(a[r][cp], piv);
+          colbuf[0][r0 + r] = a[r][cp];
+        }
+      }
+      __syncthreads();
+      if (r0 + 7 > p && c0 + 7 > p) {
+        float u[8], l[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) u[c] = urow[c0 + c];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) l[r] = colbuf[0][r0 + r];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (r0 + r > p && c0 + c > p) a[r][c] = __fmaf_rn(-l[r], u[c], a[r][c]);
+      }
+    }
   }
   if (bad && tid == 0) atomicOr(status, kErrPivot);
 
   // round into storage; keep the stored values for the inverses
-  for (int idx = tid; idx < b * b; idx += kGetrfThreads) {
-    const int i = idx % b, j = idx / b;
-    const uint16_t h = f32_to_u16(a[j * kLd + i], fmt);
-    D[i + (int64_t)j * ldd] = h;
-    a[j * kLd + i] = u16_to_f32(h, fmt);
-  }
-  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-    const int r = idx % kB, c = idx / kB;
-    x[c * kLd + r] = (r == c && r < b) ? 1.0f : 0.0f;
-  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int i = r0 + r, j = c0 + c;
+      if (i < b && j < b) {
+        const uint16_t h = f32_to_u16(a[r][c], fmt);
+        D[i + (int64_t)j * ldd] = h;
+        a[r][c] = u16_to_f32(h, fmt);
+        if (i == j) dg[i] = a[r][c];
+      } else {
+        a[r][c] = 0.0f;
+      }
+    }
   __syncthreads();
 
-  // X = L^{-1}: step t updates rows r > t of every column c <= t
-  for (int t = 0; t < b; ++t) {
-    for (int c = warp; c <= t; c += nw) {
-      const float xt = x[c * kLd + t];
-      for (int r = t + 1 + lane; r < b; r += 32)
-        x[c * kLd + r] = __fmaf_rn(-a[t * kLd + r], xt, x[c * kLd + r]);
+  // X = L^{-1}: step t adds -L[i][t] X[t][j] to rows i > t of columns j <= t
+  float x[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[r][c] = (r0 + r == c0 + c && r0 + r < b) ? 1.0f : 0.0f;
+  for (int tb = 0; tb < 16; ++tb) {
+#pragma unroll
+    for (int ct = 0; ct < 8; ++ct) {
+      const int t = tb * 8 + ct;
+      if (t >= b) break;
+      float* lcol = colbuf[t & 1];
+      float* xrow = rowbuf[t & 1];
+      if (tx == tb) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) lcol[r0 + r] = a[r][ct];
+      }
+      if (ty == tb) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) xrow[c0 + c] = x[ct][c];
+      }
+      __syncthreads();
+      if (r0 + 7 > t && c0 <= t) {
+        float l[8], xv[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) l[r] = lcol[r0 + r];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) xv[c] = xrow[c0 + c];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (r0 + r > t && c0 + c <= t) x[r][c] = __fmaf_rn(-l[r], xv[c], x[r][c]);
+      }
     }
-    __syncthreads();
   }
-  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-    const int t = idx % kB, p = idx / kB;   // Linv[p][t] = X(p, t)
-    linv[(int64_t)p * ldl + t] = (p < b && t < b) ? f32_to_u16(x[t * kLd + p], fmt) : (uint16_t)0;
-  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c)   // Linv[p][t] = X(p, t)
+      linv[(int64_t)(r0 + r) * ldl + c0 + c] = f32_to_u16(x[r][c], fmt);
   __syncthreads();
 
-  // Y = U^{-1}: x[c * kLd + r] holds the running sum for r < c, then Y(r, c)
-  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-    const int r = idx % kB, c = idx / kB;
-    x[c * kLd + r] = (r == c && r < b) ? __fdiv_rn(1.0f, a[c * kLd + c]) : 0.0f;
-  }
-  __syncthreads();
-  for (int t = b - 1; t >= 0; --t) {
-    const float utt = a[t * kLd + t];
-    for (int c = t + 1 + tid; c < b; c += kGetrfThreads) x[c * kLd + t] = __fdiv_rn(-x[c * kLd + t], utt);
-    __syncthreads();
-    for (int c = t + warp; c < b; c += nw) {
-      const float yt = x[c * kLd + t];
-      for (int r = lane; r < t; r += 32) x[c * kLd + r] = __fmaf_rn(a[t * kLd + r], yt, x[c * kLd + r]);
+  // Y = U^{-1}, t descending: finalize row t (Y[t][j] = -acc / U[t][t], j > t),
+  // then add U[i][t] Y[t][j] to rows i < t of columns j >= t
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      x[r][c] = (r0 + r == c0 + c && r0 + r < b) ? __fdiv_rn(1.0f, dg[r0 + r]) : 0.0f;
+  for (int tb = 15; tb >= 0; --tb) {
+#pragma unroll
+    for (int ct = 7; ct >= 0; --ct) {
+      const int t = tb * 8 + ct;
+      if (t >= b) continue;
+      float* ucol = colbuf[t & 1];
+      float* yrow = rowbuf[t & 1];
+      if (ty == tb) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (c0 + c > t && c0 + c < b) x[ct][c] = __fdiv_rn(-x[ct][c], dg[t]);
+          yrow[c0 + c] = x[ct][c];
+        }
+      }
+      if (tx == tb) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) ucol[r0 + r] = a[r][ct];
+      }
+      __syncthreads();
+      if (r0 < t && c0 + 7 >= t) {
+        float u[8], yv[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) u[r] = ucol[r0 + r];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) yv[c] = yrow[c0 + c];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (r0 + r < t && c0 + c >= t) x[r][c] = __fmaf_rn(u[r], yv[c], x[r][c]);
+      }
     }
-    __syncthreads();
   }
-  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-    const int t = idx % kB, p = idx / kB;   // UinvT[p][t] = Y(t, p)
-    uinvT[(int64_t)p * ldu + t] = (p < b && t < b) ? f32_to_u16(x[p * kLd + t], fmt) : (uint16_t)0;
-  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c)   // UinvT[p][t] = Y(t, p): this thread holds Y(r0+r, c0+c)
+      uinvT[(int64_t)(c0 + c) * ldu + r0 + r] = (r0 + r < b && c0 + c < b) ? f32_to_u16(x[r][c], fmt) : (uint16_t)0;
 }
 
 // Column-major block (rows x cols at src, lds) -> row-major (dst[i*ldd + j]).
@@ -415,7 +499,7 @@ struct Factorizer {
 
   void getrf_base(int64_t k, int b, int slot) {
     void* tok = prof_begin(st);
-    getrf_base_kernel<<<1, kGetrfThreads, 2 * kB * kLd * sizeof(float), st>>>(
+    getrf_base_kernel<<<1, kGetrfThreads, 0, st>>>(
         b, at(k, k), ld, fmt, aop(slot) + slot * kB, NB, bop(slot) + slot * kB, NB, w.status);
     prof_end(tok, kProfGetrf, (double)b * b * b * 2.0, st);
     count_launches(1);
@@ -553,13 +637,6 @@ size_t factor_ws_bytes(int64_t n, int prec, int nb) { return carve(nullptr, n, p
 
 hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU,
                     int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(getrf_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         2 * kB * kLd * (int)sizeof(float));
-    if (e != cudaSuccess) return status_from_cuda(e);
-    attr_set = true;
-  }
   Factorizer f;
   f.n = n; f.LU = (uint16_t*)LU; f.ld = ldlu;
   f.prec = prec; f.fmt = prec == HPMXP_FP16 ? kFP16 : kBF16;
