@@ -247,23 +247,30 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
   }
   __syncthreads();
 
-  // acc_o -= Tile(row block of o, column block c) * zc ; tile from LU
+  // acc_o -= Tile(row block of o, column block c) * zc ; tile from LU.  The
+  // 16 tile entries of a thread are loaded together (independent loads, one
+  // memory latency) before the multiply-adds.
   auto apply_tile = [&](int o, int c) {
     const int blk = me + o * G;
     const int ii = tid % kTB, jg = tid / kTB;     // 4 column groups of 16
     const int64_t i = (int64_t)blk * kTB + ii;
+    const int64_t ic = i < n ? i : n - 1;
+    T lv[16];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      int64_t j = (int64_t)c * kTB + jg * 16 + jj;
+      const bool in = i < n && j < n;
+      j = j < n ? j : n - 1;
+      const float f = u16_to_f32(LU[ic + j * ld], fmt);
+      lv[jj] = in ? (T)f : (T)0;
+    }
     T s[K];
 #pragma unroll
     for (int r = 0; r < K; ++r) s[r] = (T)0;
-    if (i < n) {
-      for (int jj = jg * 16; jj < jg * 16 + 16; ++jj) {
-        const int64_t j = (int64_t)c * kTB + jj;
-        if (j >= n) break;
-        const T l = (T)u16_to_f32(LU[i + j * ld], fmt);
 #pragma unroll
-        for (int r = 0; r < K; ++r) s[r] = l * zc[jj * K + r] + s[r];
-      }
-    }
+    for (int jj = 0; jj < 16; ++jj)
+#pragma unroll
+      for (int r = 0; r < K; ++r) s[r] = lv[jj] * zc[(jg * 16 + jj) * K + r] + s[r];
 #pragma unroll
     for (int r = 0; r < K; ++r) part[(jg * kTB + ii) * K + r] = s[r];
     __syncthreads();
@@ -277,12 +284,22 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     __syncthreads();
   };
 
-  // load diagonal block c into the shared tile
+  // load diagonal block c into the shared tile (16 independent loads per thread)
   auto load_diag = [&](int c) {
-    for (int t = tid; t < kTB * kTB; t += 256) {
+    float v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int t = tid + k * 256;
       const int ii = t % kTB, jj = t / kTB;
       const int64_t i = (int64_t)c * kTB + ii, j = (int64_t)c * kTB + jj;
-      tile[ii * (kTB + 1) + jj] = (i < n && j < n) ? u16_to_f32(LU[i + j * ld], fmt) : (i == j ? 1.0f : 0.0f);
+      const bool in = i < n && j < n;
+      const float f = u16_to_f32(LU[(in ? i : 0) + (in ? j : 0) * ld], fmt);
+      v[k] = in ? f : (i == j ? 1.0f : 0.0f);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int t = tid + k * 256;
+      tile[(t % kTB) * (kTB + 1) + t / kTB] = v[k];
     }
     __syncthreads();
   };
