@@ -90,180 +90,230 @@ __global__ void cast_kernel(int64_t n, const double* __restrict__ A, int64_t lda
 }
 
 // ---------------------------------------------------------------------------
-// (i) Diagonal block of width b <= 128, one CTA: right-looking unblocked
-// factorization in fp32 (l = a / pivot, then a -= l u by fused multiply-add,
-// pivots ascending), rounding into storage, then the fp32 inverses of the
-// stored unit-lower L and upper U:
+// (i) Diagonal block of width b <= 128, one CTA of 16 warps, entirely in
+// shared memory (fp32).  Factorization: right-looking unblocked elimination
+// (l = a / pivot, then a -= l u by fused multiply-add, pivots ascending),
+// organised in 16-column panels: warps 0-3 eliminate the panel (one row per
+// lane, pivot row through shared memory, one named barrier per pivot), all
+// warps then solve the panel's row strip and apply the rank-16 update.  Every
+// entry still receives its updates one FMA at a time in ascending pivot
+// order, so the result is identical to the unblocked loop.
+// Inverses of the stored unit-lower L and upper U, each by 16-row blocks in
+// the same per-entry operation order as the plain recurrences
 //   X = L^{-1}: X[r][c] = -sum_{t=c}^{r-1} L[r][t] X[t][c]   (t ascending)
 //   Y = U^{-1}: Y[c][c] = 1 / U[c][c];
 //               Y[r][c] = (-sum_{t=c}^{r+1} U[r][t] Y[t][c]) / U[r][r] (t descending)
-// evaluated column-parallel in the same per-entry operation order, rounded to
-// storage and written as the K-major GEMM operands Linv (Linv[p*ldl + t]) and
-// Uinv^T (UinvT[p*ldu + t] = Uinv[t][p]).  128 x 128 zero-padded.
+// computed concurrently by warps 0-7 (X) and 8-15 (Y), rounded to storage
+// and written as the K-major GEMM operands Linv (Linv[p*ldl + t]) and Uinv^T
+// (UinvT[p*ldu + t] = Uinv[t][p]).  128 x 128 zero-padded.
 // ---------------------------------------------------------------------------
-constexpr int kGetrfThreads = 256;   // 16 x 16 threads, 8 x 8 entries each
+constexpr int kGetrfThreads = 512;
+constexpr int kP = 132;    // shared pitch (floats): 16-byte aligned columns
+constexpr int kPW = 16;    // panel width
+constexpr size_t kGetrfSmem = sizeof(float) * (3 * kB * kP + 2 * kPW + 8);
+
+__device__ inline void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// rank-kPW update of the block rows [i0, i1) x cols [j0, j1) of M (pitch kP):
+// M(i, j) += sgn * sum_{t in order} L(i, t) * R(t, j) with L(i,t) = Lm[t*kP + i],
+// R(t, j) = Rm[j*kP + t]; `desc` walks t from t1-1 down to t0.  4x4 register
+// micro-tiles, warp = tile column, lane = tile row.
+__device__ inline void rank_update(float* M, const float* Lm, const float* Rm, int i0, int i1, int j0, int j1,
+                                   int t0, int t1, float sgn, bool desc, int wid, int nwarps, int lane) {
+  const int ni = (i1 - i0 + 3) / 4, nj = (j1 - j0 + 3) / 4;
+  for (int tj = wid; tj < nj; tj += nwarps) {
+    for (int ti = lane; ti < ni; ti += 32) {
+      const int i = i0 + 4 * ti, j = j0 + 4 * tj;
+      float acc[4][4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r][c] = M[(j + c) * kP + i + r];
+      for (int k = 0; k < t1 - t0; ++k) {
+        const int t = desc ? t1 - 1 - k : t0 + k;
+        const float4 l4 = *reinterpret_cast<const float4*>(&Lm[t * kP + i]);
+        const float l[4] = {sgn * l4.x, sgn * l4.y, sgn * l4.z, sgn * l4.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float u = Rm[(j + c) * kP + t];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[r][c] = __fmaf_rn(l[r], u, acc[r][c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (i + r < i1 && j + c < j1) M[(j + c) * kP + i + r] = acc[r][c];
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kGetrfThreads)
 getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_t* __restrict__ linv,
                   int64_t ldl, uint16_t* __restrict__ uinvT, int64_t ldu, uint32_t* status) {
-  __shared__ float rowbuf[2][kB];   // broadcast row of the current step (double buffered)
-  __shared__ float colbuf[2][kB];   // broadcast column of the current step
-  __shared__ float dg[kB];          // diagonal of the stored U
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int r0 = ty * 8, c0 = tx * 8;   // this thread's rows r0..r0+7 and columns c0..c0+7
-  float a[8][8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int i = r0 + r, j = c0 + c;
-      a[r][c] = (i < b && j < b) ? u16_to_f32(D[i + (int64_t)j * ldd], fmt) : 0.0f;
-    }
+  extern __shared__ float sm[];
+  float* a = sm;                  // a[j * kP + i] = D(i, j); later the stored L and U
+  float* x = sm + kB * kP;        // X = L^{-1}, x[c * kP + r] = X(r, c)
+  float* y = sm + 2 * kB * kP;    // Y = U^{-1}, y[c * kP + r] = Y(r, c)
+  float* urow = sm + 3 * kB * kP; // [2][kPW] pivot row of the current panel step
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // factorization: step p broadcasts row p (u) and the scaled column p (l)
+  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    const int i = idx % kB, j = idx / kB;
+    a[j * kP + i] = (i < b && j < b) ? u16_to_f32(D[i + (int64_t)j * ldd], fmt) : 0.0f;
+  }
+  __syncthreads();
+
   bool bad = false;
-  for (int pb = 0; pb < 16; ++pb) {
+  for (int p0 = 0; p0 < b; p0 += kPW) {
+    const int pw = min(kPW, b - p0);
+    // (a) panel: rows p0..b-1 (one per lane of warps 0-3), columns p0..p0+pw-1
+    if (warp < 4) {
+      const int i = p0 + 32 * warp + lane;
+      const bool has = i < b;
+      float pr[kPW];
 #pragma unroll
-    for (int cp = 0; cp < 8; ++cp) {
-      const int p = pb * 8 + cp;
-      if (p >= b) break;
-      float* urow = rowbuf[p & 1];
-      if (ty == pb) {
+      for (int c = 0; c < kPW; ++c) pr[c] = (has && c < pw) ? a[(p0 + c) * kP + i] : 0.0f;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) urow[c0 + c] = a[cp][c];
-      }
-      __syncthreads();
-      const float piv = urow[p];
-      if (!(isfinite(piv) && piv != 0.0f)) bad = true;
-      if (tx == pb) {
+      for (int cp = 0; cp < kPW; ++cp) {
+        if (cp >= pw) break;
+        const int p = p0 + cp;
+        float* ur = urow + (cp & 1) * kPW;
+        if (warp == 0 && lane == cp) {   // row p is lane cp of warp 0
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          if (r0 + r > p) a[r][cp] = __fdiv_rn(a[r][cp], piv);
-          colbuf[0][r0 + r] = a[r][cp];
+          for (int c = 0; c < kPW; ++c) ur[c] = pr[c];
+        }
+        named_sync(1, 128);
+        const float piv = ur[cp];
+        if (!(isfinite(piv) && piv != 0.0f)) bad = true;
+        if (has && i > p) {
+          const float l = __fdiv_rn(pr[cp], piv);
+          pr[cp] = l;
+#pragma unroll
+          for (int c = cp + 1; c < kPW; ++c)
+            if (c < pw) pr[c] = __fmaf_rn(-l, ur[c], pr[c]);
         }
       }
-      __syncthreads();
-      if (r0 + 7 > p && c0 + 7 > p) {
-        float u[8], l[8];
+      if (has) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) u[c] = urow[c0 + c];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) l[r] = colbuf[0][r0 + r];
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (r0 + r > p && c0 + c > p) a[r][c] = __fmaf_rn(-l[r], u[c], a[r][c]);
+        for (int c = 0; c < kPW; ++c)
+          if (c < pw) a[(p0 + c) * kP + i] = pr[c];
       }
     }
+    __syncthreads();
+    const int e = p0 + pw;
+    if (e >= b) break;
+    // (b) row strip: rows p0..e-1, columns e..b-1, unit-lower solve with the panel
+    for (int j = e + tid; j < b; j += kGetrfThreads) {
+      float col[kPW];
+#pragma unroll
+      for (int r = 0; r < kPW; ++r) col[r] = r < pw ? a[j * kP + p0 + r] : 0.0f;
+#pragma unroll
+      for (int r = 1; r < kPW; ++r) {
+        if (r < pw) {
+#pragma unroll
+          for (int q = 0; q < r; ++q) col[r] = __fmaf_rn(-a[(p0 + q) * kP + p0 + r], col[q], col[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kPW; ++r)
+        if (r < pw) a[j * kP + p0 + r] = col[r];
+    }
+    __syncthreads();
+    // (c) trailing update rows/cols e..b-1, pivots p0..e-1 ascending
+    rank_update(a, a, a, e, b, e, b, p0, e, -1.0f, false, warp, kGetrfThreads / 32, lane);
+    __syncthreads();
   }
   if (bad && tid == 0) atomicOr(status, kErrPivot);
 
-  // round into storage; keep the stored values for the inverses
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int i = r0 + r, j = c0 + c;
-      if (i < b && j < b) {
-        const uint16_t h = f32_to_u16(a[r][c], fmt);
-        D[i + (int64_t)j * ldd] = h;
-        a[r][c] = u16_to_f32(h, fmt);
-        if (i == j) dg[i] = a[r][c];
-      } else {
-        a[r][c] = 0.0f;
-      }
+  // round into storage; keep the stored values for the inverses; X = I, Y = diag(1/U)
+  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    const int i = idx % kB, j = idx / kB;
+    float v = 0.0f;
+    if (i < b && j < b) {
+      const uint16_t h = f32_to_u16(a[j * kP + i], fmt);
+      D[i + (int64_t)j * ldd] = h;
+      v = u16_to_f32(h, fmt);
     }
-  __syncthreads();
-
-  // X = L^{-1}: step t adds -L[i][t] X[t][j] to rows i > t of columns j <= t
-  float x[8][8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) x[r][c] = (r0 + r == c0 + c && r0 + r < b) ? 1.0f : 0.0f;
-  for (int tb = 0; tb < 16; ++tb) {
-#pragma unroll
-    for (int ct = 0; ct < 8; ++ct) {
-      const int t = tb * 8 + ct;
-      if (t >= b) break;
-      float* lcol = colbuf[t & 1];
-      float* xrow = rowbuf[t & 1];
-      if (tx == tb) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) lcol[r0 + r] = a[r][ct];
-      }
-      if (ty == tb) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) xrow[c0 + c] = x[ct][c];
-      }
-      __syncthreads();
-      if (r0 + 7 > t && c0 <= t) {
-        float l[8], xv[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) l[r] = lcol[r0 + r];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) xv[c] = xrow[c0 + c];
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (r0 + r > t && c0 + c <= t) x[r][c] = __fmaf_rn(-l[r], xv[c], x[r][c]);
-      }
-    }
+    a[j * kP + i] = v;
   }
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c)   // Linv[p][t] = X(p, t)
-      linv[(int64_t)(r0 + r) * ldl + c0 + c] = f32_to_u16(x[r][c], fmt);
+  __syncthreads();
+  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    const int i = idx % kB, j = idx / kB;
+    x[j * kP + i] = (i == j && i < b) ? 1.0f : 0.0f;
+    y[j * kP + i] = (i == j && i < b) ? __fdiv_rn(1.0f, a[j * kP + i]) : 0.0f;
+  }
   __syncthreads();
 
-  // Y = U^{-1}, t descending: finalize row t (Y[t][j] = -acc / U[t][t], j > t),
-  // then add U[i][t] Y[t][j] to rows i < t of columns j >= t
+  if (warp < 8) {
+    // ---- X = L^{-1}, 16-row blocks top-down; group barrier id 2 (256 threads)
+    const int gt = tid;   // 0..255
+    for (int t0 = 0; t0 < b; t0 += kPW) {
+      const int t1 = min(t0 + kPW, b);
+      // rows t0..t1-1, every column c < t1: within-block terms t = max(c, t0) .. r-1
+      for (int c = gt; c < t1; c += 256) {
+        float col[kPW];
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? x[c * kP + t0 + r] : 0.0f;
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
-      x[r][c] = (r0 + r == c0 + c && r0 + r < b) ? __fdiv_rn(1.0f, dg[r0 + r]) : 0.0f;
-  for (int tb = 15; tb >= 0; --tb) {
+        for (int r = 1; r < kPW; ++r) {
+          if (t0 + r < t1 && t0 + r > c) {
 #pragma unroll
-    for (int ct = 7; ct >= 0; --ct) {
-      const int t = tb * 8 + ct;
-      if (t >= b) continue;
-      float* ucol = colbuf[t & 1];
-      float* yrow = rowbuf[t & 1];
-      if (ty == tb) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (c0 + c > t && c0 + c < b) x[ct][c] = __fdiv_rn(-x[ct][c], dg[t]);
-          yrow[c0 + c] = x[ct][c];
+            for (int q = 0; q < r; ++q)
+              if (t0 + q >= c) col[r] = __fmaf_rn(-a[(t0 + q) * kP + t0 + r], col[q], col[r]);
+          }
         }
+#pragma unroll
+        for (int r = 0; r < kPW; ++r)
+          if (t0 + r < t1) x[c * kP + t0 + r] = col[r];
       }
-      if (tx == tb) {
+      named_sync(2, 256);
+      // rows t1..b-1, columns 0..t1-1: add -L(r, t) X(t, c) for t = t0..t1-1 ascending
+      if (t1 < b) rank_update(x, a, x, t1, b, 0, t1, t0, t1, -1.0f, false, warp, 8, lane);
+      named_sync(2, 256);
+    }
+  } else {
+    // ---- Y = U^{-1}, 16-row blocks bottom-up; group barrier id 3 (256 threads)
+    const int gt = tid - 256;
+    const int nblk = (b + kPW - 1) / kPW;
+    for (int bi = nblk - 1; bi >= 0; --bi) {
+      const int t0 = bi * kPW, t1 = min(t0 + kPW, b);
+      // rows t1-1 down to t0, every column c >= t0: terms t = min(c, t1-1) down to r+1, then divide
+      for (int c = t0 + gt; c < b; c += 256) {
+        float col[kPW];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) ucol[r0 + r] = a[r][ct];
+        for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? y[c * kP + t0 + r] : 0.0f;
+#pragma unroll
+        for (int r = kPW - 1; r >= 0; --r) {
+          const int rr = t0 + r;
+          if (rr < t1 && rr < c) {
+            float acc = col[r];
+#pragma unroll
+            for (int q = kPW - 1; q > r; --q)
+              if (t0 + q < t1 && t0 + q <= c) acc = __fmaf_rn(a[(t0 + q) * kP + rr], col[q], acc);
+            col[r] = __fdiv_rn(-acc, a[rr * kP + rr]);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kPW; ++r)
+          if (t0 + r < t1) y[c * kP + t0 + r] = col[r];
       }
-      __syncthreads();
-      if (r0 < t && c0 + 7 >= t) {
-        float u[8], yv[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) u[r] = ucol[r0 + r];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) yv[c] = yrow[c0 + c];
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (r0 + r < t && c0 + c >= t) x[r][c] = __fmaf_rn(u[r], yv[c], x[r][c]);
-      }
+      named_sync(3, 256);
+      // rows 0..t0-1, columns t0..b-1: add U(r, t) Y(t, c) for t = t1-1 down to t0
+      if (t0 > 0) rank_update(y, a, y, 0, t0, t0, b, t0, t1, 1.0f, true, warp - 8, 8, lane);
+      named_sync(3, 256);
     }
   }
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c)   // UinvT[p][t] = Y(t, p): this thread holds Y(r0+r, c0+c)
-      uinvT[(int64_t)(c0 + c) * ldu + r0 + r] = (r0 + r < b && c0 + c < b) ? f32_to_u16(x[r][c], fmt) : (uint16_t)0;
+  __syncthreads();
+  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    const int t = idx % kB, pp = idx / kB;
+    const bool in = pp < b && t < b;
+    linv[(int64_t)pp * ldl + t] = in ? f32_to_u16(x[t * kP + pp], fmt) : (uint16_t)0;   // Linv[p][t] = X(p, t)
+    uinvT[(int64_t)pp * ldu + t] = in ? f32_to_u16(y[pp * kP + t], fmt) : (uint16_t)0;  // UinvT[p][t] = Y(t, p)
+  }
 }
 
 // Column-major block (rows x cols at src, lds) -> row-major (dst[i*ldd + j]).
@@ -499,7 +549,7 @@ struct Factorizer {
 
   void getrf_base(int64_t k, int b, int slot) {
     void* tok = prof_begin(st);
-    getrf_base_kernel<<<1, kGetrfThreads, 0, st>>>(
+    getrf_base_kernel<<<1, kGetrfThreads, kGetrfSmem, st>>>(
         b, at(k, k), ld, fmt, aop(slot) + slot * kB, NB, bop(slot) + slot * kB, NB, w.status);
     prof_end(tok, kProfGetrf, (double)b * b * b * 2.0, st);
     count_launches(1);
@@ -637,6 +687,15 @@ size_t factor_ws_bytes(int64_t n, int prec, int nb) { return carve(nullptr, n, p
 
 hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU,
                     int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st) {
+  static int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    cudaError_t e =
+        cudaFuncSetAttribute(getrf_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGetrfSmem);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    attr_dev = dev;
+  }
   Factorizer f;
   f.n = n; f.LU = (uint16_t*)LU; f.ld = ldlu;
   f.prec = prec; f.fmt = prec == HPMXP_FP16 ? kFP16 : kBF16;
