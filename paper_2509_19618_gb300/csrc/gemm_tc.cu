@@ -7,14 +7,14 @@
 //
 // Persistent kernel, one CTA per SM, 128 x 128 output tiles in a static
 // round-robin order.  The MMA computes the TRANSPOSED tile (TMEM lane = output
-// column j, TMEM column = output row i) so each epilogue thread owns the 128
-// consecutive rows of one column of the column-major output: it loads that
-// 256-byte run of C with 16-byte loads issued before it waits for the
-// accumulator, and stores the result the same way.  Shared memory is left to
-// a 6-stage operand ring (192 KiB in flight per SM).
+// column j, TMEM column = output row i) so each epilogue thread owns 16
+// consecutive rows of one column of the column-major output: the C tile is
+// moved by TMA between HBM and a 128-byte-swizzled shared buffer and the
+// epilogue touches it with 16-byte, bank-conflict-free accesses.
 //
 // Roles: warp 0 TMA producer of the operand ring; warp 1 TMEM owner and MMA
-// issuer; warps 2..5 epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+// issuer; warps 2..5 epilogue (warp w reads TMEM lanes 32*(w%4)..+31), which
+// also prefetch C tiles two tiles ahead and issue the TMA stores.
 // Accumulators are double buffered in TMEM (single buffered for 4-slice FP8),
 // so the epilogue of one tile overlaps the MMAs of the next.  The E4M3
 // variant keeps one accumulator per 128-deep K slice and folds them with the
@@ -36,9 +36,11 @@ namespace {
 constexpr int kTI = 128;                      // output rows per tile (MMA N)
 constexpr int kTJ = 128;                      // output columns per tile (MMA M, TMEM lanes)
 constexpr int kRowBytes = 128;                // K bytes per operand row per stage (one swizzle atom)
-constexpr int kStages = 6;
+constexpr int kStages = 4;
 constexpr int kStageA = kTJ * kRowBytes;      // MMA A operand: rows j (16 KiB)
 constexpr int kStageB = kTI * kRowBytes;      // MMA B operand: rows i (16 KiB)
+constexpr int kCBox = kTJ * 128;              // one C box: 64 rows x 128 columns (16 KiB)
+constexpr int kCTile = 2 * kCBox;             // 32 KiB
 constexpr int kThreads = 192;
 constexpr int kEpiThreads = 128;
 
@@ -80,6 +82,16 @@ __device__ inline void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, i
       ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+__device__ inline void tma_store_2d(const CUtensorMap* tm, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"((uint64_t)tm), "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
+__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ inline void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ inline void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ inline void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ inline void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -176,7 +188,7 @@ struct TcParams {
   int nbuf;               // TMEM accumulator buffers (1 or 2)
   uint32_t acc_cols;      // TMEM columns per accumulator buffer
   uint32_t ncols;         // TMEM columns allocated
-  uint16_t* C; int64_t ldc;   // column-major output (and for kEpiSub input); may be NULL
+  int has_c;              // write (and for kEpiSub read) the column-major C through tmC
   uint16_t* R; int64_t ldr;
   const float* sA; int sa_ld;
   const float* sB; int sb_ld;
@@ -188,19 +200,22 @@ __device__ inline uint32_t pack16x2(float lo, float hi, int fmt) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmC, TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);   // swizzle atoms need 1024-byte alignment
   const uint32_t sOpA = smem_u32(smem);                            // [kStages][rows j][128 B]
   const uint32_t sOpB = sOpA + kStages * kStageA;                  // [kStages][rows i][128 B]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * (kStageA + kStageB));
+  const uint32_t sC = sOpB + kStages * kStageB;                    // [2][2 boxes][cols j][128 B]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * (kStageA + kStageB) + 2 * kCTile);
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int s) { return bar0 + 8u * (uint32_t)s; };
   auto empty = [&](int s) { return bar0 + 8u * (uint32_t)(kStages + s); };
   auto acc_full = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + b); };
   auto acc_empty = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + 2 + b); };
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
+  auto c_full = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + 4 + b); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 6);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -209,10 +224,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full(b), 1);
       mbar_init(acc_empty(b), kEpiThreads / 32);
+      mbar_init(c_full(b), 1);
     }
     fence_mbar_init();
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    if (p.has_c) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmC) : "memory");
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), p.ncols);
@@ -277,32 +294,29 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // epilogue: thread = output column j = j0 + jl, jl = 32 q + lane (its TMEM lane)
     const int q = warp & 3;
     const int jl = 32 * q + lane;
-    const bool sub = p.mode == kEpiSub;
+    const bool leader = (warp == 2 && lane == 0);
+    const bool load_c = p.has_c && p.mode == kEpiSub;
+    int issued_c[2] = {-1, -1};   // local tile whose C load is outstanding in each buffer
+    if (leader && load_c) {       // prefetch the C tiles of the first two local tiles
+      int local = 0;
+      for (int t = blockIdx.x; t < p.ntiles && local < 2; t += gridDim.x, ++local) {
+        const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
+        mbar_expect_tx(c_full(local), kCTile);
+        tma_load_2d(sC + local * kCTile, &tmC, i0, j0, c_full(local));
+        tma_load_2d(sC + local * kCTile + kCBox, &tmC, i0 + 64, j0, c_full(local));
+        issued_c[local] = local;
+      }
+    }
     bool ok = true;
     int local = 0;
     for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++local) {
       const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
-      const int ab = local % p.nbuf;
-      const int64_t j = (int64_t)j0 + jl;
-      const bool jin = j < p.N;
-      uint16_t* ccol = (p.C && jin) ? p.C + i0 + j * p.ldc : nullptr;
-      // C(i0 .. i0+127, j) into registers before waiting for the accumulator
-      uint4 cv[kTI / 8];
-      if (sub && ccol) {
-#pragma unroll
-        for (int k = 0; k < kTI / 8; ++k) {
-          if (i0 + 8 * k + 8 <= p.M) {
-            cv[k] = __ldcs(reinterpret_cast<const uint4*>(ccol + 8 * k));
-          } else {
-            uint16_t h[8];
-#pragma unroll
-            for (int v = 0; v < 8; ++v) h[v] = (i0 + 8 * k + v < p.M) ? ccol[8 * k + v] : (uint16_t)0;
-            cv[k] = make_uint4(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16),
-                               h[4] | ((uint32_t)h[5] << 16), h[6] | ((uint32_t)h[7] << 16));
-          }
-        }
-      }
-      bool w = mbar_wait(acc_full(ab), (uint32_t)((local / p.nbuf) & 1));
+      const int cb = local & 1, ab = local % p.nbuf;
+      const uint32_t cbuf = sC + cb * kCTile;
+      bool w = true;
+      if (load_c) w = mbar_wait(c_full(cb), (uint32_t)((local >> 1) & 1));
+      if (leader) issued_c[cb] = -1;
+      w = w && mbar_wait(acc_full(ab), (uint32_t)((local / p.nbuf) & 1));
       w = __all_sync(0xffffffffu, w);   // warp-uniform for tcgen05.ld
       if (!w) { ok = false; break; }
       tc_fence_after();
@@ -311,30 +325,35 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (p.fp8)
         for (int g = 0; g < p.nkb && g < 4; ++g)
           sc[g] = __fmul_rn(p.sA[(i0 / 128) * p.sa_ld + g], p.sB[(j0 / 128) * p.sb_ld + g]);
-#pragma unroll
-      for (int h32 = 0; h32 < kTI / 32; ++h32) {
+      const int64_t j = (int64_t)j0 + jl;
+      for (int c32 = 0; c32 < kTI / 32; ++c32) {
         float acc[32];
         uint32_t r[32];
         if (p.fp8) {
 #pragma unroll
           for (int v = 0; v < 32; ++v) acc[v] = 0.0f;
           for (int g = 0; g < p.nkb; ++g) {
-            tmem_ld32(lane_addr + (uint32_t)(g * kTI + h32 * 32), r);
+            tmem_ld32(lane_addr + (uint32_t)(g * kTI + c32 * 32), r);
 #pragma unroll
             for (int v = 0; v < 32; ++v) acc[v] = __fmaf_rn(__uint_as_float(r[v]), sc[g], acc[v]);
           }
         } else {
-          tmem_ld32(lane_addr + (uint32_t)(h32 * 32), r);
+          tmem_ld32(lane_addr + (uint32_t)(c32 * 32), r);
 #pragma unroll
           for (int v = 0; v < 32; ++v) acc[v] = __uint_as_float(r[v]);
         }
-        // rows i0 + 32 h32 .. +31 of column j: four 16-byte groups of 8 rows
+        // rows i0 + 32 c32 .. +31 of column j: four 16-byte chunks of the swizzled box
+        const int box = c32 >> 1;
+        const uint32_t row_addr = cbuf + box * kCBox + jl * 128;
 #pragma unroll
         for (int k4 = 0; k4 < 4; ++k4) {
-          const int k = h32 * 4 + k4;
+          const int ch = (c32 & 1) * 4 + k4;
+          const uint32_t ad = row_addr + ((ch ^ (jl & 7)) << 4);
           uint32_t outw[4];
-          if (sub) {
-            const uint32_t cw[4] = {cv[k].x, cv[k].y, cv[k].z, cv[k].w};
+          if (p.mode == kEpiSub) {
+            uint32_t cw[4];
+            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(cw[0]), "=r"(cw[1]), "=r"(cw[2]), "=r"(cw[3]) : "r"(ad) : "memory");
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
               const float lo = __fsub_rn(u16_to_f32((uint16_t)(cw[v] & 0xffffu), p.fmt), acc[8 * k4 + 2 * v]);
@@ -346,20 +365,15 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int v = 0; v < 4; ++v)
               outw[v] = pack16x2(p.sign * acc[8 * k4 + 2 * v], p.sign * acc[8 * k4 + 2 * v + 1], p.fmt);
           }
-          const int ib = i0 + 8 * k;
-          if (ccol) {
-            if (ib + 8 <= p.M) {
-              __stcs(reinterpret_cast<uint4*>(ccol + 8 * k), make_uint4(outw[0], outw[1], outw[2], outw[3]));
-            } else {
+          if (p.has_c)
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                         ::"r"(ad), "r"(outw[0]), "r"(outw[1]), "r"(outw[2]), "r"(outw[3]) : "memory");
+          if (p.R && j < p.N) {
 #pragma unroll
-              for (int v = 0; v < 8; ++v)
-                if (ib + v < p.M) ccol[8 * k + v] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
+            for (int v = 0; v < 8; ++v) {
+              const int64_t i = (int64_t)i0 + c32 * 32 + k4 * 8 + v;
+              if (i < p.M) p.R[i * p.ldr + j] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
             }
-          }
-          if (p.R && jin) {
-#pragma unroll
-            for (int v = 0; v < 8; ++v)
-              if (ib + v < p.M) p.R[(int64_t)(ib + v) * p.ldr + j] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
           }
         }
       }
@@ -367,8 +381,34 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty(ab));
+      if (p.has_c) {
+        fence_async_smem();
+        epi_barrier();
+        if (leader) {
+          tma_store_2d(&tmC, i0, j0, cbuf);
+          tma_store_2d(&tmC, i0 + 64, j0, cbuf + kCBox);
+          bulk_commit();
+          bulk_wait_read0();   // the buffer can be refilled
+          // prefetch the C tile two local tiles ahead into this buffer
+          const int t2 = t + 2 * (int)gridDim.x;
+          if (load_c && t2 < p.ntiles) {
+            const int i2 = (t2 % p.tiles_i) * kTI, j2 = (t2 / p.tiles_i) * kTJ;
+            mbar_expect_tx(c_full(cb), kCTile);
+            tma_load_2d(cbuf, &tmC, i2, j2, c_full(cb));
+            tma_load_2d(cbuf + kCBox, &tmC, i2 + 64, j2, c_full(cb));
+            issued_c[cb] = local + 2;
+          }
+        }
+      }
     }
     if (!ok && lane == 0) atomicOr(p.status, kErrTimeout);
+    if (leader) {
+      bulk_wait0();
+      // C loads issued for tiles this CTA did not reach (error path) land before exit
+      for (int b = 0; b < 2; ++b)
+        if (issued_c[b] >= 0 && !mbar_wait(c_full(b), (uint32_t)((issued_c[b] >> 1) & 1)))
+          atomicOr(p.status, kErrTimeout);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -409,7 +449,8 @@ bool make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-constexpr size_t kSmemBytes = 1024 + (size_t)kStages * (kStageA + kStageB) + 8 * (2 * kStages + 4) + 16;
+constexpr size_t kSmemBytes =
+    1024 + (size_t)kStages * (kStageA + kStageB) + 2 * kCTile + 8 * (2 * kStages + 6) + 16;
 
 int num_sms() {
   static int sms = 0;
@@ -429,14 +470,19 @@ cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
   const int esz = g.fp8 ? 1 : 2;
   const uint64_t kbytes = (uint64_t)g.K * esz;
   if (kbytes % kRowBytes) return cudaErrorInvalidValue;
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, tc;
   if (!make_map(&ta, g.A, kbytes / 2, (uint64_t)g.M, (uint64_t)g.lda * esz, kRowBytes / 2, kTI) ||
       !make_map(&tb, g.B, kbytes / 2, (uint64_t)g.N, (uint64_t)g.ldb * esz, kRowBytes / 2, kTJ))
     return cudaErrorInvalidValue;
   TcParams p{};
-  // the epilogue moves C in 16-byte runs along columns
-  if (g.C && ((((uintptr_t)g.C) & 15) || (g.ldc % 8))) return cudaErrorInvalidValue;
-  p.C = (uint16_t*)g.C; p.ldc = g.ldc;
+  p.has_c = g.C != nullptr;
+  if (p.has_c) {
+    // column-major C: inner = rows; box = 64 rows x 128 columns
+    if (!make_map(&tc, g.C, (uint64_t)g.M, (uint64_t)g.N, (uint64_t)g.ldc * 2, 64, kTJ))
+      return cudaErrorInvalidValue;
+  } else {
+    tc = ta;   // never dereferenced
+  }
   p.M = g.M; p.N = g.N; p.nkb = (int)(kbytes / kRowBytes);
   p.tiles_i = cdiv(g.M, kTI);
   p.ntiles = p.tiles_i * cdiv(g.N, kTJ);
@@ -467,7 +513,7 @@ cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
   const int grid = std::min(p.ntiles, num_sms());
   const double flops = 2.0 * g.M * (double)g.N * g.K;
   void* tok = prof_begin(st);
-  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, p);
+  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, tc, p);
   prof_end(tok, kProfGemm, flops, st);
   count_launches(1);
   return cudaGetLastError();

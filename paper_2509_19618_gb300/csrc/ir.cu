@@ -425,6 +425,247 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
 }
 
 // ---------------------------------------------------------------------------
+// fp32 preconditioner (the default refinement path): 128-row blocks, the
+// diagonal blocks of L and U inverted once per solve in fp32 (setup kernel
+// below), so the diagonal solve is a parallel 128 x 128 product.  Each
+// published block is a run of 64-bit words (fp32 value | epoch << 32): a
+// reader's poll of the words delivers the data itself, with no separate flag.
+// The owner of the next block prefetches its two tiles (off-diagonal and
+// inverted diagonal) into shared memory before it waits.
+// ---------------------------------------------------------------------------
+constexpr int kTB32 = 128;
+
+// Inverse of diagonal block c (c < nb) of the unit-lower L (which == 0) or of
+// U (which == 1), fp32, from the 16-bit factors: one thread per column,
+// column-oriented substitution.  Output inv[(which * nb + c) * 128 * 128 +
+// j * 128 + i] = inverse(i, j).
+__global__ void __launch_bounds__(128) diag_inv32_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
+                                                         int fmt, float* __restrict__ inv) {
+  extern __shared__ float dsm[];
+  float* t = dsm;                          // t[j * 129 + i] = block(i, j)
+  float* x = dsm + kTB32 * (kTB32 + 1);    // x[j * 129 + i] = inverse(i, j)
+  const int nb = (int)cdiv<int64_t>(n, kTB32);
+  const int c = blockIdx.x, which = blockIdx.y, tid = threadIdx.x;
+  const int64_t base = (int64_t)c * kTB32;
+  for (int idx = tid; idx < kTB32 * kTB32; idx += 128) {
+    const int i = idx % kTB32, j = idx / kTB32;
+    const bool in = base + i < n && base + j < n;
+    t[j * 129 + i] = in ? u16_to_f32(LU[base + i + (base + j) * ld], fmt) : (i == j ? 1.0f : 0.0f);
+  }
+  __syncthreads();
+  const int j = tid;   // column of the inverse
+  if (which == 0) {    // L X = I, unit lower: X(i, j) = -sum_{k=j}^{i-1} L(i, k) X(k, j)
+    for (int i = 0; i < kTB32; ++i) x[j * 129 + i] = i == j ? 1.0f : 0.0f;
+    for (int i = j + 1; i < kTB32; ++i) {
+      float s = 0.0f;
+      for (int k = j; k < i; ++k) s = __fmaf_rn(t[k * 129 + i], x[j * 129 + k], s);
+      x[j * 129 + i] = -s;
+    }
+  } else {             // U Y = I: Y(i, j) = (delta - sum_{k=i+1}^{j} U(i, k) Y(k, j)) / U(i, i)
+    for (int i = 0; i < kTB32; ++i) x[j * 129 + i] = 0.0f;
+    x[j * 129 + j] = 1.0f / t[j * 129 + j];
+    for (int i = j - 1; i >= 0; --i) {
+      float s = 0.0f;
+      for (int k = i + 1; k <= j; ++k) s = __fmaf_rn(t[k * 129 + i], x[j * 129 + k], s);
+      x[j * 129 + i] = -s / t[i * 129 + i];
+    }
+  }
+  __syncthreads();
+  float* out = inv + ((int64_t)which * nb + c) * kTB32 * kTB32;
+  for (int idx = tid; idx < kTB32 * kTB32; idx += 128) out[idx] = x[(idx / kTB32) * 129 + idx % kTB32];
+}
+
+__device__ inline unsigned long long tag_word(float v, int epoch) {
+  return (unsigned long long)__float_as_uint(v) | ((unsigned long long)(unsigned)epoch << 32);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
+                                                        int fmt, const float* __restrict__ dinv,
+                                                        const double* __restrict__ v, int64_t ldv,
+                                                        double* __restrict__ z, int64_t ldz,
+                                                        unsigned long long* __restrict__ pub, int epoch,
+                                                        uint32_t* status) {
+  extern __shared__ float smf[];
+  const int nb = (int)cdiv<int64_t>(n, kTB32);
+  const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x;
+  const int nown = (nb - me + G - 1) / G;
+  float* acc = smf;                                   // [nown][128][K]
+  float* zc = acc + (size_t)nown * kTB32 * K;          // [128][K]
+  float* tl = zc + kTB32 * K;                          // [128][128] prefetched off-diagonal tile, tl[j*128+i]
+  float* ti = tl + kTB32 * kTB32;                      // [128][128] prefetched inverse diagonal, ti[j*128+i]
+  float* part = ti + kTB32 * kTB32;                    // [2][128][K]
+  __shared__ int abort_flag;
+  if (tid == 0) abort_flag = 0;
+  unsigned long long* fpub = pub;
+  unsigned long long* bpub = pub + (size_t)nb * kTB32 * K;
+  for (int o = 0; o < nown; ++o)
+    for (int t = tid; t < kTB32 * K; t += 256) {
+      const int ii = t % kTB32, r = t / kTB32;
+      const int64_t i = (int64_t)(me + o * G) * kTB32 + ii;
+      acc[((size_t)o * kTB32 + ii) * K + r] = i < n ? (float)v[i + r * ldv] : 0.0f;
+    }
+  __syncthreads();
+
+  // 16-bit tile (row block rb, column block cb) of LU into tl (zero outside)
+  auto fetch_tile = [&](int rb, int cb) {
+    for (int idx = tid; idx < kTB32 * kTB32; idx += 256) {
+      const int ii = idx % kTB32, jj = idx / kTB32;
+      const int64_t i = (int64_t)rb * kTB32 + ii, j = (int64_t)cb * kTB32 + jj;
+      tl[jj * kTB32 + ii] = (i < n && j < n) ? u16_to_f32(LU[i + j * ld], fmt) : 0.0f;
+    }
+  };
+  auto fetch_inv = [&](int which, int cb) {
+    const float4* src = reinterpret_cast<const float4*>(dinv + ((int64_t)which * nb + cb) * kTB32 * kTB32);
+    float4* dst = reinterpret_cast<float4*>(ti);
+    for (int idx = tid; idx < kTB32 * kTB32 / 4; idx += 256) dst[idx] = src[idx];
+  };
+  // y[i][r] = sum_j T[j*128+i] w[j][r] over the 128 columns, split in two halves
+  auto tile_product = [&](const float* T, const float* w, float* out, bool subtract) {
+    const int ii = tid % kTB32, h = tid / kTB32;
+    float s[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) s[r] = 0.0f;
+    for (int jj = h * 64; jj < h * 64 + 64; ++jj) {
+      const float tv = T[jj * kTB32 + ii];
+#pragma unroll
+      for (int r = 0; r < K; ++r) s[r] = __fmaf_rn(tv, w[jj * K + r], s[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) part[(h * kTB32 + ii) * K + r] = s[r];
+    __syncthreads();
+    for (int t = tid; t < kTB32 * K; t += 256) {
+      const float tot = part[t] + part[kTB32 * K + t];
+      out[t] = subtract ? out[t] - tot : tot;
+    }
+    __syncthreads();
+  };
+  // streamed update of owned block o with column block c (tile read from global)
+  auto apply_global = [&](int o, int c) {
+    const int rb = me + o * G;
+    const int ii = tid % kTB32, h = tid / kTB32;
+    const int64_t i = (int64_t)rb * kTB32 + ii;
+    float s[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) s[r] = 0.0f;
+    for (int j0 = h * 64; j0 < h * 64 + 64; j0 += 16) {
+      float lv[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int64_t j = (int64_t)c * kTB32 + j0 + q;
+        const bool in = i < n && j < n;
+        const float f = u16_to_f32(LU[(in ? i : 0) + (in ? j : 0) * ld], fmt);
+        lv[q] = in ? f : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+#pragma unroll
+        for (int r = 0; r < K; ++r) s[r] = __fmaf_rn(lv[q], zc[(j0 + q) * K + r], s[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) part[(h * kTB32 + ii) * K + r] = s[r];
+    __syncthreads();
+    float* a = acc + (size_t)o * kTB32 * K;
+    for (int t = tid; t < kTB32 * K; t += 256) a[t] -= part[t] + part[kTB32 * K + t];
+    __syncthreads();
+  };
+  // wait for the tagged words of block c and unpack them into zc
+  auto receive = [&](const unsigned long long* src, int c) {
+    const unsigned long long* w = src + (size_t)c * kTB32 * K;
+    const unsigned long long t0 = global_ns();
+    for (int t = tid; t < kTB32 * K; t += 256) {
+      unsigned long long word;
+      for (long long it = 0;; ++it) {
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(word) : "l"(w + t) : "memory");
+        if ((int)(word >> 32) == epoch) break;
+        if (it > kSpinLimit || ((it & 63) == 63 && global_ns() - t0 > kWaitNs)) {
+          atomicOr(status, kErrTimeout);
+          abort_flag = 1;
+          break;
+        }
+      }
+      zc[t] = __uint_as_float((unsigned)(word & 0xffffffffu));
+    }
+    __syncthreads();
+  };
+  auto publish = [&](unsigned long long* dst, int c, const float* val) {
+    unsigned long long* w = dst + (size_t)c * kTB32 * K;
+    for (int t = tid; t < kTB32 * K; t += 256)
+      asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(w + t), "l"(tag_word(val[t], epoch)) : "memory");
+  };
+  // z_c = Tinv (acc_o) for owned block o, into acc_o and zc; publish
+  auto solve = [&](int o, int c, int which, unsigned long long* dst) {
+    float* a = acc + (size_t)o * kTB32 * K;
+    tile_product(ti, a, zc, false);
+    for (int t = tid; t < kTB32 * K; t += 256) a[t] = zc[t];
+    __syncthreads();
+    publish(dst, c, zc);
+    if (which == 1) {
+      for (int t = tid; t < kTB32 * K; t += 256) {
+        const int ii = t / K, r = t % K;
+        const int64_t i = (int64_t)c * kTB32 + ii;
+        if (i < n) z[i + r * ldz] = (double)zc[t];
+      }
+    }
+  };
+
+  // ---------------- forward: L y = v ----------------
+  if (me == 0) { fetch_inv(0, 0); __syncthreads(); solve(0, 0, 0, fpub); }
+  for (int c = 0; c < nb; ++c) {
+    if (abort_flag) break;
+    const bool next_mine = c + 1 < nb && (c + 1) % G == me;
+    if (next_mine) { fetch_tile(c + 1, c); fetch_inv(0, c + 1); }
+    if (c % G == me) {
+      for (int t = tid; t < kTB32 * K; t += 256) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
+      __syncthreads();
+    } else {
+      const int last = me + (nown - 1) * G;
+      if (nown == 0 || last <= c) continue;
+      receive(fpub, c);
+      if (abort_flag) break;
+    }
+    int skip = -1;
+    if (next_mine) {
+      const int o1 = (c + 1) / G;
+      tile_product(tl, zc, acc + (size_t)o1 * kTB32 * K, true);
+      solve(o1, c + 1, 0, fpub);
+      skip = o1;
+      // zc now holds block c+1; restore block c for the remaining updates
+      receive(fpub, c);
+    }
+    for (int o = 0; o < nown; ++o)
+      if (o != skip && me + o * G > c) apply_global(o, c);
+  }
+  __syncthreads();
+
+  // ---------------- backward: U z = y ----------------
+  if ((nb - 1) % G == me && !abort_flag) { fetch_inv(1, nb - 1); __syncthreads(); solve((nb - 1) / G, nb - 1, 1, bpub); }
+  for (int c = nb - 1; c >= 0; --c) {
+    if (abort_flag) break;
+    const bool next_mine = c - 1 >= 0 && (c - 1) % G == me;
+    if (next_mine) { fetch_tile(c - 1, c); fetch_inv(1, c - 1); }
+    if (c % G == me) {
+      for (int t = tid; t < kTB32 * K; t += 256) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
+      __syncthreads();
+    } else {
+      if (nown == 0 || me >= c) continue;
+      receive(bpub, c);
+      if (abort_flag) break;
+    }
+    int skip = -1;
+    if (next_mine) {
+      const int o1 = (c - 1) / G;
+      tile_product(tl, zc, acc + (size_t)o1 * kTB32 * K, true);
+      solve(o1, c - 1, 1, bpub);
+      skip = o1;
+      receive(bpub, c);
+    }
+    for (int o = 0; o < nown; ++o)
+      if (o != skip && me + o * G < c) apply_global(o, c);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Vector kernels.  Deterministic reductions: per-thread strided partials,
 // fixed-shape block tree, per-block partials summed in order by the last CTA.
 // ---------------------------------------------------------------------------
@@ -657,7 +898,8 @@ struct SolveWs {
   double* V;         // K x (m+1) x n
   double* P;         // nchunk x n x K
   void* RS;          // nchunk x n (fp64 size)
-  void* pub;         // 2 x nb x kTB x K doubles
+  void* pub;         // 2 x round_up(n, 128) x K 8-byte words
+  float* dinv;       // 2 x nb128 x 128 x 128 inverted diagonal blocks (fp32 path)
   size_t bytes;
 };
 
@@ -690,7 +932,8 @@ SolveWs carve_solve(void* base, int64_t n, int64_t K, int m) {
   w.V = (double*)take(sizeof(double) * n * (m + 1) * K);
   w.P = (double*)take(sizeof(double) * nchunk * n * K);
   w.RS = take(sizeof(double) * nchunk * n);
-  w.pub = take(sizeof(double) * 2 * nb * kTB * K);
+  w.pub = take(sizeof(double) * 2 * round_up<int64_t>(n, kTB32) * K);
+  w.dinv = (float*)take(sizeof(float) * 2 * round_up<int64_t>(n, kTB32) * kTB32);
   w.bytes = off;
   return w;
 }
@@ -768,6 +1011,38 @@ cudaError_t precond_launch_t(int K, int64_t n, const uint16_t* LU, int64_t ld, i
   }
 }
 
+size_t precond32_smem(int64_t n, int K, int G) {
+  const int nb = (int)cdiv<int64_t>(n, kTB32);
+  const int nown = cdiv(nb, G);
+  return sizeof(float) * ((size_t)nown * kTB32 * K + kTB32 * K + 2 * kTB32 * kTB32 + 2 * kTB32 * K) + 64;
+}
+
+template <int K>
+cudaError_t precond32_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt, const float* dinv,
+                               const double* v, int64_t ldv, double* z, int64_t ldz, unsigned long long* pub,
+                               int epoch, uint32_t* status, int G, size_t smem, cudaStream_t st) {
+  auto kern = precond32_kernel<K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&n, (void*)&LU, &ld, &fmt, (void*)&dinv, (void*)&v, &ldv, &z, &ldz, &pub, &epoch, &status};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(256), args, smem, st);
+}
+
+cudaError_t precond32_launch(int K, int64_t n, const uint16_t* LU, int64_t ld, int fmt, const float* dinv,
+                             const double* v, int64_t ldv, double* z, int64_t ldz, unsigned long long* pub,
+                             int epoch, uint32_t* status, int G, size_t smem, cudaStream_t st) {
+  switch (K) {
+    case 1: return precond32_launch_k<1>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 2: return precond32_launch_k<2>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 3: return precond32_launch_k<3>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 4: return precond32_launch_k<4>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 5: return precond32_launch_k<5>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 6: return precond32_launch_k<6>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 7: return precond32_launch_k<7>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    default: return precond32_launch_k<8>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+  }
+}
+
 struct Solver {
   int64_t n;
   int K, m;
@@ -789,7 +1064,8 @@ struct Solver {
     ++epoch;
     void* tok = prof_begin(st);
     cudaError_t e = prm.precond_fp32
-                        ? precond_launch_t<float>(K, n, LU, ldlu, fmt, v, ldv, z, ldz, w, epoch, G, psmem, st)
+                        ? precond32_launch(K, n, LU, ldlu, fmt, w.dinv, v, ldv, z, ldz,
+                                           (unsigned long long*)w.pub, epoch, w.status, G, psmem, st)
                         : precond_launch_t<double>(K, n, LU, ldlu, fmt, v, ldv, z, ldz, w, epoch, G, psmem, st);
     prof_end(tok, kProfPrecond, 2.0 * (double)n * (double)n, st);
     count_launches(1);
@@ -814,8 +1090,22 @@ struct Solver {
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     // one CTA per SM at most: a cooperative launch keeps all of them resident
-    G = std::max(1, std::min(nb, sms));
-    psmem = precond_smem(n, K, G, prm.precond_fp32 != 0);
+    if (prm.precond_fp32) {
+      const int nb32 = (int)cdiv<int64_t>(n, kTB32);
+      G = std::max(1, std::min(nb32, sms));
+      psmem = precond32_smem(n, K, G);
+      if ((e = cudaMemsetAsync(w.pub, 0, sizeof(double) * 2 * round_up<int64_t>(n, kTB32) * K, st)) != cudaSuccess)
+        return e;
+      const size_t ism = sizeof(float) * 2 * kTB32 * (kTB32 + 1);
+      if ((e = cudaFuncSetAttribute(diag_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism)) !=
+          cudaSuccess)
+        return e;
+      diag_inv32_kernel<<<dim3((unsigned)nb32, 2), 128, ism, st>>>(n, LU, ldlu, fmt, w.dinv);
+      count_launches(1);
+    } else {
+      G = std::max(1, std::min(nb, sms));
+      psmem = precond_smem(n, K, G, false);
+    }
     if (psmem > 200 * 1024) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(w.st, 0, sizeof(RhsState) * kMaxK, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.flags, 0, sizeof(int) * 2 * nb, st)) != cudaSuccess) return e;
