@@ -479,6 +479,13 @@ __device__ inline unsigned long long tag_word(float v, int epoch) {
   return (unsigned long long)__float_as_uint(v) | ((unsigned long long)(unsigned)epoch << 32);
 }
 
+__device__ inline void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int K>
 __global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
                                                         int fmt, const float* __restrict__ dinv,
@@ -486,15 +493,16 @@ __global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_
                                                         double* __restrict__ z, int64_t ldz,
                                                         unsigned long long* __restrict__ pub, int epoch,
                                                         uint32_t* status) {
-  extern __shared__ float smf[];
+  extern __shared__ __align__(16) float smf[];
   const int nb = (int)cdiv<int64_t>(n, kTB32);
   const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x;
   const int nown = (nb - me + G - 1) / G;
-  float* acc = smf;                                   // [nown][128][K]
-  float* zc = acc + (size_t)nown * kTB32 * K;          // [128][K]
-  float* tl = zc + kTB32 * K;                          // [128][128] prefetched off-diagonal tile, tl[j*128+i]
-  float* ti = tl + kTB32 * kTB32;                      // [128][128] prefetched inverse diagonal, ti[j*128+i]
-  float* part = ti + kTB32 * kTB32;                    // [2][128][K]
+  float* ti = smf;                                              // [128][128] inverse diagonal, ti[j*128+i]
+  uint16_t* tl = reinterpret_cast<uint16_t*>(ti + kTB32 * kTB32);  // 3 x [128][128] 16-bit tiles, tl[j*128+i]
+  float* acc = reinterpret_cast<float*>(tl + 3 * kTB32 * kTB32);   // [nown][128][K]
+  float* zc = acc + (size_t)nown * kTB32 * K;                   // [128][K] block c
+  float* zs = zc + kTB32 * K;                                   // [128][K] block being solved
+  float* part = zs + kTB32 * K;                                 // [2][128][K]
   __shared__ int abort_flag;
   if (tid == 0) abort_flag = 0;
   unsigned long long* fpub = pub;
@@ -505,29 +513,39 @@ __global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_
       const int64_t i = (int64_t)(me + o * G) * kTB32 + ii;
       acc[((size_t)o * kTB32 + ii) * K + r] = i < n ? (float)v[i + r * ldv] : 0.0f;
     }
-  __syncthreads();
 
-  // 16-bit tile (row block rb, column block cb) of LU into tl (zero outside)
-  auto fetch_tile = [&](int rb, int cb) {
-    for (int idx = tid; idx < kTB32 * kTB32; idx += 256) {
-      const int ii = idx % kTB32, jj = idx / kTB32;
-      const int64_t i = (int64_t)rb * kTB32 + ii, j = (int64_t)cb * kTB32 + jj;
-      tl[jj * kTB32 + ii] = (i < n && j < n) ? u16_to_f32(LU[i + j * ld], fmt) : 0.0f;
+  // asynchronous copies: 16-bit tile (rb, cb) of LU into buffer slot, zero outside the matrix
+  auto fetch_tile = [&](int slot, int rb, int cb) {
+    uint16_t* dst = tl + (size_t)slot * kTB32 * kTB32;
+    const int64_t i0 = (int64_t)rb * kTB32, j0 = (int64_t)cb * kTB32;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int chunk = tid + q * 256;            // 2048 chunks of 8 rows
+      const int jj = chunk >> 4, ii = (chunk & 15) * 8;
+      const int64_t i = i0 + ii, j = j0 + jj;
+      int bytes = 0;
+      if (j < n && i < n) bytes = (int)min((int64_t)16, (n - i) * 2);
+      const uint16_t* src = bytes ? LU + i + j * ld : LU;
+      cp_async16((uint32_t)__cvta_generic_to_shared(dst + jj * kTB32 + ii), src, bytes);
     }
   };
   auto fetch_inv = [&](int which, int cb) {
-    const float4* src = reinterpret_cast<const float4*>(dinv + ((int64_t)which * nb + cb) * kTB32 * kTB32);
-    float4* dst = reinterpret_cast<float4*>(ti);
-    for (int idx = tid; idx < kTB32 * kTB32 / 4; idx += 256) dst[idx] = src[idx];
+    const float* src = dinv + ((int64_t)which * nb + cb) * kTB32 * kTB32;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int chunk = tid + q * 256;            // 4096 chunks of 4 floats
+      cp_async16((uint32_t)__cvta_generic_to_shared(ti + chunk * 4), src + chunk * 4, 16);
+    }
   };
-  // y[i][r] = sum_j T[j*128+i] w[j][r] over the 128 columns, split in two halves
-  auto tile_product = [&](const float* T, const float* w, float* out, bool subtract) {
+  // out[i][r] (-)= sum_j T(i, j) w[j][r]; T 16-bit (tile) or fp32 (inverse)
+  auto product = [&](const uint16_t* T16, const float* T32, const float* w, float* out, bool subtract) {
     const int ii = tid % kTB32, h = tid / kTB32;
     float s[K];
 #pragma unroll
     for (int r = 0; r < K; ++r) s[r] = 0.0f;
+#pragma unroll 8
     for (int jj = h * 64; jj < h * 64 + 64; ++jj) {
-      const float tv = T[jj * kTB32 + ii];
+      const float tv = T16 ? u16_to_f32(T16[jj * kTB32 + ii], fmt) : T32[jj * kTB32 + ii];
 #pragma unroll
       for (int r = 0; r < K; ++r) s[r] = __fmaf_rn(tv, w[jj * K + r], s[r]);
     }
@@ -540,37 +558,11 @@ __global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_
     }
     __syncthreads();
   };
-  // streamed update of owned block o with column block c (tile read from global)
-  auto apply_global = [&](int o, int c) {
-    const int rb = me + o * G;
-    const int ii = tid % kTB32, h = tid / kTB32;
-    const int64_t i = (int64_t)rb * kTB32 + ii;
-    float s[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) s[r] = 0.0f;
-    for (int j0 = h * 64; j0 < h * 64 + 64; j0 += 16) {
-      float lv[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int64_t j = (int64_t)c * kTB32 + j0 + q;
-        const bool in = i < n && j < n;
-        const float f = u16_to_f32(LU[(in ? i : 0) + (in ? j : 0) * ld], fmt);
-        lv[q] = in ? f : 0.0f;
-      }
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-#pragma unroll
-        for (int r = 0; r < K; ++r) s[r] = __fmaf_rn(lv[q], zc[(j0 + q) * K + r], s[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < K; ++r) part[(h * kTB32 + ii) * K + r] = s[r];
-    __syncthreads();
-    float* a = acc + (size_t)o * kTB32 * K;
-    for (int t = tid; t < kTB32 * K; t += 256) a[t] -= part[t] + part[kTB32 * K + t];
-    __syncthreads();
-  };
-  // wait for the tagged words of block c and unpack them into zc
-  auto receive = [&](const unsigned long long* src, int c) {
+  // all copies issued by this CTA have landed (ready) / all but the latest group (ready_prev)
+  auto ready = [&]() { cp_async_wait<0>(); __syncthreads(); };
+  auto ready_prev = [&]() { cp_async_wait<1>(); __syncthreads(); };
+  // wait for the tagged words of block c and unpack them into dst
+  auto receive = [&](const unsigned long long* src, int c, float* dst) {
     const unsigned long long* w = src + (size_t)c * kTB32 * K;
     const unsigned long long t0 = global_ns();
     for (int t = tid; t < kTB32 * K; t += 256) {
@@ -584,85 +576,100 @@ __global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_
           break;
         }
       }
-      zc[t] = __uint_as_float((unsigned)(word & 0xffffffffu));
+      dst[t] = __uint_as_float((unsigned)(word & 0xffffffffu));
     }
     __syncthreads();
   };
-  auto publish = [&](unsigned long long* dst, int c, const float* val) {
-    unsigned long long* w = dst + (size_t)c * kTB32 * K;
-    for (int t = tid; t < kTB32 * K; t += 256)
-      asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(w + t), "l"(tag_word(val[t], epoch)) : "memory");
-  };
-  // z_c = Tinv (acc_o) for owned block o, into acc_o and zc; publish
-  auto solve = [&](int o, int c, int which, unsigned long long* dst) {
+  // zs = Tinv acc_o, stored back into acc_o and published (backward: also into z)
+  auto solve = [&](int o, int c, bool backward, unsigned long long* dst) {
     float* a = acc + (size_t)o * kTB32 * K;
-    tile_product(ti, a, zc, false);
-    for (int t = tid; t < kTB32 * K; t += 256) a[t] = zc[t];
-    __syncthreads();
-    publish(dst, c, zc);
-    if (which == 1) {
-      for (int t = tid; t < kTB32 * K; t += 256) {
+    product(nullptr, ti, a, zs, false);
+    unsigned long long* wd = dst + (size_t)c * kTB32 * K;
+    for (int t = tid; t < kTB32 * K; t += 256) {
+      a[t] = zs[t];
+      asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(wd + t), "l"(tag_word(zs[t], epoch)) : "memory");
+      if (backward) {
         const int ii = t / K, r = t % K;
         const int64_t i = (int64_t)c * kTB32 + ii;
-        if (i < n) z[i + r * ldz] = (double)zc[t];
+        if (i < n) z[i + r * ldz] = (double)zs[t];
       }
+    }
+    __syncthreads();
+  };
+  // updates of the owned blocks `o` in [first, ...) selected by `want`, tiles double buffered in slots 1, 2
+  auto stream_updates = [&](int c, bool forward, int skip) {
+    int pending = -1, slot = 1;
+    for (int o = 0; o < nown; ++o) {
+      const int rb = me + o * G;
+      if (o == skip || (forward ? rb <= c : rb >= c)) continue;
+      if (pending < 0) { fetch_tile(slot, rb, c); cp_async_commit(); pending = o; continue; }
+      // compute the pending one while the next streams in
+      fetch_tile(3 - slot, rb, c);
+      cp_async_commit();
+      ready_prev();
+      product(tl + (size_t)slot * kTB32 * kTB32, nullptr, zc, acc + (size_t)pending * kTB32 * K, true);
+      pending = o;
+      slot = 3 - slot;
+    }
+    if (pending >= 0) {
+      ready();
+      product(tl + (size_t)slot * kTB32 * kTB32, nullptr, zc, acc + (size_t)pending * kTB32 * K, true);
     }
   };
 
   // ---------------- forward: L y = v ----------------
-  if (me == 0) { fetch_inv(0, 0); __syncthreads(); solve(0, 0, 0, fpub); }
-  for (int c = 0; c < nb; ++c) {
-    if (abort_flag) break;
+  if (me == 0) { fetch_inv(0, 0); cp_async_commit(); ready(); solve(0, 0, false, fpub); }
+  for (int c = 0; c < nb && !abort_flag; ++c) {
     const bool next_mine = c + 1 < nb && (c + 1) % G == me;
-    if (next_mine) { fetch_tile(c + 1, c); fetch_inv(0, c + 1); }
+    if (next_mine) { fetch_tile(0, c + 1, c); fetch_inv(0, c + 1); cp_async_commit(); }
     if (c % G == me) {
       for (int t = tid; t < kTB32 * K; t += 256) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
-      __syncthreads();
     } else {
       const int last = me + (nown - 1) * G;
       if (nown == 0 || last <= c) continue;
-      receive(fpub, c);
+      receive(fpub, c, zc);
       if (abort_flag) break;
     }
+    ready();
     int skip = -1;
     if (next_mine) {
       const int o1 = (c + 1) / G;
-      tile_product(tl, zc, acc + (size_t)o1 * kTB32 * K, true);
-      solve(o1, c + 1, 0, fpub);
+      product(tl, nullptr, zc, acc + (size_t)o1 * kTB32 * K, true);
+      solve(o1, c + 1, false, fpub);
       skip = o1;
-      // zc now holds block c+1; restore block c for the remaining updates
-      receive(fpub, c);
     }
-    for (int o = 0; o < nown; ++o)
-      if (o != skip && me + o * G > c) apply_global(o, c);
+    stream_updates(c, true, skip);
   }
-  __syncthreads();
+  ready();
 
   // ---------------- backward: U z = y ----------------
-  if ((nb - 1) % G == me && !abort_flag) { fetch_inv(1, nb - 1); __syncthreads(); solve((nb - 1) / G, nb - 1, 1, bpub); }
-  for (int c = nb - 1; c >= 0; --c) {
-    if (abort_flag) break;
+  if ((nb - 1) % G == me && !abort_flag) {
+    fetch_inv(1, nb - 1);
+    cp_async_commit();
+    ready();
+    solve((nb - 1) / G, nb - 1, true, bpub);
+  }
+  for (int c = nb - 1; c >= 0 && !abort_flag; --c) {
     const bool next_mine = c - 1 >= 0 && (c - 1) % G == me;
-    if (next_mine) { fetch_tile(c - 1, c); fetch_inv(1, c - 1); }
+    if (next_mine) { fetch_tile(0, c - 1, c); fetch_inv(1, c - 1); cp_async_commit(); }
     if (c % G == me) {
       for (int t = tid; t < kTB32 * K; t += 256) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
-      __syncthreads();
     } else {
       if (nown == 0 || me >= c) continue;
-      receive(bpub, c);
+      receive(bpub, c, zc);
       if (abort_flag) break;
     }
+    ready();
     int skip = -1;
     if (next_mine) {
       const int o1 = (c - 1) / G;
-      tile_product(tl, zc, acc + (size_t)o1 * kTB32 * K, true);
-      solve(o1, c - 1, 1, bpub);
+      product(tl, nullptr, zc, acc + (size_t)o1 * kTB32 * K, true);
+      solve(o1, c - 1, true, bpub);
       skip = o1;
-      receive(bpub, c);
     }
-    for (int o = 0; o < nown; ++o)
-      if (o != skip && me + o * G < c) apply_global(o, c);
+    stream_updates(c, false, skip);
   }
+  ready();
 }
 
 // ---------------------------------------------------------------------------
@@ -1014,7 +1021,8 @@ cudaError_t precond_launch_t(int K, int64_t n, const uint16_t* LU, int64_t ld, i
 size_t precond32_smem(int64_t n, int K, int G) {
   const int nb = (int)cdiv<int64_t>(n, kTB32);
   const int nown = cdiv(nb, G);
-  return sizeof(float) * ((size_t)nown * kTB32 * K + kTB32 * K + 2 * kTB32 * kTB32 + 2 * kTB32 * K) + 64;
+  return sizeof(float) * kTB32 * kTB32 + sizeof(uint16_t) * 3 * kTB32 * kTB32 +
+         sizeof(float) * ((size_t)nown * kTB32 * K + 2 * kTB32 * K + 2 * kTB32 * K) + 64;
 }
 
 template <int K>
