@@ -41,8 +41,9 @@ constexpr int kStageA = kTJ * kRowBytes;      // MMA A operand: rows j (16 KiB)
 constexpr int kStageB = kTI * kRowBytes;      // MMA B operand: rows i (16 KiB)
 constexpr int kCBox = kTJ * 128;              // one C box: 64 rows x 128 columns (16 KiB)
 constexpr int kCTile = 2 * kCBox;             // 32 KiB
-constexpr int kThreads = 192;
-constexpr int kEpiThreads = 128;
+constexpr int kEpiGroups = 2;                 // epilogue groups, one per 64-row half of the tile
+constexpr int kEpiThreads = 128;              // threads per epilogue group (one warp per TMEM lane quarter)
+constexpr int kThreads = 64 + kEpiGroups * kEpiThreads;
 
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -91,7 +92,9 @@ __device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;
 __device__ inline void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ inline void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ inline void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ inline void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+__device__ inline void epi_barrier(int group) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "n"(kEpiThreads) : "memory");
+}
 
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -163,6 +166,36 @@ __device__ inline void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
                : "memory");
 }
 
+// 64 consecutive fp32 columns: two x32 loads in flight, one wait.
+__device__ inline void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+#define HPMXP_LD32(OFF, B)                                                                                       \
+  asm volatile(                                                                                                \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, " \
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"            \
+      : "=r"(r[B + 0]), "=r"(r[B + 1]), "=r"(r[B + 2]), "=r"(r[B + 3]), "=r"(r[B + 4]), "=r"(r[B + 5]),         \
+        "=r"(r[B + 6]), "=r"(r[B + 7]), "=r"(r[B + 8]), "=r"(r[B + 9]), "=r"(r[B + 10]), "=r"(r[B + 11]),       \
+        "=r"(r[B + 12]), "=r"(r[B + 13]), "=r"(r[B + 14]), "=r"(r[B + 15]), "=r"(r[B + 16]), "=r"(r[B + 17]),   \
+        "=r"(r[B + 18]), "=r"(r[B + 19]), "=r"(r[B + 20]), "=r"(r[B + 21]), "=r"(r[B + 22]), "=r"(r[B + 23]),   \
+        "=r"(r[B + 24]), "=r"(r[B + 25]), "=r"(r[B + 26]), "=r"(r[B + 27]), "=r"(r[B + 28]), "=r"(r[B + 29]),   \
+        "=r"(r[B + 30]), "=r"(r[B + 31])                                                                        \
+      : "r"(taddr + OFF))
+  HPMXP_LD32(0u, 0);
+  HPMXP_LD32(32u, 32);
+#undef HPMXP_LD32
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]),
+                 "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]), "+r"(r[40]), "+r"(r[41]), "+r"(r[42]),
+                 "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]), "+r"(r[49]),
+                 "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]), "+r"(r[56]),
+                 "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])
+               :
+               : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), leading byte
 // offset unused for this layout (set to 16 bytes), descriptor version 1.
@@ -214,8 +247,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   auto empty = [&](int s) { return bar0 + 8u * (uint32_t)(kStages + s); };
   auto acc_full = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + b); };
   auto acc_empty = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + 2 + b); };
-  auto c_full = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + 4 + b); };
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 6);
+  auto c_full = [&](int b, int h) { return bar0 + 8u * (uint32_t)(2 * kStages + 4 + 2 * b + h); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 8);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -223,8 +256,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int s = 0; s < kStages; ++s) { mbar_init(full(s), 1); mbar_init(empty(s), 1); }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full(b), 1);
-      mbar_init(acc_empty(b), kEpiThreads / 32);
-      mbar_init(c_full(b), 1);
+      mbar_init(acc_empty(b), kEpiGroups * kEpiThreads / 32);
+      mbar_init(c_full(b, 0), 1);
+      mbar_init(c_full(b, 1), 1);
     }
     fence_mbar_init();
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
@@ -291,19 +325,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (!ok) atomicOr(p.status, kErrTimeout);
     }
   } else {
-    // epilogue: thread = output column j = j0 + jl, jl = 32 q + lane (its TMEM lane)
+    // epilogue: group g = (warp - 2) / 4 owns rows i0 + 64 g .. +63 (C box g) of the tile;
+    // thread = output column j = j0 + jl, jl = 32 q + lane (its TMEM lane)
     const int q = warp & 3;
+    const int g = (warp - 2) >> 2;
     const int jl = 32 * q + lane;
-    const bool leader = (warp == 2 && lane == 0);
+    const bool leader = ((warp - 2) & 3) == 0 && lane == 0;
     const bool load_c = p.has_c && p.mode == kEpiSub;
     int issued_c[2] = {-1, -1};   // local tile whose C load is outstanding in each buffer
-    if (leader && load_c) {       // prefetch the C tiles of the first two local tiles
+    if (leader && load_c) {       // prefetch this group's C box of the first two local tiles
       int local = 0;
       for (int t = blockIdx.x; t < p.ntiles && local < 2; t += gridDim.x, ++local) {
         const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
-        mbar_expect_tx(c_full(local), kCTile);
-        tma_load_2d(sC + local * kCTile, &tmC, i0, j0, c_full(local));
-        tma_load_2d(sC + local * kCTile + kCBox, &tmC, i0 + 64, j0, c_full(local));
+        mbar_expect_tx(c_full(local, g), kCBox);
+        tma_load_2d(sC + local * kCTile + g * kCBox, &tmC, i0 + 64 * g, j0, c_full(local, g));
         issued_c[local] = local;
       }
     }
@@ -312,90 +347,86 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++local) {
       const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
       const int cb = local & 1, ab = local % p.nbuf;
-      const uint32_t cbuf = sC + cb * kCTile;
+      const uint32_t cbox = sC + cb * kCTile + g * kCBox;
       bool w = true;
-      if (load_c) w = mbar_wait(c_full(cb), (uint32_t)((local >> 1) & 1));
+      if (load_c) w = mbar_wait(c_full(cb, g), (uint32_t)((local >> 1) & 1));
       if (leader) issued_c[cb] = -1;
       w = w && mbar_wait(acc_full(ab), (uint32_t)((local / p.nbuf) & 1));
       w = __all_sync(0xffffffffu, w);   // warp-uniform for tcgen05.ld
       if (!w) { ok = false; break; }
       tc_fence_after();
-      const uint32_t lane_addr = tmem + (uint32_t)ab * p.acc_cols + ((uint32_t)(32 * q) << 16);
+      const uint32_t lane_addr = tmem + (uint32_t)ab * p.acc_cols + ((uint32_t)(32 * q) << 16) + 64u * g;
       float sc[4] = {1.0f, 1.0f, 1.0f, 1.0f};
       if (p.fp8)
-        for (int g = 0; g < p.nkb && g < 4; ++g)
-          sc[g] = __fmul_rn(p.sA[(i0 / 128) * p.sa_ld + g], p.sB[(j0 / 128) * p.sb_ld + g]);
+        for (int s2 = 0; s2 < p.nkb && s2 < 4; ++s2)
+          sc[s2] = __fmul_rn(p.sA[(i0 / 128) * p.sa_ld + s2], p.sB[(j0 / 128) * p.sb_ld + s2]);
       const int64_t j = (int64_t)j0 + jl;
-      for (int c32 = 0; c32 < kTI / 32; ++c32) {
-        float acc[32];
-        uint32_t r[32];
+      float acc[64];
+      {
+        uint32_t r[64];
         if (p.fp8) {
 #pragma unroll
-          for (int v = 0; v < 32; ++v) acc[v] = 0.0f;
-          for (int g = 0; g < p.nkb; ++g) {
-            tmem_ld32(lane_addr + (uint32_t)(g * kTI + c32 * 32), r);
+          for (int v = 0; v < 64; ++v) acc[v] = 0.0f;
+          for (int s2 = 0; s2 < p.nkb; ++s2) {
+            tmem_ld64(lane_addr + (uint32_t)(s2 * kTI), r);
 #pragma unroll
-            for (int v = 0; v < 32; ++v) acc[v] = __fmaf_rn(__uint_as_float(r[v]), sc[g], acc[v]);
+            for (int v = 0; v < 64; ++v) acc[v] = __fmaf_rn(__uint_as_float(r[v]), sc[s2], acc[v]);
           }
         } else {
-          tmem_ld32(lane_addr + (uint32_t)(c32 * 32), r);
+          tmem_ld64(lane_addr, r);
 #pragma unroll
-          for (int v = 0; v < 32; ++v) acc[v] = __uint_as_float(r[v]);
-        }
-        // rows i0 + 32 c32 .. +31 of column j: four 16-byte chunks of the swizzled box
-        const int box = c32 >> 1;
-        const uint32_t row_addr = cbuf + box * kCBox + jl * 128;
-#pragma unroll
-        for (int k4 = 0; k4 < 4; ++k4) {
-          const int ch = (c32 & 1) * 4 + k4;
-          const uint32_t ad = row_addr + ((ch ^ (jl & 7)) << 4);
-          uint32_t outw[4];
-          if (p.mode == kEpiSub) {
-            uint32_t cw[4];
-            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
-                         : "=r"(cw[0]), "=r"(cw[1]), "=r"(cw[2]), "=r"(cw[3]) : "r"(ad) : "memory");
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const float lo = __fsub_rn(u16_to_f32((uint16_t)(cw[v] & 0xffffu), p.fmt), acc[8 * k4 + 2 * v]);
-              const float hi = __fsub_rn(u16_to_f32((uint16_t)(cw[v] >> 16), p.fmt), acc[8 * k4 + 2 * v + 1]);
-              outw[v] = pack16x2(lo, hi, p.fmt);
-            }
-          } else {
-#pragma unroll
-            for (int v = 0; v < 4; ++v)
-              outw[v] = pack16x2(p.sign * acc[8 * k4 + 2 * v], p.sign * acc[8 * k4 + 2 * v + 1], p.fmt);
-          }
-          if (p.has_c)
-            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                         ::"r"(ad), "r"(outw[0]), "r"(outw[1]), "r"(outw[2]), "r"(outw[3]) : "memory");
-          if (p.R && j < p.N) {
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              const int64_t i = (int64_t)i0 + c32 * 32 + k4 * 8 + v;
-              if (i < p.M) p.R[i * p.ldr + j] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
-            }
-          }
+          for (int v = 0; v < 64; ++v) acc[v] = __uint_as_float(r[v]);
         }
       }
-      // accumulator buffer free for the MMA warp
+      // accumulator buffer free for the MMA warp as soon as it is in registers
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty(ab));
+      // rows i0 + 64 g + 8 ch .. +7 of column j: eight 16-byte chunks of the swizzled box
+      const uint32_t row_addr = cbox + jl * 128;
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) {
+        const uint32_t ad = row_addr + ((ch ^ (jl & 7)) << 4);
+        uint32_t outw[4];
+        if (p.mode == kEpiSub) {
+          uint32_t cw[4];
+          asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(cw[0]), "=r"(cw[1]), "=r"(cw[2]), "=r"(cw[3]) : "r"(ad) : "memory");
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const float lo = __fsub_rn(u16_to_f32((uint16_t)(cw[v] & 0xffffu), p.fmt), acc[8 * ch + 2 * v]);
+            const float hi = __fsub_rn(u16_to_f32((uint16_t)(cw[v] >> 16), p.fmt), acc[8 * ch + 2 * v + 1]);
+            outw[v] = pack16x2(lo, hi, p.fmt);
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            outw[v] = pack16x2(p.sign * acc[8 * ch + 2 * v], p.sign * acc[8 * ch + 2 * v + 1], p.fmt);
+        }
+        if (p.has_c)
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                       ::"r"(ad), "r"(outw[0]), "r"(outw[1]), "r"(outw[2]), "r"(outw[3]) : "memory");
+        if (p.R && j < p.N) {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const int64_t i = (int64_t)i0 + 64 * g + 8 * ch + v;
+            if (i < p.M) p.R[i * p.ldr + j] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
+          }
+        }
+      }
       if (p.has_c) {
         fence_async_smem();
-        epi_barrier();
+        epi_barrier(g);
         if (leader) {
-          tma_store_2d(&tmC, i0, j0, cbuf);
-          tma_store_2d(&tmC, i0 + 64, j0, cbuf + kCBox);
+          tma_store_2d(&tmC, i0 + 64 * g, j0, cbox);
           bulk_commit();
-          bulk_wait_read0();   // the buffer can be refilled
-          // prefetch the C tile two local tiles ahead into this buffer
+          bulk_wait_read0();   // the box can be refilled
+          // prefetch this group's C box two local tiles ahead into the same buffer
           const int t2 = t + 2 * (int)gridDim.x;
           if (load_c && t2 < p.ntiles) {
             const int i2 = (t2 % p.tiles_i) * kTI, j2 = (t2 / p.tiles_i) * kTJ;
-            mbar_expect_tx(c_full(cb), kCTile);
-            tma_load_2d(cbuf, &tmC, i2, j2, c_full(cb));
-            tma_load_2d(cbuf + kCBox, &tmC, i2 + 64, j2, c_full(cb));
+            mbar_expect_tx(c_full(cb, g), kCBox);
+            tma_load_2d(cbox, &tmC, i2 + 64 * g, j2, c_full(cb, g));
             issued_c[cb] = local + 2;
           }
         }
@@ -406,7 +437,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       bulk_wait0();
       // C loads issued for tiles this CTA did not reach (error path) land before exit
       for (int b = 0; b < 2; ++b)
-        if (issued_c[b] >= 0 && !mbar_wait(c_full(b), (uint32_t)((issued_c[b] >> 1) & 1)))
+        if (issued_c[b] >= 0 && !mbar_wait(c_full(b, g), (uint32_t)((issued_c[b] >> 1) & 1)))
           atomicOr(p.status, kErrTimeout);
     }
   }
@@ -450,7 +481,7 @@ bool make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows, 
 }
 
 constexpr size_t kSmemBytes =
-    1024 + (size_t)kStages * (kStageA + kStageB) + 2 * kCTile + 8 * (2 * kStages + 6) + 16;
+    1024 + (size_t)kStages * (kStageA + kStageB) + 2 * kCTile + 8 * (2 * kStages + 8) + 16;
 
 int num_sms() {
   static int sms = 0;
@@ -510,7 +541,7 @@ cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     configured_for = dev;
   }
-  const int grid = std::min(p.ntiles, num_sms());
+  const int grid = std::min(p.ntiles, g.max_ctas > 0 ? std::min(g.max_ctas, num_sms()) : num_sms());
   const double flops = 2.0 * g.M * (double)g.N * g.K;
   void* tok = prof_begin(st);
   gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, tc, p);

@@ -96,6 +96,7 @@ struct GemmArgs {
   const float* sA; int sa_ld;
   const float* sB; int sb_ld;
   uint32_t* status;
+  int max_ctas;         // 0: one CTA per SM; else at most this many (leaves SMs for concurrent work)
 };
 cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st);
 cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st);

@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace hpmxp {
 namespace {
@@ -490,14 +491,14 @@ __global__ void __launch_bounds__(256) quant_tile_kernel(const uint16_t* __restr
 // ---------------------------------------------------------------------------
 struct FactorWs {
   uint32_t* status;
-  uint16_t* Lp;      // packed column panel, row major, n x NB
+  uint16_t* Lp[2];   // packed column panel, row major, n x NB, by step parity
   uint16_t* Li;      // packed inner column panel, row major, NB x 128
   uint16_t* Aop;     // 4 row-panel operands [W_s | Linv_ss], 128 x NB each
   uint16_t* Bop;     // 4 column-panel operands [Z_s^T | Uinv_ss^T], 128 x NB each
-  uint8_t* Lq;       // fp8 column panel, n x NB bytes
-  uint8_t* Uq;       // fp8 row panel, n x NB bytes (K-major per column)
-  float* sL;         // fp8 scales, (n/128) x 4
-  float* sU;
+  uint8_t* Lq[2];    // fp8 column panel, n x NB bytes, by step parity
+  uint8_t* Uq[2];    // fp8 row panel, n x NB bytes (K-major per column)
+  float* sL[2];      // fp8 scales, (n/128) x 4
+  float* sU[2];
   size_t bytes;
 };
 
@@ -511,15 +512,17 @@ FactorWs carve(void* base, int64_t n, int prec, int NB) {
   };
   const int64_t nr = round_up<int64_t>(n, kB);
   w.status = (uint32_t*)take(256);
-  w.Lp = (uint16_t*)take(sizeof(uint16_t) * nr * NB);
+  for (int q = 0; q < 2; ++q) w.Lp[q] = (uint16_t*)take(sizeof(uint16_t) * nr * NB);
   w.Li = (uint16_t*)take(sizeof(uint16_t) * (size_t)NB * kB);
   w.Aop = (uint16_t*)take(sizeof(uint16_t) * 4 * kB * NB);
   w.Bop = (uint16_t*)take(sizeof(uint16_t) * 4 * kB * NB);
   if (prec == HPMXP_FP8_E4M3) {
-    w.Lq = (uint8_t*)take((size_t)nr * NB);
-    w.Uq = (uint8_t*)take((size_t)nr * NB);
-    w.sL = (float*)take(sizeof(float) * (nr / kB) * 4);
-    w.sU = (float*)take(sizeof(float) * (nr / kB) * 4);
+    for (int q = 0; q < 2; ++q) {
+      w.Lq[q] = (uint8_t*)take((size_t)nr * NB);
+      w.Uq[q] = (uint8_t*)take((size_t)nr * NB);
+      w.sL[q] = (float*)take(sizeof(float) * (nr / kB) * 4);
+      w.sU[q] = (float*)take(sizeof(float) * (nr / kB) * 4);
+    }
   }
   w.bytes = off;
   return w;
@@ -566,7 +569,7 @@ struct Factorizer {
 
   // Panels and Schur update of one sub-step inside a diagonal block wider than
   // 128: sub-block at kk (width 128) of the block ending at e.
-  void inner_step(int64_t kk, int slot, int64_t e) {
+  void inner_step(int64_t kk, int slot, int64_t e, int max_ctas) {
     const int64_t m = e - (kk + kB);
     if (m <= 0) return;
     GemmArgs u{};   // U12 = st(Linv A12), in place
@@ -575,6 +578,7 @@ struct Factorizer {
     u.B = at(kk, kk + kB); u.ldb = ld;
     u.C = at(kk, kk + kB); u.ldc = ld;
     u.mode = kEpiStore; u.sign = 1.0f;
+    u.max_ctas = max_ctas;
     gemm(u);
     pack(m, kB, at(kk + kB, kk), w.Li, kB);
     GemmArgs l{};   // L21 = st(A21 Uinv): column major into LU, row major over the packed copy
@@ -584,6 +588,7 @@ struct Factorizer {
     l.C = at(kk + kB, kk); l.ldc = ld;
     l.R = w.Li; l.ldr = kB;
     l.mode = kEpiStore; l.sign = 1.0f;
+    l.max_ctas = max_ctas;
     gemm(l);
     GemmArgs t{};   // A22 <- st(A22 - L21 U12)
     t.M = (int)m; t.N = (int)m; t.K = kB;
@@ -591,23 +596,41 @@ struct Factorizer {
     t.B = at(kk, kk + kB); t.ldb = ld;
     t.C = at(kk + kB, kk + kB); t.ldc = ld;
     t.mode = kEpiSub;
+    t.max_ctas = max_ctas;
     gemm(t);
   }
 
+  // Look-ahead schedule.  Step k's Schur update is split into "near" (the
+  // next block's column and row, on the caller's stream `st`) and "far" (the
+  // rest, on the side stream `st2`).  Step k+1's diagonal block and panels run
+  // on `st` while far(k) runs on `st2`; near(k+1) waits for far(k).  far(k)
+  // is held below the SM count (and the panel products at `reserve` CTAs)
+  // so both streams make progress.  Buffers read by far(k) are double
+  // buffered by step parity.
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t evP = nullptr, evF = nullptr;
+  int reserve = 0, sms = 0;
+
   void run() {
-    for (int64_t k = 0; k < n && err == cudaSuccess; k += NB) {
+    const bool overlap = st2 != nullptr;
+    int step = 0;
+    bool far_pending = false;
+    for (int64_t k = 0; k < n && err == cudaSuccess; k += NB, ++step) {
       const int64_t b = std::min<int64_t>(NB, n - k);
       const int nsub = (int)cdiv<int64_t>(b, kB);
+      const int par = step & 1;
+      uint16_t* Lp = w.Lp[par];
+      const int panel_ctas = overlap && far_pending ? reserve : 0;
       // (i) diagonal block
       for (int s = 0; s < nsub; ++s) {
         const int64_t kk = k + (int64_t)s * kB;
         getrf_base(kk, (int)std::min<int64_t>(kB, k + b - kk), s);
-        if (nsub > 1) inner_step(kk, s, k + b);
+        if (nsub > 1) inner_step(kk, s, k + b, panel_ctas);
       }
       const int64_t m = n - (k + b);
       if (m <= 0) break;
       // (ii) row panel U12 and column panel L21, block substitution over s
-      pack(m, (int)b, at(k + b, k), w.Lp, NB);
+      pack(m, (int)b, at(k + b, k), Lp, NB);
       for (int s = 0; s < nsub; ++s) {
         const int64_t s0 = k + (int64_t)s * kB;
         if (s > 0) {
@@ -624,40 +647,82 @@ struct Factorizer {
         u.B = at(k, k + b); u.ldb = ld;
         u.C = at(s0, k + b); u.ldc = ld;
         u.mode = kEpiStore; u.sign = 1.0f;
+        u.max_ctas = panel_ctas;
         gemm(u);
         GemmArgs l{};
         l.M = (int)m; l.N = kB; l.K = (s + 1) * kB;
-        l.A = w.Lp; l.lda = NB;
+        l.A = Lp; l.lda = NB;
         l.B = bop(s); l.ldb = NB;
         l.C = at(k + b, s0); l.ldc = ld;
-        l.R = w.Lp + s * kB; l.ldr = NB;
+        l.R = Lp + s * kB; l.ldr = NB;
         l.mode = kEpiStore; l.sign = 1.0f;
+        l.max_ctas = panel_ctas;
         gemm(l);
       }
-      // (iii) Schur update of depth b
+      // (iii) Schur update of depth b: A22 <- st(A22 - L21 U12)
       GemmArgs t{};
-      t.M = (int)m; t.N = (int)m; t.K = (int)b;
-      t.C = at(k + b, k + b); t.ldc = ld;
+      t.K = (int)b;
       t.mode = kEpiSub;
+      const uint8_t* qL = nullptr;
+      const uint8_t* qU = nullptr;
       if (prec == HPMXP_FP8_E4M3) {
         const int ng = nsub;
         quant_tile_kernel<<<dim3((unsigned)cdiv<int64_t>(m, kB), ng), 256, 0, st>>>(
-            w.Lp, NB, 1, m, (int)b, fmt, w.Lq, NB, w.sL, 4);
+            Lp, NB, 1, m, (int)b, fmt, w.Lq[par], NB, w.sL[par], 4);
         quant_tile_kernel<<<dim3((unsigned)cdiv<int64_t>(m, kB), ng), 256, 0, st>>>(
-            at(k, k + b), ld, 0, m, (int)b, fmt, w.Uq, NB, w.sU, 4);
+            at(k, k + b), ld, 0, m, (int)b, fmt, w.Uq[par], NB, w.sU[par], 4);
         count_launches(2);
         check(cudaGetLastError());
         t.fp8 = 1;
-        t.A = w.Lq; t.lda = NB;
-        t.B = w.Uq; t.ldb = NB;
-        t.sA = w.sL; t.sa_ld = 4;
-        t.sB = w.sU; t.sb_ld = 4;
+        t.lda = NB; t.ldb = NB;
+        t.sa_ld = 4; t.sb_ld = 4;
+        qL = w.Lq[par];
+        qU = w.Uq[par];
       } else {
-        t.A = w.Lp; t.lda = NB;
-        t.B = at(k, k + b); t.ldb = ld;
+        t.lda = NB; t.ldb = ld;
       }
-      gemm(t);
+      // operand views for rows [r0, r0+M) of L21 and columns [c0, c0+N) of U12 (offsets from k+b)
+      auto part = [&](int64_t r0, int64_t M, int64_t c0, int64_t N, int max_ctas) {
+        GemmArgs g = t;
+        g.M = (int)M; g.N = (int)N;
+        if (g.fp8) {
+          g.A = qL + r0 * NB; g.B = qU + c0 * NB;
+          g.sA = w.sL[par] + (r0 / kB) * 4; g.sB = w.sU[par] + (c0 / kB) * 4;
+        } else {
+          g.A = Lp + r0 * NB; g.B = at(k, k + b + c0);
+        }
+        g.C = at(k + b + r0, k + b + c0); g.ldc = ld;
+        g.max_ctas = max_ctas;
+        gemm(g);
+      };
+      if (!overlap) {
+        part(0, m, 0, m, 0);
+        continue;
+      }
+      const int64_t b1 = std::min<int64_t>(NB, m);   // next diagonal block
+      check(cudaEventRecord(evP, st));
+      if (far_pending) check(cudaStreamWaitEvent(st, evF, 0));
+      // near(k): the next block's column (all rows) and its row (remaining columns);
+      // held to `reserve` CTAs so that far(k), which becomes ready at the same
+      // moment, cannot take every SM and delay it
+      part(0, m, 0, b1, reserve);
+      if (m > b1) part(0, b1, b1, m - b1, reserve);
+      // far(k) on the side stream, after this step's panels
+      if (m > b1) {
+        check(cudaStreamWaitEvent(st2, evP, 0));
+        {
+          cudaStream_t keep = st;
+          st = st2;
+          part(b1, m - b1, b1, m - b1, sms - reserve);
+          st = keep;
+        }
+        check(cudaEventRecord(evF, st2));
+        far_pending = true;
+      } else {
+        far_pending = false;
+      }
     }
+    if (overlap && far_pending) check(cudaStreamWaitEvent(st, evF, 0));
   }
 };
 
@@ -673,6 +738,31 @@ cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st) {
   gemm_simt_kernel<<<grid, 256, 0, st>>>(g);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// Side stream and events of the look-ahead schedule, one set per device,
+// created on first use and kept for the life of the process.
+struct SideStream {
+  std::mutex mu;   // one look-ahead factorization enqueues on this device at a time
+  bool ok = false;
+  cudaStream_t st = nullptr;
+  cudaEvent_t evP = nullptr, evF = nullptr;
+};
+
+SideStream& side_stream(int dev) {
+  static SideStream tab[64];
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  SideStream& s = tab[dev & 63];
+  if (!s.ok) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&s.st, cudaStreamNonBlocking, lo) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s.evP, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s.evF, cudaEventDisableTiming) == cudaSuccess)
+      s.ok = true;
+  }
+  return s;
 }
 
 cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st) {
@@ -704,7 +794,18 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
   f.st = st;
   f.check(cudaMemsetAsync(f.w.status, 0, sizeof(uint32_t), st));
   f.check(launch_cast(n, A, lda, LU, ldlu, f.fmt, st));
+  SideStream& ss = side_stream(dev);
+  std::unique_lock<std::mutex> lk(ss.mu, std::defer_lock);
+  if (ss.ok && n > 2 * nb && getenv("HPMXP_NO_LOOKAHEAD") == nullptr) {
+    lk.lock();
+    f.st2 = ss.st;
+    f.evP = ss.evP;
+    f.evF = ss.evF;
+    cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
+    f.reserve = std::max(4, f.sms / 12);
+  }
   f.run();
+  if (lk.owns_lock()) lk.unlock();
   if (f.err != cudaSuccess) return status_from_cuda(f.err);
   uint32_t word = 0;
   cudaError_t e = cudaMemcpyAsync(&word, f.w.status, sizeof(word), cudaMemcpyDeviceToHost, st);
