@@ -610,6 +610,7 @@ struct Factorizer {
   cudaStream_t st2 = nullptr;
   cudaEvent_t evP = nullptr, evF = nullptr;
   int reserve = 0, sms = 0;
+  int64_t overlap_min = 8192;   // smallest far(k) trailing size run concurrently
 
   void run() {
     const bool overlap = st2 != nullptr;
@@ -700,25 +701,28 @@ struct Factorizer {
         continue;
       }
       const int64_t b1 = std::min<int64_t>(NB, m);   // next diagonal block
-      check(cudaEventRecord(evP, st));
       if (far_pending) check(cudaStreamWaitEvent(st, evF, 0));
-      // near(k): the next block's column (all rows) and its row (remaining columns);
-      // held to `reserve` CTAs so that far(k), which becomes ready at the same
-      // moment, cannot take every SM and delay it
-      part(0, m, 0, b1, reserve);
-      if (m > b1) part(0, b1, b1, m - b1, reserve);
-      // far(k) on the side stream, after this step's panels
-      if (m > b1) {
+      // near(k): the next block's column (all rows) and its row (remaining
+      // columns), on every SM, before far(k) is released
+      part(0, m, 0, b1, 0);
+      if (m > b1) part(0, b1, b1, m - b1, 0);
+      // far(k) on the side stream, held below the SM count so that step k+1's
+      // diagonal block and panels (on `reserve` SMs) overlap it; for small
+      // trailing matrices the panels would be starved, so no overlap there
+      const int64_t mf = m - b1;
+      if (mf > 0 && mf >= overlap_min) {
+        check(cudaEventRecord(evP, st));
         check(cudaStreamWaitEvent(st2, evP, 0));
         {
           cudaStream_t keep = st;
           st = st2;
-          part(b1, m - b1, b1, m - b1, sms - reserve);
+          part(b1, mf, b1, mf, sms - reserve);
           st = keep;
         }
         check(cudaEventRecord(evF, st2));
         far_pending = true;
       } else {
+        if (mf > 0) part(b1, mf, b1, mf, 0);
         far_pending = false;
       }
     }
@@ -803,6 +807,7 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
     f.evF = ss.evF;
     cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
     f.reserve = std::max(4, f.sms / 12);
+    if (const char* om = getenv("HPMXP_OVERLAP_MIN")) f.overlap_min = atoll(om);
   }
   f.run();
   if (lk.owns_lock()) lk.unlock();
