@@ -46,7 +46,10 @@ def parse():
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--nb", type=int, default=0, help="Schur update depth; 0 = autotune over 128/256/512")
     ap.add_argument("--prec", default="bf16", choices=list(PREC))
-    ap.add_argument("--precond-fp32", type=int, default=-1, help="-1 = library default")
+    ap.add_argument("--precond-fp32", type=int, default=1,
+                    help="1: fp32 inner-GMRES operator (the benchmark default), 0: all fp64")
+    ap.add_argument("--inner-tol", type=float, default=-1.0,
+                    help="inner GMRES tolerance floor; -1: 1e-5 with the fp32 operator, library default otherwise")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -144,6 +147,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
+IR_KW = {}   # refinement parameters of the GPU arm, mirrored by the oracle legs
+
+
 def oracle_solve_timed(n: int, seed: int, prec: str, nb: int):
     import oracle
     A, b = oracle.generate(n, seed)
@@ -151,7 +157,7 @@ def oracle_solve_timed(n: int, seed: int, prec: str, nb: int):
     upd = oracle.E4M3 if prec == "fp8" else None
     t0 = time.perf_counter()
     LU, _ = oracle.factor(A, fmt, nb, fmt_update=upd)
-    X, info, rc = oracle.solve_ir(A, LU, b)
+    X, info, rc = oracle.solve_ir(A, LU, b, **IR_KW)
     dt = time.perf_counter() - t0
     return dt, info[0], rc
 
@@ -207,6 +213,8 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
+    IR_KW.update(precond_prec=args.precond_fp32,
+                 inner_tol=args.inner_tol if args.inner_tol >= 0 else (1e-5 if args.precond_fp32 else 1e-12))
     if args.impl == "reference":
         run_reference(args)
         return
@@ -222,8 +230,11 @@ def main():
 
     A, b = api.generate(n, seed=args.seed, device=dev)          # untimed (paper: generation not timed)
     params = capi.hpmxp_ir_params_default()
-    if args.precond_fp32 >= 0:
-        params.precond_fp32 = args.precond_fp32
+    params.precond_fp32 = args.precond_fp32
+    if args.inner_tol >= 0:
+        params.inner_tol = args.inner_tol
+    elif args.precond_fp32:
+        params.inner_tol = 1e-5
     nb = args.nb or autotune.pick_nb(n, prec, A, device=dev)
     solver = api.Solver(n, 1, prec, nb, device=dev, params=params)
     stream = torch.cuda.current_stream(dev)
@@ -260,8 +271,8 @@ def main():
     solver(A, b)
     torch.cuda.synchronize(dev)
     capi.hpmxp_prof_enable(False)
-    kinds = {"gemm": capi.PROF_GEMM, "gemv": capi.PROF_GEMV, "precond": capi.PROF_PRECOND,
-             "getrf": capi.PROF_GETRF}
+    kinds = {"gemm": capi.PROF_GEMM, "gemv": capi.PROF_GEMV, "gemv32": capi.PROF_GEMV32,
+             "precond": capi.PROF_PRECOND, "getrf": capi.PROF_GETRF}
     prof = {k: capi.hpmxp_prof_read(v) for k, v in kinds.items()}
     g = prof["gemm"]
     bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0

@@ -129,7 +129,9 @@ typedef struct {
   double inner_tol;      /* relative floor of the inner stopping test (default 1e-12) */
   double theta;          /* adaptive inner-stopping factor, 0 disables (default 0.1) */
   double accept;         /* acceptance threshold of the scaled residual (default 16) */
-  int32_t precond_fp32;  /* 1: apply M^{-1} in fp32 arithmetic, 0: fp64 (default 0) */
+  int32_t precond_fp32;  /* 1: the inner GMRES operator (M^{-1} and the Arnoldi product A v) in fp32
+                            arithmetic; the residual, orthogonalization, rotations and update stay
+                            fp64.  0: everything fp64 (default 0) */
   int32_t reserved;
 } hpmxp_ir_params;
 
@@ -182,6 +184,7 @@ hpmxp_status hpmxp_residual(int64_t n, const double* A, int64_t lda, const doubl
  *   kind 1  fp64 GEMV (residual)    work = 8 n^2 bytes of A per launch
  *   kind 2  preconditioner apply    work = 2 n^2 bytes of factors per launch
  *   kind 3  diagonal-block getrf    work = 2 b^3 flops per launch
+ *   kind 4  fp32 GEMV (Arnoldi product with the fp32 operator)  work = 8 n^2 bytes of A
  * hpmxp_prof_read synchronizes the recorded events and returns the summed
  * event time, work and launch count of one kind since the last reset.
  * Returns HPMXP_EINVAL for a bad kind or NULL output. */

@@ -402,6 +402,26 @@ void precond_apply(int64_t n, const double* LU, int64_t ld, const double* v, dou
   for (int64_t i = 0; i < n; ++i) z[i] = (double)y[i];
 }
 
+// w = A v with fp32 operands and accumulation: A_ij truncated toward zero to
+// fp32, v_j rounded to nearest fp32, products accumulated by fused
+// multiply-add in fp32, j ascending (the fp32 operator of GMRES when the
+// preconditioner is applied in fp32).
+void matvec_f32(int64_t n, const double* A, int64_t lda, const double* v, double* w) {
+  std::vector<float> vf((size_t)n);
+  for (int64_t j = 0; j < n; ++j) vf[j] = (float)v[j];
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    float acc = 0.0f;
+    for (int64_t j = 0; j < n; ++j) {
+      const double a = A[i + j * lda];
+      float f = (float)a;
+      if (std::fabs((double)f) > std::fabs(a)) f = std::nextafter(f, 0.0f);
+      acc = std::fmaf(f, vf[j], acc);
+    }
+    w[i] = (double)acc;
+  }
+}
+
 // r = b - A x, fp64, one fused multiply-add per term, j ascending.
 void residual_vec(int64_t n, const double* A, int64_t lda, const double* x, const double* b,
                   double* r) {
@@ -611,7 +631,9 @@ struct oracle_ir_info {
 // The inner loop of a cycle stops when the least-squares residual estimate
 // |g_{j+1}| <= beta * max(inner_tol, theta * accept / sr0), sr0 being the
 // scaled residual at the start of the cycle (theta = 0 disables the adaptive
-// term).  Arithmetic: fp64; the preconditioner in fp64 (pprec 0) or fp32 (1).
+// term).  Arithmetic: fp64; with pprec 1 the operator of the inner GMRES
+// (preconditioner and matrix-vector product) is applied in fp32 while the
+// outer residual, orthogonalization, rotations and update stay fp64.
 // Reading: "iterations" in the 50 cap are inner Arnoldi steps summed over
 // restarts.
 int oracle_solve_ir(int64_t n, const double* A, int64_t lda, const double* LU, int64_t ldlu,
@@ -651,8 +673,12 @@ int oracle_solve_ir(int64_t n, const double* A, int64_t lda, const double* LU, i
         std::vector<double> Av(n);
         std::vector<double> zero(n, 0.0);
         // w = M^{-1} (A v_j): the residual routine with b = 0 gives -A v_j
-        residual_vec(n, A, lda, &V[(size_t)j * n], zero.data(), Av.data());
-        for (int64_t i = 0; i < n; ++i) Av[i] = -Av[i];
+        if (pprec == 1) {
+          matvec_f32(n, A, lda, &V[(size_t)j * n], Av.data());
+        } else {
+          residual_vec(n, A, lda, &V[(size_t)j * n], zero.data(), Av.data());
+          for (int64_t i = 0; i < n; ++i) Av[i] = -Av[i];
+        }
         oracle_precond(n, LU, ldlu, Av.data(), w.data(), pprec);
         for (int i = 0; i <= j; ++i) {            // modified Gram-Schmidt
           const double h = dot(n, w.data(), &V[(size_t)i * n]);

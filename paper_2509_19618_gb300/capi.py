@@ -158,7 +158,7 @@ def hpmxp_prof_reset():
     load().hpmxp_prof_reset()
 
 
-PROF_GEMM, PROF_GEMV, PROF_PRECOND, PROF_GETRF = 0, 1, 2, 3
+PROF_GEMM, PROF_GEMV, PROF_PRECOND, PROF_GETRF, PROF_GEMV32 = 0, 1, 2, 3, 4
 
 
 def hpmxp_prof_read(kind: int) -> dict:

@@ -44,6 +44,18 @@ __device__ inline float abs_f32_est(double a) {
   return t > 0 ? __int_as_float(min(t, 0x7f7fffff >> 3) << 3) : 0.0f;
 }
 
+// fp64 -> fp32 truncated toward zero, integer operations only (exponent
+// rebias and the top 23 mantissa bits; values below the fp32 normal range
+// flush to zero, which the generated systems never produce).
+__device__ inline float trunc_f32(double a) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const int e = (int)((hi >> 20) & 0x7ff) - 896;          // fp32 biased exponent
+  const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t sign = hi & 0x80000000u;
+  return e > 0 ? __uint_as_float(sign | ((uint32_t)min(e, 255) << 23) | mant) : __uint_as_float(sign);
+}
+
 // ---------------------------------------------------------------------------
 // Per right-hand-side state of the refinement (device memory).
 // ---------------------------------------------------------------------------
@@ -78,7 +90,7 @@ struct SolveParams {
 // ---------------------------------------------------------------------------
 constexpr int kGemvRows = 256;
 
-template <int K, int kAbs>   // kAbs: 0 none, 1 fp32 estimate, 2 fp64 exact
+template <int K, int kAbs, bool kF32 = false>   // kAbs: 0 none, 1 fp32 estimate, 2 fp64 exact
 __global__ void __launch_bounds__(128) gemv_partial_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
                                                            const double* __restrict__ X, int64_t ldx,
                                                            int64_t chunk, double* __restrict__ P,
@@ -87,8 +99,9 @@ __global__ void __launch_bounds__(128) gemv_partial_kernel(int64_t n, const doub
   const int64_t i = (int64_t)blockIdx.x * kGemvRows + 2 * threadIdx.x;
   const int64_t j0 = (int64_t)blockIdx.y * chunk, j1 = min(j0 + chunk, n);
   double acc0[K], acc1[K];
+  float facc0[K], facc1[K];
 #pragma unroll
-  for (int r = 0; r < K; ++r) { acc0[r] = 0.0; acc1[r] = 0.0; }
+  for (int r = 0; r < K; ++r) { acc0[r] = 0.0; acc1[r] = 0.0; facc0[r] = 0.0f; facc1[r] = 0.0f; }
   float s0 = 0.0f, s1 = 0.0f;
   double d0 = 0.0, d1 = 0.0;
   const bool two = i + 1 < n;
@@ -114,11 +127,22 @@ __global__ void __launch_bounds__(128) gemv_partial_kernel(int64_t n, const doub
           a1 = two ? col[1] : 0.0;
         }
         col += lda;
+        if (kF32) {
+          // fp32 operator: A truncated to fp32, products accumulated in fp32
+          const float f0 = trunc_f32(a0), f1 = trunc_f32(a1);
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-          const double xv = xs[r * 64 + jj];
-          acc0[r] = __fma_rn(a0, xv, acc0[r]);
-          acc1[r] = __fma_rn(a1, xv, acc1[r]);
+          for (int r = 0; r < K; ++r) {
+            const float xv = (float)xs[r * 64 + jj];
+            facc0[r] = __fmaf_rn(f0, xv, facc0[r]);
+            facc1[r] = __fmaf_rn(f1, xv, facc1[r]);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < K; ++r) {
+            const double xv = xs[r * 64 + jj];
+            acc0[r] = __fma_rn(a0, xv, acc0[r]);
+            acc1[r] = __fma_rn(a1, xv, acc1[r]);
+          }
         }
         if (kAbs == 1) { s0 += abs_f32_est(a0); s1 += abs_f32_est(a1); }
         if (kAbs == 2) { d0 += fabs(a0); d1 += fabs(a1); }
@@ -129,8 +153,8 @@ __global__ void __launch_bounds__(128) gemv_partial_kernel(int64_t n, const doub
   double* Pc = P + (int64_t)blockIdx.y * n * K;
 #pragma unroll
   for (int r = 0; r < K; ++r) {
-    Pc[i + r * n] = acc0[r];
-    if (two) Pc[i + 1 + r * n] = acc1[r];
+    Pc[i + r * n] = kF32 ? (double)facc0[r] : acc0[r];
+    if (two) Pc[i + 1 + r * n] = kF32 ? (double)facc1[r] : acc1[r];
   }
   if (kAbs == 1) {
     float* R = (float*)RS + (int64_t)blockIdx.y * n;
@@ -950,7 +974,8 @@ cudaError_t gemv_k(int64_t n, const double* A, int64_t lda, const double* X, int
                    double* P, void* RS, int nchunk, cudaStream_t st) {
   const int64_t chunk = cdiv<int64_t>(n, nchunk);
   dim3 grid((unsigned)cdiv<int64_t>(n, kGemvRows), (unsigned)nchunk);
-  if (abs_mode == 0) gemv_partial_kernel<K, 0><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  if (abs_mode == 3) gemv_partial_kernel<K, 0, true><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  else if (abs_mode == 0) gemv_partial_kernel<K, 0><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
   else if (abs_mode == 1) gemv_partial_kernel<K, 1><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
   else gemv_partial_kernel<K, 2><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
   return cudaGetLastError();
@@ -975,8 +1000,9 @@ cudaError_t residual(int64_t n, int K, const double* A, int64_t lda, const doubl
   }
   if (e != cudaSuccess) return e;
   gemv_finish_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, nchunk, w.P, B, ldb, out, ldo, X, ldx,
-                                                                      abs_mode, w.RS, w.st, track);
-  prof_end(tok, kProfGemv, 8.0 * (double)n * (double)n, st);
+                                                                      abs_mode == 3 ? 0 : abs_mode, w.RS, w.st,
+                                                                      track);
+  prof_end(tok, abs_mode == 3 ? kProfGemv32 : kProfGemv, 8.0 * (double)n * (double)n, st);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -1150,9 +1176,9 @@ struct Solver {
       if ((e = read_brief()) != cudaSuccess) return e;
       if (!any(&Brief::outer_active)) break;
       for (int j = 0; j < m && any(&Brief::cycle_active); ++j) {
-        // w = M^{-1} (A v_j)
-        if ((e = residual(n, K, A, lda, w.V + (int64_t)j * n, ldv_rhs(), nullptr, 0, w.tmp, n, 0, 0, w, st)) !=
-            cudaSuccess)
+        // w = M^{-1} (A v_j); with the fp32 preconditioner the product is fp32 too
+        if ((e = residual(n, K, A, lda, w.V + (int64_t)j * n, ldv_rhs(), nullptr, 0, w.tmp, n,
+                          prm.precond_fp32 ? 3 : 0, 0, w, st)) != cudaSuccess)
           return e;
         if ((e = precond(w.tmp, n, w.w, n)) != cudaSuccess) return e;
         for (int i = 0; i <= j + 1; ++i)

@@ -330,6 +330,26 @@ def test_solve_against_oracle(n, nb, prec, k):
         assert info[c]["iters"] <= 50
 
 
+@pytest.mark.parametrize("n,nb,k", [(300, 128, 1), (1024, 128, 2), (2049, 512, 1), (4096, 512, 3)])
+def test_solve_fp32_operator_against_oracle(n, nb, k):
+    # inner GMRES operator (preconditioner and Arnoldi product) in fp32, same
+    # parameters on both sides
+    A, b = api.generate(n, seed=n + 3, nrhs=k, device=DEV)
+    LU = api.factor(A, capi.BF16, nb)
+    x, info, st = api.solve_ir(A, LU, b, capi.BF16, api.ir_params(precond_fp32=1, inner_tol=1e-5))
+    torch.cuda.synchronize()
+    sr = api.residual(A, x, b)
+    A_o, b_o = oracle.generate(n, n + 3, nrhs=k)
+    LU_o, _ = oracle.factor(A_o, oracle.BF16, nb)
+    X_o, info_o, rc = oracle.solve_ir(A_o, LU_o, b_o, precond_prec=1, inner_tol=1e-5)
+    xg = to_np(x)
+    assert st == capi.OK and rc == 0
+    for c in range(k):
+        assert sr[c] < 16.0
+        assert np.abs(xg[:, c] - X_o[:, c]).max() <= 1e-10 * np.abs(X_o[:, c]).max()
+        assert abs(info[c]["iters"] - info_o[c]["iters"]) <= 1
+
+
 def test_solve_fp32_preconditioner():
     n = 2000
     A, b = api.generate(n, seed=5, device=DEV)
