@@ -86,18 +86,29 @@ struct SolveParams {
 // ---------------------------------------------------------------------------
 // GEMV: P[c][i + r*n] = sum_{j in chunk c} A(i, j) X(j, r); optional |A| row
 // sums (fp32 estimate or exact fp64) into RS[c][i].
-// 128 threads x 2 rows = 256 rows per CTA, columns of the chunk in order.
+// 256 threads x 2 rows = 512 rows per CTA; the chunk's X is staged in shared
+// memory once; each thread keeps 8 independent 16-byte column loads in
+// flight (HBM bytes in flight per SM is what bounds this kernel).
 // ---------------------------------------------------------------------------
-constexpr int kGemvRows = 256;
+constexpr int kGemvRows = 512;
+constexpr int kGemvThreads = 256;
+constexpr int kGemvChunkElems = 4096;   // columns x right-hand sides staged per CTA
 
 template <int K, int kAbs, bool kF32 = false>   // kAbs: 0 none, 1 fp32 estimate, 2 fp64 exact
-__global__ void __launch_bounds__(128) gemv_partial_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
-                                                           const double* __restrict__ X, int64_t ldx,
-                                                           int64_t chunk, double* __restrict__ P,
-                                                           void* __restrict__ RS) {
-  __shared__ double xs[64 * K];
+__global__ void __launch_bounds__(kGemvThreads) gemv_partial_kernel(int64_t n, const double* __restrict__ A,
+                                                                    int64_t lda, const double* __restrict__ X,
+                                                                    int64_t ldx, int64_t chunk,
+                                                                    double* __restrict__ P, void* __restrict__ RS) {
+  __shared__ double xs[kGemvChunkElems];   // xs[r * chunk + jj]
   const int64_t i = (int64_t)blockIdx.x * kGemvRows + 2 * threadIdx.x;
   const int64_t j0 = (int64_t)blockIdx.y * chunk, j1 = min(j0 + chunk, n);
+  const int cnt = (int)(j1 - j0);
+  for (int t = threadIdx.x; t < cnt * K; t += kGemvThreads) {
+    const int jj = t % cnt, r = t / cnt;
+    xs[r * chunk + jj] = X[j0 + jj + r * ldx];
+  }
+  __syncthreads();
+  if (i >= n) return;
   double acc0[K], acc1[K];
   float facc0[K], facc1[K];
 #pragma unroll
@@ -106,50 +117,44 @@ __global__ void __launch_bounds__(128) gemv_partial_kernel(int64_t n, const doub
   double d0 = 0.0, d1 = 0.0;
   const bool two = i + 1 < n;
   const bool vec = two && ((((uintptr_t)(A + i)) & 15) == 0) && ((lda & 1) == 0);
-  for (int64_t jb = j0; jb < j1; jb += 64) {
-    const int cnt = (int)min((int64_t)64, j1 - jb);
-    __syncthreads();
-    for (int t = threadIdx.x; t < cnt * K; t += 128) {
-      const int jj = t % cnt, r = t / cnt;
-      xs[r * 64 + jj] = X[jb + jj + r * ldx];
-    }
-    __syncthreads();
-    if (i < n) {
-      const double* col = A + i + jb * lda;
-#pragma unroll 4
-      for (int jj = 0; jj < cnt; ++jj) {
-        double a0, a1;
-        if (vec) {
-          const double2 v = *reinterpret_cast<const double2*>(col);
-          a0 = v.x; a1 = v.y;
-        } else {
-          a0 = col[0];
-          a1 = two ? col[1] : 0.0;
-        }
-        col += lda;
-        if (kF32) {
-          // fp32 operator: A truncated to fp32, products accumulated in fp32
-          const float f0 = trunc_f32(a0), f1 = trunc_f32(a1);
+  const double* col = A + i + j0 * lda;
+  auto body = [&](double a0, double a1, int jj) {
+    if (kF32) {
+      // fp32 operator: A truncated to fp32, products accumulated in fp32
+      const float f0 = trunc_f32(a0), f1 = trunc_f32(a1);
 #pragma unroll
-          for (int r = 0; r < K; ++r) {
-            const float xv = (float)xs[r * 64 + jj];
-            facc0[r] = __fmaf_rn(f0, xv, facc0[r]);
-            facc1[r] = __fmaf_rn(f1, xv, facc1[r]);
-          }
-        } else {
+      for (int r = 0; r < K; ++r) {
+        const float xv = (float)xs[r * chunk + jj];
+        facc0[r] = __fmaf_rn(f0, xv, facc0[r]);
+        facc1[r] = __fmaf_rn(f1, xv, facc1[r]);
+      }
+    } else {
 #pragma unroll
-          for (int r = 0; r < K; ++r) {
-            const double xv = xs[r * 64 + jj];
-            acc0[r] = __fma_rn(a0, xv, acc0[r]);
-            acc1[r] = __fma_rn(a1, xv, acc1[r]);
-          }
-        }
-        if (kAbs == 1) { s0 += abs_f32_est(a0); s1 += abs_f32_est(a1); }
-        if (kAbs == 2) { d0 += fabs(a0); d1 += fabs(a1); }
+      for (int r = 0; r < K; ++r) {
+        const double xv = xs[r * chunk + jj];
+        acc0[r] = __fma_rn(a0, xv, acc0[r]);
+        acc1[r] = __fma_rn(a1, xv, acc1[r]);
       }
     }
+    if (kAbs == 1) { s0 += abs_f32_est(a0); s1 += abs_f32_est(a1); }
+    if (kAbs == 2) { d0 += fabs(a0); d1 += fabs(a1); }
+  };
+  int jj = 0;
+  if (vec) {
+    for (; jj + 8 <= cnt; jj += 8) {
+      double2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcs(reinterpret_cast<const double2*>(col + (int64_t)u * lda));
+      col += 8 * lda;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) body(v[u].x, v[u].y, jj + u);
+    }
   }
-  if (i >= n) return;
+  for (; jj < cnt; ++jj) {
+    const double a0 = col[0], a1 = two ? col[1] : 0.0;
+    col += lda;
+    body(a0, a1, jj);
+  }
   double* Pc = P + (int64_t)blockIdx.y * n * K;
 #pragma unroll
   for (int r = 0; r < K; ++r) {
@@ -934,11 +939,13 @@ struct SolveWs {
   size_t bytes;
 };
 
-int gemv_chunks(int64_t n) {
+// Column chunks of the GEMV: each chunk's X (chunk x K doubles) fits the
+// CTA's staging buffer, and there are enough CTAs to keep every SM loaded.
+int gemv_chunks(int64_t n, int K = kMaxK) {
   const int64_t rb = cdiv<int64_t>(n, kGemvRows);
-  int64_t c = cdiv<int64_t>(4 * 152, rb);
-  c = std::max<int64_t>(1, std::min<int64_t>(c, cdiv<int64_t>(n, 64)));
-  return (int)std::min<int64_t>(c, 64);
+  int64_t c = std::max<int64_t>(cdiv<int64_t>(n * K, kGemvChunkElems), cdiv<int64_t>(8 * 152, rb));
+  c = std::max<int64_t>(1, std::min<int64_t>(c, cdiv<int64_t>(n, 8)));
+  return (int)c;
 }
 
 SolveWs carve_solve(void* base, int64_t n, int64_t K, int m) {
@@ -973,11 +980,13 @@ template <int K>
 cudaError_t gemv_k(int64_t n, const double* A, int64_t lda, const double* X, int64_t ldx, int abs_mode,
                    double* P, void* RS, int nchunk, cudaStream_t st) {
   const int64_t chunk = cdiv<int64_t>(n, nchunk);
+  if (chunk * K > kGemvChunkElems) return cudaErrorInvalidValue;
   dim3 grid((unsigned)cdiv<int64_t>(n, kGemvRows), (unsigned)nchunk);
-  if (abs_mode == 3) gemv_partial_kernel<K, 0, true><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
-  else if (abs_mode == 0) gemv_partial_kernel<K, 0><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
-  else if (abs_mode == 1) gemv_partial_kernel<K, 1><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
-  else gemv_partial_kernel<K, 2><<<grid, 128, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  const int T = kGemvThreads;
+  if (abs_mode == 3) gemv_partial_kernel<K, 0, true><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  else if (abs_mode == 0) gemv_partial_kernel<K, 0><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  else if (abs_mode == 1) gemv_partial_kernel<K, 1><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  else gemv_partial_kernel<K, 2><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
   return cudaGetLastError();
 }
 
@@ -985,7 +994,7 @@ cudaError_t gemv_k(int64_t n, const double* A, int64_t lda, const double* X, int
 cudaError_t residual(int64_t n, int K, const double* A, int64_t lda, const double* X, int64_t ldx,
                      const double* B, int64_t ldb, double* out, int64_t ldo, int abs_mode, int track,
                      const SolveWs& w, cudaStream_t st) {
-  const int nchunk = gemv_chunks(n);
+  const int nchunk = gemv_chunks(n, K);
   cudaError_t e;
   void* tok = prof_begin(st);
   switch (K) {
