@@ -339,29 +339,60 @@ __global__ void pack_rows_kernel(int64_t rows, int cols, const uint16_t* __restr
 // W_s = st(-Linv_ss L_{s,0:s}) into the first ws columns of the row-major
 // operand Aop (row p, column q), fp32 accumulation over t ascending:
 //   W[p][q] = -sum_t Linv[p][t] * L(s0 + t, k + q)
-// Linv is Aop[p * ld + ws + t]; L(s0+t, k+q) = Lsub[t + q * ldlu].
-__global__ void make_w_kernel(int ws, uint16_t* aop, int64_t ld, const uint16_t* __restrict__ Lsub,
-                              int64_t ldlu, int fmt) {
+// Linv is Aop[p * ld + ws + t]; L(s0+t, k+q) = Lsub[t + q * ldlu].  Both runs
+// of 128 values are contiguous and 16-byte aligned: loaded as 16-byte vectors
+// before the multiply-adds.
+__global__ void __launch_bounds__(128) make_w_kernel(int ws, uint16_t* aop, int64_t ld,
+                                                     const uint16_t* __restrict__ Lsub, int64_t ldlu, int fmt) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
   if (q >= ws) return;
-  const uint16_t* li = aop + (int64_t)p * ld + ws;
-  const uint16_t* lc = Lsub + (int64_t)q * ldlu;
+  const uint4* li = reinterpret_cast<const uint4*>(aop + (int64_t)p * ld + ws);
+  const uint4* lc = reinterpret_cast<const uint4*>(Lsub + (int64_t)q * ldlu);
+  uint4 lv[16], cv[16];
+#pragma unroll
+  for (int k8 = 0; k8 < 16; ++k8) { lv[k8] = li[k8]; cv[k8] = lc[k8]; }
   float acc = 0.0f;
-  for (int t = 0; t < kB; ++t) acc = __fmaf_rn(u16_to_f32(li[t], fmt), u16_to_f32(lc[t], fmt), acc);
+#pragma unroll
+  for (int k8 = 0; k8 < 16; ++k8) {
+    const uint32_t lw[4] = {lv[k8].x, lv[k8].y, lv[k8].z, lv[k8].w};
+    const uint32_t cw[4] = {cv[k8].x, cv[k8].y, cv[k8].z, cv[k8].w};
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const uint16_t a16 = (uint16_t)(lw[h >> 1] >> ((h & 1) * 16));
+      const uint16_t c16 = (uint16_t)(cw[h >> 1] >> ((h & 1) * 16));
+      acc = __fmaf_rn(u16_to_f32(a16, fmt), u16_to_f32(c16, fmt), acc);
+    }
+  }
   aop[(int64_t)p * ld + q] = f32_to_u16(-acc, fmt);
 }
 
 // Z_s^T into the first zs columns of the row-major operand Bop (row p, column q):
 //   Z[q][p] = -sum_t U(k + q, s0 + t) * Uinv[t][p]
-// Uinv[t][p] = Bop[p * ld + zs + t]; U(k+q, s0+t) = Usub[q + t * ldlu].
-__global__ void make_z_kernel(int zs, uint16_t* bop, int64_t ld, const uint16_t* __restrict__ Usub,
-                              int64_t ldlu, int fmt) {
+// Uinv[t][p] = Bop[p * ld + zs + t] (contiguous, vector loads); U(k+q, s0+t) =
+// Usub[q + t * ldlu] (coalesced across q), loaded 32 at a time before use.
+__global__ void __launch_bounds__(128) make_z_kernel(int zs, uint16_t* bop, int64_t ld,
+                                                     const uint16_t* __restrict__ Usub, int64_t ldlu, int fmt) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
   if (q >= zs) return;
-  const uint16_t* ui = bop + (int64_t)p * ld + zs;
+  const uint4* ui = reinterpret_cast<const uint4*>(bop + (int64_t)p * ld + zs);
   float acc = 0.0f;
-  for (int t = 0; t < kB; ++t)
-    acc = __fmaf_rn(u16_to_f32(Usub[q + (int64_t)t * ldlu], fmt), u16_to_f32(ui[t], fmt), acc);
+#pragma unroll
+  for (int t0 = 0; t0 < kB; t0 += 32) {
+    uint16_t uv[32];
+    uint4 iv[4];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) uv[u] = Usub[q + (int64_t)(t0 + u) * ldlu];
+#pragma unroll
+    for (int k8 = 0; k8 < 4; ++k8) iv[k8] = ui[t0 / 8 + k8];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const uint32_t w = (u >> 3) == 0 ? (&iv[0].x)[(u & 7) >> 1]
+                       : (u >> 3) == 1 ? (&iv[1].x)[(u & 7) >> 1]
+                       : (u >> 3) == 2 ? (&iv[2].x)[(u & 7) >> 1] : (&iv[3].x)[(u & 7) >> 1];
+      const uint16_t i16 = (uint16_t)(w >> ((u & 1) * 16));
+      acc = __fmaf_rn(u16_to_f32(uv[u], fmt), u16_to_f32(i16, fmt), acc);
+    }
+  }
   bop[(int64_t)p * ld + q] = f32_to_u16(-acc, fmt);
 }
 
