@@ -83,8 +83,9 @@ def factor_storage_dtype(prec: int):
 
 
 def factor(A: ColMajor, prec: int = capi.BF16, nb: int = 128, LU: ColMajor | None = None, ws=None,
-           stream=None) -> ColMajor:
-    """Low-precision LU without pivoting of A; returns the packed factors."""
+           stream=None, check: bool = True) -> ColMajor:
+    """Low-precision LU without pivoting of A; returns the packed factors.
+    With check=False a breakdown status is left in `factor.last_status` instead of raising."""
     n = A.rows
     if LU is None:
         LU = ColMajor.empty(n, n, factor_storage_dtype(prec), A.storage.device)
@@ -92,7 +93,9 @@ def factor(A: ColMajor, prec: int = capi.BF16, nb: int = 128, LU: ColMajor | Non
         ws = workspace(capi.hpmxp_factor_workspace(n, prec, nb), A.storage.device)
     st = capi.hpmxp_factor(n, A.ptr, A.ld, prec, nb, LU.ptr, LU.ld, ws.data_ptr(), ws.numel(),
                            stream_handle(stream))
-    _check("hpmxp_factor", st)
+    factor.last_status = st
+    if check or st not in (capi.OK, capi.EBREAKDOWN):
+        _check("hpmxp_factor", st)
     return LU
 
 
@@ -152,7 +155,9 @@ class Solver:
         self.sws = workspace(capi.hpmxp_solve_workspace(n, nrhs, self.params.restart), self.device)
 
     def factor(self, A: ColMajor, stream=None) -> ColMajor:
-        return factor(A, self.prec, self.nb, LU=self.LU, ws=self.fws, stream=stream)
+        LU = factor(A, self.prec, self.nb, LU=self.LU, ws=self.fws, stream=stream, check=False)
+        self.factor_status = factor.last_status
+        return LU
 
     def solve(self, A: ColMajor, b: ColMajor, stream=None):
         return solve_ir(A, self.LU, b, self.prec, self.params, x=self.x, ws=self.sws, stream=stream)
