@@ -89,6 +89,29 @@ hpmxp_status hpmxp_generate(int64_t n, uint64_t seed, double margin, int diag_mo
                             int64_t lda, double* b, int64_t ldb, int64_t nrhs, void* ws,
                             size_t ws_bytes, void* stream);
 
+/* hpmxp_generate without a workspace argument, for callers that cannot hand
+ * the library scratch memory: a program whose device memory is all held by
+ * its own pool (a caching allocator, or a solver that sized A, LU and the
+ * solve workspace to fill HBM), or one that must not call cudaMalloc/cudaFree
+ * around generation because those calls synchronize the device.  The paper
+ * has no counterpart: this is a convenience of this library.
+ *
+ * Same arguments, output and bit-for-bit result as hpmxp_generate.  The 16 n
+ * bytes of 128-bit row sums live in a fixed 2 MiB array inside libhpmxp.so,
+ * which every GPU that loads the library holds until the process exits; this
+ * call allocates nothing.  The array is cleared on `stream` at the start of
+ * every call.
+ *
+ *   n > 131072   HPMXP_ENOMEM (the fixed array holds 131072 rows); nothing runs
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and keeps it; make that first call before any stream
+ * capture begins.  All calls on a device share the one array: two calls whose
+ * work overlaps on the GPU (different streams, no ordering between them) race
+ * on it and give wrong diagonals.  Order such calls on one stream or by events. */
+hpmxp_status hpmxp_generate_noalloc(int64_t n, uint64_t seed, double margin, int diag_mode, double* A,
+                                    int64_t lda, double* b, int64_t ldb, int64_t nrhs, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Low-precision LU without pivoting (section "Algorithmic Framework", Fig. 1).
  *

@@ -62,6 +62,7 @@ def load():
             "hpmxp_version": ([], i32),
             "hpmxp_generate_workspace": ([i64], sz),
             "hpmxp_generate": ([i64, u64, d, i32, P, i64, P, i64, i64, P, sz, P], i32),
+            "hpmxp_generate_noalloc": ([i64, u64, d, i32, P, i64, P, i64, i64, P], i32),
             "hpmxp_factor_workspace": ([i64, i32, i32], sz),
             "hpmxp_factor": ([i64, P, i64, i32, i32, P, i64, P, sz, P], i32),
             "hpmxp_ir_params_default": ([ctypes.POINTER(IRParams)], None),
@@ -113,6 +114,10 @@ def hpmxp_generate_workspace(n):
 
 def hpmxp_generate(n, seed, margin, diag_mode, A, lda, b, ldb, nrhs, ws, ws_bytes, stream):
     return _call("hpmxp_generate", n, seed, margin, diag_mode, A, lda, b, ldb, nrhs, ws, ws_bytes, stream)
+
+
+def hpmxp_generate_noalloc(n, seed, margin, diag_mode, A, lda, b, ldb, nrhs, stream):
+    return _call("hpmxp_generate_noalloc", n, seed, margin, diag_mode, A, lda, b, ldb, nrhs, stream)
 
 
 def hpmxp_factor_workspace(n, prec, nb):

@@ -11,6 +11,8 @@
 // associative, so the diagonal is bit-for-bit independent of scheduling.
 #include "internal.h"
 
+#include <mutex>
+
 namespace hpmxp {
 namespace {
 
@@ -142,3 +144,59 @@ cudaError_t launch_generate(int64_t n, uint64_t seed, double margin, int mode, d
 }
 
 }  // namespace hpmxp
+
+// ---------------------------------------------------------------------------
+// Generation with library-held scratch (hpmxp_generate_noalloc).  The 128-bit
+// row sums live in a fixed array of this module instead of caller memory; the
+// arithmetic and the kernels are those of hpmxp_generate.
+
+namespace hpmxp {
+namespace {
+
+constexpr int64_t kNoallocMaxN = int64_t(1) << 17;   // 131072 rows: 2 MiB per GPU
+
+// Two 64-bit words (low, high) per row; must be zero when gen_matrix_kernel
+// starts, and keeps the previous call's sums afterwards.
+static __device__ __align__(256) unsigned long long g_row_sums[2 * kNoallocMaxN];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_sums_mutex;
+void* g_sums_ptr[kMaxDevices];   // device address of g_row_sums, per device
+
+// The device address of g_row_sums on the current device.  Host code cannot
+// use the symbol itself (it names a host-side stand-in), so the address is
+// asked for once per device, with that device current, and kept.
+cudaError_t row_sums_address(unsigned long long** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_sums_mutex);
+  if (!g_sums_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_row_sums);
+    if (e != cudaSuccess) return e;
+    if (!ptr) return cudaErrorInvalidSymbol;
+    g_sums_ptr[dev] = ptr;
+  }
+  *out = static_cast<unsigned long long*>(g_sums_ptr[dev]);
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace hpmxp
+
+extern "C" hpmxp_status hpmxp_generate_noalloc(int64_t n, uint64_t seed, double margin, int diag_mode,
+                                               double* A, int64_t lda, double* b, int64_t ldb, int64_t nrhs,
+                                               void* stream) {
+  using namespace hpmxp;
+  if (n > kNoallocMaxN) return HPMXP_ENOMEM;
+  if (n < 1 || !A || lda < n || nrhs < 0 || (nrhs > 0 && (!b || ldb < n))) return HPMXP_EINVAL;
+  if (diag_mode < HPMXP_DIAG_DOMINANT || diag_mode > HPMXP_DIAG_NONE) return HPMXP_EINVAL;
+  unsigned long long* sums = nullptr;
+  cudaError_t e = row_sums_address(&sums);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  // launch_generate clears the first 2n words on `stream` before the sums are made
+  e = launch_generate(n, seed, margin, diag_mode, A, lda, b, ldb, nrhs, sums, (cudaStream_t)stream);
+  return status_from_cuda(e);
+}
