@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 namespace hpmxp {
@@ -207,17 +208,18 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
     __syncthreads();
     const int e = p0 + pw;
     if (e >= b) break;
-    // (b) row strip: rows p0..e-1, columns e..b-1, unit-lower solve with the panel
+    // (b) row strip: rows p0..e-1, columns e..b-1, unit-lower solve with the
+    // panel, right-looking (pivot q ascending, so each entry's terms keep
+    // their order and the loads of step q+1 overlap step q)
     for (int j = e + tid; j < b; j += kGetrfThreads) {
       float col[kPW];
 #pragma unroll
       for (int r = 0; r < kPW; ++r) col[r] = r < pw ? a[j * kP + p0 + r] : 0.0f;
 #pragma unroll
-      for (int r = 1; r < kPW; ++r) {
-        if (r < pw) {
+      for (int q = 0; q < kPW - 1; ++q) {
 #pragma unroll
-          for (int q = 0; q < r; ++q) col[r] = __fmaf_rn(-a[(p0 + q) * kP + p0 + r], col[q], col[r]);
-        }
+        for (int r = q + 1; r < kPW; ++r)
+          if (r < pw) col[r] = __fmaf_rn(-a[(p0 + q) * kP + p0 + r], col[q], col[r]);
       }
 #pragma unroll
       for (int r = 0; r < kPW; ++r)
@@ -254,18 +256,18 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
     const int gt = tid;   // 0..255
     for (int t0 = 0; t0 < b; t0 += kPW) {
       const int t1 = min(t0 + kPW, b);
-      // rows t0..t1-1, every column c < t1: within-block terms t = max(c, t0) .. r-1
+      // rows t0..t1-1, every column c < t1: within-block terms t = t0 .. r-1 in
+      // ascending order; X(t, c) = 0 for t < c, so those terms are exact no-ops
+      // and each entry sees the same operations as the plain recurrence
       for (int c = gt; c < t1; c += 256) {
         float col[kPW];
 #pragma unroll
         for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? x[c * kP + t0 + r] : 0.0f;
 #pragma unroll
-        for (int r = 1; r < kPW; ++r) {
-          if (t0 + r < t1 && t0 + r > c) {
+        for (int q = 0; q < kPW - 1; ++q) {
 #pragma unroll
-            for (int q = 0; q < r; ++q)
-              if (t0 + q >= c) col[r] = __fmaf_rn(-a[(t0 + q) * kP + t0 + r], col[q], col[r]);
-          }
+          for (int r = q + 1; r < kPW; ++r)
+            if (t0 + r < t1) col[r] = __fmaf_rn(-a[(t0 + q) * kP + t0 + r], col[q], col[r]);
         }
 #pragma unroll
         for (int r = 0; r < kPW; ++r)
@@ -282,21 +284,20 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
     const int nblk = (b + kPW - 1) / kPW;
     for (int bi = nblk - 1; bi >= 0; --bi) {
       const int t0 = bi * kPW, t1 = min(t0 + kPW, b);
-      // rows t1-1 down to t0, every column c >= t0: terms t = min(c, t1-1) down to r+1, then divide
+      // rows t1-1 down to t0, every column c >= t0, right-looking: finalize row
+      // t0+q (divide, unless it is the diagonal or below it), then add its term
+      // to the rows above it; terms come in descending t, rows t > c carry 0
       for (int c = t0 + gt; c < b; c += 256) {
         float col[kPW];
 #pragma unroll
         for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? y[c * kP + t0 + r] : 0.0f;
 #pragma unroll
-        for (int r = kPW - 1; r >= 0; --r) {
-          const int rr = t0 + r;
-          if (rr < t1 && rr < c) {
-            float acc = col[r];
+        for (int q = kPW - 1; q >= 0; --q) {
+          const int rq = t0 + q;
+          if (rq < t1 && rq < c) col[q] = __fdiv_rn(-col[q], a[rq * kP + rq]);
 #pragma unroll
-            for (int q = kPW - 1; q > r; --q)
-              if (t0 + q < t1 && t0 + q <= c) acc = __fmaf_rn(a[(t0 + q) * kP + rr], col[q], acc);
-            col[r] = __fdiv_rn(-acc, a[rr * kP + rr]);
-          }
+          for (int r = 0; r < q; ++r)
+            if (rq < t1) col[r] = __fmaf_rn(a[rq * kP + t0 + r], col[q], col[r]);
         }
 #pragma unroll
         for (int r = 0; r < kPW; ++r)
@@ -812,14 +813,14 @@ size_t factor_ws_bytes(int64_t n, int prec, int nb) { return carve(nullptr, n, p
 
 hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU,
                     int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st) {
-  static int attr_dev = -1;
+  static std::atomic<int> attr_dev{-1};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (attr_dev != dev) {
+  if (attr_dev.load() != dev) {
     cudaError_t e =
         cudaFuncSetAttribute(getrf_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGetrfSmem);
     if (e != cudaSuccess) return status_from_cuda(e);
-    attr_dev = dev;
+    attr_dev.store(dev);
   }
   Factorizer f;
   f.n = n; f.LU = (uint16_t*)LU; f.ld = ldlu;
@@ -829,16 +830,21 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
   f.st = st;
   f.check(cudaMemsetAsync(f.w.status, 0, sizeof(uint32_t), st));
   f.check(launch_cast(n, A, lda, LU, ldlu, f.fmt, st));
-  SideStream& ss = side_stream(dev);
-  std::unique_lock<std::mutex> lk(ss.mu, std::defer_lock);
-  if (ss.ok && n > 2 * nb && getenv("HPMXP_NO_LOOKAHEAD") == nullptr) {
-    lk.lock();
-    f.st2 = ss.st;
-    f.evP = ss.evP;
-    f.evF = ss.evF;
-    cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
-    f.reserve = std::max(4, f.sms / 12);
-    if (const char* om = getenv("HPMXP_OVERLAP_MIN")) f.overlap_min = atoll(om);
+  if (const char* om = getenv("HPMXP_OVERLAP_MIN")) f.overlap_min = atoll(om);
+  // the largest far part is n - 2 nb (first step); below overlap_min the
+  // schedule never uses the side stream, so it is not taken (concurrent
+  // factorizations of small systems on other streams then do not serialize)
+  std::unique_lock<std::mutex> lk;
+  if (n - 2 * (int64_t)nb >= std::max<int64_t>(f.overlap_min, 1) && getenv("HPMXP_NO_LOOKAHEAD") == nullptr) {
+    SideStream& ss = side_stream(dev);
+    if (ss.ok) {
+      lk = std::unique_lock<std::mutex>(ss.mu);
+      f.st2 = ss.st;
+      f.evP = ss.evP;
+      f.evF = ss.evF;
+      cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
+      f.reserve = std::max(4, f.sms / 12);
+    }
   }
   f.run();
   if (lk.owns_lock()) lk.unlock();
