@@ -45,6 +45,18 @@ hpmxp_status hpmxp_test_precond(int64_t n, const void* LU, int64_t ldlu, int pre
                                 int64_t ldv, double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws,
                                 size_t ws_bytes, void* stream);
 
+/* Fills the shared memory of every SM with `pattern` (one kernel on
+ * `stream`), so that the next kernel starts on nonzero leftovers: a check
+ * that kernels initialise every shared variable they read. */
+hpmxp_status hpmxp_test_fill_smem(uint32_t pattern, void* stream);
+
+/* Host-only check of the request executor's arena allocator (no device
+ * memory is touched).  ops[i] > 0: allocate that many bytes, result[i] = the
+ * 256-byte aligned offset or -1 when no free block fits (first fit);
+ * ops[i] = -(k + 1): release the block allocated by op k, result[i] = free
+ * bytes afterwards (freed blocks coalesce with their neighbours). */
+int hpmxp_test_arena(size_t arena_bytes, const int64_t* ops, int nops, int64_t* result);
+
 #ifdef __cplusplus
 }
 #endif

@@ -164,4 +164,8 @@ hpmxp_status hpmxp_test_precond(int64_t n, const void* LU, int64_t ldlu, int pre
                        (cudaStream_t)stream);
 }
 
+hpmxp_status hpmxp_test_fill_smem(uint32_t pattern, void* stream) {
+  return status_from_cuda(fill_smem(pattern, (cudaStream_t)stream));
+}
+
 }  // extern "C"

@@ -542,6 +542,9 @@ __global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_
       const int64_t i = (int64_t)(me + o * G) * kTB32 + ii;
       acc[((size_t)o * kTB32 + ii) * K + r] = i < n ? (float)v[i + r * ldv] : 0.0f;
     }
+  // abort_flag (and acc) must be written before any thread reads them: shared
+  // memory starts with whatever the SM's previous block left there
+  __syncthreads();
 
   // asynchronous copies: 16-bit tile (rb, cb) of LU into buffer slot, zero outside the matrix
   auto fetch_tile = [&](int slot, int rb, int cb) {
@@ -1016,6 +1019,10 @@ cudaError_t residual(int64_t n, int K, const double* A, int64_t lda, const doubl
   return cudaGetLastError();
 }
 
+// Dynamic shared memory cap of the preconditioner kernels (the attribute is
+// set to this one value, never to a per-call size).
+constexpr size_t kMaxPrecondSmem = 200 * 1024;
+
 size_t precond_smem(int64_t n, int K, int G, bool fp32) {
   const int nb = (int)cdiv<int64_t>(n, kTB);
   const int nown = cdiv(nb, G);
@@ -1028,7 +1035,8 @@ cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt,
                              double* z, int64_t ldz, const SolveWs& w, int epoch, int G, size_t smem,
                              cudaStream_t st) {
   auto kern = precond_kernel<T, K>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // one value for every call: concurrent solves on other threads set the same cap
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPrecondSmem);
   if (e != cudaSuccess) return e;
   T* pub = (T*)w.pub;
   int* flags = w.flags;
@@ -1065,7 +1073,7 @@ cudaError_t precond32_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fm
                                const double* v, int64_t ldv, double* z, int64_t ldz, unsigned long long* pub,
                                int epoch, uint32_t* status, int G, size_t smem, cudaStream_t st) {
   auto kern = precond32_kernel<K>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPrecondSmem);
   if (e != cudaSuccess) return e;
   void* args[] = {&n, (void*)&LU, &ld, &fmt, (void*)&dinv, (void*)&v, &ldv, &z, &ldz, &pub, &epoch, &status};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(256), args, smem, st);
@@ -1149,7 +1157,7 @@ struct Solver {
       G = std::max(1, std::min(nb, sms));
       psmem = precond_smem(n, K, G, false);
     }
-    if (psmem > 200 * 1024) return cudaErrorInvalidValue;
+    if (psmem > kMaxPrecondSmem) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(w.st, 0, sizeof(RhsState) * kMaxK, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.flags, 0, sizeof(int) * 2 * nb, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.counter, 0, 256, st)) != cudaSuccess) return e;
@@ -1210,6 +1218,29 @@ struct Solver {
 };
 
 }  // namespace
+
+// Test support: every SM's shared memory filled with `pattern`, so that a
+// kernel launched next finds nonzero leftovers there instead of the zeros a
+// quiet GPU tends to leave.
+__global__ void fill_smem_kernel(uint32_t pattern, uint32_t words) {
+  extern __shared__ uint32_t sw[];
+  for (uint32_t t = threadIdx.x; t < words; t += blockDim.x) sw[t] = pattern;
+  __syncthreads();
+  if (sw[(threadIdx.x * 7u) % words] != pattern) asm volatile("" ::: "memory");
+}
+
+cudaError_t fill_smem(uint32_t pattern, cudaStream_t st) {
+  int dev = 0, sms = 0, maxb = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxb, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fill_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+  if (e != cudaSuccess) return e;
+  fill_smem_kernel<<<2 * sms, 1024, (size_t)maxb, st>>>(pattern, (uint32_t)maxb / 4);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 size_t solve_ws_bytes(int64_t n, int64_t nrhs, int restart) { return carve_solve(nullptr, n, nrhs, restart).bytes; }
 size_t residual_ws_bytes(int64_t n, int64_t nrhs) { return carve_solve(nullptr, n, nrhs, 1).bytes; }

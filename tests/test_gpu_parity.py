@@ -303,6 +303,31 @@ def test_precond_against_oracle(n, k, fp32):
         assert np.abs(got[:, c] - want).max() <= tol * np.abs(want).max()
 
 
+@pytest.mark.parametrize("fp32", [0, 1])
+@pytest.mark.parametrize("pattern", [0xFFFFFFFF, 0x7FC00001])
+def test_precond_ignores_stale_shared_memory(fp32, pattern):
+    """The preconditioner kernels read nothing from shared memory that they did
+    not write first: leftovers of a previous kernel change no result."""
+    n, k = 1100, 2
+    A_o, _ = oracle.generate(n, 9)
+    LU_o, _ = oracle.factor(A_o, oracle.BF16, 128)
+    LU = api.ColMajor.from_tensor(torch.from_numpy(LU_o), DEV, dtype=torch.bfloat16)
+    V = vectors(n, k, 18)
+    v = api.ColMajor.from_tensor(torch.from_numpy(V), DEV)
+    ws = api.workspace(capi.hpmxp_solve_workspace(n, k, 1), DEV)
+    outs = []
+    for fill in (False, True, True):
+        z = api.ColMajor.empty(n, k, torch.float64, DEV)
+        if fill:
+            assert capi.hpmxp_test_fill_smem(pattern, api.stream_handle()) == capi.OK
+        st = capi.hpmxp_test_precond(n, LU.ptr, LU.ld, capi.BF16, v.ptr, v.ld, z.ptr, z.ld, k, fp32,
+                                     ws.data_ptr(), ws.numel(), api.stream_handle())
+        assert st == capi.OK
+        torch.cuda.synchronize()
+        outs.append(to_np(z))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
 @pytest.mark.parametrize("n,nb,prec,k", [(1, 128, capi.BF16, 1), (2, 128, capi.BF16, 1), (64, 128, capi.BF16, 1),
                                          (300, 128, capi.BF16, 3), (1024, 128, capi.BF16, 1),
                                          (1024, 256, capi.FP16, 2), (1500, 512, capi.FP8_E4M3, 1),
