@@ -59,6 +59,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
+    ap.add_argument("--workload", default="solve", choices=["solve", "serving"],
+                    help="solve: one large system (default); serving: a stream of small systems")
+    ap.add_argument("--rate", type=float, default=1000.0, help="serving: Poisson arrival rate, requests/s")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the timed stream")
+    ap.add_argument("--workers", type=int, default=12, help="serving: executor worker streams")
+    ap.add_argument("--arena-gb", type=float, default=16.0, help="serving: executor arena (admission budget)")
+    ap.add_argument("--serial-requests", type=int, default=300,
+                    help="serving: requests of the one-at-a-time comparison (0: skip)")
     return ap.parse_args()
 
 
@@ -184,9 +192,110 @@ def cpu_baseline(args, nb: int) -> dict:
                       f"(the full n is out of reach on the host), {dt:.2f} s, status {rc}, iters {info['iters']}"}
 
 
+SERVING_METRIC = "served systems/s (n log-uniform in [256, 8192], 1-8 rhs, Poisson arrivals), scaled residual < 16"
+
+
+def serving_config(args, workers):
+    return {"workload": f"serving: {args.requests} requests, n log-uniform 256..8192, nrhs 1..8, "
+                        f"Poisson {args.rate:g}/s, stream seed 2509, {args.prec}",
+            "rate": args.rate, "requests": args.requests, "workers": workers, "prec": args.prec,
+            "parallelism": "replicas", "l2": "every request's A is new (generated on the device per request)"}
+
+
+def run_reference_serving(args):
+    import oracle
+    from paper_2509_19618_gb300 import serve
+    specs = serve.request_stream(args.requests, args.rate, stream_seed=2509)
+    fmt = oracle.FP16 if args.prec == "fp16" else oracle.BF16
+    upd = oracle.E4M3 if args.prec == "fp8" else None
+    budget = max(5.0, min(60.0, 10.0 * max(1, args.steps)))
+    done, ops, t = 0, 0.0, 0.0
+    for s in specs:
+        A, b = oracle.generate(s.n, s.seed, nrhs=s.nrhs)
+        t0 = time.perf_counter()
+        LU, _ = oracle.factor(A, fmt, 128 if s.n < 4096 else 256, fmt_update=upd)
+        oracle.solve_ir(A, LU, b, **IR_KW)
+        t += time.perf_counter() - t0
+        done += 1
+        ops += 2.0 / 3.0 * s.n**3 - 0.5 * s.n**2 + 2.0 * s.nrhs * s.n**2
+        if t > budget:
+            break
+    value = done / t
+    sample = f"the first {done} requests of the same stream, solved one at a time by the oracle ({t:.1f} s)"
+    line = {"metric": SERVING_METRIC, "value": value, "unit": "systems/s", "n_gpus": args.gpus, "steps": done,
+            "warmup": 0, "ms_per_step": t / done * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.prec, "data": "synthetic (generated on the host by the oracle)",
+            "impl": "reference", "config": serving_config(args, 1),
+            "cpu_baseline": {"value": value, "unit": "systems/s", "kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": sample, "tflops": ops / t / 1e12},
+            "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    rank, local, ws = dist_setup("nccl")
+    import torch
+    from paper_2509_19618_gb300 import capi, serve
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = PREC[args.prec]
+    params = capi.hpmxp_ir_params_default()
+    params.precond_fp32 = args.precond_fp32
+    params.inner_tol = IR_KW["inner_tol"]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    specs = serve.request_stream(args.requests, args.rate, stream_seed=2509 + rank)
+    warm = serve.request_stream(max(3 * args.workers, 24), 0.0, stream_seed=1)
+    with serve.Executor(workers=args.workers, arena_bytes=int(args.arena_gb * (1 << 30)), device=dev) as ex:
+        serve.run_stream(ex, warm, prec, params)
+        barrier(ws)
+        launches0 = capi.hpmxp_launch_count()
+        with ClockSampler(local) as clk:
+            comps = serve.run_stream(ex, specs, prec, params)
+        launches = capi.hpmxp_launch_count() - launches0
+    summ = serve.summarize(specs, comps)
+    span = allmax(summ["seconds"], ws, dev)
+    serial = None
+    if args.serial_requests > 0 and rank == 0:
+        sub = specs[: args.serial_requests]
+        with serve.Executor(workers=1, arena_bytes=int(args.arena_gb * (1 << 30)), device=dev) as ex1:
+            c1 = serve.run_stream(ex1, sub, prec, params, one_at_a_time=True)
+        s1 = serve.summarize(sub, c1)
+        mixed_sub = serve.summarize(sub, [c for c in comps if c["id"] < len(sub)])
+        serial = {"requests": len(sub), "systems_per_s": s1["systems_per_s"], "tflops": s1["tflops"],
+                  "service_p50_ms": s1["p50_ms"], "service_p99_ms": s1["p99_ms"], "valid": s1["valid"],
+                  "what": "the first requests of the stream, each submitted after the previous one completed "
+                          "(one worker); latency here is service time only",
+                  "mixed_p50_ms_same_requests": mixed_sub["p50_ms"]}
+    if rank == 0:
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        tf = ws * summ["tflops"] * summ["seconds"] / span
+        line = {"metric": SERVING_METRIC, "value": ws * args.requests / span, "unit": "systems/s", "n_gpus": ws,
+                "steps": args.requests, "warmup": len(warm), "ms_per_step": span / args.requests * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+                "data": "synthetic (each request's system generated on the device from its seed)",
+                "config": serving_config(args, args.workers),
+                "valid": summ["valid"], "failed": summ["failed"], "statuses": summ["statuses"],
+                "failed_examples": summ["failed_examples"], "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
+                "mean_queue_ms": summ["mean_queue_ms"], "tflops": tf, "mean_ir_iters": summ["mean_iters"],
+                "max_scaled_residual": summ["max_scaled_resid"], "one_at_a_time": serial,
+                "gpu_launches": int(launches),
+                "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                             "traffic": None, "kernel": "whole request mix (HPL-MxP operation count / wall time)"},
+                "clocks": clk.summary(), "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_reference(args):
     rank, local, ws = dist_setup("gloo")
     if rank != 0:
+        return
+    if args.workload == "serving":
+        run_reference_serving(args)
         return
     import oracle
     nb = args.nb or 128
@@ -222,6 +331,9 @@ def main():
                  inner_tol=args.inner_tol if args.inner_tol >= 0 else (1e-5 if args.precond_fp32 else 1e-12))
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     rank, local, ws = dist_setup("nccl")
     import torch

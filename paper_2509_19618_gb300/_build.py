@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libhpmxp.so")
-SOURCES = ["gen.cu", "lu.cu", "gemm_tc.cu", "ir.cu", "capi.cu", "prof.cu"]
+SOURCES = ["gen.cu", "lu.cu", "gemm_tc.cu", "ir.cu", "capi.cu", "prof.cu", "serve.cu"]
 HEADERS = ["internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -30,7 +30,7 @@ def nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
-    files += [os.path.join(ROOT, "include", h) for h in ("hpmxp.h", "hpmxp_testing.h")]
+    files += [os.path.join(ROOT, "include", h) for h in ("hpmxp.h", "hpmxp_testing.h", "hpmxp_serve.h")]
     return files
 
 

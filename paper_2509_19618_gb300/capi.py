@@ -1,4 +1,5 @@
-"""ctypes binding of libhpmxp.so (include/hpmxp.h, include/hpmxp_testing.h).
+"""ctypes binding of libhpmxp.so (include/hpmxp.h, include/hpmxp_serve.h,
+include/hpmxp_testing.h).
 
 The ``hpmxp_*`` functions here have the C names and take raw pointers (ints),
 sizes and a stream handle; they only marshal arguments.  PyTorch is used by
@@ -34,6 +35,20 @@ class IRParams(ctypes.Structure):
 class IRInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("scaled_resid", ctypes.c_double),
                 ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("n", ctypes.c_int64), ("nrhs", ctypes.c_int64), ("prec", ctypes.c_int32),
+                ("nb", ctypes.c_int32), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("b", ctypes.c_void_p),
+                ("ldb", ctypes.c_int64), ("x", ctypes.c_void_p), ("ldx", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("margin", ctypes.c_double), ("diag_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("params", IRParams)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("info", IRInfo * 8), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
 
 
 class HpmxpError(RuntimeError):
@@ -79,6 +94,15 @@ def load():
             "hpmxp_prof_reset": ([], None),
             "hpmxp_prof_read": ([i32, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)], i32),
             "hpmxp_test_precond": ([i64, P, i64, i32, P, i64, P, i64, i64, i32, P, sz, P], i32),
+            "hpmxp_test_arena": ([sz, ctypes.POINTER(i64), i32, ctypes.POINTER(i64)], i32),
+            "hpmxp_test_fill_smem": ([ctypes.c_uint32, P], i32),
+            "hpmxp_request_footprint": ([ctypes.POINTER(Request)], sz),
+            "hpmxp_executor_create": ([i32, i32, P, sz, ctypes.POINTER(P)], i32),
+            "hpmxp_executor_submit": ([P, ctypes.POINTER(Request)], i32),
+            "hpmxp_executor_poll": ([P, ctypes.POINTER(Completion), i32, i32], i32),
+            "hpmxp_executor_outstanding": ([P], i64),
+            "hpmxp_executor_clock": ([P], d),
+            "hpmxp_executor_destroy": ([P], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -184,3 +208,48 @@ def hpmxp_test_cast(*args):
 
 def hpmxp_test_precond(*args):
     return _call("hpmxp_test_precond", *args)
+
+
+def hpmxp_test_fill_smem(pattern: int, stream) -> int:
+    return _call("hpmxp_test_fill_smem", pattern, stream)
+
+
+def hpmxp_test_arena(arena_bytes: int, ops: list[int]) -> list[int]:
+    n = len(ops)
+    a = (ctypes.c_int64 * max(n, 1))(*ops)
+    r = (ctypes.c_int64 * max(n, 1))()
+    st = load().hpmxp_test_arena(arena_bytes, a, n, r)
+    if st != OK:
+        raise HpmxpError("hpmxp_test_arena", st)
+    return list(r[:n])
+
+
+def hpmxp_request_footprint(req: Request) -> int:
+    return int(load().hpmxp_request_footprint(ctypes.byref(req)))
+
+
+def hpmxp_executor_create(device: int, workers: int, arena: int, arena_bytes: int):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    st = load().hpmxp_executor_create(device, workers, arena, arena_bytes, ctypes.byref(h))
+    return st, h
+
+
+def hpmxp_executor_submit(ex, req: Request) -> int:
+    return _call("hpmxp_executor_submit", ex, ctypes.byref(req))
+
+
+def hpmxp_executor_poll(ex, out, max_count: int, timeout_ms: int) -> int:
+    return _call("hpmxp_executor_poll", ex, out, max_count, timeout_ms)
+
+
+def hpmxp_executor_outstanding(ex) -> int:
+    return int(_call("hpmxp_executor_outstanding", ex))
+
+
+def hpmxp_executor_clock(ex) -> float:
+    return float(_call("hpmxp_executor_clock", ex))
+
+
+def hpmxp_executor_destroy(ex) -> int:
+    return _call("hpmxp_executor_destroy", ex)

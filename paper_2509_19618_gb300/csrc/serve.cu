@@ -1,0 +1,321 @@
+// Request executor (include/hpmxp_serve.h): independent systems solved
+// concurrently on one GPU.  Host code only; every step of a request is the
+// library's own entry points (hpmxp_generate, hpmxp_factor, hpmxp_solve_ir)
+// on the worker's stream.
+#include "internal.h"
+#include "../../include/hpmxp_serve.h"
+#include "../../include/hpmxp_testing.h"
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace hpmxp {
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kNone = ~(size_t)0;
+constexpr int64_t kMaxRhs = 8;   // right-hand sides one solve refines together
+
+// First-fit sub-allocator of [0, bytes): host bookkeeping of device memory.
+// Free blocks are kept by offset and merged with their neighbours on release.
+class Arena {
+ public:
+  explicit Arena(size_t bytes) : bytes_(bytes / kAlign * kAlign) {
+    if (bytes_) free_[0] = bytes_;
+  }
+  size_t alloc(size_t n) {
+    n = round_up(n, kAlign);
+    if (n == 0) n = kAlign;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < n) continue;
+      const size_t off = it->first, left = it->second - n;
+      free_.erase(it);
+      if (left) free_[off + n] = left;
+      return off;
+    }
+    return kNone;
+  }
+  void release(size_t off, size_t n) {
+    n = round_up(n, kAlign);
+    if (n == 0) n = kAlign;
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + n == next->first) {   // merge with the block after
+      n += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {                            // and with the block before
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += n;
+        return;
+      }
+    }
+    free_[off] = n;
+  }
+  size_t capacity() const { return bytes_; }
+  size_t free_bytes() const {
+    size_t s = 0;
+    for (auto& kv : free_) s += kv.second;
+    return s;
+  }
+
+ private:
+  size_t bytes_;
+  std::map<size_t, size_t> free_;
+};
+
+// Byte offsets of a request's buffers inside its arena block.
+struct Layout {
+  size_t lu = 0, fws = 0, sws = 0, a = 0, b = 0, x = 0, total = 0;
+  size_t fws_bytes = 0, sws_bytes = 0;
+  int64_t ld = 0;   // leading dimension of every n-row buffer the executor places
+  int nb = 0;
+};
+
+int pick_nb(const hpmxp_request& r) { return r.nb ? r.nb : (r.n < 4096 ? 128 : 256); }
+
+bool request_ok(const hpmxp_request& r) {
+  if (r.n < 1 || r.n > (int64_t(1) << 17) || r.nrhs < 1 || r.nrhs > kMaxRhs) return false;
+  if (!(r.prec == HPMXP_BF16 || r.prec == HPMXP_FP16 || r.prec == HPMXP_FP8_E4M3)) return false;
+  const int nb = pick_nb(r);
+  if (!(nb == 128 || nb == 256 || nb == 512)) return false;
+  if ((r.A == nullptr) != (r.b == nullptr)) return false;
+  if (r.A && (r.lda < r.n || r.ldb < r.n)) return false;
+  if (!r.A && (r.diag_mode < HPMXP_DIAG_DOMINANT || r.diag_mode > HPMXP_DIAG_NONE)) return false;
+  if (r.x && r.ldx < r.n) return false;
+  const hpmxp_ir_params& p = r.params;
+  if (p.restart < 1 || p.restart > 64 || p.max_iters < 0) return false;
+  return true;
+}
+
+Layout layout(const hpmxp_request& r) {
+  Layout L;
+  L.nb = pick_nb(r);
+  L.ld = round_up<int64_t>(r.n, 8);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += round_up(bytes, kAlign);
+    return at;
+  };
+  L.lu = take(2 * (size_t)L.ld * (size_t)r.n);
+  L.fws_bytes = factor_ws_bytes(r.n, r.prec, L.nb);
+  L.fws = take(L.fws_bytes);
+  // the solve workspace also serves generation (16 n bytes), which is done before the solve starts
+  L.sws_bytes = std::max(solve_ws_bytes(r.n, r.nrhs, r.params.restart), round_up<size_t>(16 * (size_t)r.n, kAlign));
+  L.sws = take(L.sws_bytes);
+  if (!r.A) {
+    L.a = take(8 * (size_t)L.ld * (size_t)r.n);
+    L.b = take(8 * (size_t)L.ld * (size_t)r.nrhs);
+  }
+  if (!r.x) L.x = take(8 * (size_t)L.ld * (size_t)r.nrhs);
+  L.total = off;
+  return L;
+}
+
+struct Job {
+  hpmxp_request r;
+  Layout L;
+  double t_submit;
+};
+
+}  // namespace
+}  // namespace hpmxp
+
+using namespace hpmxp;
+
+struct hpmxp_executor {
+  int device = 0;
+  char* arena_base = nullptr;
+  Arena arena{0};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job> queue;
+  std::deque<hpmxp_completion> done;
+  std::vector<std::thread> threads;
+  int64_t outstanding = 0;
+  bool stopping = false;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+  double clock() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+
+  hpmxp_completion run(const Job& job, char* blk, cudaStream_t st) {
+    const hpmxp_request& r = job.r;
+    const Layout& L = job.L;
+    hpmxp_completion c{};
+    c.id = r.id;
+    c.nrhs = (int)r.nrhs;
+    c.t_submit = job.t_submit;
+    c.t_start = clock();
+    void* LU = blk + L.lu;
+    void* fws = blk + L.fws;
+    void* sws = blk + L.sws;
+    const double* A = r.A;
+    const double* b = r.b;
+    int64_t lda = r.lda, ldb = r.ldb;
+    double* x = r.x;
+    int64_t ldx = r.ldx;
+    hpmxp_status s = HPMXP_OK;
+    if (!A) {
+      double* Ag = (double*)(blk + L.a);
+      double* bg = (double*)(blk + L.b);
+      s = hpmxp_generate(r.n, r.seed, r.margin, r.diag_mode, Ag, L.ld, bg, L.ld, r.nrhs, sws, L.sws_bytes, st);
+      A = Ag; b = bg; lda = L.ld; ldb = L.ld;
+    }
+    if (!x) {
+      x = (double*)(blk + L.x);
+      ldx = L.ld;
+    }
+    if (s == HPMXP_OK) s = hpmxp_factor(r.n, A, lda, r.prec, L.nb, LU, L.ld, fws, L.fws_bytes, st);
+    if (s == HPMXP_OK)
+      s = hpmxp_solve_ir(r.n, A, lda, LU, L.ld, r.prec, b, ldb, x, ldx, r.nrhs, &r.params, c.info, sws,
+                         L.sws_bytes, st);
+    else
+      cudaStreamSynchronize(st);   // nothing of this request may still run when its block is released
+    c.status = (int32_t)s;
+    c.t_done = clock();
+    return c;
+  }
+
+  void worker() {
+    cudaStream_t st = nullptr;
+    const bool ok = cudaSetDevice(device) == cudaSuccess &&
+                    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    for (;;) {
+      Job job;
+      size_t off = kNone;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        // strict arrival order: the head is admitted once its block fits
+        cv_work.wait(lk, [&] {
+          if (queue.empty()) return stopping;
+          off = arena.alloc(queue.front().L.total);
+          return off != kNone;
+        });
+        if (queue.empty()) break;
+        job = queue.front();
+        queue.pop_front();
+        if (!queue.empty()) cv_work.notify_one();   // the next head may fit too
+      }
+      hpmxp_completion c;
+      if (ok) {
+        c = run(job, arena_base + off, st);
+      } else {
+        c = hpmxp_completion{};
+        c.id = job.r.id;
+        c.nrhs = (int)job.r.nrhs;
+        c.t_submit = job.t_submit;
+        c.t_start = c.t_done = clock();
+        c.status = HPMXP_ECUDA;
+      }
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        arena.release(off, job.L.total);
+        done.push_back(c);
+      }
+      cv_work.notify_all();
+      cv_done.notify_all();
+    }
+    if (st) cudaStreamDestroy(st);
+  }
+};
+
+extern "C" {
+
+size_t hpmxp_request_footprint(const hpmxp_request* r) {
+  if (!r || !request_ok(*r)) return 0;
+  return layout(*r).total;
+}
+
+hpmxp_status hpmxp_executor_create(int device, int workers, void* arena, size_t arena_bytes,
+                                   hpmxp_executor** out) {
+  if (!out || workers < 1 || workers > 64 || !arena || ((uintptr_t)arena % kAlign) != 0 || arena_bytes < kAlign)
+    return HPMXP_EINVAL;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return HPMXP_EINVAL;
+  hpmxp_executor* ex = new hpmxp_executor();
+  ex->device = device;
+  ex->arena_base = (char*)arena;
+  ex->arena = Arena(arena_bytes);
+  for (int i = 0; i < workers; ++i) ex->threads.emplace_back([ex] { ex->worker(); });
+  *out = ex;
+  return HPMXP_OK;
+}
+
+hpmxp_status hpmxp_executor_submit(hpmxp_executor* ex, const hpmxp_request* r) {
+  if (!ex || !r || !request_ok(*r)) return HPMXP_EINVAL;
+  Job job{*r, layout(*r), 0.0};
+  if (job.L.total > ex->arena.capacity()) return HPMXP_ENOMEM;
+  {
+    std::lock_guard<std::mutex> lk(ex->mu);
+    if (ex->stopping) return HPMXP_EINVAL;
+    job.t_submit = ex->clock();
+    ex->queue.push_back(job);
+    ++ex->outstanding;
+  }
+  ex->cv_work.notify_one();
+  return HPMXP_OK;
+}
+
+int hpmxp_executor_poll(hpmxp_executor* ex, hpmxp_completion* out, int max, int timeout_ms) {
+  if (!ex || !out || max < 1) return 0;
+  std::unique_lock<std::mutex> lk(ex->mu);
+  if (ex->done.empty() && timeout_ms > 0)
+    ex->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return !ex->done.empty(); });
+  int k = 0;
+  while (k < max && !ex->done.empty()) {
+    out[k++] = ex->done.front();
+    ex->done.pop_front();
+    --ex->outstanding;
+  }
+  return k;
+}
+
+int64_t hpmxp_executor_outstanding(hpmxp_executor* ex) {
+  if (!ex) return 0;
+  std::lock_guard<std::mutex> lk(ex->mu);
+  return ex->outstanding;
+}
+
+double hpmxp_executor_clock(hpmxp_executor* ex) { return ex ? ex->clock() : 0.0; }
+
+hpmxp_status hpmxp_executor_destroy(hpmxp_executor* ex) {
+  if (!ex) return HPMXP_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(ex->mu);
+    ex->stopping = true;
+  }
+  ex->cv_work.notify_all();
+  for (auto& t : ex->threads) t.join();
+  delete ex;
+  return HPMXP_OK;
+}
+
+// Host-only check of the arena: ops[i] > 0 allocates that many bytes
+// (result[i] = offset or -1), ops[i] = -(k + 1) releases the block of op k
+// (result[i] = bytes free afterwards).
+int hpmxp_test_arena(size_t arena_bytes, const int64_t* ops, int nops, int64_t* result) {
+  if (!ops || !result || nops < 0) return HPMXP_EINVAL;
+  Arena a(arena_bytes);
+  for (int i = 0; i < nops; ++i) {
+    if (ops[i] > 0) {
+      const size_t off = a.alloc((size_t)ops[i]);
+      result[i] = off == kNone ? -1 : (int64_t)off;
+    } else {
+      const int64_t k = -ops[i] - 1;
+      if (k < 0 || k >= i || ops[k] <= 0 || result[k] < 0) return HPMXP_EINVAL;
+      a.release((size_t)result[k], (size_t)ops[k]);
+      result[i] = (int64_t)a.free_bytes();
+    }
+  }
+  return HPMXP_OK;
+}
+
+}  // extern "C"
