@@ -124,6 +124,8 @@ bool prof_on();
 void* prof_begin(cudaStream_t st);
 void prof_end(void* token, int kind, double work, cudaStream_t st);
 
+cudaError_t host_wait(cudaStream_t st);   // waits for `st` (spinning unless HPMXP_BLOCKING_WAIT=1)
+cudaError_t read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t st);   // + host_wait
 hpmxp_status status_from_cuda(cudaError_t e);
 hpmxp_status status_from_word(uint32_t w);
 

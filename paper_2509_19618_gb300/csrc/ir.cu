@@ -1124,9 +1124,7 @@ struct Solver {
   }
 
   cudaError_t read_brief() {
-    cudaError_t e = cudaMemcpyAsync(brief, w.brief, sizeof(Brief) * K, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return e;
+    return read_to_host(brief, w.brief, sizeof(Brief) * K, st);
   }
   bool any(int Brief::*f) const {
     for (int r = 0; r < K; ++r)
@@ -1259,7 +1257,7 @@ hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, i
   cudaError_t e = s.run();
   if (e != cudaSuccess) return status_from_cuda(e);
   uint32_t word = 0;
-  e = cudaMemcpyAsync(&word, s.w.status, 4, cudaMemcpyDeviceToHost, st);
+  e = read_to_host(&word, s.w.status, 4, st);
   if (e == cudaSuccess) e = s.read_brief();
   if (e != cudaSuccess) return status_from_cuda(e);
   if (word) return status_from_word(word);
@@ -1289,8 +1287,7 @@ hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, con
   cudaError_t e = s.setup();
   if (e == cudaSuccess) e = s.precond(v, ldv, z, ldz);
   uint32_t word = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&word, s.w.status, 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = read_to_host(&word, s.w.status, 4, st);
   if (e != cudaSuccess) return status_from_cuda(e);
   return status_from_word(word);
 }
@@ -1303,11 +1300,7 @@ hpmxp_status residual_check(int64_t n, const double* A, int64_t lda, const doubl
   e = residual(n, (int)nrhs, A, lda, x, ldx, b, ldb, w.r, n, 2, 1, w, st);
   if (e != cudaSuccess) return status_from_cuda(e);
   std::vector<RhsState> hs(nrhs);
-  for (int64_t r = 0; r < nrhs; ++r) {
-    e = cudaMemcpyAsync(&hs[r], w.st + r, sizeof(RhsState), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return status_from_cuda(e);
-  }
-  e = cudaStreamSynchronize(st);
+  e = read_to_host(hs.data(), w.st, sizeof(RhsState) * (size_t)nrhs, st);
   if (e != cudaSuccess) return status_from_cuda(e);
   for (int64_t r = 0; r < nrhs; ++r) {
     double rn, xn, bn, an;

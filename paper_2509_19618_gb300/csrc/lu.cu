@@ -850,8 +850,7 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
   if (lk.owns_lock()) lk.unlock();
   if (f.err != cudaSuccess) return status_from_cuda(f.err);
   uint32_t word = 0;
-  cudaError_t e = cudaMemcpyAsync(&word, f.w.status, sizeof(word), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaError_t e = read_to_host(&word, f.w.status, sizeof(word), st);
   if (e != cudaSuccess) return status_from_cuda(e);
   return status_from_word(word);
 }

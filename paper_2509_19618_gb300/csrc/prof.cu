@@ -4,6 +4,10 @@
 // time and work to the dominant kernel without a profiler.
 #include "internal.h"
 
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -52,6 +56,67 @@ void resolve_locked() {
 }
 
 }  // namespace
+
+// Host waits of the library.  By default the calling thread spins in
+// cudaStreamSynchronize (lowest latency); HPMXP_BLOCKING_WAIT=1 makes it
+// sleep on a blocking-sync event instead, which frees host cores when many
+// threads each drive their own stream but adds a wake-up delay to every wait.
+cudaError_t host_wait(cudaStream_t st) {
+  static const bool blocking = [] {
+    const char* e = getenv("HPMXP_BLOCKING_WAIT");
+    return e && e[0] == '1';
+  }();
+  if (!blocking) return cudaStreamSynchronize(st);
+  struct Events {
+    cudaEvent_t ev[64] = {};
+    ~Events() {
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    }
+  };
+  thread_local Events tl;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaStreamSynchronize(st);
+  cudaEvent_t& ev = tl.ev[dev];
+  if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventBlockingSync | cudaEventDisableTiming)) != cudaSuccess) {
+    ev = nullptr;
+    return e;
+  }
+  if ((e = cudaEventRecord(ev, st)) != cudaSuccess) return e;
+  return cudaEventSynchronize(ev);
+}
+
+// Device -> host read of `bytes` through a per-thread pinned staging buffer
+// (a copy into pageable memory would wait inside the driver, spinning), then
+// host_wait.  Returns once `dst` holds the data.
+cudaError_t read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  struct Staging {
+    void* p = nullptr;
+    size_t cap = 0;
+    ~Staging() {
+      if (p) cudaFreeHost(p);
+    }
+  };
+  thread_local Staging tl;
+  if (tl.cap < bytes) {
+    if (tl.p) cudaFreeHost(tl.p);
+    tl.p = nullptr;
+    tl.cap = 0;
+    const size_t cap = std::max<size_t>(bytes, 4096);
+    cudaError_t e = cudaMallocHost(&tl.p, cap);
+    if (e != cudaSuccess) {
+      tl.p = nullptr;
+      return e;
+    }
+    tl.cap = cap;
+  }
+  cudaError_t e = cudaMemcpyAsync(tl.p, src, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = host_wait(st);
+  if (e == cudaSuccess) memcpy(dst, tl.p, bytes);
+  return e;
+}
 
 void count_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 

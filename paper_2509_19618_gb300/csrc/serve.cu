@@ -178,7 +178,7 @@ struct hpmxp_executor {
       s = hpmxp_solve_ir(r.n, A, lda, LU, L.ld, r.prec, b, ldb, x, ldx, r.nrhs, &r.params, c.info, sws,
                          L.sws_bytes, st);
     else
-      cudaStreamSynchronize(st);   // nothing of this request may still run when its block is released
+      host_wait(st);   // nothing of this request may still run when its block is released
     c.status = (int32_t)s;
     c.t_done = clock();
     return c;
