@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--margin", type=float, default=1.0, help="diagonal-dominance margin")
     ap.add_argument("--fp64-comparator", action="store_true",
                     help="also time an fp64 LU solve with partial pivoting (torch/cuSOLVER) of the same A")
+    ap.add_argument("--fp64-operator-steps", type=int, default=3,
+                    help="also time this many solves with the inner GMRES operator in fp64 (0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
@@ -433,6 +435,32 @@ def main():
     if pc["launches"]:
         roofline["precond_gbs"] = pc["work"] / (pc["ms"] / 1e3) / 1e9
 
+    # the same solve with every step of the refinement in fp64 (inner operator included)
+    fp64op = None
+    if args.fp64_operator_steps > 0 and params.precond_fp32:
+        p64 = capi.hpmxp_ir_params_default()
+        keep = solver.params
+        solver.params = p64
+        solver(A, b)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        res = []
+        e0.record(stream)
+        for _ in range(args.fp64_operator_steps):
+            x64, info64, st64 = solver(A, b)
+            res.append((st64, info64[0]))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t64 = e0.elapsed_time(e1) / 1e3 / args.fp64_operator_steps
+        sr64 = float(api.residual(A, solver.x, b)[0])
+        solver.params = keep
+        fp64op = {"value": hpl_ops(n) / t64 / 1e12, "unit": "TFLOP/s", "ms_per_step": t64 * 1e3,
+                  "steps": args.fp64_operator_steps, "scaled_residual": sr64,
+                  "valid": bool(all(st == capi.OK for st, _ in res) and sr64 < 16.0),
+                  "ir_iters": res[-1][1]["iters"], "ir_outer": res[-1][1]["outer"],
+                  "what": "same solve, inner GMRES operator (preconditioner and Arnoldi product) in fp64, "
+                          "inner tolerance 1e-12"}
+
     # timed region 2: end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -479,7 +507,7 @@ def main():
                 "valid": bool(ok and sr < 16.0), "scaled_residual": sr,
                 "ir_iters": infos[-1][1]["iters"], "ir_outer": infos[-1][1]["outer"],
                 "ir_status": int(infos[-1][0]), "diag": args.diag, "margin": args.margin,
-                "fp64_lu_comparator": fp64,
+                "fp64_lu_comparator": fp64, "fp64_inner_operator": fp64op,
                 "gpu_launches": int(launches), "roofline": roofline, "clocks": clk.summary(),
                 "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
