@@ -8,11 +8,12 @@
 //       column major) is read once for all columns, coalesced 16-byte loads,
 //       split over column chunks with a deterministic second pass.  The
 //       first pass can also accumulate |A| row sums (||A||_inf).
-//   precond_kernel  z = U^{-1} L^{-1} v with the 16-bit factors, both sweeps
-//       in one cooperative launch: block rows of 64 are owned round-robin by
-//       the CTAs; the owner of a block solves its diagonal block as soon as
-//       every earlier block has been applied and publishes it behind a
-//       release flag; others wait (bounded) with acquire loads.
+//   precond_kernel<T>  z = U^{-1} L^{-1} v with the 16-bit factors, in T =
+//       float or double arithmetic, both sweeps in one cooperative launch:
+//       block rows of 128 are owned round-robin by the CTAs; the owner of a
+//       block solves it (a product with the inverted diagonal block) as soon
+//       as every earlier block has been applied, and publishes it as tagged
+//       64-bit words that the other CTAs poll (bounded).
 //   mgs_step / vec_norm / givens / cycle_start / cycle_finish / update:
 //       modified Gram-Schmidt Arnoldi, Givens least squares, x += V y.
 // All control decisions are taken on the device; the host reads a few
@@ -29,7 +30,6 @@ namespace {
 
 constexpr int kMaxM = 64;     // largest restart length
 constexpr int kMaxK = 8;      // right-hand sides refined together
-constexpr int kTB = 64;       // preconditioner block rows
 constexpr int kRedBlocks = 304;
 
 __device__ inline unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
@@ -216,263 +216,32 @@ __global__ void gemv_finish_kernel(int64_t n, int K, int nchunk, const double* _
 }
 
 // ---------------------------------------------------------------------------
-// Preconditioner z = U^{-1} L^{-1} v, arithmetic T (double or float).
-// ---------------------------------------------------------------------------
-template <class T>
-__device__ inline T as_t(float f) { return (T)f; }
-
-template <class T>
-__device__ inline void spin_until(const int* flag, int epoch, uint32_t* status, int* abort_flag) {
-  if (threadIdx.x == 0) {
-    const unsigned long long t0 = global_ns();
-    for (long long i = 0;; ++i) {
-      int v;
-      asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
-      if (v == epoch) break;
-      if (i > kSpinLimit || ((i & 63) == 0 && global_ns() - t0 > kWaitNs)) {
-        atomicOr(status, kErrTimeout);
-        *abort_flag = 1;
-        break;
-      }
-      if (i > 64) __nanosleep(32);
-    }
-  }
-  __syncthreads();
-}
-
-__device__ inline void publish_flag(int* flag, int epoch) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(flag), "r"(epoch) : "memory");
-}
-
-template <class T, int K>
-__global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
-                                                      int fmt, const double* __restrict__ v, int64_t ldv,
-                                                      double* __restrict__ z, int64_t ldz, T* __restrict__ pub,
-                                                      int* __restrict__ flags, int epoch, uint32_t* status) {
-  extern __shared__ unsigned char smraw[];
-  const int nb = (int)cdiv<int64_t>(n, kTB);
-  const int G = gridDim.x, me = blockIdx.x;
-  const int nown = (nb - me + G - 1) / G;      // blocks me, me+G, ...
-  T* acc = reinterpret_cast<T*>(smraw);        // [nown][kTB][K]
-  T* zc = acc + (size_t)nown * kTB * K;        // [kTB][K] current published block
-  float* tile = reinterpret_cast<float*>(zc + kTB * K);   // [kTB][kTB + 1] diagonal block
-  T* part = reinterpret_cast<T*>(tile + kTB * (kTB + 1)); // [4][kTB][K] partial sums
-  __shared__ int abort_flag;
-  const int tid = threadIdx.x;
-  if (tid == 0) abort_flag = 0;
-  int* fflags = flags;          // forward sweep
-  int* bflags = flags + nb;     // backward sweep
-  T* fpub = pub;
-  T* bpub = pub + (size_t)nb * kTB * K;
-
-  // initialize accumulators with v
-  for (int o = 0; o < nown; ++o) {
-    const int blk = me + o * G;
-    for (int t = tid; t < kTB * K; t += 256) {
-      const int ii = t % kTB, r = t / kTB;
-      const int64_t i = (int64_t)blk * kTB + ii;
-      acc[((size_t)o * kTB + ii) * K + r] = i < n ? (T)v[i + r * ldv] : (T)0;
-    }
-  }
-  __syncthreads();
-
-  // acc_o -= Tile(row block of o, column block c) * zc ; tile from LU.  The
-  // 16 tile entries of a thread are loaded together (independent loads, one
-  // memory latency) before the multiply-adds.
-  auto apply_tile = [&](int o, int c) {
-    const int blk = me + o * G;
-    const int ii = tid % kTB, jg = tid / kTB;     // 4 column groups of 16
-    const int64_t i = (int64_t)blk * kTB + ii;
-    const int64_t ic = i < n ? i : n - 1;
-    T lv[16];
-#pragma unroll
-    for (int jj = 0; jj < 16; ++jj) {
-      int64_t j = (int64_t)c * kTB + jg * 16 + jj;
-      const bool in = i < n && j < n;
-      j = j < n ? j : n - 1;
-      const float f = u16_to_f32(LU[ic + j * ld], fmt);
-      lv[jj] = in ? (T)f : (T)0;
-    }
-    T s[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) s[r] = (T)0;
-#pragma unroll
-    for (int jj = 0; jj < 16; ++jj)
-#pragma unroll
-      for (int r = 0; r < K; ++r) s[r] = lv[jj] * zc[(jg * 16 + jj) * K + r] + s[r];
-#pragma unroll
-    for (int r = 0; r < K; ++r) part[(jg * kTB + ii) * K + r] = s[r];
-    __syncthreads();
-    for (int t = tid; t < kTB * K; t += 256) {
-      const int i2 = t / K, r = t % K;
-      T tot = part[(0 * kTB + i2) * K + r] + part[(1 * kTB + i2) * K + r];
-      tot = tot + part[(2 * kTB + i2) * K + r];
-      tot = tot + part[(3 * kTB + i2) * K + r];
-      acc[((size_t)o * kTB + i2) * K + r] -= tot;
-    }
-    __syncthreads();
-  };
-
-  // load diagonal block c into the shared tile (16 independent loads per thread)
-  auto load_diag = [&](int c) {
-    float v[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int t = tid + k * 256;
-      const int ii = t % kTB, jj = t / kTB;
-      const int64_t i = (int64_t)c * kTB + ii, j = (int64_t)c * kTB + jj;
-      const bool in = i < n && j < n;
-      const float f = u16_to_f32(LU[(in ? i : 0) + (in ? j : 0) * ld], fmt);
-      v[k] = in ? f : (i == j ? 1.0f : 0.0f);
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int t = tid + k * 256;
-      tile[(t % kTB) * (kTB + 1) + t / kTB] = v[k];
-    }
-    __syncthreads();
-  };
-
-  // Solve the diagonal block of owned block o (forward: unit lower L;
-  // backward: upper U), publish it and keep it in zc.
-  auto solve_publish = [&](int o, int c, bool forward) {
-    load_diag(c);
-    if (tid < 32) {   // one warp, rows lane and lane + 32, pivots in order
-      T* a = acc + (size_t)o * kTB * K;
-      if (forward) {
-        for (int p = 0; p < kTB; ++p) {
-          T zp[K];
-#pragma unroll
-          for (int r = 0; r < K; ++r) zp[r] = a[p * K + r];
-          __syncwarp();
-          for (int ii = tid; ii < kTB; ii += 32)
-            if (ii > p) {
-              const T l = (T)tile[ii * (kTB + 1) + p];
-#pragma unroll
-              for (int r = 0; r < K; ++r) a[ii * K + r] = a[ii * K + r] - l * zp[r];
-            }
-          __syncwarp();
-        }
-      } else {
-        for (int p = kTB - 1; p >= 0; --p) {
-          const T u = (T)tile[p * (kTB + 1) + p];
-          T zp[K];
-#pragma unroll
-          for (int r = 0; r < K; ++r) zp[r] = a[p * K + r] / u;
-          __syncwarp();
-          if (tid == 0) {
-#pragma unroll
-            for (int r = 0; r < K; ++r) a[p * K + r] = zp[r];
-          }
-          for (int ii = tid; ii < p; ii += 32) {
-            const T uu = (T)tile[ii * (kTB + 1) + p];
-#pragma unroll
-            for (int r = 0; r < K; ++r) a[ii * K + r] = a[ii * K + r] - uu * zp[r];
-          }
-          __syncwarp();
-        }
-      }
-    }
-    __syncthreads();
-    T* dst = forward ? fpub : bpub;
-    for (int t = tid; t < kTB * K; t += 256) {
-      const T val = acc[(size_t)o * kTB * K + t];
-      dst[(size_t)c * kTB * K + t] = val;
-      if (!forward) {
-        const int ii = t / K, r = t % K;
-        const int64_t i = (int64_t)c * kTB + ii;
-        if (i < n) z[i + r * ldz] = (double)val;
-      }
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) publish_flag(forward ? &fflags[c] : &bflags[c], epoch);
-  };
-
-  // ---------------- forward sweep: unit lower L ----------------
-  // Look-ahead: the owner of block c+1 applies block c to it, solves and
-  // publishes it before updating its other blocks with block c.
-  int solved = -1;   // forward: last block this CTA solved ahead of its turn
-  for (int c = 0; c < nb; ++c) {
-    if (abort_flag) break;
-    const int owner = c % G;
-    const int last = me + (nown - 1) * G;
-    if (owner == me) {
-      const int o = c / G;
-      if (solved != c) solve_publish(o, c, true);
-      for (int t = tid; t < kTB * K; t += 256) zc[t] = acc[(size_t)o * kTB * K + t];
-      __syncthreads();
-    } else {
-      if (nown == 0 || last <= c) continue;   // no owned block after c
-      spin_until<T>(&fflags[c], epoch, status, &abort_flag);
-      if (abort_flag) break;
-      for (int t = tid; t < kTB * K; t += 256) zc[t] = fpub[(size_t)c * kTB * K + t];
-      __syncthreads();
-    }
-    int skip = -1;
-    if (c + 1 < nb && (c + 1) % G == me) {
-      const int o1 = (c + 1) / G;
-      apply_tile(o1, c);
-      solve_publish(o1, c + 1, true);
-      solved = c + 1;
-      skip = o1;   // solve_publish leaves zc (block c) untouched
-    }
-    for (int o = 0; o < nown; ++o)
-      if (o != skip && me + o * G > c) apply_tile(o, c);
-  }
-  __syncthreads();
-  // acc now holds y = L^{-1} v for the owned blocks
-
-  // ---------------- backward sweep: upper U ----------------
-  solved = nb;
-  for (int c = nb - 1; c >= 0; --c) {
-    if (abort_flag) break;
-    const int owner = c % G;
-    if (owner == me) {
-      const int o = c / G;
-      if (solved != c) solve_publish(o, c, false);
-      for (int t = tid; t < kTB * K; t += 256) zc[t] = acc[(size_t)o * kTB * K + t];
-      __syncthreads();
-    } else {
-      if (nown == 0 || me >= c) continue;   // owned blocks are me, me+G, ...; none before c
-      spin_until<T>(&bflags[c], epoch, status, &abort_flag);
-      if (abort_flag) break;
-      for (int t = tid; t < kTB * K; t += 256) zc[t] = bpub[(size_t)c * kTB * K + t];
-      __syncthreads();
-    }
-    int skip = -1;
-    if (c - 1 >= 0 && (c - 1) % G == me) {
-      const int o1 = (c - 1) / G;
-      apply_tile(o1, c);
-      solve_publish(o1, c - 1, false);
-      solved = c - 1;
-      skip = o1;
-    }
-    for (int o = 0; o < nown; ++o)
-      if (o != skip && me + o * G < c) apply_tile(o, c);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// fp32 preconditioner (the default refinement path): 128-row blocks, the
-// diagonal blocks of L and U inverted once per solve in fp32 (setup kernel
-// below), so the diagonal solve is a parallel 128 x 128 product.  Each
-// published block is a run of 64-bit words (fp32 value | epoch << 32): a
-// reader's poll of the words delivers the data itself, with no separate flag.
-// The owner of the next block prefetches its two tiles (off-diagonal and
-// inverted diagonal) into shared memory before it waits.
+// Preconditioner: 128-row blocks, the diagonal blocks of L and U inverted once
+// per solve (setup kernel below, in the arithmetic type T), so the diagonal
+// solve is a parallel 128 x 128 product.  Each published block is a run of
+// 64-bit words that carry their epoch: (fp32 value | epoch << 32) for T =
+// float, two words (high half | epoch << 32), (low half | epoch << 32) per
+// value for T = double; a reader's poll of the words delivers the data itself,
+// with no separate flag.  The owner of the next block prefetches its
+// off-diagonal tile (and, for float, the inverted diagonal block) into shared
+// memory before it waits; the fp64 inverse (128 KB) is read from L2.
 // ---------------------------------------------------------------------------
 constexpr int kTB32 = 128;
 
+template <class T> __device__ inline T fma_t(T a, T b, T c);
+template <> __device__ inline float fma_t<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ inline double fma_t<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Inverse of diagonal block c (c < nb) of the unit-lower L (which == 0) or of
-// U (which == 1), fp32, from the 16-bit factors: one thread per column,
-// column-oriented substitution.  Output inv[(which * nb + c) * 128 * 128 +
-// j * 128 + i] = inverse(i, j).
-__global__ void __launch_bounds__(128) diag_inv32_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
-                                                         int fmt, float* __restrict__ inv) {
-  extern __shared__ float dsm[];
-  float* t = dsm;                          // t[j * 129 + i] = block(i, j)
-  float* x = dsm + kTB32 * (kTB32 + 1);    // x[j * 129 + i] = inverse(i, j)
+// U (which == 1) in T arithmetic, from the 16-bit factors: one thread per
+// column, column-oriented substitution.  Output inv[(which * nb + c) * 128 *
+// 128 + j * 128 + i] = inverse(i, j).
+template <class T>
+__global__ void __launch_bounds__(128) diag_inv_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
+                                                       int fmt, T* __restrict__ inv) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  float* t = reinterpret_cast<float*>(dsm_raw);                         // t[j * 129 + i] = block(i, j)
+  T* x = reinterpret_cast<T*>(dsm_raw + sizeof(float) * kTB32 * 130);   // x[j * 129 + i] = inverse(i, j)
   const int nb = (int)cdiv<int64_t>(n, kTB32);
   const int c = blockIdx.x, which = blockIdx.y, tid = threadIdx.x;
   const int64_t base = (int64_t)c * kTB32;
@@ -484,28 +253,34 @@ __global__ void __launch_bounds__(128) diag_inv32_kernel(int64_t n, const uint16
   __syncthreads();
   const int j = tid;   // column of the inverse
   if (which == 0) {    // L X = I, unit lower: X(i, j) = -sum_{k=j}^{i-1} L(i, k) X(k, j)
-    for (int i = 0; i < kTB32; ++i) x[j * 129 + i] = i == j ? 1.0f : 0.0f;
+    for (int i = 0; i < kTB32; ++i) x[j * 129 + i] = i == j ? (T)1 : (T)0;
     for (int i = j + 1; i < kTB32; ++i) {
-      float s = 0.0f;
-      for (int k = j; k < i; ++k) s = __fmaf_rn(t[k * 129 + i], x[j * 129 + k], s);
+      T s = (T)0;
+      for (int k = j; k < i; ++k) s = fma_t<T>((T)t[k * 129 + i], x[j * 129 + k], s);
       x[j * 129 + i] = -s;
     }
   } else {             // U Y = I: Y(i, j) = (delta - sum_{k=i+1}^{j} U(i, k) Y(k, j)) / U(i, i)
-    for (int i = 0; i < kTB32; ++i) x[j * 129 + i] = 0.0f;
-    x[j * 129 + j] = 1.0f / t[j * 129 + j];
+    for (int i = 0; i < kTB32; ++i) x[j * 129 + i] = (T)0;
+    x[j * 129 + j] = (T)1 / (T)t[j * 129 + j];
     for (int i = j - 1; i >= 0; --i) {
-      float s = 0.0f;
-      for (int k = i + 1; k <= j; ++k) s = __fmaf_rn(t[k * 129 + i], x[j * 129 + k], s);
-      x[j * 129 + i] = -s / t[i * 129 + i];
+      T s = (T)0;
+      for (int k = i + 1; k <= j; ++k) s = fma_t<T>((T)t[k * 129 + i], x[j * 129 + k], s);
+      x[j * 129 + i] = -s / (T)t[i * 129 + i];
     }
   }
   __syncthreads();
-  float* out = inv + ((int64_t)which * nb + c) * kTB32 * kTB32;
+  T* out = inv + ((int64_t)which * nb + c) * kTB32 * kTB32;
   for (int idx = tid; idx < kTB32 * kTB32; idx += 128) out[idx] = x[(idx / kTB32) * 129 + idx % kTB32];
 }
 
-__device__ inline unsigned long long tag_word(float v, int epoch) {
-  return (unsigned long long)__float_as_uint(v) | ((unsigned long long)(unsigned)epoch << 32);
+template <class T>
+size_t diag_inv_smem() { return sizeof(float) * kTB32 * 130 + sizeof(T) * kTB32 * 129; }
+
+// words of one published value
+template <class T> constexpr int kWords = sizeof(T) / 4;
+
+__device__ inline unsigned long long tag_word(uint32_t bits, int epoch) {
+  return (unsigned long long)bits | ((unsigned long long)(unsigned)epoch << 32);
 }
 
 __device__ inline void cp_async16(uint32_t dst, const void* src, int bytes) {
@@ -515,32 +290,34 @@ __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;"
 template <int N>
 __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int K>
-__global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
-                                                        int fmt, const float* __restrict__ dinv,
-                                                        const double* __restrict__ v, int64_t ldv,
-                                                        double* __restrict__ z, int64_t ldz,
-                                                        unsigned long long* __restrict__ pub, int epoch,
-                                                        uint32_t* status) {
-  extern __shared__ __align__(16) float smf[];
+template <class T, int K>
+__global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
+                                                      int fmt, const T* __restrict__ dinv,
+                                                      const double* __restrict__ v, int64_t ldv,
+                                                      double* __restrict__ z, int64_t ldz,
+                                                      unsigned long long* __restrict__ pub, int epoch,
+                                                      uint32_t* status) {
+  constexpr bool kInvInSmem = sizeof(T) == 4;   // the fp32 inverse (64 KB) is staged; the fp64 one stays in L2
+  constexpr int W = kWords<T>;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   const int nb = (int)cdiv<int64_t>(n, kTB32);
   const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x;
   const int nown = (nb - me + G - 1) / G;
-  float* ti = smf;                                              // [128][128] inverse diagonal, ti[j*128+i]
-  uint16_t* tl = reinterpret_cast<uint16_t*>(ti + kTB32 * kTB32);  // 3 x [128][128] 16-bit tiles, tl[j*128+i]
-  float* acc = reinterpret_cast<float*>(tl + 3 * kTB32 * kTB32);   // [nown][128][K]
-  float* zc = acc + (size_t)nown * kTB32 * K;                   // [128][K] block c
-  float* zs = zc + kTB32 * K;                                   // [128][K] block being solved
-  float* part = zs + kTB32 * K;                                 // [2][128][K]
+  uint16_t* tl = reinterpret_cast<uint16_t*>(sm_raw);             // 3 x [128][128] 16-bit tiles, tl[j*128+i]
+  float* ti = reinterpret_cast<float*>(tl + 3 * kTB32 * kTB32);   // [128][128] fp32 inverse (float only)
+  T* acc = reinterpret_cast<T*>(kInvInSmem ? (unsigned char*)(ti + kTB32 * kTB32) : (unsigned char*)ti);
+  T* zc = acc + (size_t)nown * kTB32 * K;                         // [128][K] block c
+  T* zs = zc + kTB32 * K;                                         // [128][K] block being solved
+  T* part = zs + kTB32 * K;                                       // [2][128][K]
   __shared__ int abort_flag;
   if (tid == 0) abort_flag = 0;
   unsigned long long* fpub = pub;
-  unsigned long long* bpub = pub + (size_t)nb * kTB32 * K;
+  unsigned long long* bpub = pub + (size_t)nb * kTB32 * K * W;
   for (int o = 0; o < nown; ++o)
     for (int t = tid; t < kTB32 * K; t += 256) {
       const int ii = t % kTB32, r = t / kTB32;
       const int64_t i = (int64_t)(me + o * G) * kTB32 + ii;
-      acc[((size_t)o * kTB32 + ii) * K + r] = i < n ? (float)v[i + r * ldv] : 0.0f;
+      acc[((size_t)o * kTB32 + ii) * K + r] = i < n ? (T)v[i + r * ldv] : (T)0;
     }
   // abort_flag (and acc) must be written before any thread reads them: shared
   // memory starts with whatever the SM's previous block left there
@@ -561,31 +338,51 @@ __global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_
       cp_async16((uint32_t)__cvta_generic_to_shared(dst + jj * kTB32 + ii), src, bytes);
     }
   };
+  auto inv_block = [&](int which, int cb) { return dinv + ((int64_t)which * nb + cb) * kTB32 * kTB32; };
+  // fp64: the 64 inverse entries a thread multiplies, M(ii, h*64 .. h*64+63),
+  // loaded into registers when the block becomes next; used by its solve
+  T invr[kInvInSmem ? 1 : 64];
   auto fetch_inv = [&](int which, int cb) {
-    const float* src = dinv + ((int64_t)which * nb + cb) * kTB32 * kTB32;
+    const T* src = inv_block(which, cb);
+    if constexpr (kInvInSmem) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int chunk = tid + q * 256;            // 4096 chunks of 4 floats
-      cp_async16((uint32_t)__cvta_generic_to_shared(ti + chunk * 4), src + chunk * 4, 16);
+      for (int q = 0; q < 16; ++q) {
+        const int chunk = tid + q * 256;          // 4096 chunks of 4 floats
+        cp_async16((uint32_t)__cvta_generic_to_shared(ti + chunk * 4), src + chunk * 4, 16);
+      }
+    } else {
+      const int ii = tid % kTB32, h = tid / kTB32;
+#pragma unroll
+      for (int q = 0; q < 64; ++q) invr[q] = __ldcg(src + (h * 64 + q) * kTB32 + ii);
     }
   };
-  // out[i][r] (-)= sum_j T(i, j) w[j][r]; T 16-bit (tile) or fp32 (inverse)
-  auto product = [&](const uint16_t* T16, const float* T32, const float* w, float* out, bool subtract) {
+  // out[i][r] (-)= sum_j M(i, j) w[j][r]; M a 16-bit tile (T16) or the inverse (Tinv, fp32 in
+  // shared memory or T in global memory)
+  auto product = [&](const uint16_t* T16, const T* Tinv, const T* w, T* out, bool subtract) {
     const int ii = tid % kTB32, h = tid / kTB32;
-    float s[K];
+    T s[K];
 #pragma unroll
-    for (int r = 0; r < K; ++r) s[r] = 0.0f;
+    for (int r = 0; r < K; ++r) s[r] = (T)0;
+    if (T16) {
 #pragma unroll 8
-    for (int jj = h * 64; jj < h * 64 + 64; ++jj) {
-      const float tv = T16 ? u16_to_f32(T16[jj * kTB32 + ii], fmt) : T32[jj * kTB32 + ii];
+      for (int jj = h * 64; jj < h * 64 + 64; ++jj) {
+        const T tv = (T)u16_to_f32(T16[jj * kTB32 + ii], fmt);
 #pragma unroll
-      for (int r = 0; r < K; ++r) s[r] = __fmaf_rn(tv, w[jj * K + r], s[r]);
+        for (int r = 0; r < K; ++r) s[r] = fma_t<T>(tv, w[jj * K + r], s[r]);
+      }
+    } else {
+#pragma unroll 16
+      for (int jj = h * 64; jj < h * 64 + 64; ++jj) {
+        const T tv = Tinv[jj * kTB32 + ii];
+#pragma unroll
+        for (int r = 0; r < K; ++r) s[r] = fma_t<T>(tv, w[jj * K + r], s[r]);
+      }
     }
 #pragma unroll
     for (int r = 0; r < K; ++r) part[(h * kTB32 + ii) * K + r] = s[r];
     __syncthreads();
     for (int t = tid; t < kTB32 * K; t += 256) {
-      const float tot = part[t] + part[kTB32 * K + t];
+      const T tot = part[t] + part[kTB32 * K + t];
       out[t] = subtract ? out[t] - tot : tot;
     }
     __syncthreads();
@@ -594,32 +391,63 @@ __global__ void __launch_bounds__(256) precond32_kernel(int64_t n, const uint16_
   auto ready = [&]() { cp_async_wait<0>(); __syncthreads(); };
   auto ready_prev = [&]() { cp_async_wait<1>(); __syncthreads(); };
   // wait for the tagged words of block c and unpack them into dst
-  auto receive = [&](const unsigned long long* src, int c, float* dst) {
-    const unsigned long long* w = src + (size_t)c * kTB32 * K;
+  auto receive = [&](const unsigned long long* src, int c, T* dst) {
+    const unsigned long long* w = src + (size_t)c * kTB32 * K * W;
     const unsigned long long t0 = global_ns();
     for (int t = tid; t < kTB32 * K; t += 256) {
-      unsigned long long word;
-      for (long long it = 0;; ++it) {
-        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(word) : "l"(w + t) : "memory");
-        if ((int)(word >> 32) == epoch) break;
-        if (it > kSpinLimit || ((it & 63) == 63 && global_ns() - t0 > kWaitNs)) {
-          atomicOr(status, kErrTimeout);
-          abort_flag = 1;
-          break;
+      uint32_t bits[W];
+#pragma unroll
+      for (int h = 0; h < W; ++h) {
+        unsigned long long word;
+        for (long long it = 0;; ++it) {
+          asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(word) : "l"(w + (size_t)t * W + h) : "memory");
+          if ((int)(word >> 32) == epoch) break;
+          if (it > kSpinLimit || ((it & 63) == 63 && global_ns() - t0 > kWaitNs)) {
+            atomicOr(status, kErrTimeout);
+            abort_flag = 1;
+            break;
+          }
         }
+        bits[h] = (uint32_t)(word & 0xffffffffu);
       }
-      dst[t] = __uint_as_float((unsigned)(word & 0xffffffffu));
+      if constexpr (W == 1) dst[t] = __uint_as_float(bits[0]);
+      else dst[t] = __hiloint2double((int)bits[0], (int)bits[1]);
     }
     __syncthreads();
   };
   // zs = Tinv acc_o, stored back into acc_o and published (backward: also into z)
   auto solve = [&](int o, int c, bool backward, unsigned long long* dst) {
-    float* a = acc + (size_t)o * kTB32 * K;
-    product(nullptr, ti, a, zs, false);
-    unsigned long long* wd = dst + (size_t)c * kTB32 * K;
+    T* a = acc + (size_t)o * kTB32 * K;
+    if constexpr (kInvInSmem) {
+      product(nullptr, reinterpret_cast<const T*>(ti), a, zs, false);
+    } else {
+      const int ii = tid % kTB32, h = tid / kTB32;
+      T sr[K];
+#pragma unroll
+      for (int r = 0; r < K; ++r) sr[r] = (T)0;
+#pragma unroll
+      for (int q = 0; q < 64; ++q)
+#pragma unroll
+        for (int r = 0; r < K; ++r) sr[r] = fma_t<T>(invr[q], a[(h * 64 + q) * K + r], sr[r]);
+#pragma unroll
+      for (int r = 0; r < K; ++r) part[(h * kTB32 + ii) * K + r] = sr[r];
+      __syncthreads();
+      for (int t = tid; t < kTB32 * K; t += 256) zs[t] = part[t] + part[kTB32 * K + t];
+      __syncthreads();
+    }
+    unsigned long long* wd = dst + (size_t)c * kTB32 * K * W;
     for (int t = tid; t < kTB32 * K; t += 256) {
       a[t] = zs[t];
-      asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(wd + t), "l"(tag_word(zs[t], epoch)) : "memory");
+      if constexpr (W == 1) {
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(wd + t), "l"(tag_word(__float_as_uint(zs[t]), epoch))
+                     : "memory");
+      } else {
+        const double d = zs[t];
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(wd + 2 * t),
+                     "l"(tag_word((uint32_t)__double2hiint(d), epoch)) : "memory");
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(wd + 2 * t + 1),
+                     "l"(tag_word((uint32_t)__double2loint(d), epoch)) : "memory");
+      }
       if (backward) {
         const int ii = t / K, r = t % K;
         const int64_t i = (int64_t)c * kTB32 + ii;
@@ -929,7 +757,6 @@ struct SolveWs {
   RhsState* st;
   Brief* brief;
   unsigned int* counter;
-  int* flags;        // 2 * nb
   double* partials;  // kMaxK * kRedBlocks
   double* r;         // n x K
   double* w;         // n x K
@@ -937,8 +764,8 @@ struct SolveWs {
   double* V;         // K x (m+1) x n
   double* P;         // nchunk x n x K
   void* RS;          // nchunk x n (fp64 size)
-  void* pub;         // 2 x round_up(n, 128) x K 8-byte words
-  float* dinv;       // 2 x nb128 x 128 x 128 inverted diagonal blocks (fp32 path)
+  void* pub;         // 2 sweeps x round_up(n, 128) x K values x (1 or 2) 8-byte tagged words
+  void* dinv;        // 2 x nb128 x 128 x 128 inverted diagonal blocks (float or double)
   size_t bytes;
 };
 
@@ -951,6 +778,9 @@ int gemv_chunks(int64_t n, int K = kMaxK) {
   return (int)c;
 }
 
+// tagged words of both sweeps, sized for fp64 values (two words each)
+size_t pub_bytes(int64_t n, int64_t K) { return sizeof(unsigned long long) * 2 * 2 * round_up<int64_t>(n, kTB32) * K; }
+
 SolveWs carve_solve(void* base, int64_t n, int64_t K, int m) {
   SolveWs w{};
   size_t off = 0;
@@ -959,13 +789,11 @@ SolveWs carve_solve(void* base, int64_t n, int64_t K, int m) {
     off += round_up<size_t>(bytes, 256);
     return p;
   };
-  const int64_t nb = cdiv<int64_t>(n, kTB);
   const int nchunk = gemv_chunks(n);
   w.status = (uint32_t*)take(256);
   w.st = (RhsState*)take(sizeof(RhsState) * kMaxK);
   w.brief = (Brief*)take(sizeof(Brief) * kMaxK);
   w.counter = (unsigned int*)take(256);
-  w.flags = (int*)take(sizeof(int) * 2 * nb);
   w.partials = (double*)take(sizeof(double) * kMaxK * kRedBlocks);
   w.r = (double*)take(sizeof(double) * n * K);
   w.w = (double*)take(sizeof(double) * n * K);
@@ -973,8 +801,8 @@ SolveWs carve_solve(void* base, int64_t n, int64_t K, int m) {
   w.V = (double*)take(sizeof(double) * n * (m + 1) * K);
   w.P = (double*)take(sizeof(double) * nchunk * n * K);
   w.RS = take(sizeof(double) * nchunk * n);
-  w.pub = take(sizeof(double) * 2 * round_up<int64_t>(n, kTB32) * K);
-  w.dinv = (float*)take(sizeof(float) * 2 * round_up<int64_t>(n, kTB32) * kTB32);
+  w.pub = take(pub_bytes(n, K));
+  w.dinv = take(sizeof(double) * 2 * round_up<int64_t>(n, kTB32) * kTB32);
   w.bytes = off;
   return w;
 }
@@ -1023,75 +851,51 @@ cudaError_t residual(int64_t n, int K, const double* A, int64_t lda, const doubl
 // set to this one value, never to a per-call size).
 constexpr size_t kMaxPrecondSmem = 200 * 1024;
 
-size_t precond_smem(int64_t n, int K, int G, bool fp32) {
-  const int nb = (int)cdiv<int64_t>(n, kTB);
+template <class T>
+size_t precond_smem(int64_t n, int K, int G) {
+  const int nb = (int)cdiv<int64_t>(n, kTB32);
   const int nown = cdiv(nb, G);
-  const size_t ts = fp32 ? 4 : 8;
-  return ts * ((size_t)nown * kTB * K + kTB * K + 4 * kTB * K) + sizeof(float) * kTB * (kTB + 1) + 64;
+  const size_t inv = sizeof(T) == 4 ? sizeof(float) * kTB32 * kTB32 : 0;
+  return sizeof(uint16_t) * 3 * kTB32 * kTB32 + inv +
+         sizeof(T) * ((size_t)nown * kTB32 * K + 2 * kTB32 * K + 2 * kTB32 * K) + 64;
 }
 
 template <class T, int K>
-cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt, const double* v, int64_t ldv,
-                             double* z, int64_t ldz, const SolveWs& w, int epoch, int G, size_t smem,
-                             cudaStream_t st) {
+cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt, const T* dinv, const double* v,
+                             int64_t ldv, double* z, int64_t ldz, unsigned long long* pub, int epoch,
+                             uint32_t* status, int G, size_t smem, cudaStream_t st) {
   auto kern = precond_kernel<T, K>;
   // one value for every call: concurrent solves on other threads set the same cap
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPrecondSmem);
-  if (e != cudaSuccess) return e;
-  T* pub = (T*)w.pub;
-  int* flags = w.flags;
-  uint32_t* status = w.status;
-  void* args[] = {&n, (void*)&LU, &ld, &fmt, (void*)&v, &ldv, &z, &ldz, &pub, &flags, &epoch, &status};
-  return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(256), args, smem, st);
-}
-
-template <class T>
-cudaError_t precond_launch_t(int K, int64_t n, const uint16_t* LU, int64_t ld, int fmt, const double* v,
-                             int64_t ldv, double* z, int64_t ldz, const SolveWs& w, int epoch, int G, size_t smem,
-                             cudaStream_t st) {
-  switch (K) {
-    case 1: return precond_launch_k<T, 1>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
-    case 2: return precond_launch_k<T, 2>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
-    case 3: return precond_launch_k<T, 3>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
-    case 4: return precond_launch_k<T, 4>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
-    case 5: return precond_launch_k<T, 5>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
-    case 6: return precond_launch_k<T, 6>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
-    case 7: return precond_launch_k<T, 7>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
-    default: return precond_launch_k<T, 8>(n, LU, ld, fmt, v, ldv, z, ldz, w, epoch, G, smem, st);
-  }
-}
-
-size_t precond32_smem(int64_t n, int K, int G) {
-  const int nb = (int)cdiv<int64_t>(n, kTB32);
-  const int nown = cdiv(nb, G);
-  return sizeof(float) * kTB32 * kTB32 + sizeof(uint16_t) * 3 * kTB32 * kTB32 +
-         sizeof(float) * ((size_t)nown * kTB32 * K + 2 * kTB32 * K + 2 * kTB32 * K) + 64;
-}
-
-template <int K>
-cudaError_t precond32_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt, const float* dinv,
-                               const double* v, int64_t ldv, double* z, int64_t ldz, unsigned long long* pub,
-                               int epoch, uint32_t* status, int G, size_t smem, cudaStream_t st) {
-  auto kern = precond32_kernel<K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPrecondSmem);
   if (e != cudaSuccess) return e;
   void* args[] = {&n, (void*)&LU, &ld, &fmt, (void*)&dinv, (void*)&v, &ldv, &z, &ldz, &pub, &epoch, &status};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(256), args, smem, st);
 }
 
-cudaError_t precond32_launch(int K, int64_t n, const uint16_t* LU, int64_t ld, int fmt, const float* dinv,
-                             const double* v, int64_t ldv, double* z, int64_t ldz, unsigned long long* pub,
-                             int epoch, uint32_t* status, int G, size_t smem, cudaStream_t st) {
+template <class T>
+cudaError_t precond_launch(int K, int64_t n, const uint16_t* LU, int64_t ld, int fmt, const T* dinv,
+                           const double* v, int64_t ldv, double* z, int64_t ldz, unsigned long long* pub,
+                           int epoch, uint32_t* status, int G, size_t smem, cudaStream_t st) {
   switch (K) {
-    case 1: return precond32_launch_k<1>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 2: return precond32_launch_k<2>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 3: return precond32_launch_k<3>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 4: return precond32_launch_k<4>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 5: return precond32_launch_k<5>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 6: return precond32_launch_k<6>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 7: return precond32_launch_k<7>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    default: return precond32_launch_k<8>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 1: return precond_launch_k<T, 1>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 2: return precond_launch_k<T, 2>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 3: return precond_launch_k<T, 3>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 4: return precond_launch_k<T, 4>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 5: return precond_launch_k<T, 5>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 6: return precond_launch_k<T, 6>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 7: return precond_launch_k<T, 7>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    default: return precond_launch_k<T, 8>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
   }
+}
+
+template <class T>
+cudaError_t diag_inv_launch(int64_t n, const uint16_t* LU, int64_t ld, int fmt, void* dinv, cudaStream_t st) {
+  const size_t ism = diag_inv_smem<T>();
+  cudaError_t e = cudaFuncSetAttribute(diag_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+  if (e != cudaSuccess) return e;
+  diag_inv_kernel<T><<<dim3((unsigned)cdiv<int64_t>(n, kTB32), 2), 128, ism, st>>>(n, LU, ld, fmt, (T*)dinv);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 struct Solver {
@@ -1114,10 +918,12 @@ struct Solver {
   cudaError_t precond(const double* v, int64_t ldv, double* z, int64_t ldz) {
     ++epoch;
     void* tok = prof_begin(st);
+    unsigned long long* pub = (unsigned long long*)w.pub;
     cudaError_t e = prm.precond_fp32
-                        ? precond32_launch(K, n, LU, ldlu, fmt, w.dinv, v, ldv, z, ldz,
-                                           (unsigned long long*)w.pub, epoch, w.status, G, psmem, st)
-                        : precond_launch_t<double>(K, n, LU, ldlu, fmt, v, ldv, z, ldz, w, epoch, G, psmem, st);
+                        ? precond_launch<float>(K, n, LU, ldlu, fmt, (const float*)w.dinv, v, ldv, z, ldz, pub,
+                                                epoch, w.status, G, psmem, st)
+                        : precond_launch<double>(K, n, LU, ldlu, fmt, (const double*)w.dinv, v, ldv, z, ldz, pub,
+                                                 epoch, w.status, G, psmem, st);
     prof_end(tok, kProfPrecond, 2.0 * (double)n * (double)n, st);
     count_launches(1);
     return e;
@@ -1134,30 +940,19 @@ struct Solver {
 
   cudaError_t setup() {
     cudaError_t e;
-    const int nb = (int)cdiv<int64_t>(n, kTB);
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     // one CTA per SM at most: a cooperative launch keeps all of them resident
-    if (prm.precond_fp32) {
-      const int nb32 = (int)cdiv<int64_t>(n, kTB32);
-      G = std::max(1, std::min(nb32, sms));
-      psmem = precond32_smem(n, K, G);
-      if ((e = cudaMemsetAsync(w.pub, 0, sizeof(double) * 2 * round_up<int64_t>(n, kTB32) * K, st)) != cudaSuccess)
-        return e;
-      const size_t ism = sizeof(float) * 2 * kTB32 * (kTB32 + 1);
-      if ((e = cudaFuncSetAttribute(diag_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism)) !=
-          cudaSuccess)
-        return e;
-      diag_inv32_kernel<<<dim3((unsigned)nb32, 2), 128, ism, st>>>(n, LU, ldlu, fmt, w.dinv);
-      count_launches(1);
-    } else {
-      G = std::max(1, std::min(nb, sms));
-      psmem = precond_smem(n, K, G, false);
-    }
+    const int nb = (int)cdiv<int64_t>(n, kTB32);
+    G = std::max(1, std::min(nb, sms));
+    psmem = prm.precond_fp32 ? precond_smem<float>(n, K, G) : precond_smem<double>(n, K, G);
     if (psmem > kMaxPrecondSmem) return cudaErrorInvalidValue;
+    if ((e = cudaMemsetAsync(w.pub, 0, pub_bytes(n, K), st)) != cudaSuccess) return e;
+    e = prm.precond_fp32 ? diag_inv_launch<float>(n, LU, ldlu, fmt, w.dinv, st)
+                         : diag_inv_launch<double>(n, LU, ldlu, fmt, w.dinv, st);
+    if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.st, 0, sizeof(RhsState) * kMaxK, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w.flags, 0, sizeof(int) * 2 * nb, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.counter, 0, 256, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.status, 0, 4, st)) != cudaSuccess) return e;
     init_kernel<<<1, 32, 0, st>>>(K, w.st);
