@@ -203,18 +203,26 @@ hpmxp_status hpmxp_residual(int64_t n, const double* A, int64_t lda, const doubl
  * hpmxp_launch_count: kernels this library has launched since it was loaded.
  * hpmxp_prof_enable(1) makes the library record a CUDA event pair around
  * every launch of the timed kinds, on the launching stream:
- *   kind 0  tensor-core GEMM        work = 2 M N K flops per launch
+ *   kind 0  tensor-core GEMM, Schur update (C -= A B^T)   work = 2 M N K flops per launch
  *   kind 1  fp64 GEMV (residual)    work = 8 n^2 bytes of A per launch
  *   kind 2  preconditioner apply    work = 2 n^2 bytes of factors per launch
  *   kind 3  diagonal-block getrf    work = 2 b^3 flops per launch
  *   kind 4  fp32 GEMV (Arnoldi product with the fp32 operator)  work = 8 n^2 bytes of A
+ *   kind 5  fp64 -> 16-bit cast     work = 10 n^2 bytes per launch
+ *   kind 6  panel operand kernels (column-panel pack, substitution operands)
+ *   kind 7  tensor-core GEMM, panel products (C = sign A B^T)  work = 2 M N K flops
  * hpmxp_prof_read synchronizes the recorded events and returns the summed
  * event time, work and launch count of one kind since the last reset.
- * Returns HPMXP_EINVAL for a bad kind or NULL output. */
+ * Returns HPMXP_EINVAL for a bad kind or NULL output.
+ * hpmxp_prof_timeline writes up to max_spans recorded spans since the last
+ * reset as triples (kind, start ms, end ms) on one clock (the first span's
+ * start is 0) into out (3 * max_spans doubles, may be NULL) and returns how
+ * many spans there are. */
 unsigned long long hpmxp_launch_count(void);
 void hpmxp_prof_enable(int on);
 void hpmxp_prof_reset(void);
 int hpmxp_prof_read(int kind, double* total_ms, double* total_work, long long* launches);
+int hpmxp_prof_timeline(double* out, int max_spans);
 
 #ifdef __cplusplus
 }

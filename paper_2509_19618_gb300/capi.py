@@ -93,6 +93,7 @@ def load():
             "hpmxp_prof_enable": ([i32], None),
             "hpmxp_prof_reset": ([], None),
             "hpmxp_prof_read": ([i32, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)], i32),
+            "hpmxp_prof_timeline": ([P, i32], i32),
             "hpmxp_test_precond": ([i64, P, i64, i32, P, i64, P, i64, i64, i32, P, sz, P], i32),
             "hpmxp_test_arena": ([sz, ctypes.POINTER(i64), i32, ctypes.POINTER(i64)], i32),
             "hpmxp_test_fill_smem": ([ctypes.c_uint32, P], i32),
@@ -187,7 +188,9 @@ def hpmxp_prof_reset():
     load().hpmxp_prof_reset()
 
 
-PROF_GEMM, PROF_GEMV, PROF_PRECOND, PROF_GETRF, PROF_GEMV32 = 0, 1, 2, 3, 4
+PROF_GEMM, PROF_GEMV, PROF_PRECOND, PROF_GETRF, PROF_GEMV32, PROF_CAST, PROF_PANEL, PROF_GEMM_STORE = range(8)
+PROF_NAMES = {0: "gemm_update", 1: "gemv", 2: "precond", 3: "getrf", 4: "gemv32", 5: "cast", 6: "panel",
+              7: "gemm_panel"}
 
 
 def hpmxp_prof_read(kind: int) -> dict:
@@ -253,3 +256,11 @@ def hpmxp_executor_clock(ex) -> float:
 
 def hpmxp_executor_destroy(ex) -> int:
     return _call("hpmxp_executor_destroy", ex)
+
+
+def hpmxp_prof_timeline() -> list[tuple[int, float, float]]:
+    """Recorded spans since the last reset: (kind, start ms, end ms)."""
+    n = int(load().hpmxp_prof_timeline(None, 0))
+    buf = (ctypes.c_double * max(3 * n, 1))()
+    n = min(n, int(load().hpmxp_prof_timeline(buf, n)))
+    return [(int(buf[3 * i]), buf[3 * i + 1], buf[3 * i + 2]) for i in range(n)]

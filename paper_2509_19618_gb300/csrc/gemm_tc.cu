@@ -545,7 +545,7 @@ cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
   const double flops = 2.0 * g.M * (double)g.N * g.K;
   void* tok = prof_begin(st);
   gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, tc, p);
-  prof_end(tok, kProfGemm, flops, st);
+  prof_end(tok, g.mode == kEpiSub ? kProfGemm : kProfGemmStore, flops, st);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -118,7 +118,8 @@ hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, con
                            double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws, cudaStream_t st);
 
 // prof.cu: launch counting and optional event timing (kinds below).
-enum ProfKind { kProfGemm = 0, kProfGemv = 1, kProfPrecond = 2, kProfGetrf = 3, kProfGemv32 = 4, kProfKinds = 5 };
+enum ProfKind { kProfGemm = 0, kProfGemv = 1, kProfPrecond = 2, kProfGetrf = 3, kProfGemv32 = 4, kProfCast = 5,
+                kProfPanel = 6, kProfGemmStore = 7, kProfKinds = 8 };
 void count_launches(int k);
 bool prof_on();
 void* prof_begin(cudaStream_t st);

@@ -594,7 +594,9 @@ struct Factorizer {
   void pack(int64_t rows, int cols, const uint16_t* src, uint16_t* dst, int64_t ldd) {
     if (rows <= 0) return;
     dim3 grid((unsigned)cdiv<int64_t>(rows, 32), (unsigned)cdiv(cols, 32));
+    void* tok = prof_begin(st);
     pack_rows_kernel<<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, ld, dst, ldd);
+    prof_end(tok, kProfPanel, 4.0 * (double)rows * cols, st);
     count_launches(1);
     check(cudaGetLastError());
   }
@@ -611,17 +613,21 @@ struct Factorizer {
     u.C = at(kk, kk + kB); u.ldc = ld;
     u.mode = kEpiStore; u.sign = 1.0f;
     u.max_ctas = max_ctas;
+    fork();
     gemm(u);
-    pack(m, kB, at(kk + kB, kk), w.Li, kB);
-    GemmArgs l{};   // L21 = st(A21 Uinv): column major into LU, row major over the packed copy
-    l.M = (int)m; l.N = kB; l.K = kB;
-    l.A = w.Li; l.lda = kB;
-    l.B = bop(slot) + slot * kB; l.ldb = NB;
-    l.C = at(kk + kB, kk); l.ldc = ld;
-    l.R = w.Li; l.ldr = kB;
-    l.mode = kEpiStore; l.sign = 1.0f;
-    l.max_ctas = max_ctas;
-    gemm(l);
+    on_st3([&] {
+      pack(m, kB, at(kk + kB, kk), w.Li, kB);
+      GemmArgs l{};   // L21 = st(A21 Uinv): column major into LU, row major over the packed copy
+      l.M = (int)m; l.N = kB; l.K = kB;
+      l.A = w.Li; l.lda = kB;
+      l.B = bop(slot) + slot * kB; l.ldb = NB;
+      l.C = at(kk + kB, kk); l.ldc = ld;
+      l.R = w.Li; l.ldr = kB;
+      l.mode = kEpiStore; l.sign = 1.0f;
+      l.max_ctas = max_ctas;
+      gemm(l);
+    });
+    join();
     GemmArgs t{};   // A22 <- st(A22 - L21 U12)
     t.M = (int)m; t.N = (int)m; t.K = kB;
     t.A = w.Li; t.lda = kB;
@@ -642,6 +648,29 @@ struct Factorizer {
   cudaStream_t st2 = nullptr;
   cudaEvent_t evP = nullptr, evF = nullptr;
   int reserve = 0, sms = 0;
+  // The row-panel (U12) and column-panel (L21) substitution chains depend on
+  // nothing of each other: with a third stream the L21 chain runs on st3
+  // between a fork and a join on `st`.
+  cudaStream_t st3 = nullptr;
+  cudaEvent_t evS = nullptr, evJ = nullptr;
+  void fork() {
+    if (!st3) return;
+    check(cudaEventRecord(evS, st));
+    check(cudaStreamWaitEvent(st3, evS, 0));
+  }
+  void join() {
+    if (!st3) return;
+    check(cudaEventRecord(evJ, st3));
+    check(cudaStreamWaitEvent(st, evJ, 0));
+  }
+  template <class F>
+  void on_st3(F&& f) {
+    if (!st3) { f(); return; }
+    cudaStream_t keep = st;
+    st = st3;
+    f();
+    st = keep;
+  }
   int64_t overlap_min = 8192;   // smallest far(k) trailing size run concurrently
 
   void run() {
@@ -662,16 +691,18 @@ struct Factorizer {
       }
       const int64_t m = n - (k + b);
       if (m <= 0) break;
-      // (ii) row panel U12 and column panel L21, block substitution over s
-      pack(m, (int)b, at(k + b, k), Lp, NB);
+      // (ii) row panel U12 (on st) and column panel L21 (on st3 when there is
+      // one), block substitution over s; the chains meet before the update
+      fork();
+      on_st3([&] { pack(m, (int)b, at(k + b, k), Lp, NB); });
       for (int s = 0; s < nsub; ++s) {
         const int64_t s0 = k + (int64_t)s * kB;
         if (s > 0) {
+          void* tok = prof_begin(st);
           make_w_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(
               s * kB, aop(s), NB, at(s0, k), ld, fmt);
-          make_z_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(
-              s * kB, bop(s), NB, at(k, s0), ld, fmt);
-          count_launches(2);
+          prof_end(tok, kProfPanel, 2.0 * s * kB * kB * kB, st);
+          count_launches(1);
           check(cudaGetLastError());
         }
         GemmArgs u{};
@@ -682,16 +713,27 @@ struct Factorizer {
         u.mode = kEpiStore; u.sign = 1.0f;
         u.max_ctas = panel_ctas;
         gemm(u);
-        GemmArgs l{};
-        l.M = (int)m; l.N = kB; l.K = (s + 1) * kB;
-        l.A = Lp; l.lda = NB;
-        l.B = bop(s); l.ldb = NB;
-        l.C = at(k + b, s0); l.ldc = ld;
-        l.R = Lp + s * kB; l.ldr = NB;
-        l.mode = kEpiStore; l.sign = 1.0f;
-        l.max_ctas = panel_ctas;
-        gemm(l);
+        on_st3([&] {
+          if (s > 0) {
+            void* tok = prof_begin(st);
+            make_z_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(
+                s * kB, bop(s), NB, at(k, s0), ld, fmt);
+            prof_end(tok, kProfPanel, 2.0 * s * kB * kB * kB, st);
+            count_launches(1);
+            check(cudaGetLastError());
+          }
+          GemmArgs l{};
+          l.M = (int)m; l.N = kB; l.K = (s + 1) * kB;
+          l.A = Lp; l.lda = NB;
+          l.B = bop(s); l.ldb = NB;
+          l.C = at(k + b, s0); l.ldc = ld;
+          l.R = Lp + s * kB; l.ldr = NB;
+          l.mode = kEpiStore; l.sign = 1.0f;
+          l.max_ctas = panel_ctas;
+          gemm(l);
+        });
       }
+      join();
       // (iii) Schur update of depth b: A22 <- st(A22 - L21 U12)
       GemmArgs t{};
       t.K = (int)b;
@@ -781,8 +823,9 @@ cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st) {
 struct SideStream {
   std::mutex mu;   // one look-ahead factorization enqueues on this device at a time
   bool ok = false;
-  cudaStream_t st = nullptr;
-  cudaEvent_t evP = nullptr, evF = nullptr;
+  cudaStream_t st = nullptr;    // far part of the Schur update
+  cudaStream_t st3 = nullptr;   // column-panel (L21) chain, beside the row-panel chain
+  cudaEvent_t evP = nullptr, evF = nullptr, evS = nullptr, evJ = nullptr;
 };
 
 SideStream& side_stream(int dev) {
@@ -794,8 +837,11 @@ SideStream& side_stream(int dev) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (cudaStreamCreateWithPriority(&s.st, cudaStreamNonBlocking, lo) == cudaSuccess &&
+        cudaStreamCreateWithPriority(&s.st3, cudaStreamNonBlocking, hi) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evP, cudaEventDisableTiming) == cudaSuccess &&
-        cudaEventCreateWithFlags(&s.evF, cudaEventDisableTiming) == cudaSuccess)
+        cudaEventCreateWithFlags(&s.evF, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s.evS, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s.evJ, cudaEventDisableTiming) == cudaSuccess)
       s.ok = true;
   }
   return s;
@@ -804,7 +850,9 @@ SideStream& side_stream(int dev) {
 cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st) {
   const int64_t work = (n + 1) / 2 * n;
   const int blocks = (int)std::min<int64_t>(cdiv<int64_t>(work, 256), 152 * 16);
+  void* tok = prof_begin(st);
   cast_kernel<<<blocks, 256, 0, st>>>(n, A, lda, (uint16_t*)out, ldo, fmt);
+  prof_end(tok, kProfCast, 10.0 * (double)n * (double)n, st);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -840,10 +888,14 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
     if (ss.ok) {
       lk = std::unique_lock<std::mutex>(ss.mu);
       f.st2 = ss.st;
+      f.st3 = ss.st3;
       f.evP = ss.evP;
       f.evF = ss.evF;
+      f.evS = ss.evS;
+      f.evJ = ss.evJ;
       cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
-      f.reserve = std::max(4, f.sms / 12);
+      f.reserve = std::max(4, f.sms / 6);
+      if (const char* rv = getenv("HPMXP_RESERVE_SMS")) f.reserve = std::max(1, std::min(f.sms - 1, atoi(rv)));
     }
   }
   f.run();

@@ -26,6 +26,13 @@ struct Span {
 
 std::mutex g_mu;
 std::vector<Span> g_open;             // recorded, not yet resolved
+cudaEvent_t g_origin = nullptr;       // first span start since the last reset
+struct Interval {
+  int kind;
+  double t0, t1;                      // ms after g_origin
+};
+std::vector<Interval> g_timeline;     // resolved spans, in recording order
+constexpr size_t kMaxTimeline = size_t(1) << 20;
 double g_ms[kProfKinds], g_work[kProfKinds];
 long long g_count[kProfKinds];
 std::vector<cudaEvent_t> g_pool;
@@ -48,8 +55,11 @@ void resolve_locked() {
       g_ms[s.kind] += ms;
       g_work[s.kind] += s.work;
       g_count[s.kind] += 1;
+      float t0 = 0.0f;
+      if (g_origin && g_timeline.size() < kMaxTimeline && cudaEventElapsedTime(&t0, g_origin, s.a) == cudaSuccess)
+        g_timeline.push_back(Interval{s.kind, (double)t0, (double)t0 + ms});
     }
-    g_pool.push_back(s.a);
+    if (s.a != g_origin) g_pool.push_back(s.a);
     g_pool.push_back(s.b);
   }
   g_open.clear();
@@ -127,6 +137,7 @@ void* prof_begin(cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t a = take_event();
   cudaEventRecord(a, st);
+  if (!g_origin) g_origin = a;     // kept out of the pool until the next reset
   return (void*)a;
 }
 
@@ -153,6 +164,23 @@ void hpmxp_prof_reset(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   resolve_locked();
   for (int k = 0; k < kProfKinds; ++k) { g_ms[k] = 0.0; g_work[k] = 0.0; g_count[k] = 0; }
+  if (g_origin) g_pool.push_back(g_origin);
+  g_origin = nullptr;
+  g_timeline.clear();
+}
+
+int hpmxp_prof_timeline(double* out, int max_spans) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  resolve_locked();
+  const int k = (int)std::min<size_t>(g_timeline.size(), max_spans > 0 ? (size_t)max_spans : 0);
+  if (out) {
+    for (int i = 0; i < k; ++i) {
+      out[3 * i] = g_timeline[i].kind;
+      out[3 * i + 1] = g_timeline[i].t0;
+      out[3 * i + 2] = g_timeline[i].t1;
+    }
+  }
+  return (int)g_timeline.size();
 }
 
 int hpmxp_prof_read(int kind, double* total_ms, double* total_work, long long* launches) {
