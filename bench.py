@@ -50,6 +50,8 @@ def parse():
                     help="1: fp32 inner-GMRES operator (the benchmark default), 0: all fp64")
     ap.add_argument("--inner-tol", type=float, default=-1.0,
                     help="inner GMRES tolerance floor; -1: 1e-5 with the fp32 operator, library default otherwise")
+    ap.add_argument("--theta", type=float, default=-1.0,
+                    help="adaptive inner-stopping factor of GMRES-IR; -1: the library default")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--diag", default="dominant", choices=["dominant", "sqrtn", "none"],
                     help="diagonal of the generated matrix (row sum + margin, sqrt(n) scaling, unscaled)")
@@ -245,6 +247,8 @@ def run_serving(args):
     params = capi.hpmxp_ir_params_default()
     params.precond_fp32 = args.precond_fp32
     params.inner_tol = IR_KW["inner_tol"]
+    if args.theta >= 0:
+        params.theta = args.theta
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     specs = serve.request_stream(args.requests, args.rate, stream_seed=2509 + rank)
@@ -331,6 +335,8 @@ def main():
     args = parse()
     IR_KW.update(precond_prec=args.precond_fp32,
                  inner_tol=args.inner_tol if args.inner_tol >= 0 else (1e-5 if args.precond_fp32 else 1e-12))
+    if args.theta >= 0:
+        IR_KW.update(theta=args.theta)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -355,6 +361,8 @@ def main():
         params.inner_tol = args.inner_tol
     elif args.precond_fp32:
         params.inner_tol = 1e-5
+    if args.theta >= 0:
+        params.theta = args.theta
     nb = args.nb or autotune.pick_nb(n, prec, A, device=dev)
     fp64 = None
     if args.fp64_comparator and rank == 0:

@@ -642,12 +642,14 @@ struct Factorizer {
   // next block's column and row, on the caller's stream `st`) and "far" (the
   // rest, on the side stream `st2`).  Step k+1's diagonal block and panels run
   // on `st` while far(k) runs on `st2`; near(k+1) waits for far(k).  far(k)
-  // is held below the SM count (and the panel products at `reserve` CTAs)
-  // so both streams make progress.  Buffers read by far(k) are double
-  // buffered by step parity.
+  // is a persistent grid held `reserve` SMs below the SM count, so the panel
+  // chain always finds free SMs; the panel products themselves are not capped
+  // and spread over every SM that far(k) has released.  Buffers read by far(k)
+  // are double buffered by step parity.
   cudaStream_t st2 = nullptr;
   cudaEvent_t evP = nullptr, evF = nullptr;
   int reserve = 0, sms = 0;
+  bool cap_panels = false;  // panel products limited to `reserve` CTAs while far(k) runs
   // The row-panel (U12) and column-panel (L21) substitution chains depend on
   // nothing of each other: with a third stream the L21 chain runs on st3
   // between a fork and a join on `st`.
@@ -682,7 +684,7 @@ struct Factorizer {
       const int nsub = (int)cdiv<int64_t>(b, kB);
       const int par = step & 1;
       uint16_t* Lp = w.Lp[par];
-      const int panel_ctas = overlap && far_pending ? reserve : 0;
+      const int panel_ctas = overlap && far_pending && cap_panels ? reserve : 0;
       // (i) diagonal block
       for (int s = 0; s < nsub; ++s) {
         const int64_t kk = k + (int64_t)s * kB;
@@ -894,8 +896,9 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
       f.evS = ss.evS;
       f.evJ = ss.evJ;
       cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
-      f.reserve = std::max(4, f.sms / 6);
+      f.reserve = std::max(4, f.sms / 16);
       if (const char* rv = getenv("HPMXP_RESERVE_SMS")) f.reserve = std::max(1, std::min(f.sms - 1, atoi(rv)));
+      if (const char* cp = getenv("HPMXP_CAP_PANELS")) f.cap_panels = cp[0] != '0';
     }
   }
   f.run();
