@@ -41,6 +41,7 @@ constexpr int kStageA = kTJ * kRowBytes;      // MMA A operand: rows j (16 KiB)
 constexpr int kStageB = kTI * kRowBytes;      // MMA B operand: rows i (16 KiB)
 constexpr int kCBox = kTJ * 128;              // one C box: 64 rows x 128 columns (16 KiB)
 constexpr int kCTile = 2 * kCBox;             // 32 KiB
+constexpr int kCBufs = 3;                     // C tile buffers: one in the epilogue, one being stored, one loading
 constexpr int kEpiGroups = 2;                 // epilogue groups, one per 64-row half of the tile
 constexpr int kEpiThreads = 128;              // threads per epilogue group (one warp per TMEM lane quarter)
 constexpr int kThreads = 64 + kEpiGroups * kEpiThreads;
@@ -228,8 +229,13 @@ struct TcParams {
   uint32_t* status;
 };
 
+// Two floats rounded to nearest even into one 32-bit word of 16-bit values (lo
+// in the low half): one packed conversion instruction.
 __device__ inline uint32_t pack16x2(float lo, float hi, int fmt) {
-  return (uint32_t)f32_to_u16(lo, fmt) | ((uint32_t)f32_to_u16(hi, fmt) << 16);
+  uint32_t r;
+  if (fmt == kBF16) asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  else asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -241,14 +247,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const uint32_t sOpA = smem_u32(smem);                            // [kStages][rows j][128 B]
   const uint32_t sOpB = sOpA + kStages * kStageA;                  // [kStages][rows i][128 B]
   const uint32_t sC = sOpB + kStages * kStageB;                    // [2][2 boxes][cols j][128 B]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * (kStageA + kStageB) + 2 * kCTile);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * (kStageA + kStageB) + kCBufs * kCTile);
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int s) { return bar0 + 8u * (uint32_t)s; };
   auto empty = [&](int s) { return bar0 + 8u * (uint32_t)(kStages + s); };
   auto acc_full = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + b); };
   auto acc_empty = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + 2 + b); };
   auto c_full = [&](int b, int h) { return bar0 + 8u * (uint32_t)(2 * kStages + 4 + 2 * b + h); };
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 8);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4 + 2 * kCBufs);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -257,6 +263,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full(b), 1);
       mbar_init(acc_empty(b), kEpiGroups * kEpiThreads / 32);
+    }
+    for (int b = 0; b < kCBufs; ++b) {
       mbar_init(c_full(b, 0), 1);
       mbar_init(c_full(b, 1), 1);
     }
@@ -332,7 +340,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int jl = 32 * q + lane;
     const bool leader = ((warp - 2) & 3) == 0 && lane == 0;
     const bool load_c = p.has_c && p.mode == kEpiSub;
-    int issued_c[2] = {-1, -1};   // local tile whose C load is outstanding in each buffer
+    // C tile buffers rotate over local tiles: tile l uses buffer l % kCBufs.  The
+    // C of tile l + 2 is loaded into the buffer of tile l - 1 as soon as the
+    // store of tile l - 1 has been read, which is checked one tile later, when
+    // it is long done, so the epilogue never waits on its own store.
+    int issued_c[kCBufs];         // local tile whose C load is outstanding in each buffer
+    for (int b = 0; b < kCBufs; ++b) issued_c[b] = -1;
     if (leader && load_c) {       // prefetch this group's C box of the first two local tiles
       int local = 0;
       for (int t = blockIdx.x; t < p.ntiles && local < 2; t += gridDim.x, ++local) {
@@ -346,10 +359,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     int local = 0;
     for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++local) {
       const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
-      const int cb = local & 1, ab = local % p.nbuf;
+      const int cb = local % kCBufs, ab = local % p.nbuf;
       const uint32_t cbox = sC + cb * kCTile + g * kCBox;
       bool w = true;
-      if (load_c) w = mbar_wait(c_full(cb, g), (uint32_t)((local >> 1) & 1));
+      if (load_c) w = mbar_wait(c_full(cb, g), (uint32_t)((local / kCBufs) & 1));
       if (leader) issued_c[cb] = -1;
       w = w && mbar_wait(acc_full(ab), (uint32_t)((local / p.nbuf) & 1));
       w = __all_sync(0xffffffffu, w);   // warp-uniform for tcgen05.ld
@@ -420,14 +433,16 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (leader) {
           tma_store_2d(&tmC, i0 + 64 * g, j0, cbox);
           bulk_commit();
-          bulk_wait_read0();   // the box can be refilled
-          // prefetch this group's C box two local tiles ahead into the same buffer
+          // the store issued one tile ago has finished reading its buffer, which
+          // now receives the C of the tile two ahead
+          asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
           const int t2 = t + 2 * (int)gridDim.x;
           if (load_c && t2 < p.ntiles) {
+            const int b2 = (local + 2) % kCBufs;
             const int i2 = (t2 % p.tiles_i) * kTI, j2 = (t2 / p.tiles_i) * kTJ;
-            mbar_expect_tx(c_full(cb, g), kCBox);
-            tma_load_2d(cbox, &tmC, i2 + 64 * g, j2, c_full(cb, g));
-            issued_c[cb] = local + 2;
+            mbar_expect_tx(c_full(b2, g), kCBox);
+            tma_load_2d(sC + b2 * kCTile + g * kCBox, &tmC, i2 + 64 * g, j2, c_full(b2, g));
+            issued_c[b2] = local + 2;
           }
         }
       }
@@ -436,8 +451,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (leader) {
       bulk_wait0();
       // C loads issued for tiles this CTA did not reach (error path) land before exit
-      for (int b = 0; b < 2; ++b)
-        if (issued_c[b] >= 0 && !mbar_wait(c_full(b, g), (uint32_t)((issued_c[b] >> 1) & 1)))
+      for (int b = 0; b < kCBufs; ++b)
+        if (issued_c[b] >= 0 && !mbar_wait(c_full(b, g), (uint32_t)((issued_c[b] / kCBufs) & 1)))
           atomicOr(p.status, kErrTimeout);
     }
   }
@@ -481,7 +496,7 @@ bool make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows, 
 }
 
 constexpr size_t kSmemBytes =
-    1024 + (size_t)kStages * (kStageA + kStageB) + 2 * kCTile + 8 * (2 * kStages + 8) + 16;
+    1024 + (size_t)kStages * (kStageA + kStageB) + kCBufs * kCTile + 8 * (2 * kStages + 4 + 2 * kCBufs) + 16;
 
 int num_sms() {
   static int sms = 0;
