@@ -181,6 +181,14 @@ void hpmxp_ir_params_default(hpmxp_ir_params* p);
  * Synchronizes `stream`.  Returns HPMXP_OK when every right-hand side met the
  * threshold, else the worst per-column status (ENOCONV, EBREAKDOWN). */
 size_t hpmxp_solve_workspace(int64_t n, int64_t nrhs, int restart);
+
+/* Optional room for an fp32 copy of A (truncated toward zero), used when
+ * prm->precond_fp32 = 1 and ws_bytes >= hpmxp_solve_workspace(n, nrhs,
+ * restart) + hpmxp_solve_workspace_a32(n): the first residual of the solve
+ * writes the copy as it reads A, and the inner GMRES operator's products read
+ * it (4 bytes per entry instead of 8).  The products, and so every result, are
+ * bit-for-bit those computed from A itself.  4 n^2 bytes, rounded up. */
+size_t hpmxp_solve_workspace_a32(int64_t n);
 hpmxp_status hpmxp_solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu,
                             int prec, const double* b, int64_t ldb, double* x, int64_t ldx,
                             int64_t nrhs, const hpmxp_ir_params* prm, hpmxp_ir_info* info,

@@ -82,6 +82,7 @@ def load():
             "hpmxp_factor": ([i64, P, i64, i32, i32, P, i64, P, sz, P], i32),
             "hpmxp_ir_params_default": ([ctypes.POINTER(IRParams)], None),
             "hpmxp_solve_workspace": ([i64, i64, i32], sz),
+            "hpmxp_solve_workspace_a32": ([i64], sz),
             "hpmxp_solve_ir": ([i64, P, i64, P, i64, i32, P, i64, P, i64, i64, ctypes.POINTER(IRParams),
                                 ctypes.POINTER(IRInfo), P, sz, P], i32),
             "hpmxp_residual_workspace": ([i64, i64], sz),
@@ -166,6 +167,10 @@ def hpmxp_solve_workspace(n, nrhs, restart):
 def hpmxp_solve_ir(n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs, params, info, ws, ws_bytes, stream):
     return _call("hpmxp_solve_ir", n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs,
                  None if params is None else ctypes.byref(params), info, ws, ws_bytes, stream)
+
+
+def hpmxp_solve_workspace_a32(n):
+    return _call("hpmxp_solve_workspace_a32", n)
 
 
 def hpmxp_residual_workspace(n, nrhs):

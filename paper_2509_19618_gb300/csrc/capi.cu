@@ -20,7 +20,8 @@ hpmxp_status status_from_word(uint32_t w) {
 
 hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu, int prec,
                       const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs,
-                      const hpmxp_ir_params& prm, hpmxp_ir_info* info, void* ws, cudaStream_t st);
+                      const hpmxp_ir_params& prm, hpmxp_ir_info* info, void* ws, size_t ws_bytes,
+                      cudaStream_t st);
 hpmxp_status residual_check(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
                             const double* b, int64_t ldb, int64_t nrhs, double* out, void* ws, cudaStream_t st);
 
@@ -96,6 +97,8 @@ size_t hpmxp_solve_workspace(int64_t n, int64_t nrhs, int restart) {
   return solve_ws_bytes(n, nrhs, restart);
 }
 
+size_t hpmxp_solve_workspace_a32(int64_t n) { return n < 1 ? 0 : solve_a32_bytes(n); }
+
 hpmxp_status hpmxp_solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu, int prec,
                             const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs,
                             const hpmxp_ir_params* prm, hpmxp_ir_info* info, void* ws, size_t ws_bytes,
@@ -108,7 +111,7 @@ hpmxp_status hpmxp_solve_ir(int64_t n, const double* A, int64_t lda, const void*
       p.max_iters < 0 || !(p.accept > 0.0) || p.inner_tol < 0.0 || p.theta < 0.0)
     return HPMXP_EINVAL;
   if (ws_bytes < solve_ws_bytes(n, nrhs, p.restart)) return HPMXP_ENOMEM;
-  return solve_ir(n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs, p, info, ws, (cudaStream_t)stream);
+  return solve_ir(n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs, p, info, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 size_t hpmxp_residual_workspace(int64_t n, int64_t nrhs) {

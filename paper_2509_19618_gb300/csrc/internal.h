@@ -112,6 +112,7 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
 
 // ir.cu
 size_t solve_ws_bytes(int64_t n, int64_t nrhs, int restart);
+size_t solve_a32_bytes(int64_t n);   // optional fp32 copy of A after the solve workspace
 cudaError_t fill_smem(uint32_t pattern, cudaStream_t st);   // test support
 size_t residual_ws_bytes(int64_t n, int64_t nrhs);
 hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, const double* v, int64_t ldv,

@@ -98,6 +98,7 @@ template <int K, int kAbs, bool kF32 = false>   // kAbs: 0 none, 1 fp32 estimate
 __global__ void __launch_bounds__(kGemvThreads) gemv_partial_kernel(int64_t n, const double* __restrict__ A,
                                                                     int64_t lda, const double* __restrict__ X,
                                                                     int64_t ldx, int64_t chunk,
+                                                                    float* __restrict__ A32, int64_t ld32,
                                                                     double* __restrict__ P, void* __restrict__ RS) {
   __shared__ double xs[kGemvChunkElems];   // xs[r * chunk + jj]
   const int64_t i = (int64_t)blockIdx.x * kGemvRows + 2 * threadIdx.x;
@@ -118,6 +119,8 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_partial_kernel(int64_t n, c
   const bool two = i + 1 < n;
   const bool vec = two && ((((uintptr_t)(A + i)) & 15) == 0) && ((lda & 1) == 0);
   const double* col = A + i + j0 * lda;
+  // optional copy of the visited entries, truncated to fp32, for the fp32 operator's later products
+  float* col32 = A32 ? A32 + i + j0 * ld32 : nullptr;
   auto body = [&](double a0, double a1, int jj) {
     if (kF32) {
       // fp32 operator: A truncated to fp32, products accumulated in fp32
@@ -146,6 +149,12 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_partial_kernel(int64_t n, c
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = __ldcs(reinterpret_cast<const double2*>(col + (int64_t)u * lda));
       col += 8 * lda;
+      if (col32) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          *reinterpret_cast<float2*>(col32 + (int64_t)u * ld32) = make_float2(trunc_f32(v[u].x), trunc_f32(v[u].y));
+        col32 += 8 * ld32;
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u) body(v[u].x, v[u].y, jj + u);
     }
@@ -153,6 +162,11 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_partial_kernel(int64_t n, c
   for (; jj < cnt; ++jj) {
     const double a0 = col[0], a1 = two ? col[1] : 0.0;
     col += lda;
+    if (col32) {
+      col32[0] = trunc_f32(a0);
+      if (two) col32[1] = trunc_f32(a1);
+      col32 += ld32;
+    }
     body(a0, a1, jj);
   }
   double* Pc = P + (int64_t)blockIdx.y * n * K;
@@ -170,6 +184,69 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_partial_kernel(int64_t n, c
     R[i] = d0;
     if (two) R[i + 1] = d1;
   }
+}
+
+// The fp32 operator's product from the fp32 copy of A: the same chunks, the
+// same fp32 accumulation over each chunk's columns in order as the fp64-read
+// variant (so the same partial sums), 4 rows per thread, 16-byte loads.
+constexpr int kGemv32Rows = 4 * kGemvThreads;
+template <int K>
+__global__ void __launch_bounds__(kGemvThreads) gemv32_partial_kernel(int64_t n, const float* __restrict__ A32,
+                                                                      int64_t ld32, const double* __restrict__ X,
+                                                                      int64_t ldx, int64_t chunk,
+                                                                      double* __restrict__ P) {
+  __shared__ double xs[kGemvChunkElems];
+  const int64_t i = (int64_t)blockIdx.x * kGemv32Rows + 4 * threadIdx.x;
+  const int64_t j0 = (int64_t)blockIdx.y * chunk, j1 = min(j0 + chunk, n);
+  const int cnt = (int)(j1 - j0);
+  for (int t = threadIdx.x; t < cnt * K; t += kGemvThreads) {
+    const int jj = t % cnt, r = t / cnt;
+    xs[r * chunk + jj] = X[j0 + jj + r * ldx];
+  }
+  __syncthreads();
+  if (i >= n) return;
+  const int rows = (int)min((int64_t)4, n - i);
+  float acc[4][K];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int r = 0; r < K; ++r) acc[q][r] = 0.0f;
+  const float* col = A32 + i + j0 * ld32;
+  int jj = 0;
+  if (rows == 4) {
+    for (; jj + 8 <= cnt; jj += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcs(reinterpret_cast<const float4*>(col + (int64_t)u * ld32));
+      col += 8 * ld32;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float a[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const float xv = (float)xs[r * chunk + jj + u];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q][r] = __fmaf_rn(a[q], xv, acc[q][r]);
+        }
+      }
+    }
+  }
+  for (; jj < cnt; ++jj) {
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+      const float xv = (float)xs[r * chunk + jj];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < rows) acc[q][r] = __fmaf_rn(col[q], xv, acc[q][r]);
+    }
+    col += ld32;
+  }
+  double* Pc = P + (int64_t)blockIdx.y * n * K;
+#pragma unroll
+  for (int r = 0; r < K; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < rows) Pc[i + q + r * n] = (double)acc[q][r];
 }
 
 // out(i, r) = B(i, r) - sum_c P[c](i, r), or + sum_c P[c](i, r) when B is NULL
@@ -766,6 +843,8 @@ struct SolveWs {
   void* RS;          // nchunk x n (fp64 size)
   void* pub;         // 2 sweeps x round_up(n, 128) x K values x (1 or 2) 8-byte tagged words
   void* dinv;        // 2 x nb128 x 128 x 128 inverted diagonal blocks (float or double)
+  float* a32;        // optional fp32 copy of A (ld32), written by the first residual, NULL if none
+  int64_t ld32;
   size_t bytes;
 };
 
@@ -807,17 +886,30 @@ SolveWs carve_solve(void* base, int64_t n, int64_t K, int m) {
   return w;
 }
 
+// abs_mode: 0 plain, 1 with the fp32 |A| estimate (the first residual; also
+// fills w.a32 when there is one), 2 exact |A| row sums, 3 the fp32 operator's
+// product (from w.a32 when there is one)
 template <int K>
 cudaError_t gemv_k(int64_t n, const double* A, int64_t lda, const double* X, int64_t ldx, int abs_mode,
-                   double* P, void* RS, int nchunk, cudaStream_t st) {
+                   const SolveWs& w, int nchunk, cudaStream_t st) {
   const int64_t chunk = cdiv<int64_t>(n, nchunk);
   if (chunk * K > kGemvChunkElems) return cudaErrorInvalidValue;
   dim3 grid((unsigned)cdiv<int64_t>(n, kGemvRows), (unsigned)nchunk);
   const int T = kGemvThreads;
-  if (abs_mode == 3) gemv_partial_kernel<K, 0, true><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
-  else if (abs_mode == 0) gemv_partial_kernel<K, 0><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
-  else if (abs_mode == 1) gemv_partial_kernel<K, 1><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
-  else gemv_partial_kernel<K, 2><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, P, RS);
+  double* P = w.P;
+  void* RS = w.RS;
+  if (abs_mode == 3 && w.a32) {
+    dim3 g32((unsigned)cdiv<int64_t>(n, kGemv32Rows), (unsigned)nchunk);
+    gemv32_partial_kernel<K><<<g32, T, 0, st>>>(n, w.a32, w.ld32, X, ldx, chunk, P);
+  } else if (abs_mode == 3) {
+    gemv_partial_kernel<K, 0, true><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, nullptr, 0, P, RS);
+  } else if (abs_mode == 0) {
+    gemv_partial_kernel<K, 0><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, nullptr, 0, P, RS);
+  } else if (abs_mode == 1) {
+    gemv_partial_kernel<K, 1><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, w.a32, w.ld32, P, RS);
+  } else {
+    gemv_partial_kernel<K, 2><<<grid, T, 0, st>>>(n, A, lda, X, ldx, chunk, nullptr, 0, P, RS);
+  }
   return cudaGetLastError();
 }
 
@@ -829,14 +921,14 @@ cudaError_t residual(int64_t n, int K, const double* A, int64_t lda, const doubl
   cudaError_t e;
   void* tok = prof_begin(st);
   switch (K) {
-    case 1: e = gemv_k<1>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
-    case 2: e = gemv_k<2>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
-    case 3: e = gemv_k<3>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
-    case 4: e = gemv_k<4>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
-    case 5: e = gemv_k<5>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
-    case 6: e = gemv_k<6>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
-    case 7: e = gemv_k<7>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
-    default: e = gemv_k<8>(n, A, lda, X, ldx, abs_mode, w.P, w.RS, nchunk, st); break;
+    case 1: e = gemv_k<1>(n, A, lda, X, ldx, abs_mode, w, nchunk, st); break;
+    case 2: e = gemv_k<2>(n, A, lda, X, ldx, abs_mode, w, nchunk, st); break;
+    case 3: e = gemv_k<3>(n, A, lda, X, ldx, abs_mode, w, nchunk, st); break;
+    case 4: e = gemv_k<4>(n, A, lda, X, ldx, abs_mode, w, nchunk, st); break;
+    case 5: e = gemv_k<5>(n, A, lda, X, ldx, abs_mode, w, nchunk, st); break;
+    case 6: e = gemv_k<6>(n, A, lda, X, ldx, abs_mode, w, nchunk, st); break;
+    case 7: e = gemv_k<7>(n, A, lda, X, ldx, abs_mode, w, nchunk, st); break;
+    default: e = gemv_k<8>(n, A, lda, X, ldx, abs_mode, w, nchunk, st); break;
   }
   if (e != cudaSuccess) return e;
   gemv_finish_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, nchunk, w.P, B, ldb, out, ldo, X, ldx,
@@ -1036,11 +1128,14 @@ cudaError_t fill_smem(uint32_t pattern, cudaStream_t st) {
 }
 
 size_t solve_ws_bytes(int64_t n, int64_t nrhs, int restart) { return carve_solve(nullptr, n, nrhs, restart).bytes; }
+int64_t a32_ld(int64_t n) { return round_up<int64_t>(n, 4); }
+size_t solve_a32_bytes(int64_t n) { return round_up<size_t>(sizeof(float) * (size_t)a32_ld(n) * (size_t)n, 256); }
 size_t residual_ws_bytes(int64_t n, int64_t nrhs) { return carve_solve(nullptr, n, nrhs, 1).bytes; }
 
 hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu, int prec,
                       const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs,
-                      const hpmxp_ir_params& prm, hpmxp_ir_info* info, void* ws, cudaStream_t st) {
+                      const hpmxp_ir_params& prm, hpmxp_ir_info* info, void* ws, size_t ws_bytes,
+                      cudaStream_t st) {
   Solver s;
   s.n = n; s.K = (int)nrhs; s.m = prm.restart;
   s.A = A; s.lda = lda;
@@ -1048,6 +1143,12 @@ hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, i
   s.B = b; s.ldb = ldb; s.X = x; s.ldx = ldx;
   s.prm = prm;
   s.w = carve_solve(ws, n, nrhs, prm.restart);
+  // room for the fp32 copy of A after the workspace proper: the fp32 operator's
+  // products then read 4 instead of 8 bytes per entry
+  if (prm.precond_fp32 && ws_bytes >= s.w.bytes + solve_a32_bytes(n)) {
+    s.w.a32 = (float*)((char*)ws + s.w.bytes);
+    s.w.ld32 = a32_ld(n);
+  }
   s.st = st;
   cudaError_t e = s.run();
   if (e != cudaSuccess) return status_from_cuda(e);

@@ -432,3 +432,22 @@ def test_full_size_solve_n32768():
         assert abs(r) <= 16 * n * 2.0**-53 * (an * np.abs(xv).max() + np.abs(bv).max())
     del A, b, s
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,k", [(1000, 1), (2049, 3)])
+def test_fp32_copy_of_A_changes_no_bit(n, k):
+    """With room for the fp32 copy of A the fp32 operator's products read it
+    instead of A; the solution and the iteration counts are identical."""
+    A, b = api.generate(n, seed=n + 1, nrhs=k, device=DEV)
+    LU = api.factor(A, capi.BF16, 128)
+    p = api.ir_params(precond_fp32=1, inner_tol=1e-5)
+    base = capi.hpmxp_solve_workspace(n, k, p.restart)
+    outs = []
+    for extra in (0, capi.hpmxp_solve_workspace_a32(n)):
+        ws = api.workspace(base + extra, DEV)
+        x, info, st = api.solve_ir(A, LU, b, capi.BF16, p, ws=ws)
+        torch.cuda.synchronize()
+        assert st == capi.OK, info
+        outs.append((x.view().clone(), [i["iters"] for i in info]))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
