@@ -849,10 +849,13 @@ struct SolveWs {
 };
 
 // Column chunks of the GEMV: each chunk's X (chunk x K doubles) fits the
-// CTA's staging buffer, and there are enough CTAs to keep every SM loaded.
+// CTA's staging buffer; there are enough CTAs to keep every SM loaded (about
+// 8 per SM), but no CTA reads fewer than 32 columns (128 KB of A), so a small
+// system does not spread a short product over every SM.
 int gemv_chunks(int64_t n, int K = kMaxK) {
   const int64_t rb = cdiv<int64_t>(n, kGemvRows);
-  int64_t c = std::max<int64_t>(cdiv<int64_t>(n * K, kGemvChunkElems), cdiv<int64_t>(8 * 152, rb));
+  const int64_t spread = std::min<int64_t>(cdiv<int64_t>(8 * 152, rb), cdiv<int64_t>(n, 32));
+  int64_t c = std::max<int64_t>(cdiv<int64_t>(n * K, kGemvChunkElems), spread);
   c = std::max<int64_t>(1, std::min<int64_t>(c, cdiv<int64_t>(n, 8)));
   return (int)c;
 }

@@ -52,7 +52,7 @@ def _req(n, nrhs=1, **kw):
 def test_footprint_covers_buffers_and_grows():
     f1 = capi.hpmxp_request_footprint(_req(1000))
     assert f1 >= 10 * 1000 * 1000          # 8 n^2 (A) + 2 n^2 (LU)
-    assert capi.hpmxp_request_footprint(_req(2000)) > 3.5 * f1
+    assert capi.hpmxp_request_footprint(_req(2000)) > 3.2 * f1   # 10 n^2 grows 4x; fixed parts do not
     assert capi.hpmxp_request_footprint(_req(1000, 8)) > f1
     assert capi.hpmxp_request_footprint(_req(1000, 9)) == 0    # nrhs above 8
     assert capi.hpmxp_request_footprint(_req(0)) == 0
