@@ -68,26 +68,29 @@ __device__ inline uint16_t f64_to_u16(double x, int fmt) {
   return fmt == kBF16 ? f64_to_f16bits<7, 127>(x) : f64_to_f16bits<10, 15>(x);
 }
 
-// A (fp64, column major) -> LU (16-bit, column major).  Each thread converts
-// two consecutive rows of one column with one 16-byte load when aligned.
-__global__ void cast_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
-                            uint16_t* __restrict__ LU, int64_t ldlu, int fmt) {
-  const int64_t pairs = (n + 1) / 2;
-  const int64_t total = pairs * n;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = g / pairs, i = (g % pairs) * 2;
-    const double* src = A + i + j * lda;
-    uint16_t* dst = LU + i + j * ldlu;
-    if (i + 1 < n) {
-      double2 v;
-      if ((((uintptr_t)src) & 15) == 0) v = *reinterpret_cast<const double2*>(src);
-      else { v.x = src[0]; v.y = src[1]; }
-      const uint32_t packed = (uint32_t)f64_to_u16(v.x, fmt) | ((uint32_t)f64_to_u16(v.y, fmt) << 16);
-      *reinterpret_cast<uint32_t*>(dst) = packed;   // ldlu even and LU 16-byte aligned
-    } else {
-      dst[0] = f64_to_u16(src[0], fmt);
-    }
+// A (fp64, column major) -> LU (16-bit, column major).  CTA (x, y) converts
+// rows 2048 y .. +2047 of column x; each thread 8 consecutive rows with four
+// 16-byte loads and one 16-byte store when aligned (LU is 16-byte aligned
+// with ldlu % 8 == 0), entry by entry otherwise.
+constexpr int kCastRows = 256 * 8;
+__global__ void __launch_bounds__(256) cast_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
+                                                   uint16_t* __restrict__ LU, int64_t ldlu, int fmt) {
+  const int64_t j = blockIdx.x;
+  const int64_t i = (int64_t)blockIdx.y * kCastRows + 8 * (int64_t)threadIdx.x;
+  if (i >= n) return;
+  const double* src = A + i + j * lda;
+  uint16_t* dst = LU + i + j * ldlu;
+  if (i + 8 <= n && (((uintptr_t)src) & 15) == 0) {
+    double2 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __ldcs(reinterpret_cast<const double2*>(src) + k);
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      w[k] = (uint32_t)f64_to_u16(v[k].x, fmt) | ((uint32_t)f64_to_u16(v[k].y, fmt) << 16);
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    for (int k = 0; k < 8 && i + k < n; ++k) dst[k] = f64_to_u16(src[k], fmt);
   }
 }
 
@@ -412,62 +415,79 @@ __device__ inline float e4m3_to_f32(uint8_t v) {
   return s ? -f : f;
 }
 
-__global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs g) {
+// One CTA computes sub_m x sub_n tiles of 64 x 64 (sub_m = 2 when 64 < M <=
+// 128, sub_n likewise): the panel products write their result over an operand
+// (U12 over the B rows it reads, the row-major L21 copy over the A columns it
+// reads), so a CTA must cover the whole 128-wide dimension and finish reading
+// before it writes.  Each output's accumulation is the same in every case.
+__global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs g, int sub_m, int sub_n) {
   __shared__ float As[64][33], Bs[64][33];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
-  float acc[4][4], accg[4][4];
-  for (int a = 0; a < 4; ++a)
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
-  for (int k0 = 0; k0 < g.K; k0 += 32) {
-    if (g.fp8 && (k0 % 128) == 0) {
-      for (int a = 0; a < 4; ++a)
-        for (int c = 0; c < 4; ++c) accg[a][c] = 0.0f;
-    }
-    for (int idx = tid; idx < 64 * 32; idx += 256) {
-      const int r = idx / 32, kk = idx % 32;
-      const int64_t i = m0 + r, j = n0 + r;
-      float av = 0.0f, bv = 0.0f;
-      if (g.fp8) {
-        if (i < g.M) av = e4m3_to_f32(((const uint8_t*)g.A)[i * g.lda + k0 + kk]);
-        if (j < g.N) bv = e4m3_to_f32(((const uint8_t*)g.B)[j * g.ldb + k0 + kk]);
-      } else {
-        if (i < g.M) av = u16_to_f32(((const uint16_t*)g.A)[i * g.lda + k0 + kk], g.fmt);
-        if (j < g.N) bv = u16_to_f32(((const uint16_t*)g.B)[j * g.ldb + k0 + kk], g.fmt);
+  const int64_t mb = (int64_t)blockIdx.y * 64 * sub_m, nb = (int64_t)blockIdx.x * 64 * sub_n;
+  float acc[4][4][4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (t >= sub_m * sub_n) break;
+    const int64_t m0 = mb + 64 * (t % sub_m), n0 = nb + 64 * (t / sub_m);
+    float accg[4][4];
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c) acc[t][a][c] = 0.0f;
+    for (int k0 = 0; k0 < g.K; k0 += 32) {
+      if (g.fp8 && (k0 % 128) == 0) {
+        for (int a = 0; a < 4; ++a)
+          for (int c = 0; c < 4; ++c) accg[a][c] = 0.0f;
       }
-      As[r][kk] = av;
-      Bs[r][kk] = bv;
-    }
-    __syncthreads();
-    for (int kk = 0; kk < 32; ++kk)
-      for (int a = 0; a < 4; ++a)
-        for (int c = 0; c < 4; ++c) {
-          if (g.fp8) accg[a][c] = __fmaf_rn(As[ty * 4 + a][kk], Bs[tx * 4 + c][kk], accg[a][c]);
-          else acc[a][c] = __fmaf_rn(As[ty * 4 + a][kk], Bs[tx * 4 + c][kk], acc[a][c]);
+      for (int idx = tid; idx < 64 * 32; idx += 256) {
+        const int r = idx / 32, kk = idx % 32;
+        const int64_t i = m0 + r, j = n0 + r;
+        float av = 0.0f, bv = 0.0f;
+        if (g.fp8) {
+          if (i < g.M) av = e4m3_to_f32(((const uint8_t*)g.A)[i * g.lda + k0 + kk]);
+          if (j < g.N) bv = e4m3_to_f32(((const uint8_t*)g.B)[j * g.ldb + k0 + kk]);
+        } else {
+          if (i < g.M) av = u16_to_f32(((const uint16_t*)g.A)[i * g.lda + k0 + kk], g.fmt);
+          if (j < g.N) bv = u16_to_f32(((const uint16_t*)g.B)[j * g.ldb + k0 + kk], g.fmt);
         }
-    __syncthreads();
-    if (g.fp8 && ((k0 + 32) % 128) == 0) {
-      const int kb = k0 / 128;
-      for (int a = 0; a < 4; ++a)
-        for (int c = 0; c < 4; ++c) {
-          const int64_t i = min(m0 + ty * 4 + a, (int64_t)g.M - 1), j = min(n0 + tx * 4 + c, (int64_t)g.N - 1);
-          const float sc = __fmul_rn(g.sA[(i / 128) * g.sa_ld + kb], g.sB[(j / 128) * g.sb_ld + kb]);
-          acc[a][c] = __fmaf_rn(accg[a][c], sc, acc[a][c]);
-        }
+        As[r][kk] = av;
+        Bs[r][kk] = bv;
+      }
+      __syncthreads();
+      for (int kk = 0; kk < 32; ++kk)
+        for (int a = 0; a < 4; ++a)
+          for (int c = 0; c < 4; ++c) {
+            if (g.fp8) accg[a][c] = __fmaf_rn(As[ty * 4 + a][kk], Bs[tx * 4 + c][kk], accg[a][c]);
+            else acc[t][a][c] = __fmaf_rn(As[ty * 4 + a][kk], Bs[tx * 4 + c][kk], acc[t][a][c]);
+          }
+      __syncthreads();
+      if (g.fp8 && ((k0 + 32) % 128) == 0) {
+        const int kb = k0 / 128;
+        for (int a = 0; a < 4; ++a)
+          for (int c = 0; c < 4; ++c) {
+            const int64_t i = min(m0 + ty * 4 + a, (int64_t)g.M - 1), j = min(n0 + tx * 4 + c, (int64_t)g.N - 1);
+            const float sc = __fmul_rn(g.sA[(i / 128) * g.sa_ld + kb], g.sB[(j / 128) * g.sb_ld + kb]);
+            acc[t][a][c] = __fmaf_rn(accg[a][c], sc, acc[t][a][c]);
+          }
+      }
     }
   }
-  for (int a = 0; a < 4; ++a)
-    for (int c = 0; c < 4; ++c) {
-      const int64_t i = m0 + ty * 4 + a, j = n0 + tx * 4 + c;
-      if (i >= g.M || j >= g.N) continue;
-      uint16_t* cp = g.C ? (uint16_t*)g.C + i + j * g.ldc : nullptr;
-      float v;
-      if (g.mode == kEpiSub) v = __fsub_rn(u16_to_f32(*cp, g.fmt), acc[a][c]);
-      else v = g.sign * acc[a][c];
-      const uint16_t h = f32_to_u16(v, g.fmt);
-      if (cp) *cp = h;
-      if (g.R) ((uint16_t*)g.R)[i * g.ldr + j] = h;
-    }
+  // every read of this CTA's operands is done (the loop ends on a barrier)
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (t >= sub_m * sub_n) break;
+    const int64_t m0 = mb + 64 * (t % sub_m), n0 = nb + 64 * (t / sub_m);
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c) {
+        const int64_t i = m0 + ty * 4 + a, j = n0 + tx * 4 + c;
+        if (i >= g.M || j >= g.N) continue;
+        uint16_t* cp = g.C ? (uint16_t*)g.C + i + j * g.ldc : nullptr;
+        float v;
+        if (g.mode == kEpiSub) v = __fsub_rn(u16_to_f32(*cp, g.fmt), acc[t][a][c]);
+        else v = g.sign * acc[t][a][c];
+        const uint16_t h = f32_to_u16(v, g.fmt);
+        if (cp) *cp = h;
+        if (g.R) ((uint16_t*)g.R)[i * g.ldr + j] = h;
+      }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -814,8 +834,9 @@ int gemm_engine() {
 }
 
 cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st) {
-  dim3 grid((unsigned)cdiv(g.N, 64), (unsigned)cdiv(g.M, 64));
-  gemm_simt_kernel<<<grid, 256, 0, st>>>(g);
+  const int sub_m = (g.M > 64 && g.M <= 128) ? 2 : 1, sub_n = (g.N > 64 && g.N <= 128) ? 2 : 1;
+  dim3 grid((unsigned)cdiv(g.N, 64 * sub_n), (unsigned)cdiv(g.M, 64 * sub_m));
+  gemm_simt_kernel<<<grid, 256, 0, st>>>(g, sub_m, sub_n);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -850,10 +871,9 @@ SideStream& side_stream(int dev) {
 }
 
 cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st) {
-  const int64_t work = (n + 1) / 2 * n;
-  const int blocks = (int)std::min<int64_t>(cdiv<int64_t>(work, 256), 152 * 16);
   void* tok = prof_begin(st);
-  cast_kernel<<<blocks, 256, 0, st>>>(n, A, lda, (uint16_t*)out, ldo, fmt);
+  cast_kernel<<<dim3((unsigned)n, (unsigned)cdiv<int64_t>(n, kCastRows)), 256, 0, st>>>(n, A, lda, (uint16_t*)out,
+                                                                                    ldo, fmt);
   prof_end(tok, kProfCast, 10.0 * (double)n * (double)n, st);
   count_launches(1);
   return cudaGetLastError();
