@@ -123,11 +123,15 @@ __device__ inline void named_sync(int id, int nthreads) {
 
 // rank-kPW update of the block rows [i0, i1) x cols [j0, j1) of M (pitch kP):
 // M(i, j) += sgn * sum_{t in order} L(i, t) * R(t, j) with L(i,t) = Lm[t*kP + i],
-// R(t, j) = Rm[j*kP + t]; `desc` walks t from t1-1 down to t0.  4x4 register
-// micro-tiles, warp = tile column, lane = tile row.
+// R(t, j) = Rm[j*kP + t]; kDesc walks t from t1-1 down to t0, else up.  4x4
+// register micro-tiles, warp = tile column, lane = tile row.  A full 16-deep
+// slice (t0 a multiple of 16) reads R four pivots at a time; the terms of
+// every entry still come one FMA at a time in the same order.
+template <bool kDesc>
 __device__ inline void rank_update(float* M, const float* Lm, const float* Rm, int i0, int i1, int j0, int j1,
-                                   int t0, int t1, float sgn, bool desc, int wid, int nwarps, int lane) {
+                                   int t0, int t1, float sgn, int wid, int nwarps, int lane) {
   const int ni = (i1 - i0 + 3) / 4, nj = (j1 - j0 + 3) / 4;
+  const bool full = t1 - t0 == kPW && (t0 & 3) == 0;
   for (int tj = wid; tj < nj; tj += nwarps) {
     for (int ti = lane; ti < ni; ti += 32) {
       const int i = i0 + 4 * ti, j = j0 + 4 * tj;
@@ -136,15 +140,38 @@ __device__ inline void rank_update(float* M, const float* Lm, const float* Rm, i
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int r = 0; r < 4; ++r) acc[r][c] = M[(j + c) * kP + i + r];
-      for (int k = 0; k < t1 - t0; ++k) {
-        const int t = desc ? t1 - 1 - k : t0 + k;
-        const float4 l4 = *reinterpret_cast<const float4*>(&Lm[t * kP + i]);
-        const float l[4] = {sgn * l4.x, sgn * l4.y, sgn * l4.z, sgn * l4.w};
+      if (full) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float u = Rm[(j + c) * kP + t];
+        for (int g = 0; g < 4; ++g) {
+          const int tg = t0 + 4 * (kDesc ? 3 - g : g);
+          float rv[4][4];   // rv[c][u] = R(tg + u, j + c)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) acc[r][c] = __fmaf_rn(l[r], u, acc[r][c]);
+          for (int c = 0; c < 4; ++c) {
+            const float4 r4 = *reinterpret_cast<const float4*>(&Rm[(j + c) * kP + tg]);
+            rv[c][0] = r4.x; rv[c][1] = r4.y; rv[c][2] = r4.z; rv[c][3] = r4.w;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int uu = kDesc ? 3 - u : u;
+            const float4 l4 = *reinterpret_cast<const float4*>(&Lm[(tg + uu) * kP + i]);
+            const float l[4] = {sgn * l4.x, sgn * l4.y, sgn * l4.z, sgn * l4.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int r = 0; r < 4; ++r) acc[r][c] = __fmaf_rn(l[r], rv[c][uu], acc[r][c]);
+          }
+        }
+      } else {
+        for (int k = 0; k < t1 - t0; ++k) {
+          const int t = kDesc ? t1 - 1 - k : t0 + k;
+          const float4 l4 = *reinterpret_cast<const float4*>(&Lm[t * kP + i]);
+          const float l[4] = {sgn * l4.x, sgn * l4.y, sgn * l4.z, sgn * l4.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float u = Rm[(j + c) * kP + t];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r][c] = __fmaf_rn(l[r], u, acc[r][c]);
+          }
         }
       }
 #pragma unroll
@@ -154,6 +181,20 @@ __device__ inline void rank_update(float* M, const float* Lm, const float* Rm, i
           if (i + r < i1 && j + c < j1) M[(j + c) * kP + i + r] = acc[r][c];
     }
   }
+}
+
+// The 16 floats v[0..15] = p[0..15] (p 16-byte aligned).
+__device__ inline void load16(float (&v)[kPW], const float* p) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const float4 q = *reinterpret_cast<const float4*>(p + 4 * m);
+    v[4 * m] = q.x; v[4 * m + 1] = q.y; v[4 * m + 2] = q.z; v[4 * m + 3] = q.w;
+  }
+}
+__device__ inline void store16(float* p, const float (&v)[kPW]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    *reinterpret_cast<float4*>(p + 4 * m) = make_float4(v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
 }
 
 __global__ void __launch_bounds__(kGetrfThreads)
@@ -187,19 +228,18 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
         if (cp >= pw) break;
         const int p = p0 + cp;
         float* ur = urow + (cp & 1) * kPW;
-        if (warp == 0 && lane == cp) {   // row p is lane cp of warp 0
-#pragma unroll
-          for (int c = 0; c < kPW; ++c) ur[c] = pr[c];
-        }
+        if (warp == 0 && lane == cp) store16(ur, pr);   // row p is lane cp of warp 0
         named_sync(1, 128);
-        const float piv = ur[cp];
+        float u[kPW];
+        load16(u, ur);
+        const float piv = u[cp];
         if (!(isfinite(piv) && piv != 0.0f)) bad = true;
         if (has && i > p) {
           const float l = __fdiv_rn(pr[cp], piv);
           pr[cp] = l;
 #pragma unroll
           for (int c = cp + 1; c < kPW; ++c)
-            if (c < pw) pr[c] = __fmaf_rn(-l, ur[c], pr[c]);
+            if (c < pw) pr[c] = __fmaf_rn(-l, u[c], pr[c]);
         }
       }
       if (has) {
@@ -214,23 +254,22 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
     // (b) row strip: rows p0..e-1, columns e..b-1, unit-lower solve with the
     // panel, right-looking (pivot q ascending, so each entry's terms keep
     // their order and the loads of step q+1 overlap step q)
+    // (pw = kPW here: a ragged panel is the last one and ended the loop)
     for (int j = e + tid; j < b; j += kGetrfThreads) {
       float col[kPW];
-#pragma unroll
-      for (int r = 0; r < kPW; ++r) col[r] = r < pw ? a[j * kP + p0 + r] : 0.0f;
+      load16(col, &a[j * kP + p0]);
 #pragma unroll
       for (int q = 0; q < kPW - 1; ++q) {
+        float lq[kPW];   // column p0 + q of the panel, rows p0 .. p0 + 15
+        load16(lq, &a[(p0 + q) * kP + p0]);
 #pragma unroll
-        for (int r = q + 1; r < kPW; ++r)
-          if (r < pw) col[r] = __fmaf_rn(-a[(p0 + q) * kP + p0 + r], col[q], col[r]);
+        for (int r = q + 1; r < kPW; ++r) col[r] = __fmaf_rn(-lq[r], col[q], col[r]);
       }
-#pragma unroll
-      for (int r = 0; r < kPW; ++r)
-        if (r < pw) a[j * kP + p0 + r] = col[r];
+      store16(&a[j * kP + p0], col);
     }
     __syncthreads();
     // (c) trailing update rows/cols e..b-1, pivots p0..e-1 ascending
-    rank_update(a, a, a, e, b, e, b, p0, e, -1.0f, false, warp, kGetrfThreads / 32, lane);
+    rank_update<false>(a, a, a, e, b, e, b, p0, e, -1.0f, warp, kGetrfThreads / 32, lane);
     __syncthreads();
   }
   if (bad && tid == 0) atomicOr(status, kErrPivot);
@@ -264,21 +303,33 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
       // and each entry sees the same operations as the plain recurrence
       for (int c = gt; c < t1; c += 256) {
         float col[kPW];
+        if (t1 - t0 == kPW) {
+          load16(col, &x[c * kP + t0]);
 #pragma unroll
-        for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? x[c * kP + t0 + r] : 0.0f;
+          for (int q = 0; q < kPW - 1; ++q) {
+            float lq[kPW];   // column t0 + q of L, rows t0 .. t0 + 15
+            load16(lq, &a[(t0 + q) * kP + t0]);
 #pragma unroll
-        for (int q = 0; q < kPW - 1; ++q) {
+            for (int r = q + 1; r < kPW; ++r) col[r] = __fmaf_rn(-lq[r], col[q], col[r]);
+          }
+          store16(&x[c * kP + t0], col);
+        } else {
 #pragma unroll
-          for (int r = q + 1; r < kPW; ++r)
-            if (t0 + r < t1) col[r] = __fmaf_rn(-a[(t0 + q) * kP + t0 + r], col[q], col[r]);
+          for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? x[c * kP + t0 + r] : 0.0f;
+#pragma unroll
+          for (int q = 0; q < kPW - 1; ++q) {
+#pragma unroll
+            for (int r = q + 1; r < kPW; ++r)
+              if (t0 + r < t1) col[r] = __fmaf_rn(-a[(t0 + q) * kP + t0 + r], col[q], col[r]);
+          }
+#pragma unroll
+          for (int r = 0; r < kPW; ++r)
+            if (t0 + r < t1) x[c * kP + t0 + r] = col[r];
         }
-#pragma unroll
-        for (int r = 0; r < kPW; ++r)
-          if (t0 + r < t1) x[c * kP + t0 + r] = col[r];
       }
       named_sync(2, 256);
       // rows t1..b-1, columns 0..t1-1: add -L(r, t) X(t, c) for t = t0..t1-1 ascending
-      if (t1 < b) rank_update(x, a, x, t1, b, 0, t1, t0, t1, -1.0f, false, warp, 8, lane);
+      if (t1 < b) rank_update<false>(x, a, x, t1, b, 0, t1, t0, t1, -1.0f, warp, 8, lane);
       named_sync(2, 256);
     }
   } else {
@@ -292,23 +343,37 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
       // to the rows above it; terms come in descending t, rows t > c carry 0
       for (int c = t0 + gt; c < b; c += 256) {
         float col[kPW];
+        if (t1 - t0 == kPW) {
+          load16(col, &y[c * kP + t0]);
 #pragma unroll
-        for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? y[c * kP + t0 + r] : 0.0f;
+          for (int q = kPW - 1; q >= 0; --q) {
+            const int rq = t0 + q;
+            float uq[kPW];   // column rq of U, rows t0 .. t0 + 15 (uq[q] = U(rq, rq))
+            load16(uq, &a[rq * kP + t0]);
+            if (rq < c) col[q] = __fdiv_rn(-col[q], uq[q]);
 #pragma unroll
-        for (int q = kPW - 1; q >= 0; --q) {
-          const int rq = t0 + q;
-          if (rq < t1 && rq < c) col[q] = __fdiv_rn(-col[q], a[rq * kP + rq]);
+            for (int r = 0; r < q; ++r) col[r] = __fmaf_rn(uq[r], col[q], col[r]);
+          }
+          store16(&y[c * kP + t0], col);
+        } else {
 #pragma unroll
-          for (int r = 0; r < q; ++r)
-            if (rq < t1) col[r] = __fmaf_rn(a[rq * kP + t0 + r], col[q], col[r]);
+          for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? y[c * kP + t0 + r] : 0.0f;
+#pragma unroll
+          for (int q = kPW - 1; q >= 0; --q) {
+            const int rq = t0 + q;
+            if (rq < t1 && rq < c) col[q] = __fdiv_rn(-col[q], a[rq * kP + rq]);
+#pragma unroll
+            for (int r = 0; r < q; ++r)
+              if (rq < t1) col[r] = __fmaf_rn(a[rq * kP + t0 + r], col[q], col[r]);
+          }
+#pragma unroll
+          for (int r = 0; r < kPW; ++r)
+            if (t0 + r < t1) y[c * kP + t0 + r] = col[r];
         }
-#pragma unroll
-        for (int r = 0; r < kPW; ++r)
-          if (t0 + r < t1) y[c * kP + t0 + r] = col[r];
       }
       named_sync(3, 256);
       // rows 0..t0-1, columns t0..b-1: add U(r, t) Y(t, c) for t = t1-1 down to t0
-      if (t0 > 0) rank_update(y, a, y, 0, t0, t0, b, t0, t1, 1.0f, true, warp - 8, 8, lane);
+      if (t0 > 0) rank_update<true>(y, a, y, 0, t0, t0, b, t0, t1, 1.0f, warp - 8, 8, lane);
       named_sync(3, 256);
     }
   }
