@@ -124,16 +124,18 @@ __device__ inline void named_sync(int id, int nthreads) {
 // rank-kPW update of the block rows [i0, i1) x cols [j0, j1) of M (pitch kP):
 // M(i, j) += sgn * sum_{t in order} L(i, t) * R(t, j) with L(i,t) = Lm[t*kP + i],
 // R(t, j) = Rm[j*kP + t]; kDesc walks t from t1-1 down to t0, else up.  4x4
-// register micro-tiles, warp = tile column, lane = tile row.  A full 16-deep
-// slice (t0 a multiple of 16) reads R four pivots at a time; the terms of
-// every entry still come one FMA at a time in the same order.
+// register micro-tiles dealt out one per thread of the group (tile rows
+// fastest), so a narrow block keeps every lane busy.  A full 16-deep slice
+// (t0 a multiple of 16) reads R four pivots at a time; the terms of every
+// entry still come one FMA at a time in the same order.
 template <bool kDesc>
 __device__ inline void rank_update(float* M, const float* Lm, const float* Rm, int i0, int i1, int j0, int j1,
                                    int t0, int t1, float sgn, int wid, int nwarps, int lane) {
   const int ni = (i1 - i0 + 3) / 4, nj = (j1 - j0 + 3) / 4;
   const bool full = t1 - t0 == kPW && (t0 & 3) == 0;
-  for (int tj = wid; tj < nj; tj += nwarps) {
-    for (int ti = lane; ti < ni; ti += 32) {
+  for (int k = 32 * wid + lane; k < ni * nj; k += 32 * nwarps) {
+    {
+      const int ti = k % ni, tj = k / ni;
       const int i = i0 + 4 * ti, j = j0 + 4 * tj;
       float acc[4][4];
 #pragma unroll
@@ -345,14 +347,21 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
         float col[kPW];
         if (t1 - t0 == kPW) {
           load16(col, &y[c * kP + t0]);
+          // uq = column rq of U, rows t0 .. t0 + 15 (uq[q] = U(rq, rq)); the
+          // next column is fetched while this one is applied
+          float uq[kPW], un[kPW];
+          load16(uq, &a[(t0 + kPW - 1) * kP + t0]);
 #pragma unroll
           for (int q = kPW - 1; q >= 0; --q) {
             const int rq = t0 + q;
-            float uq[kPW];   // column rq of U, rows t0 .. t0 + 15 (uq[q] = U(rq, rq))
-            load16(uq, &a[rq * kP + t0]);
+            if (q > 0) load16(un, &a[(rq - 1) * kP + t0]);
             if (rq < c) col[q] = __fdiv_rn(-col[q], uq[q]);
 #pragma unroll
             for (int r = 0; r < q; ++r) col[r] = __fmaf_rn(uq[r], col[q], col[r]);
+            if (q > 0) {
+#pragma unroll
+              for (int r = 0; r < kPW; ++r) uq[r] = un[r];
+            }
           }
           store16(&y[c * kP + t0], col);
         } else {
