@@ -209,54 +209,72 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
   float* urow = sm + 3 * kB * kP; // [2][kPW] pivot row of the current panel step
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-    const int i = idx % kB, j = idx / kB;
-    a[j * kP + i] = (i < b && j < b) ? u16_to_f32(D[i + (int64_t)j * ldd], fmt) : 0.0f;
+  // a full block whose columns start on 16-byte boundaries moves 8 entries
+  // (16 bytes) per access
+  const bool vec = b == kB && (reinterpret_cast<uintptr_t>(D) & 15) == 0 && (ldd & 7) == 0;
+  if (vec) {
+    for (int v = tid; v < kB * kB / 8; v += kGetrfThreads) {
+      const int i = 8 * (v % (kB / 8)), j = v / (kB / 8);
+      const uint4 w = *reinterpret_cast<const uint4*>(D + i + (int64_t)j * ldd);
+      const uint32_t h[4] = {w.x, w.y, w.z, w.w};
+      float f[8];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        f[2 * m] = u16_to_f32((uint16_t)(h[m] & 0xFFFFu), fmt);
+        f[2 * m + 1] = u16_to_f32((uint16_t)(h[m] >> 16), fmt);
+      }
+      *reinterpret_cast<float4*>(&a[j * kP + i]) = make_float4(f[0], f[1], f[2], f[3]);
+      *reinterpret_cast<float4*>(&a[j * kP + i + 4]) = make_float4(f[4], f[5], f[6], f[7]);
+    }
+  } else {
+    for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+      const int i = idx % kB, j = idx / kB;
+      a[j * kP + i] = (i < b && j < b) ? u16_to_f32(D[i + (int64_t)j * ldd], fmt) : 0.0f;
+    }
   }
   __syncthreads();
 
   bool bad = false;
-  for (int p0 = 0; p0 < b; p0 += kPW) {
-    const int pw = min(kPW, b - p0);
-    // (a) panel: rows p0..b-1 (one per lane of warps 0-3), columns p0..p0+pw-1
-    if (warp < 4) {
-      const int i = p0 + 32 * warp + lane;
-      const bool has = i < b;
-      float pr[kPW];
+  // (a) panel: rows p0..b-1 (one per lane of warps 0-3), columns p0..p0+pw-1
+  auto eliminate = [&](int p0, int pw) {
+    const int i = p0 + 32 * warp + lane;
+    const bool has = i < b;
+    float pr[kPW];
 #pragma unroll
-      for (int c = 0; c < kPW; ++c) pr[c] = (has && c < pw) ? a[(p0 + c) * kP + i] : 0.0f;
+    for (int c = 0; c < kPW; ++c) pr[c] = (has && c < pw) ? a[(p0 + c) * kP + i] : 0.0f;
 #pragma unroll
-      for (int cp = 0; cp < kPW; ++cp) {
-        if (cp >= pw) break;
-        const int p = p0 + cp;
-        float* ur = urow + (cp & 1) * kPW;
-        if (warp == 0 && lane == cp) store16(ur, pr);   // row p is lane cp of warp 0
-        named_sync(1, 128);
-        float u[kPW];
-        load16(u, ur);
-        const float piv = u[cp];
-        if (!(isfinite(piv) && piv != 0.0f)) bad = true;
-        if (has && i > p) {
-          const float l = __fdiv_rn(pr[cp], piv);
-          pr[cp] = l;
+    for (int cp = 0; cp < kPW; ++cp) {
+      if (cp >= pw) break;
+      const int p = p0 + cp;
+      float* ur = urow + (cp & 1) * kPW;
+      if (warp == 0 && lane == cp) store16(ur, pr);   // row p is lane cp of warp 0
+      named_sync(1, 128);
+      float u[kPW];
+      load16(u, ur);
+      const float piv = u[cp];
+      if (!(isfinite(piv) && piv != 0.0f)) bad = true;
+      if (has && i > p) {
+        const float l = __fdiv_rn(pr[cp], piv);
+        pr[cp] = l;
 #pragma unroll
-          for (int c = cp + 1; c < kPW; ++c)
-            if (c < pw) pr[c] = __fmaf_rn(-l, u[c], pr[c]);
-        }
-      }
-      if (has) {
-#pragma unroll
-        for (int c = 0; c < kPW; ++c)
-          if (c < pw) a[(p0 + c) * kP + i] = pr[c];
+        for (int c = cp + 1; c < kPW; ++c)
+          if (c < pw) pr[c] = __fmaf_rn(-l, u[c], pr[c]);
       }
     }
-    __syncthreads();
-    const int e = p0 + pw;
+    if (has) {
+#pragma unroll
+      for (int c = 0; c < kPW; ++c)
+        if (c < pw) a[(p0 + c) * kP + i] = pr[c];
+    }
+  };
+  if (warp < 4) eliminate(0, min(kPW, b));
+  __syncthreads();
+  for (int p0 = 0; p0 < b; p0 += kPW) {
+    const int e = p0 + kPW;   // a ragged panel is the last one: nothing follows it
     if (e >= b) break;
     // (b) row strip: rows p0..e-1, columns e..b-1, unit-lower solve with the
     // panel, right-looking (pivot q ascending, so each entry's terms keep
     // their order and the loads of step q+1 overlap step q)
-    // (pw = kPW here: a ragged panel is the last one and ended the loop)
     for (int j = e + tid; j < b; j += kGetrfThreads) {
       float col[kPW];
       load16(col, &a[j * kP + p0]);
@@ -270,28 +288,61 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
       store16(&a[j * kP + p0], col);
     }
     __syncthreads();
-    // (c) trailing update rows/cols e..b-1, pivots p0..e-1 ascending
-    rank_update<false>(a, a, a, e, b, e, b, p0, e, -1.0f, warp, kGetrfThreads / 32, lane);
+    // (c) trailing update rows/cols e..b-1, pivots p0..e-1 ascending, with
+    // look-ahead: warps 0-3 update the next panel's columns [e, e2) and go on
+    // to eliminate it while warps 4-15 update the columns after it
+    const int e2 = min(e + kPW, b);
+    if (warp < 4) {
+      rank_update<false>(a, a, a, e, b, e, e2, p0, e, -1.0f, warp, 4, lane);
+      named_sync(1, 128);
+      eliminate(e, e2 - e);
+    } else if (e2 < b) {
+      rank_update<false>(a, a, a, e, b, e2, b, p0, e, -1.0f, warp - 4, kGetrfThreads / 32 - 4, lane);
+    }
     __syncthreads();
   }
   if (bad && tid == 0) atomicOr(status, kErrPivot);
 
-  // round into storage; keep the stored values for the inverses; X = I, Y = diag(1/U)
-  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-    const int i = idx % kB, j = idx / kB;
-    float v = 0.0f;
-    if (i < b && j < b) {
-      const uint16_t h = f32_to_u16(a[j * kP + i], fmt);
-      D[i + (int64_t)j * ldd] = h;
-      v = u16_to_f32(h, fmt);
+  // round into storage and keep the stored values for the inverses; X = I,
+  // Y = diag(1 / stored U)
+  if (vec) {
+    for (int v = tid; v < kB * kB / 8; v += kGetrfThreads) {
+      const int i = 8 * (v % (kB / 8)), j = v / (kB / 8);
+      float f[8];
+      const float4 f0 = *reinterpret_cast<const float4*>(&a[j * kP + i]);
+      const float4 f1 = *reinterpret_cast<const float4*>(&a[j * kP + i + 4]);
+      f[0] = f0.x; f[1] = f0.y; f[2] = f0.z; f[3] = f0.w; f[4] = f1.x; f[5] = f1.y; f[6] = f1.z; f[7] = f1.w;
+      uint32_t h[4];
+      float xs[8], ys[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const uint16_t hm = f32_to_u16(f[m], fmt);
+        if (m & 1) h[m >> 1] |= (uint32_t)hm << 16; else h[m >> 1] = hm;
+        f[m] = u16_to_f32(hm, fmt);
+        xs[m] = i + m == j ? 1.0f : 0.0f;
+        ys[m] = i + m == j ? __fdiv_rn(1.0f, f[m]) : 0.0f;
+      }
+      *reinterpret_cast<uint4*>(D + i + (int64_t)j * ldd) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(&a[j * kP + i]) = make_float4(f[0], f[1], f[2], f[3]);
+      *reinterpret_cast<float4*>(&a[j * kP + i + 4]) = make_float4(f[4], f[5], f[6], f[7]);
+      *reinterpret_cast<float4*>(&x[j * kP + i]) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+      *reinterpret_cast<float4*>(&x[j * kP + i + 4]) = make_float4(xs[4], xs[5], xs[6], xs[7]);
+      *reinterpret_cast<float4*>(&y[j * kP + i]) = make_float4(ys[0], ys[1], ys[2], ys[3]);
+      *reinterpret_cast<float4*>(&y[j * kP + i + 4]) = make_float4(ys[4], ys[5], ys[6], ys[7]);
     }
-    a[j * kP + i] = v;
-  }
-  __syncthreads();
-  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-    const int i = idx % kB, j = idx / kB;
-    x[j * kP + i] = (i == j && i < b) ? 1.0f : 0.0f;
-    y[j * kP + i] = (i == j && i < b) ? __fdiv_rn(1.0f, a[j * kP + i]) : 0.0f;
+  } else {
+    for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+      const int i = idx % kB, j = idx / kB;
+      float v = 0.0f;
+      if (i < b && j < b) {
+        const uint16_t h = f32_to_u16(a[j * kP + i], fmt);
+        D[i + (int64_t)j * ldd] = h;
+        v = u16_to_f32(h, fmt);
+      }
+      a[j * kP + i] = v;
+      x[j * kP + i] = (i == j && i < b) ? 1.0f : 0.0f;
+      y[j * kP + i] = (i == j && i < b) ? __fdiv_rn(1.0f, v) : 0.0f;
+    }
   }
   __syncthreads();
 
@@ -387,11 +438,30 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-    const int t = idx % kB, pp = idx / kB;
-    const bool in = pp < b && t < b;
-    linv[(int64_t)pp * ldl + t] = in ? f32_to_u16(x[t * kP + pp], fmt) : (uint16_t)0;   // Linv[p][t] = X(p, t)
-    uinvT[(int64_t)pp * ldu + t] = in ? f32_to_u16(y[pp * kP + t], fmt) : (uint16_t)0;  // UinvT[p][t] = Y(t, p)
+  // Linv[p][t] = X(p, t), UinvT[p][t] = Y(t, p), rounded; zero outside b x b
+  if ((reinterpret_cast<uintptr_t>(linv) & 15) == 0 && (ldl & 7) == 0 &&
+      (reinterpret_cast<uintptr_t>(uinvT) & 15) == 0 && (ldu & 7) == 0) {
+    for (int v = tid; v < kB * kB / 8; v += kGetrfThreads) {
+      const int t0 = 8 * (v % (kB / 8)), pp = v / (kB / 8);
+      uint32_t hl[4], hu[4];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const bool in = pp < b && t0 + m < b;
+        const uint16_t l = in ? f32_to_u16(x[(t0 + m) * kP + pp], fmt) : (uint16_t)0;
+        const uint16_t u = in ? f32_to_u16(y[pp * kP + t0 + m], fmt) : (uint16_t)0;
+        if (m & 1) { hl[m >> 1] |= (uint32_t)l << 16; hu[m >> 1] |= (uint32_t)u << 16; }
+        else { hl[m >> 1] = l; hu[m >> 1] = u; }
+      }
+      *reinterpret_cast<uint4*>(linv + (int64_t)pp * ldl + t0) = make_uint4(hl[0], hl[1], hl[2], hl[3]);
+      *reinterpret_cast<uint4*>(uinvT + (int64_t)pp * ldu + t0) = make_uint4(hu[0], hu[1], hu[2], hu[3]);
+    }
+  } else {
+    for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+      const int t = idx % kB, pp = idx / kB;
+      const bool in = pp < b && t < b;
+      linv[(int64_t)pp * ldl + t] = in ? f32_to_u16(x[t * kP + pp], fmt) : (uint16_t)0;
+      uinvT[(int64_t)pp * ldu + t] = in ? f32_to_u16(y[pp * kP + t], fmt) : (uint16_t)0;
+    }
   }
 }
 
