@@ -765,6 +765,26 @@ struct Factorizer {
     check(cudaGetLastError());
   }
 
+  // W_s = st(-Linv_ss L_{s,0:s}) and Z_s = st(-U_{0:s,s} Uinv_ss) of the
+  // diagonal block at k (sub-block s > 0): they need only sub-block s's
+  // inverses and the factors left of / above it, all final once getrf(s) ran.
+  void make_w(int64_t k, int s) {
+    const int64_t s0 = k + (int64_t)s * kB;
+    void* tok = prof_begin(st);
+    make_w_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(s * kB, aop(s), NB, at(s0, k), ld, fmt);
+    prof_end(tok, kProfPanel, 2.0 * s * kB * kB * kB, st);
+    count_launches(1);
+    check(cudaGetLastError());
+  }
+  void make_z(int64_t k, int s) {
+    const int64_t s0 = k + (int64_t)s * kB;
+    void* tok = prof_begin(st);
+    make_z_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(s * kB, bop(s), NB, at(k, s0), ld, fmt);
+    prof_end(tok, kProfPanel, 2.0 * s * kB * kB * kB, st);
+    count_launches(1);
+    check(cudaGetLastError());
+  }
+
   // Panels and Schur update of one sub-step inside a diagonal block wider than
   // 128: sub-block at kk (width 128) of the block ending at e.
   void inner_step(int64_t kk, int slot, int64_t e, int max_ctas) {
@@ -849,28 +869,27 @@ struct Factorizer {
       const int par = step & 1;
       uint16_t* Lp = w.Lp[par];
       const int panel_ctas = overlap && far_pending && cap_panels ? reserve : 0;
-      // (i) diagonal block
+      const int64_t m = n - (k + b);
+      // (i) diagonal block.  Beside it on st3 (after each inner step's own
+      // work there): W_s and Z_s of the sub-blocks 0 < s < nsub - 1
       for (int s = 0; s < nsub; ++s) {
         const int64_t kk = k + (int64_t)s * kB;
         getrf_base(kk, (int)std::min<int64_t>(kB, k + b - kk), s);
-        if (nsub > 1) inner_step(kk, s, k + b, panel_ctas);
+        if (nsub > 1 && s + 1 < nsub) {
+          inner_step(kk, s, k + b, panel_ctas);
+          if (s > 0) on_st3([&] { make_w(k, s); make_z(k, s); });
+        }
       }
-      const int64_t m = n - (k + b);
       if (m <= 0) break;
       // (ii) row panel U12 (on st) and column panel L21 (on st3 when there is
-      // one), block substitution over s; the chains meet before the update
+      // one), block substitution over s; the chains meet before the update.
+      // The last sub-block's W_s / Z_s head its own chain's last product.
+      join();
       fork();
       on_st3([&] { pack(m, (int)b, at(k + b, k), Lp, NB); });
       for (int s = 0; s < nsub; ++s) {
         const int64_t s0 = k + (int64_t)s * kB;
-        if (s > 0) {
-          void* tok = prof_begin(st);
-          make_w_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(
-              s * kB, aop(s), NB, at(s0, k), ld, fmt);
-          prof_end(tok, kProfPanel, 2.0 * s * kB * kB * kB, st);
-          count_launches(1);
-          check(cudaGetLastError());
-        }
+        if (s > 0 && s == nsub - 1) make_w(k, s);
         GemmArgs u{};
         u.M = kB; u.N = (int)m; u.K = (s + 1) * kB;
         u.A = aop(s); u.lda = NB;
@@ -880,14 +899,7 @@ struct Factorizer {
         u.max_ctas = panel_ctas;
         gemm(u);
         on_st3([&] {
-          if (s > 0) {
-            void* tok = prof_begin(st);
-            make_z_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(
-                s * kB, bop(s), NB, at(k, s0), ld, fmt);
-            prof_end(tok, kProfPanel, 2.0 * s * kB * kB * kB, st);
-            count_launches(1);
-            check(cudaGetLastError());
-          }
+          if (s > 0 && s == nsub - 1) make_z(k, s);
           GemmArgs l{};
           l.M = (int)m; l.N = kB; l.K = (s + 1) * kB;
           l.A = Lp; l.lda = NB;
