@@ -465,22 +465,43 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
   }
 }
 
-// Column-major block (rows x cols at src, lds) -> row-major (dst[i*ldd + j]).
-__global__ void pack_rows_kernel(int64_t rows, int cols, const uint16_t* __restrict__ src, int64_t lds,
-                                 uint16_t* __restrict__ dst, int64_t ldd) {
-  __shared__ uint16_t t[32][33];
-  const int64_t i0 = (int64_t)blockIdx.x * 32;
-  const int j0 = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t i = i0 + threadIdx.x;
-    const int j = j0 + k;
-    t[k][threadIdx.x] = (i < rows && j < cols) ? src[i + (int64_t)j * lds] : (uint16_t)0;
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t i = i0 + k;
-    const int j = j0 + threadIdx.x;
-    if (i < rows && j < cols) dst[i * ldd + j] = t[threadIdx.x][k];
+// Column-major block (rows x cols at src, lds) -> row-major (dst[i*ldd + j]),
+// through 64 x 64 tiles in shared memory (t[j][i], rows padded to 144 bytes).
+// A whole tile with 16-byte aligned columns and rows moves by 16-byte loads
+// (8 rows of one column) and 16-byte stores (8 columns of one row); the
+// gathers in between read 32 consecutive rows per warp (no bank conflicts).
+constexpr int kPackT = 64, kPackPad = 72;
+__global__ void __launch_bounds__(256) pack_rows_kernel(int64_t rows, int cols, const uint16_t* __restrict__ src,
+                                                        int64_t lds, uint16_t* __restrict__ dst, int64_t ldd) {
+  __shared__ __align__(16) uint16_t t[kPackT][kPackPad];
+  const int64_t i0 = (int64_t)blockIdx.x * kPackT;
+  const int j0 = blockIdx.y * kPackT;
+  const bool whole = i0 + kPackT <= rows && j0 + kPackT <= cols && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
+                     (lds & 7) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 && (ldd & 7) == 0;
+  if (whole) {
+    for (int v = threadIdx.x; v < kPackT * kPackT / 8; v += blockDim.x) {
+      const int j = v >> 3, ic = (v & 7) * 8;
+      *reinterpret_cast<uint4*>(&t[j][ic]) =
+          *reinterpret_cast<const uint4*>(src + (i0 + ic) + (int64_t)(j0 + j) * lds);
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < kPackT * kPackT / 8; v += blockDim.x) {
+      const int i = v & (kPackT - 1), jc = (v >> 6) * 8;
+      uint32_t h[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) h[e] = (uint32_t)t[jc + 2 * e][i] | ((uint32_t)t[jc + 2 * e + 1][i] << 16);
+      *reinterpret_cast<uint4*>(dst + (i0 + i) * ldd + j0 + jc) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+  } else {
+    for (int v = threadIdx.x; v < kPackT * kPackT; v += blockDim.x) {
+      const int j = v >> 6, i = v & (kPackT - 1);
+      t[j][i] = (i0 + i < rows && j0 + j < cols) ? src[(i0 + i) + (int64_t)(j0 + j) * lds] : (uint16_t)0;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < kPackT * kPackT; v += blockDim.x) {
+      const int i = v >> 6, j = v & (kPackT - 1);
+      if (i0 + i < rows && j0 + j < cols) dst[(i0 + i) * ldd + j0 + j] = t[j][i];
+    }
   }
 }
 
@@ -757,9 +778,9 @@ struct Factorizer {
 
   void pack(int64_t rows, int cols, const uint16_t* src, uint16_t* dst, int64_t ldd) {
     if (rows <= 0) return;
-    dim3 grid((unsigned)cdiv<int64_t>(rows, 32), (unsigned)cdiv(cols, 32));
+    dim3 grid((unsigned)cdiv<int64_t>(rows, kPackT), (unsigned)cdiv(cols, kPackT));
     void* tok = prof_begin(st);
-    pack_rows_kernel<<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, ld, dst, ldd);
+    pack_rows_kernel<<<grid, 256, 0, st>>>(rows, cols, src, ld, dst, ldd);
     prof_end(tok, kProfPanel, 4.0 * (double)rows * cols, st);
     count_launches(1);
     check(cudaGetLastError());
