@@ -281,6 +281,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // the setup above may run while the previous kernel of the stream finishes;
+  // no global memory is touched before it has completed
+  pdl_wait();
+  pdl_trigger();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -559,10 +563,10 @@ cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
   const int grid = std::min(p.ntiles, g.max_ctas > 0 ? std::min(g.max_ctas, num_sms()) : num_sms());
   const double flops = 2.0 * g.M * (double)g.N * g.K;
   void* tok = prof_begin(st);
-  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, tc, p);
+  const cudaError_t e = launch_pdl(gemm_tc_kernel, dim3(grid), dim3(kThreads), kSmemBytes, st, ta, tb, tc, p);
   prof_end(tok, g.mode == kEpiSub ? kProfGemm : kProfGemmStore, flops, st);
   count_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace hpmxp

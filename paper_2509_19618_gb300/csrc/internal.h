@@ -123,6 +123,32 @@ enum ProfKind { kProfGemm = 0, kProfGemv = 1, kProfPrecond = 2, kProfGetrf = 3, 
                 kProfPanel = 6, kProfGemmStore = 7, kProfKinds = 8 };
 void count_launches(int k);
 bool prof_on();
+// Programmatic dependent launch.  A kernel launched by launch_pdl may start
+// while the previous kernel of its stream is still running: it must call
+// pdl_wait() before its first access to global memory (the wait returns once
+// that kernel has completed and its writes are visible; it is a no-op for a
+// normal launch).  pdl_trigger() lets the next such kernel start early.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+bool pdl_enabled();   // HPMXP_PDL=0 turns it off (every launch_pdl becomes a plain launch)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 void* prof_begin(cudaStream_t st);
 void prof_end(void* token, int kind, double work, cudaStream_t st);
 

@@ -208,6 +208,8 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
   float* y = sm + 2 * kB * kP;    // Y = U^{-1}, y[c * kP + r] = Y(r, c)
   float* urow = sm + 3 * kB * kP; // [2][kPW] pivot row of the current panel step
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  pdl_wait();      // may start while the previous kernel of the stream finishes
+  pdl_trigger();
 
   // a full block whose columns start on 16-byte boundaries moves 8 entries
   // (16 bytes) per access
@@ -474,6 +476,8 @@ constexpr int kPackT = 64, kPackPad = 72;
 __global__ void __launch_bounds__(256) pack_rows_kernel(int64_t rows, int cols, const uint16_t* __restrict__ src,
                                                         int64_t lds, uint16_t* __restrict__ dst, int64_t ldd) {
   __shared__ __align__(16) uint16_t t[kPackT][kPackPad];
+  pdl_wait();
+  pdl_trigger();
   const int64_t i0 = (int64_t)blockIdx.x * kPackT;
   const int j0 = blockIdx.y * kPackT;
   const bool whole = i0 + kPackT <= rows && j0 + kPackT <= cols && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
@@ -513,6 +517,8 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(int64_t rows, int cols, 
 // before the multiply-adds.
 __global__ void __launch_bounds__(128) make_w_kernel(int ws, uint16_t* aop, int64_t ld,
                                                      const uint16_t* __restrict__ Lsub, int64_t ldlu, int fmt) {
+  pdl_wait();
+  pdl_trigger();
   const int q = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
   if (q >= ws) return;
   const uint4* li = reinterpret_cast<const uint4*>(aop + (int64_t)p * ld + ws);
@@ -541,6 +547,8 @@ __global__ void __launch_bounds__(128) make_w_kernel(int ws, uint16_t* aop, int6
 // Usub[q + t * ldlu] (coalesced across q), loaded 32 at a time before use.
 __global__ void __launch_bounds__(128) make_z_kernel(int zs, uint16_t* bop, int64_t ld,
                                                      const uint16_t* __restrict__ Usub, int64_t ldlu, int fmt) {
+  pdl_wait();
+  pdl_trigger();
   const int q = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
   if (q >= zs) return;
   const uint4* ui = reinterpret_cast<const uint4*>(bop + (int64_t)p * ld + zs);
@@ -769,21 +777,19 @@ struct Factorizer {
 
   void getrf_base(int64_t k, int b, int slot) {
     void* tok = prof_begin(st);
-    getrf_base_kernel<<<1, kGetrfThreads, kGetrfSmem, st>>>(
-        b, at(k, k), ld, fmt, aop(slot) + slot * kB, NB, bop(slot) + slot * kB, NB, w.status);
+    check(launch_pdl(getrf_base_kernel, dim3(1), dim3(kGetrfThreads), kGetrfSmem, st, b, at(k, k), ld, fmt,
+                     aop(slot) + slot * kB, NB, bop(slot) + slot * kB, NB, w.status));
     prof_end(tok, kProfGetrf, (double)b * b * b * 2.0, st);
     count_launches(1);
-    check(cudaGetLastError());
   }
 
   void pack(int64_t rows, int cols, const uint16_t* src, uint16_t* dst, int64_t ldd) {
     if (rows <= 0) return;
     dim3 grid((unsigned)cdiv<int64_t>(rows, kPackT), (unsigned)cdiv(cols, kPackT));
     void* tok = prof_begin(st);
-    pack_rows_kernel<<<grid, 256, 0, st>>>(rows, cols, src, ld, dst, ldd);
+    check(launch_pdl(pack_rows_kernel, grid, dim3(256), 0, st, rows, cols, src, ld, dst, ldd));
     prof_end(tok, kProfPanel, 4.0 * (double)rows * cols, st);
     count_launches(1);
-    check(cudaGetLastError());
   }
 
   // W_s = st(-Linv_ss L_{s,0:s}) and Z_s = st(-U_{0:s,s} Uinv_ss) of the
@@ -792,18 +798,18 @@ struct Factorizer {
   void make_w(int64_t k, int s) {
     const int64_t s0 = k + (int64_t)s * kB;
     void* tok = prof_begin(st);
-    make_w_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(s * kB, aop(s), NB, at(s0, k), ld, fmt);
+    check(launch_pdl(make_w_kernel, dim3((unsigned)cdiv(s * kB, 128), kB), dim3(128), 0, st, s * kB, aop(s), NB,
+                     (const uint16_t*)at(s0, k), ld, fmt));
     prof_end(tok, kProfPanel, 2.0 * s * kB * kB * kB, st);
     count_launches(1);
-    check(cudaGetLastError());
   }
   void make_z(int64_t k, int s) {
     const int64_t s0 = k + (int64_t)s * kB;
     void* tok = prof_begin(st);
-    make_z_kernel<<<dim3((unsigned)cdiv(s * kB, 128), kB), 128, 0, st>>>(s * kB, bop(s), NB, at(k, s0), ld, fmt);
+    check(launch_pdl(make_z_kernel, dim3((unsigned)cdiv(s * kB, 128), kB), dim3(128), 0, st, s * kB, bop(s), NB,
+                     (const uint16_t*)at(k, s0), ld, fmt));
     prof_end(tok, kProfPanel, 2.0 * s * kB * kB * kB, st);
     count_launches(1);
-    check(cudaGetLastError());
   }
 
   // Panels and Schur update of one sub-step inside a diagonal block wider than

@@ -13,6 +13,15 @@
 #include <vector>
 
 namespace hpmxp {
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("HPMXP_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 namespace {
 
 std::atomic<unsigned long long> g_launches{0};
