@@ -28,23 +28,39 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 namespace hpmxp {
 namespace {
 
-constexpr int kTI = 128;                      // output rows per tile (MMA N)
 constexpr int kTJ = 128;                      // output columns per tile (MMA M, TMEM lanes)
 constexpr int kRowBytes = 128;                // K bytes per operand row per stage (one swizzle atom)
-constexpr int kStages = 4;
 constexpr int kStageA = kTJ * kRowBytes;      // MMA A operand: rows j (16 KiB)
-constexpr int kStageB = kTI * kRowBytes;      // MMA B operand: rows i (16 KiB)
 constexpr int kCBox = kTJ * 128;              // one C box: 64 rows x 128 columns (16 KiB)
-constexpr int kCTile = 2 * kCBox;             // 32 KiB
-constexpr int kCBufs = 3;                     // C tile buffers: one in the epilogue, one being stored, one loading
-constexpr int kEpiGroups = 2;                 // epilogue groups, one per 64-row half of the tile
+constexpr int kEpiGroups = 2;                 // epilogue groups, one per half of the tile's rows
 constexpr int kEpiThreads = 128;              // threads per epilogue group (one warp per TMEM lane quarter)
 constexpr int kThreads = 64 + kEpiGroups * kEpiThreads;
+
+// Tile height TI (output rows i per tile = MMA N): 128, or 256 for the large
+// 16-bit products, where every operand byte an SM receives feeds twice the
+// flops (the SM's operand intake is what bounds this kernel at K >= 256).
+template <int TI>
+struct TileCfg {
+  static constexpr int kStages = TI == 128 ? 4 : 3;
+  static constexpr int kStageB = TI * kRowBytes;            // MMA B operand: rows i (16 or 32 KiB)
+  static constexpr int kBoxes = TI / 128;                   // 64-row C boxes per epilogue group
+  static constexpr int kCTile = kEpiGroups * kBoxes * kCBox;  // 32 or 64 KiB
+  // C tile buffers: with three, one is in the epilogue, one being stored and
+  // one loading; the 256-row tile has room for one only
+  static constexpr int kCBufs = TI == 128 ? 3 : 1;
+  static constexpr int kAhead = kCBufs >= 2 ? kCBufs - 1 : 1;   // C prefetch distance (local tiles)
+  static constexpr int kReadWait = kCBufs >= 2 ? kCBufs - 2 : 0; // stores allowed to be still reading
+  static constexpr size_t kSmem = 1024 + (size_t)kStages * (kStageA + kStageB) + (size_t)kCBufs * kCTile +
+                                  8 * (2 * kStages + 4 + 2 * kCBufs) + 16;
+};
 
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -205,10 +221,10 @@ __device__ inline uint64_t sdesc_sw128(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Instruction descriptor: fp32 accumulator, K-major A and B, M = 128, N = 128.
+// Instruction descriptor: fp32 accumulator, K-major A and B, M = 128, N = TI.
 // Operand format code: kind::f16 -> 0 F16, 1 BF16; kind::f8f6f4 -> 0 E4M3.
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt_code) {
-  return (1u << 4) | (fmt_code << 7) | (fmt_code << 10) | ((uint32_t)(kTI >> 3) << 17) |
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt_code, int ti) {
+  return (1u << 4) | (fmt_code << 7) | (fmt_code << 10) | ((uint32_t)(ti >> 3) << 17) |
          ((uint32_t)(kTJ >> 4) << 24);
 }
 
@@ -238,15 +254,19 @@ __device__ inline uint32_t pack16x2(float lo, float hi, int fmt) {
   return r;
 }
 
+template <int TI>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, TcParams p) {
+  using Cfg = TileCfg<TI>;
+  constexpr int kStages = Cfg::kStages, kStageB = Cfg::kStageB, kCTile = Cfg::kCTile, kCBufs = Cfg::kCBufs;
+  constexpr int kBoxes = Cfg::kBoxes;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);   // swizzle atoms need 1024-byte alignment
   const uint32_t sOpA = smem_u32(smem);                            // [kStages][rows j][128 B]
   const uint32_t sOpB = sOpA + kStages * kStageA;                  // [kStages][rows i][128 B]
-  const uint32_t sC = sOpB + kStages * kStageB;                    // [2][2 boxes][cols j][128 B]
+  const uint32_t sC = sOpB + kStages * kStageB;                    // [kCBufs][group][box][cols j][128 B]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * (kStageA + kStageB) + kCBufs * kCTile);
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int s) { return bar0 + 8u * (uint32_t)s; };
@@ -292,7 +312,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       long long pos = 0;   // ring position over all tiles of this CTA
       bool ok = true;
       for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-        const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
+        const int i0 = (t % p.tiles_i) * TI, j0 = (t / p.tiles_i) * kTJ;
         for (int kb = 0; kb < p.nkb; ++kb, ++pos) {
           const int s = (int)(pos % kStages);
           const long long use = pos / kStages;
@@ -309,7 +329,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = p.fp8 ? make_idesc(0) : make_idesc(p.fmt == kBF16 ? 1u : 0u);
+      const uint32_t idesc = p.fp8 ? make_idesc(0, TI) : make_idesc(p.fmt == kBF16 ? 1u : 0u, TI);
       long long pos = 0;
       bool ok = true;
       int local = 0;
@@ -322,7 +342,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const int s = (int)(pos % kStages);
           if (!mbar_wait(full(s), (uint32_t)((pos / kStages) & 1))) { ok = false; break; }
           tc_fence_after();
-          const uint32_t d = d0 + (p.fp8 ? (uint32_t)(kb * kTI) : 0u);
+          const uint32_t d = d0 + (p.fp8 ? (uint32_t)(kb * TI) : 0u);
           for (int kk = 0; kk < 4; ++kk) {   // 4 MMAs of 32 bytes of K each
             const uint64_t a = sdesc_sw128(sOpA + s * kStageA + kk * 32);
             const uint64_t b = sdesc_sw128(sOpB + s * kStageB + kk * 32);
@@ -337,34 +357,41 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (!ok) atomicOr(p.status, kErrTimeout);
     }
   } else {
-    // epilogue: group g = (warp - 2) / 4 owns rows i0 + 64 g .. +63 (C box g) of the tile;
-    // thread = output column j = j0 + jl, jl = 32 q + lane (its TMEM lane)
+    // epilogue: group g = (warp - 2) / 4 owns rows i0 + (TI/2) g .. + TI/2 - 1 of the
+    // tile, as kBoxes C boxes of 64 rows; thread = output column j = j0 + jl,
+    // jl = 32 q + lane (its TMEM lane)
     const int q = warp & 3;
     const int g = (warp - 2) >> 2;
     const int jl = 32 * q + lane;
     const bool leader = ((warp - 2) & 3) == 0 && lane == 0;
     const bool load_c = p.has_c && p.mode == kEpiSub;
-    // C tile buffers rotate over local tiles: tile l uses buffer l % kCBufs.  The
-    // C of tile l + 2 is loaded into the buffer of tile l - 1 as soon as the
-    // store of tile l - 1 has been read, which is checked one tile later, when
-    // it is long done, so the epilogue never waits on its own store.
+    // C tile buffers rotate over local tiles: tile l uses buffer l % kCBufs.
+    // With three buffers the C of tile l + 2 is loaded into the buffer of tile
+    // l - 1 as soon as the store of tile l - 1 has been read, which is checked
+    // one tile later, when it is long done, so the epilogue never waits on its
+    // own store; with one buffer the C of tile l + 1 follows the store of l.
     int issued_c[kCBufs];         // local tile whose C load is outstanding in each buffer
     for (int b = 0; b < kCBufs; ++b) issued_c[b] = -1;
-    if (leader && load_c) {       // prefetch this group's C box of the first two local tiles
+    auto load_c_tile = [&](int tt, int b) {   // this group's boxes of tile tt's C into buffer b
+      const int ii0 = (tt % p.tiles_i) * TI, jj0 = (tt / p.tiles_i) * kTJ;
+      mbar_expect_tx(c_full(b, g), kBoxes * kCBox);
+#pragma unroll
+      for (int h = 0; h < kBoxes; ++h)
+        tma_load_2d(sC + b * kCTile + (g * kBoxes + h) * kCBox, &tmC, ii0 + (TI / 2) * g + 64 * h, jj0,
+                    c_full(b, g));
+    };
+    if (leader && load_c) {       // prefetch the C of the first kAhead local tiles
       int local = 0;
-      for (int t = blockIdx.x; t < p.ntiles && local < 2; t += gridDim.x, ++local) {
-        const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
-        mbar_expect_tx(c_full(local, g), kCBox);
-        tma_load_2d(sC + local * kCTile + g * kCBox, &tmC, i0 + 64 * g, j0, c_full(local, g));
-        issued_c[local] = local;
+      for (int t = blockIdx.x; t < p.ntiles && local < Cfg::kAhead; t += gridDim.x, ++local) {
+        load_c_tile(t, local % kCBufs);
+        issued_c[local % kCBufs] = local;
       }
     }
     bool ok = true;
     int local = 0;
     for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++local) {
-      const int i0 = (t % p.tiles_i) * kTI, j0 = (t / p.tiles_i) * kTJ;
+      const int i0 = (t % p.tiles_i) * TI, j0 = (t / p.tiles_i) * kTJ;
       const int cb = local % kCBufs, ab = local % p.nbuf;
-      const uint32_t cbox = sC + cb * kCTile + g * kCBox;
       bool w = true;
       if (load_c) w = mbar_wait(c_full(cb, g), (uint32_t)((local / kCBufs) & 1));
       if (leader) issued_c[cb] = -1;
@@ -372,62 +399,72 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       w = __all_sync(0xffffffffu, w);   // warp-uniform for tcgen05.ld
       if (!w) { ok = false; break; }
       tc_fence_after();
-      const uint32_t lane_addr = tmem + (uint32_t)ab * p.acc_cols + ((uint32_t)(32 * q) << 16) + 64u * g;
+      const uint32_t lane_base = tmem + (uint32_t)ab * p.acc_cols + ((uint32_t)(32 * q) << 16) + (TI / 2) * g;
       float sc[4] = {1.0f, 1.0f, 1.0f, 1.0f};
       if (p.fp8)
         for (int s2 = 0; s2 < p.nkb && s2 < 4; ++s2)
           sc[s2] = __fmul_rn(p.sA[(i0 / 128) * p.sa_ld + s2], p.sB[(j0 / 128) * p.sb_ld + s2]);
       const int64_t j = (int64_t)j0 + jl;
-      float acc[64];
-      {
-        uint32_t r[64];
-        if (p.fp8) {
+      // one buffer, no C to load: the buffer's previous store was read (the
+      // leader waited for it before it reached this barrier)
+      if (kCBufs == 1 && p.has_c && !load_c) epi_barrier(g);
+#pragma unroll 1
+      for (int h = 0; h < kBoxes; ++h) {
+        const uint32_t lane_addr = lane_base + 64u * h;
+        float acc[64];
+        {
+          uint32_t r[64];
+          if (p.fp8) {
 #pragma unroll
-          for (int v = 0; v < 64; ++v) acc[v] = 0.0f;
-          for (int s2 = 0; s2 < p.nkb; ++s2) {
-            tmem_ld64(lane_addr + (uint32_t)(s2 * kTI), r);
+            for (int v = 0; v < 64; ++v) acc[v] = 0.0f;
+            for (int s2 = 0; s2 < p.nkb; ++s2) {
+              tmem_ld64(lane_addr + (uint32_t)(s2 * TI), r);
 #pragma unroll
-            for (int v = 0; v < 64; ++v) acc[v] = __fmaf_rn(__uint_as_float(r[v]), sc[s2], acc[v]);
+              for (int v = 0; v < 64; ++v) acc[v] = __fmaf_rn(__uint_as_float(r[v]), sc[s2], acc[v]);
+            }
+          } else {
+            tmem_ld64(lane_addr, r);
+#pragma unroll
+            for (int v = 0; v < 64; ++v) acc[v] = __uint_as_float(r[v]);
           }
-        } else {
-          tmem_ld64(lane_addr, r);
-#pragma unroll
-          for (int v = 0; v < 64; ++v) acc[v] = __uint_as_float(r[v]);
         }
-      }
-      // accumulator buffer free for the MMA warp as soon as it is in registers
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty(ab));
-      // rows i0 + 64 g + 8 ch .. +7 of column j: eight 16-byte chunks of the swizzled box
-      const uint32_t row_addr = cbox + jl * 128;
+        if (h == kBoxes - 1) {
+          // accumulator buffer free for the MMA warp as soon as it is in registers
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty(ab));
+        }
+        // rows i0 + (TI/2) g + 64 h + 8 ch .. +7 of column j: eight 16-byte chunks of the swizzled box
+        const uint32_t cbox = sC + cb * kCTile + (g * kBoxes + h) * kCBox;
+        const uint32_t row_addr = cbox + jl * 128;
 #pragma unroll
-      for (int ch = 0; ch < 8; ++ch) {
-        const uint32_t ad = row_addr + ((ch ^ (jl & 7)) << 4);
-        uint32_t outw[4];
-        if (p.mode == kEpiSub) {
-          uint32_t cw[4];
-          asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
-                       : "=r"(cw[0]), "=r"(cw[1]), "=r"(cw[2]), "=r"(cw[3]) : "r"(ad) : "memory");
+        for (int ch = 0; ch < 8; ++ch) {
+          const uint32_t ad = row_addr + ((ch ^ (jl & 7)) << 4);
+          uint32_t outw[4];
+          if (p.mode == kEpiSub) {
+            uint32_t cw[4];
+            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(cw[0]), "=r"(cw[1]), "=r"(cw[2]), "=r"(cw[3]) : "r"(ad) : "memory");
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const float lo = __fsub_rn(u16_to_f32((uint16_t)(cw[v] & 0xffffu), p.fmt), acc[8 * ch + 2 * v]);
-            const float hi = __fsub_rn(u16_to_f32((uint16_t)(cw[v] >> 16), p.fmt), acc[8 * ch + 2 * v + 1]);
-            outw[v] = pack16x2(lo, hi, p.fmt);
+            for (int v = 0; v < 4; ++v) {
+              const float lo = __fsub_rn(u16_to_f32((uint16_t)(cw[v] & 0xffffu), p.fmt), acc[8 * ch + 2 * v]);
+              const float hi = __fsub_rn(u16_to_f32((uint16_t)(cw[v] >> 16), p.fmt), acc[8 * ch + 2 * v + 1]);
+              outw[v] = pack16x2(lo, hi, p.fmt);
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              outw[v] = pack16x2(p.sign * acc[8 * ch + 2 * v], p.sign * acc[8 * ch + 2 * v + 1], p.fmt);
           }
-        } else {
+          if (p.has_c)
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                         ::"r"(ad), "r"(outw[0]), "r"(outw[1]), "r"(outw[2]), "r"(outw[3]) : "memory");
+          if (p.R && j < p.N) {
 #pragma unroll
-          for (int v = 0; v < 4; ++v)
-            outw[v] = pack16x2(p.sign * acc[8 * ch + 2 * v], p.sign * acc[8 * ch + 2 * v + 1], p.fmt);
-        }
-        if (p.has_c)
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                       ::"r"(ad), "r"(outw[0]), "r"(outw[1]), "r"(outw[2]), "r"(outw[3]) : "memory");
-        if (p.R && j < p.N) {
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const int64_t i = (int64_t)i0 + 64 * g + 8 * ch + v;
-            if (i < p.M) p.R[i * p.ldr + j] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
+            for (int v = 0; v < 8; ++v) {
+              const int64_t i = (int64_t)i0 + (TI / 2) * g + 64 * h + 8 * ch + v;
+              if (i < p.M) p.R[i * p.ldr + j] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
+            }
           }
         }
       }
@@ -435,18 +472,19 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         fence_async_smem();
         epi_barrier(g);
         if (leader) {
-          tma_store_2d(&tmC, i0 + 64 * g, j0, cbox);
+#pragma unroll
+          for (int h = 0; h < kBoxes; ++h)
+            tma_store_2d(&tmC, i0 + (TI / 2) * g + 64 * h, j0, sC + cb * kCTile + (g * kBoxes + h) * kCBox);
           bulk_commit();
-          // the store issued one tile ago has finished reading its buffer, which
-          // now receives the C of the tile two ahead
-          asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-          const int t2 = t + 2 * (int)gridDim.x;
+          // the stores issued kCBufs - 1 tiles ago (one buffer: this tile's)
+          // have finished reading their buffer, which now receives the C of
+          // the tile kAhead ahead
+          asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(Cfg::kReadWait) : "memory");
+          const int t2 = t + Cfg::kAhead * (int)gridDim.x;
           if (load_c && t2 < p.ntiles) {
-            const int b2 = (local + 2) % kCBufs;
-            const int i2 = (t2 % p.tiles_i) * kTI, j2 = (t2 / p.tiles_i) * kTJ;
-            mbar_expect_tx(c_full(b2, g), kCBox);
-            tma_load_2d(sC + b2 * kCTile + g * kCBox, &tmC, i2 + 64 * g, j2, c_full(b2, g));
-            issued_c[b2] = local + 2;
+            const int b2 = (local + Cfg::kAhead) % kCBufs;
+            load_c_tile(t2, b2);
+            issued_c[b2] = local + Cfg::kAhead;
           }
         }
       }
@@ -499,8 +537,6 @@ bool make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-constexpr size_t kSmemBytes =
-    1024 + (size_t)kStages * (kStageA + kStageB) + kCBufs * kCTile + 8 * (2 * kStages + 4 + 2 * kCBufs) + 16;
 
 int num_sms() {
   static int sms = 0;
@@ -515,13 +551,16 @@ int num_sms() {
 
 }  // namespace
 
-cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
-  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+namespace {
+
+template <int TI>
+cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
+  using Cfg = TileCfg<TI>;
   const int esz = g.fp8 ? 1 : 2;
   const uint64_t kbytes = (uint64_t)g.K * esz;
   if (kbytes % kRowBytes) return cudaErrorInvalidValue;
   CUtensorMap ta, tb, tc;
-  if (!make_map(&ta, g.A, kbytes / 2, (uint64_t)g.M, (uint64_t)g.lda * esz, kRowBytes / 2, kTI) ||
+  if (!make_map(&ta, g.A, kbytes / 2, (uint64_t)g.M, (uint64_t)g.lda * esz, kRowBytes / 2, TI) ||
       !make_map(&tb, g.B, kbytes / 2, (uint64_t)g.N, (uint64_t)g.ldb * esz, kRowBytes / 2, kTJ))
     return cudaErrorInvalidValue;
   TcParams p{};
@@ -534,39 +573,59 @@ cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
     tc = ta;   // never dereferenced
   }
   p.M = g.M; p.N = g.N; p.nkb = (int)(kbytes / kRowBytes);
-  p.tiles_i = cdiv(g.M, kTI);
+  p.tiles_i = cdiv(g.M, TI);
   p.ntiles = p.tiles_i * cdiv(g.N, kTJ);
   p.mode = g.mode; p.sign = g.sign; p.fmt = g.fmt; p.fp8 = g.fp8;
   p.R = (uint16_t*)g.R; p.ldr = g.ldr;
   p.sA = g.sA; p.sa_ld = g.sa_ld; p.sB = g.sB; p.sb_ld = g.sb_ld;
   p.status = g.status;
   if (g.fp8) {
-    if (p.nkb > 4) return cudaErrorInvalidValue;   // one 128-column accumulator per slice
-    p.acc_cols = (uint32_t)(kTI * p.nkb);
+    if (TI != 128 || p.nkb > 4) return cudaErrorInvalidValue;   // one 128-column accumulator per slice
+    p.acc_cols = (uint32_t)(TI * p.nkb);
   } else {
-    p.acc_cols = kTI;
+    p.acc_cols = TI;
   }
   p.nbuf = (2 * p.acc_cols <= 512u) ? 2 : 1;
   uint32_t need = p.acc_cols * (uint32_t)p.nbuf, ncols = 32;
   while (ncols < need) ncols <<= 1;
   p.ncols = ncols;
 
-  static int configured_for = -1;
+  static std::atomic<int> configured_for{-1};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (configured_for != dev) {
-    cudaError_t e =
-        cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (configured_for.load() != dev) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg::kSmem);
     if (e != cudaSuccess) return e;
-    configured_for = dev;
+    configured_for.store(dev);
   }
   const int grid = std::min(p.ntiles, g.max_ctas > 0 ? std::min(g.max_ctas, num_sms()) : num_sms());
   const double flops = 2.0 * g.M * (double)g.N * g.K;
   void* tok = prof_begin(st);
-  const cudaError_t e = launch_pdl(gemm_tc_kernel, dim3(grid), dim3(kThreads), kSmemBytes, st, ta, tb, tc, p);
+  const cudaError_t e =
+      launch_pdl(gemm_tc_kernel<TI>, dim3(grid), dim3(kThreads), Cfg::kSmem, st, ta, tb, tc, p);
   prof_end(tok, g.mode == kEpiSub ? kProfGemm : kProfGemmStore, flops, st);
   count_launches(1);
   return e;
+}
+
+// HPMXP_GEMM_TILE=128 keeps every product on the 128-row tile.
+bool wide_tiles_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("HPMXP_GEMM_TILE");
+    return !(e && strcmp(e, "128") == 0);
+  }();
+  return on;
+}
+
+}  // namespace
+
+cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  // 256-row tiles for the 16-bit products that fill them (M >= 256) and have
+  // enough depth (K >= 256) for one C buffer to keep up
+  if (!g.fp8 && g.M >= 256 && g.K >= 256 && wide_tiles_enabled()) return gemm_tc_tiles<256>(g, st);
+  return gemm_tc_tiles<128>(g, st);
 }
 
 }  // namespace hpmxp

@@ -112,7 +112,9 @@ def _bf16(x):
     return oracle.round_to(x, oracle.BF16)
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 128), (200, 333, 128), (384, 256, 256), (130, 520, 512)])
+# (2000, 5000, 256): 320 tiles of 256 x 128, so CTAs run several tiles through one C buffer
+@pytest.mark.parametrize("M,N,K", [(128, 128, 128), (200, 333, 128), (384, 256, 256), (130, 520, 512),
+                                   (1000, 700, 512), (2000, 5000, 256)])
 @pytest.mark.parametrize("eng", [0, 1])
 def test_gemm_engines(M, N, K, eng):
     g = np.random.default_rng(M * 7 + N + K)
