@@ -866,6 +866,28 @@ struct Factorizer {
   // between a fork and a join on `st`.
   cudaStream_t st3 = nullptr;
   cudaEvent_t evS = nullptr, evJ = nullptr;
+  // W_s / Z_s run on their own lowest-priority stream: their CTAs must not
+  // take the SMs the chain's GEMMs are waiting for
+  cudaStream_t stw = nullptr;
+  cudaEvent_t evW = nullptr, evW2 = nullptr;
+  bool w_pending = false;
+  void make_wz(int64_t k, int s) {
+    if (!stw || !st3) { on_st3([&] { make_w(k, s); make_z(k, s); }); return; }
+    check(cudaEventRecord(evW2, st3));   // after this sub-block's inner step (and so its getrf)
+    check(cudaStreamWaitEvent(stw, evW2, 0));
+    cudaStream_t keep = st;
+    st = stw;
+    make_w(k, s);
+    make_z(k, s);
+    st = keep;
+    w_pending = true;
+  }
+  void join_wz() {   // the chains may use every W_s / Z_s made so far
+    if (!w_pending) return;
+    check(cudaEventRecord(evW, stw));
+    check(cudaStreamWaitEvent(st, evW, 0));
+    w_pending = false;
+  }
   void fork() {
     if (!st3) return;
     check(cudaEventRecord(evS, st));
@@ -904,7 +926,7 @@ struct Factorizer {
         getrf_base(kk, (int)std::min<int64_t>(kB, k + b - kk), s);
         if (nsub > 1 && s + 1 < nsub) {
           inner_step(kk, s, k + b, panel_ctas);
-          if (s > 0) on_st3([&] { make_w(k, s); make_z(k, s); });
+          if (s > 0 && m > 0) make_wz(k, s);   // they feed only the panel chains below
         }
       }
       if (m <= 0) break;
@@ -912,6 +934,7 @@ struct Factorizer {
       // one), block substitution over s; the chains meet before the update.
       // The last sub-block's W_s / Z_s head its own chain's last product.
       join();
+      join_wz();
       fork();
       on_st3([&] { pack(m, (int)b, at(k + b, k), Lp, NB); });
       for (int s = 0; s < nsub; ++s) {
@@ -1006,6 +1029,7 @@ struct Factorizer {
       }
     }
     if (overlap && far_pending) check(cudaStreamWaitEvent(st, evF, 0));
+    join_wz();
   }
 };
 
@@ -1031,7 +1055,8 @@ struct SideStream {
   bool ok = false;
   cudaStream_t st = nullptr;    // far part of the Schur update
   cudaStream_t st3 = nullptr;   // column-panel (L21) chain, beside the row-panel chain
-  cudaEvent_t evP = nullptr, evF = nullptr, evS = nullptr, evJ = nullptr;
+  cudaStream_t stw = nullptr;   // W_s / Z_s of the diagonal block, lowest priority
+  cudaEvent_t evP = nullptr, evF = nullptr, evS = nullptr, evJ = nullptr, evW = nullptr, evW2 = nullptr;
 };
 
 SideStream& side_stream(int dev) {
@@ -1044,6 +1069,9 @@ SideStream& side_stream(int dev) {
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (cudaStreamCreateWithPriority(&s.st, cudaStreamNonBlocking, lo) == cudaSuccess &&
         cudaStreamCreateWithPriority(&s.st3, cudaStreamNonBlocking, hi) == cudaSuccess &&
+        cudaStreamCreateWithPriority(&s.stw, cudaStreamNonBlocking, lo) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s.evW, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s.evW2, cudaEventDisableTiming) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evP, cudaEventDisableTiming) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evF, cudaEventDisableTiming) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evS, cudaEventDisableTiming) == cudaSuccess &&
@@ -1098,6 +1126,9 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
       f.evF = ss.evF;
       f.evS = ss.evS;
       f.evJ = ss.evJ;
+      f.stw = ss.stw;
+      f.evW = ss.evW;
+      f.evW2 = ss.evW2;
       cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
       f.reserve = std::max(4, f.sms / 16);
       if (const char* rv = getenv("HPMXP_RESERVE_SMS")) f.reserve = std::max(1, std::min(f.sms - 1, atoi(rv)));
