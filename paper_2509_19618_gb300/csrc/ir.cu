@@ -533,12 +533,32 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     }
     __syncthreads();
   };
-  // updates of the owned blocks `o` in [first, ...) selected by `want`, tiles double buffered in slots 1, 2
-  auto stream_updates = [&](int c, bool forward, int skip) {
+  // The first two owned blocks that block c updates (past c in the sweep's
+  // direction, other than `skip`): their tiles go to slots 1 and 2 before z_c
+  // is awaited, since the tiles do not depend on it.  Returns how many.
+  int pre_o[2];
+  auto prefetch_updates = [&](int c, bool forward, int skip) {
+    int k = 0;
+    for (int o = 0; o < nown && k < 2; ++o) {
+      const int rb = me + o * G;
+      if (o == skip || (forward ? rb <= c : rb >= c)) continue;
+      fetch_tile(1 + k, rb, c);
+      pre_o[k++] = o;
+    }
+    return k;
+  };
+  // updates of the owned blocks by z_c: the `npre` prefetched ones from slots 1, 2, then
+  // the rest with tiles double buffered in slots 1, 2
+  auto stream_updates = [&](int c, bool forward, int skip, int npre) {
+    for (int k = 0; k < npre; ++k)
+      product(tl + (size_t)(1 + k) * kTB32 * kTB32, nullptr, zc, acc + (size_t)pre_o[k] * kTB32 * K, true);
     int pending = -1, slot = 1;
     for (int o = 0; o < nown; ++o) {
       const int rb = me + o * G;
       if (o == skip || (forward ? rb <= c : rb >= c)) continue;
+      bool done = false;
+      for (int k = 0; k < npre; ++k) done = done || pre_o[k] == o;
+      if (done) continue;
       if (pending < 0) { fetch_tile(slot, rb, c); cp_async_commit(); pending = o; continue; }
       // compute the pending one while the next streams in
       fetch_tile(3 - slot, rb, c);
@@ -558,24 +578,26 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
   if (me == 0) { fetch_inv(0, 0); cp_async_commit(); ready(); solve(0, 0, false, fpub); }
   for (int c = 0; c < nb && !abort_flag; ++c) {
     const bool next_mine = c + 1 < nb && (c + 1) % G == me;
-    if (next_mine) { fetch_tile(0, c + 1, c); fetch_inv(0, c + 1); cp_async_commit(); }
+    if (c % G != me) {
+      const int last = me + (nown - 1) * G;
+      if (nown == 0 || last <= c) continue;
+    }
+    const int skip = next_mine ? (c + 1) / G : -1;
+    if (next_mine) { fetch_tile(0, c + 1, c); fetch_inv(0, c + 1); }
+    const int npre = prefetch_updates(c, true, skip);
+    cp_async_commit();
     if (c % G == me) {
       for (int t = tid; t < kTB32 * K; t += 256) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
     } else {
-      const int last = me + (nown - 1) * G;
-      if (nown == 0 || last <= c) continue;
       receive(fpub, c, zc);
       if (abort_flag) break;
     }
     ready();
-    int skip = -1;
     if (next_mine) {
-      const int o1 = (c + 1) / G;
-      product(tl, nullptr, zc, acc + (size_t)o1 * kTB32 * K, true);
-      solve(o1, c + 1, false, fpub);
-      skip = o1;
+      product(tl, nullptr, zc, acc + (size_t)skip * kTB32 * K, true);
+      solve(skip, c + 1, false, fpub);
     }
-    stream_updates(c, true, skip);
+    stream_updates(c, true, skip, npre);
   }
   ready();
 
@@ -588,23 +610,23 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
   }
   for (int c = nb - 1; c >= 0 && !abort_flag; --c) {
     const bool next_mine = c - 1 >= 0 && (c - 1) % G == me;
-    if (next_mine) { fetch_tile(0, c - 1, c); fetch_inv(1, c - 1); cp_async_commit(); }
+    if (c % G != me && (nown == 0 || me >= c)) continue;
+    const int skip = next_mine ? (c - 1) / G : -1;
+    if (next_mine) { fetch_tile(0, c - 1, c); fetch_inv(1, c - 1); }
+    const int npre = prefetch_updates(c, false, skip);
+    cp_async_commit();
     if (c % G == me) {
       for (int t = tid; t < kTB32 * K; t += 256) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
     } else {
-      if (nown == 0 || me >= c) continue;
       receive(bpub, c, zc);
       if (abort_flag) break;
     }
     ready();
-    int skip = -1;
     if (next_mine) {
-      const int o1 = (c - 1) / G;
-      product(tl, nullptr, zc, acc + (size_t)o1 * kTB32 * K, true);
-      solve(o1, c - 1, true, bpub);
-      skip = o1;
+      product(tl, nullptr, zc, acc + (size_t)skip * kTB32 * K, true);
+      solve(skip, c - 1, true, bpub);
     }
-    stream_updates(c, false, skip);
+    stream_updates(c, false, skip, npre);
   }
   ready();
 }
