@@ -5,16 +5,18 @@
 // thread with fp32 accumulators in tensor memory, and read back with
 // tcgen05.ld by four epilogue warps.
 //
-// Persistent kernel, one CTA per SM, 128 x 128 output tiles in a static
-// round-robin order.  The MMA computes the TRANSPOSED tile (TMEM lane = output
-// column j, TMEM column = output row i) so each epilogue thread owns 16
-// consecutive rows of one column of the column-major output: the C tile is
-// moved by TMA between HBM and a 128-byte-swizzled shared buffer and the
-// epilogue touches it with 16-byte, bank-conflict-free accesses.
+// Persistent kernel, one CTA per SM, TI x 128 output tiles (TI = 128, or 256
+// for the large 16-bit products) in a static round-robin order.  The MMA
+// computes the TRANSPOSED tile (TMEM lane = output column j, TMEM column =
+// output row i) so each epilogue thread owns consecutive rows of one column of
+// the column-major output: the C tile is moved by TMA between HBM and
+// 128-byte-swizzled shared boxes of 64 rows and the epilogue touches them with
+// 16-byte, bank-conflict-free accesses.
 //
 // Roles: warp 0 TMA producer of the operand ring; warp 1 TMEM owner and MMA
-// issuer; warps 2..5 epilogue (warp w reads TMEM lanes 32*(w%4)..+31), which
-// also prefetch C tiles two tiles ahead and issue the TMA stores.
+// issuer; warps 2..9 epilogue in two groups of four (warp w reads TMEM lanes
+// 32*(w%4)..+31; group g takes rows TI/2 g .. of the tile), which also
+// prefetch C tiles ahead and issue the TMA stores.
 // Accumulators are double buffered in TMEM (single buffered for 4-slice FP8),
 // so the epilogue of one tile overlaps the MMAs of the next.  The E4M3
 // variant keeps one accumulator per 128-deep K slice and folds them with the
