@@ -27,7 +27,6 @@ namespace hpmxp {
 namespace {
 
 constexpr int kB = 128;         // base (sub-)block width
-constexpr int kLd = kB + 1;     // padded shared-memory leading dimension
 
 // ---------------------------------------------------------------------------
 // fp64 -> 16-bit float, round to nearest even, written from the IEEE 754
