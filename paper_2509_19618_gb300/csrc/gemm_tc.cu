@@ -63,6 +63,10 @@ struct TileCfg {
   static constexpr size_t kSmem = 1024 + (size_t)kStages * (kStageA + kStageB) + (size_t)kCBufs * kCTile +
                                   8 * (2 * kStages + 4 + 2 * kCBufs) + 16;
 };
+// 227 KB of dynamic shared memory per CTA; two TI-column fp32 accumulators in
+// the 512 TMEM columns; a TMA box is at most 256 rows
+static_assert(TileCfg<128>::kSmem <= 232448 && TileCfg<256>::kSmem <= 232448, "shared memory per CTA");
+static_assert(2 * 256 <= 512 && 256 <= 256, "TMEM columns, TMA box rows");
 
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

@@ -115,6 +115,7 @@ constexpr int kGetrfThreads = 512;
 constexpr int kP = 132;    // shared pitch (floats): 16-byte aligned columns
 constexpr int kPW = 16;    // panel width
 constexpr size_t kGetrfSmem = sizeof(float) * (3 * kB * kP + 2 * kPW + 8);
+static_assert(kGetrfSmem <= 232448, "getrf's shared memory fits one CTA");
 
 __device__ inline void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
