@@ -66,7 +66,9 @@ struct TileCfg {
 // 227 KB of dynamic shared memory per CTA; two TI-column fp32 accumulators in
 // the 512 TMEM columns; a TMA box is at most 256 rows
 static_assert(TileCfg<128>::kSmem <= 232448 && TileCfg<256>::kSmem <= 232448, "shared memory per CTA");
-static_assert(2 * 256 <= 512 && 256 <= 256, "TMEM columns, TMA box rows");
+template <int TI>
+constexpr bool tile_fits() { return 2 * TI <= 512 && TI <= 256 && TI % 128 == 0; }
+static_assert(tile_fits<128>() && tile_fits<256>(), "two accumulators in TMEM, one TMA box per stage");
 
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
