@@ -14,6 +14,14 @@
 // Every product runs on the GEMM engine (tcgen05 by default).  Operands are
 // kept K-major: U12 is K-major in the column-major factor array already, and
 // the column panel is packed row-major once per step.
+//
+// Streams (Factorizer::run): the caller's stream carries the diagonal block
+// and the U12 chain; a third stream the L21 chain; a lowest-priority fourth
+// W_s / Z_s (they depend only on the diagonal block, so they are made while it
+// is still being factored); with look-ahead a second stream takes the far part
+// of each Schur update.  The chain's kernels are launched as programmatic
+// dependents (launch_pdl) and wait for their predecessor before touching
+// global memory.
 #include "internal.h"
 
 #include <stdlib.h>
