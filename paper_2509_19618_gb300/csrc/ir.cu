@@ -299,9 +299,11 @@ __global__ void gemv_finish_kernel(int64_t n, int K, int nchunk, const double* _
 // 64-bit words that carry their epoch: (fp32 value | epoch << 32) for T =
 // float, two words (high half | epoch << 32), (low half | epoch << 32) per
 // value for T = double; a reader's poll of the words delivers the data itself,
-// with no separate flag.  The owner of the next block prefetches its
-// off-diagonal tile (and, for float, the inverted diagonal block) into shared
-// memory before it waits; the fp64 inverse (128 KB) is read from L2.
+// with no separate flag.  Before it waits for z_c, every CTA issues the copies
+// of what it will multiply z_c with: the owner of block c+1 its off-diagonal
+// tile (and, for float, the inverted diagonal block; the fp64 inverse, 128 KB,
+// is read from L2), and each CTA the tiles of its first two blocks that z_c
+// updates.
 // ---------------------------------------------------------------------------
 constexpr int kTB32 = 128;
 
