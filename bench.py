@@ -47,19 +47,23 @@ def parse():
     ap.add_argument("--nb", type=int, default=0, help="Schur update depth; 0 = autotune over 128/256/512")
     ap.add_argument("--prec", default="bf16", choices=list(PREC))
     ap.add_argument("--precond-fp32", type=int, default=1,
-                    help="1: fp32 inner-GMRES operator (the benchmark default), 0: all fp64")
+                    help="1: the preconditioner U^-1 L^-1 of the inner GMRES applied in fp32 (default), 0: fp64")
+    ap.add_argument("--matvec-fp32", type=int, default=0,
+                    help="1: the Arnoldi product A v of the inner GMRES in fp32, 0: fp64 (default)")
     ap.add_argument("--inner-tol", type=float, default=-1.0,
-                    help="inner GMRES tolerance floor; -1: 1e-5 with the fp32 operator, library default otherwise")
+                    help="inner GMRES tolerance floor; -1: 1e-5 with an fp32 preconditioner, library default otherwise")
     ap.add_argument("--theta", type=float, default=-1.0,
                     help="adaptive inner-stopping factor of GMRES-IR; -1: the library default")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--diag", default="dominant", choices=["dominant", "sqrtn", "none"],
                     help="diagonal of the generated matrix (row sum + margin, sqrt(n) scaling, unscaled)")
     ap.add_argument("--margin", type=float, default=1.0, help="diagonal-dominance margin")
-    ap.add_argument("--fp64-comparator", action="store_true",
-                    help="also time an fp64 LU solve with partial pivoting (torch/cuSOLVER) of the same A")
-    ap.add_argument("--fp64-operator-steps", type=int, default=3,
-                    help="also time this many solves with the inner GMRES operator in fp64 (0: skip)")
+    ap.add_argument("--no-fp64-comparator", action="store_true",
+                    help="skip the fp64 LU solve with partial pivoting (torch/cuSOLVER) of the same A")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the all-fp64 and all-fp32 inner-operator variants (timed over --steps each)")
+    ap.add_argument("--serving-requests", type=int, default=600,
+                    help="requests of the serving sub-record at 1000/s (a third of them at 100/s); 0: skip")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
@@ -188,12 +192,26 @@ def oracle_sample_size(target_s: float, seed: int, prec: str, nb: int) -> tuple[
 
 
 def cpu_baseline(args, nb: int) -> dict:
+    """The oracle on the host's cores (all of them, then one), each on a sample
+    sized to about --cpu-seconds."""
     import oracle
+    cores = oracle.num_threads()
     n, _ = oracle_sample_size(args.cpu_seconds, args.seed, args.prec, nb)
     dt, info, rc = oracle_solve_timed(n, args.seed, args.prec, min(nb, 512))
-    return {"value": hpl_ops(n) / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+    single = None
+    try:
+        oracle.set_num_threads(1)
+        n1, _ = oracle_sample_size(args.cpu_seconds / 2, args.seed, args.prec, nb)
+        dt1, info1, rc1 = oracle_solve_timed(n1, args.seed, args.prec, min(nb, 512))
+        single = {"value": hpl_ops(n1) / dt1 / 1e12, "unit": "TFLOP/s", "cores": 1,
+                  "sample": f"one oracle solve at n={n1}, {dt1:.2f} s, status {rc1}, iters {info1['iters']}"}
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": hpl_ops(n) / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "cpu_model": oracle.cpu_model(),
             "sample": f"one oracle solve (factor + GMRES-IR) of the same generated system at n={n} "
-                      f"(the full n is out of reach on the host), {dt:.2f} s, status {rc}, iters {info['iters']}"}
+                      f"(the full n is out of reach on the host), {dt:.2f} s, status {rc}, iters {info['iters']}",
+            "single_thread": single}
 
 
 SERVING_METRIC = "served systems/s (n log-uniform in [256, 8192], 1-8 rhs, Poisson arrivals), scaled residual < 16"
@@ -244,11 +262,7 @@ def run_serving(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = PREC[args.prec]
-    params = capi.hpmxp_ir_params_default()
-    params.precond_fp32 = args.precond_fp32
-    params.inner_tol = IR_KW["inner_tol"]
-    if args.theta >= 0:
-        params.theta = args.theta
+    params = ir_params_for(args, args.precond_fp32, args.matvec_fp32)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     specs = serve.request_stream(args.requests, args.rate, stream_seed=2509 + rank)
@@ -331,9 +345,73 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def ir_params_for(args, precond_fp32: int, matvec_fp32: int):
+    from paper_2509_19618_gb300 import capi
+    p = capi.hpmxp_ir_params_default()
+    p.precond_fp32 = precond_fp32
+    p.matvec_fp32 = matvec_fp32
+    if args.inner_tol >= 0:
+        p.inner_tol = args.inner_tol
+    elif precond_fp32:
+        p.inner_tol = 1e-5
+    if args.theta >= 0:
+        p.theta = args.theta
+    return p
+
+
+def operator_label(p) -> str:
+    return (f"fp64 GMRES-IR(30): fp64 residual, MGS, Givens, update; preconditioner apply in "
+            f"{'fp32' if p.precond_fp32 else 'fp64'}, Arnoldi product A v in {'fp32' if p.matvec_fp32 else 'fp64'}")
+
+
+def time_solves(solver, A, b, steps: int, stream, dev):
+    """Device time of `steps` whole solves (factor + GMRES-IR) on `stream`."""
+    import torch
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = []
+    e0.record(stream)
+    for _ in range(steps):
+        x, info, st = solver(A, b)
+        res.append((st, info[0]))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / 1e3 / steps, res
+
+
+def serving_record(args, dev, params) -> dict:
+    """Short serving runs of the request mix (n log-uniform 256..8192, 1-8 rhs):
+    Poisson arrivals at 1000/s and 100/s, and the same requests one at a time."""
+    from paper_2509_19618_gb300 import serve
+    out = {"what": "request executor: each request generates its system on the device, factors it (BF16) and "
+                   "refines it (fp64 GMRES-IR); requests are admitted by device footprint into a "
+                   f"{args.arena_gb:g} GB arena and run on {args.workers} worker streams",
+           "runs": []}
+    warm = serve.request_stream(max(3 * args.workers, 24), 0.0, stream_seed=1)
+    with serve.Executor(workers=args.workers, arena_bytes=int(args.arena_gb * (1 << 30)), device=dev) as ex:
+        serve.run_stream(ex, warm, PREC[args.prec], params)
+        for rate, count in ((1000.0, args.serving_requests), (100.0, max(1, args.serving_requests // 3))):
+            specs = serve.request_stream(count, rate, stream_seed=2509)
+            comps = serve.run_stream(ex, specs, PREC[args.prec], params)
+            sm = serve.summarize(specs, comps)
+            out["runs"].append({"rate": rate, "requests": count, "systems_per_s": sm["systems_per_s"],
+                                "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "mean_queue_ms": sm["mean_queue_ms"],
+                                "tflops": sm["tflops"], "valid": sm["valid"], "failed": sm["failed"],
+                                "mean_ir_iters": sm["mean_iters"], "max_scaled_residual": sm["max_scaled_resid"]})
+    sub = serve.request_stream(max(1, args.serving_requests // 3), 0.0, stream_seed=2509)
+    with serve.Executor(workers=1, arena_bytes=int(args.arena_gb * (1 << 30)), device=dev) as ex1:
+        c1 = serve.run_stream(ex1, sub, PREC[args.prec], params, one_at_a_time=True)
+    s1 = serve.summarize(sub, c1)
+    out["one_at_a_time"] = {"requests": len(sub), "systems_per_s": s1["systems_per_s"], "p50_ms": s1["p50_ms"],
+                            "p99_ms": s1["p99_ms"], "valid": s1["valid"],
+                            "what": "the first requests of the same stream, each submitted after the previous one "
+                                    "completed (one worker): service time only"}
+    return out
+
+
 def main():
     args = parse()
-    IR_KW.update(precond_prec=args.precond_fp32,
+    IR_KW.update(precond_prec=args.precond_fp32, matvec_prec=args.matvec_fp32,
                  inner_tol=args.inner_tol if args.inner_tol >= 0 else (1e-5 if args.precond_fp32 else 1e-12))
     if args.theta >= 0:
         IR_KW.update(theta=args.theta)
@@ -355,20 +433,15 @@ def main():
 
     diag = {"dominant": capi.DIAG_DOMINANT, "sqrtn": capi.DIAG_SQRTN, "none": capi.DIAG_NONE}[args.diag]
     A, b = api.generate(n, seed=args.seed, margin=args.margin, diag=diag, device=dev)   # untimed (not timed by the paper)
-    params = capi.hpmxp_ir_params_default()
-    params.precond_fp32 = args.precond_fp32
-    if args.inner_tol >= 0:
-        params.inner_tol = args.inner_tol
-    elif args.precond_fp32:
-        params.inner_tol = 1e-5
-    if args.theta >= 0:
-        params.theta = args.theta
+    params = ir_params_for(args, args.precond_fp32, args.matvec_fp32)
     nb = args.nb or autotune.pick_nb(n, prec, A, device=dev)
     fp64 = None
-    if args.fp64_comparator and rank == 0:
-        # same system, fp64 LU with partial pivoting + solve (cuSOLVER through torch), one run
+    if not args.no_fp64_comparator and rank == 0:
+        # same system, fp64 LU with partial pivoting + solve (cuSOLVER through torch), one run after one warm-up
         Af = A.view().clone()
         bf = b.view().clone()
+        LUw, pw = torch.linalg.lu_factor(Af[:1024, :1024])
+        del LUw, pw
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -380,10 +453,14 @@ def main():
         xs = api.ColMajor.from_tensor(xf, dev)
         srf = float(api.residual(A, xs, b)[0])
         fp64 = {"value": hpl_ops(n) / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms": ms, "scaled_residual": srf,
-                "what": "torch.linalg.lu_factor + lu_solve (fp64, partial pivoting) on the same A, one run"}
+                "what": "torch.linalg.lu_factor + lu_solve (cuSOLVER, fp64, partial pivoting) on the same A, one run"}
         del Af, bf, LUf, piv, xf, xs
         torch.cuda.empty_cache()
     solver = api.Solver(n, 1, prec, nb, device=dev, params=params)
+    if not args.no_variants:
+        # room for the fp32 copy of A that the all-fp32 variant's Arnoldi products read
+        solver.sws = api.workspace(capi.hpmxp_solve_workspace(n, 1, params.restart) + capi.hpmxp_solve_workspace_a32(n),
+                                   dev)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(max(args.warmup, 0)):
@@ -393,20 +470,11 @@ def main():
     capi.hpmxp_prof_enable(False)
     # timed region 1: device time of K whole solves, inputs resident in HBM
     launches0 = capi.hpmxp_launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    infos = []
-    with ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
+    with ClockSampler(local) as clk:
         barrier(ws)
-        torch.cuda.synchronize(dev)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            x, info, st = solver(A, b)
-            infos.append((st, info[0]))
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
+        t_step, infos = time_solves(solver, A, b, args.steps, stream, dev)
         barrier(ws)
     launches = capi.hpmxp_launch_count() - launches0
-    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
     t_step = allmax(t_step, ws, dev)
     ok = all(st == capi.OK for st, _ in infos)
     sr = float(api.residual(A, solver.x, b)[0])                 # untimed backward-error check
@@ -428,14 +496,21 @@ def main():
     # every launch of the tensor-core GEMM kernel (Schur updates and panel products)
     g = {f: prof["gemm_update"][f] + prof["gemm_panel"][f] for f in ("ms", "work", "launches")}
     bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
     dom_ms_launch = g["ms"] / max(g["launches"], 1)
     achieved = (g["work"] / max(g["launches"], 1)) / (dom_ms_launch / 1e3) / 1e12 if g["launches"] else None
     peak = bf16_peak * (2.0 if prec == 2 else 1.0)
+    # whole-solve roofline: 2/3 n^3 at the tensor peak plus 10 n^2 bytes per refinement
+    # iteration (8 n^2 of A, 2 n^2 of factors) and once more for x0, at the HBM peak
+    iters = infos[-1][1]["iters"]
+    t_roof = (2.0 / 3.0 * n**3) / (peak * 1e12) + 10.0 * n * n * (iters + 1) / (hbm_peak * 1e9)
     roofline = {"bound": "tensor", "kernel": "gemm_tc_kernel (tcgen05 panel + Schur-update products)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback 1.7 PF/s")
-                + (" x2 nominal fp8/bf16 ratio" if prec == 2 else ""),
+                "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops_sustained" if peaks
+                                else "of fallback 1.7 PF/s") + (" x2 nominal fp8/bf16 ratio" if prec == 2 else ""),
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "whole_solve": {"t_roof_ms": t_roof * 1e3, "t_meas_ms": t_step * 1e3, "frac": t_roof / t_step,
+                                "what": "T_roof = 2/3 n^3 / tensor peak + 10 n^2 (iters + 1) bytes / HBM peak"},
                 "per_kind_ms_per_solve": {k: v["ms"] for k, v in prof.items()},
                 "per_kind_launches": {k: v["launches"] for k, v in prof.items()}}
     gv = prof["gemv"]
@@ -444,32 +519,26 @@ def main():
     pc = prof["precond"]
     if pc["launches"]:
         roofline["precond_gbs"] = pc["work"] / (pc["ms"] / 1e3) / 1e9
+        roofline["precond_ms_per_apply"] = pc["ms"] / pc["launches"]
 
-    # the same solve with every step of the refinement in fp64 (inner operator included)
-    fp64op = None
-    if args.fp64_operator_steps > 0 and params.precond_fp32:
-        p64 = capi.hpmxp_ir_params_default()
+    # the same solve with other inner-operator precisions, over the same number of steps
+    variants = {}
+    if not args.no_variants:
         keep = solver.params
-        solver.params = p64
-        solver(A, b)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        res = []
-        e0.record(stream)
-        for _ in range(args.fp64_operator_steps):
-            x64, info64, st64 = solver(A, b)
-            res.append((st64, info64[0]))
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        t64 = e0.elapsed_time(e1) / 1e3 / args.fp64_operator_steps
-        sr64 = float(api.residual(A, solver.x, b)[0])
+        for name, (pp, mp) in (("fp64_inner_operator", (0, 0)), ("fp32_inner_operator", (1, 1))):
+            if (pp, mp) == (keep.precond_fp32, keep.matvec_fp32):
+                continue
+            solver.params = ir_params_for(args, pp, mp)
+            solver(A, b)
+            t_v, res = time_solves(solver, A, b, args.steps, stream, dev)
+            sr_v = float(api.residual(A, solver.x, b)[0])
+            variants[name] = {"value": hpl_ops(n) / t_v / 1e12, "unit": "TFLOP/s", "ms_per_step": t_v * 1e3,
+                              "steps": args.steps, "scaled_residual": sr_v,
+                              "valid": bool(all(st == capi.OK for st, _ in res) and sr_v < 16.0),
+                              "ir_iters": res[-1][1]["iters"], "ir_outer": res[-1][1]["outer"],
+                              "what": operator_label(solver.params) +
+                                      f", inner tolerance {solver.params.inner_tol:g}"}
         solver.params = keep
-        fp64op = {"value": hpl_ops(n) / t64 / 1e12, "unit": "TFLOP/s", "ms_per_step": t64 * 1e3,
-                  "steps": args.fp64_operator_steps, "scaled_residual": sr64,
-                  "valid": bool(all(st == capi.OK for st, _ in res) and sr64 < 16.0),
-                  "ir_iters": res[-1][1]["iters"], "ir_outer": res[-1][1]["outer"],
-                  "what": "same solve, inner GMRES operator (preconditioner and Arnoldi product) in fp64, "
-                          "inner tolerance 1e-12"}
 
     # timed region 2: end to end through the public API with host buffers
     e2e = None
@@ -481,8 +550,6 @@ def main():
         x_h = torch.empty((1, solver.x.ld), dtype=torch.float64, pin_memory=True)
         A2 = api.ColMajor(torch.empty_like(A.storage), n, n)
         b2 = api.ColMajor(torch.empty_like(b.storage), n, 1)
-        del A
-        torch.cuda.empty_cache()
         steps = max(1, min(args.steps, 5))
         barrier(ws)
         torch.cuda.synchronize(dev)
@@ -499,26 +566,36 @@ def main():
         e2e = {"value": ws * hpl_ops(n) / t_e2e / 1e12, "unit": "TFLOP/s", "ms_per_step": t_e2e * 1e3,
                "h2d_bytes_per_step": int(A_h.numel() * 8 + b_h.numel() * 8),
                "d2h_bytes_per_step": int(x_h.numel() * 8)}
+        del A_h, b_h, x_h, A2, b2
+    del A, b, solver
+    torch.cuda.empty_cache()
+
+    serving = None
+    if args.serving_requests > 0 and rank == 0:
+        serving = serving_record(args, dev, ir_params_for(args, args.precond_fp32, args.matvec_fp32))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, nb)
 
     if rank == 0:
+        speedup = (value / fp64["value"]) if fp64 else None
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.prec, "data": "synthetic (on-device LCG generator, seed %d)"
                 % args.seed,
-                "config": {"workload": f"HPL-MxP single system n={n}, {args.prec} LU nb={nb} + fp64 GMRES-IR(30)",
+                "config": {"workload": f"HPL-MxP single system n={n}, {args.prec} LU nb={nb} + "
+                                       + operator_label(params),
                            "n": n, "nb": nb, "prec": args.prec, "global_batch": ws, "seq_len": None,
                            "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (A is %.1f GB)" % (8 * n * n / 1e9),
-                           "precond_fp32": int(params.precond_fp32)},
+                           "precond_fp32": int(params.precond_fp32), "matvec_fp32": int(params.matvec_fp32),
+                           "inner_tol": params.inner_tol},
                 "valid": bool(ok and sr < 16.0), "scaled_residual": sr,
                 "ir_iters": infos[-1][1]["iters"], "ir_outer": infos[-1][1]["outer"],
                 "ir_status": int(infos[-1][0]), "diag": args.diag, "margin": args.margin,
-                "fp64_lu_comparator": fp64, "fp64_inner_operator": fp64op,
-                "gpu_launches": int(launches), "roofline": roofline, "clocks": clk.summary(),
+                "fp64_lu_comparator": fp64, "speedup_vs_fp64_lu": speedup, "variants": variants,
+                "serving": serving, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk.summary(),
                 "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if ws > 1:

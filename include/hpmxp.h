@@ -106,7 +106,9 @@ hpmxp_status hpmxp_generate(int64_t n, uint64_t seed, double margin, int diag_mo
  *
  * The first call on a device looks up the array's device address (with that
  * device current) and keeps it; make that first call before any stream
- * capture begins.  All calls on a device share the one array: two calls whose
+ * capture begins.  A reset of the device's primary context (cudaDeviceReset)
+ * invalidates the kept address: calling this entry point after such a reset
+ * is not supported.  All calls on a device share the one array: two calls whose
  * work overlaps on the GPU (different streams, no ordering between them) race
  * on it and give wrong diagonals.  Order such calls on one stream or by events. */
 hpmxp_status hpmxp_generate_noalloc(int64_t n, uint64_t seed, double margin, int diag_mode, double* A,
@@ -152,10 +154,12 @@ typedef struct {
   double inner_tol;      /* relative floor of the inner stopping test (default 1e-12) */
   double theta;          /* adaptive inner-stopping factor, 0 disables (default 0.1) */
   double accept;         /* acceptance threshold of the scaled residual (default 16) */
-  int32_t precond_fp32;  /* 1: the inner GMRES operator (M^{-1} and the Arnoldi product A v) in fp32
-                            arithmetic; the residual, orthogonalization, rotations and update stay
-                            fp64.  0: everything fp64 (default 0) */
-  int32_t reserved;
+  int32_t precond_fp32;  /* 1: the preconditioner M^{-1} = U^{-1} L^{-1} applied in fp32 arithmetic
+                            (x0, each cycle's start and each Arnoldi step); 0: fp64 (default 0) */
+  int32_t matvec_fp32;   /* 1: the Arnoldi product A v of the inner GMRES in fp32 (A truncated toward
+                            zero, fp32 accumulation); 0: fp64 (default 0).  The outer residual
+                            b - A x, the orthogonalization, rotations, update and the acceptance
+                            check are fp64 whatever these two fields say */
 } hpmxp_ir_params;
 
 typedef struct {
@@ -183,7 +187,7 @@ void hpmxp_ir_params_default(hpmxp_ir_params* p);
 size_t hpmxp_solve_workspace(int64_t n, int64_t nrhs, int restart);
 
 /* Optional room for an fp32 copy of A (truncated toward zero), used when
- * prm->precond_fp32 = 1 and ws_bytes >= hpmxp_solve_workspace(n, nrhs,
+ * prm->matvec_fp32 = 1 and ws_bytes >= hpmxp_solve_workspace(n, nrhs,
  * restart) + hpmxp_solve_workspace_a32(n): the first residual of the solve
  * writes the copy as it reads A, and the inner GMRES operator's products read
  * it (4 bytes per entry instead of 8).  The products, and so every result, are

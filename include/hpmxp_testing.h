@@ -45,6 +45,19 @@ hpmxp_status hpmxp_test_precond(int64_t n, const void* LU, int64_t ldlu, int pre
                                 int64_t ldv, double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws,
                                 size_t ws_bytes, void* stream);
 
+/* Bound of the library's device-side waits whose running out is an error
+ * (a CTA of the preconditioner polling for a block that another CTA has not
+ * published yet; a stage of the tensor-core GEMM's operand, accumulator or C
+ * pipeline that has not filled yet): at most `polls` polls and `ns`
+ * nanoseconds of the GPU's global timer.  Kernels launched afterwards, by any
+ * host thread, use it; a wait that runs out makes the call return
+ * HPMXP_ETIMEOUT after the kernel has drained its own copies and tensor-core
+ * work, which always keep the default bound.  A short budget is a way to make
+ * those waits run out on purpose, with no peer missing and no GPU fault.
+ *   polls 1 .. 2^28, ns <= 2e9; (0, 0) restores the defaults (2^28 polls, 2 s)
+ * Returns HPMXP_EINVAL for other values. */
+hpmxp_status hpmxp_test_set_wait_budget(long long polls, unsigned long long ns);
+
 /* Fills the shared memory of every SM with `pattern` (one kernel on
  * `stream`), so that the next kernel starts on nonzero leftovers: a check
  * that kernels initialise every shared variable they read. */

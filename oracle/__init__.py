@@ -87,9 +87,10 @@ def lib():
             L.oracle_scaled_residual.argtypes = [i64, P, i64, P, i64, P, i64, i64, P]
             L.oracle_scaled_residual.restype = None
             L.oracle_solve_ir.argtypes = [i64, P, i64, P, i64, P, i64, P, i64, i64, i32, i32, d, d,
-                                          d, i32, ctypes.POINTER(IRInfo)]
+                                          d, i32, i32, ctypes.POINTER(IRInfo)]
             L.oracle_solve_ir.restype = i32
             L.oracle_num_threads.argtypes = []; L.oracle_num_threads.restype = i32
+            L.oracle_set_num_threads.argtypes = [i32]; L.oracle_set_num_threads.restype = i32
             _lib = L
     return _lib
 
@@ -189,8 +190,10 @@ def scaled_residual(A, X, B) -> np.ndarray:
 
 
 def solve_ir(A, LU, B, restart: int = 30, max_iters: int = 50, inner_tol: float = 1e-12,
-             theta: float = 0.1, accept: float = 16.0, precond_prec: int = 0):
-    """GMRES-IR.  Returns (X, [info dict per rhs], worst status)."""
+             theta: float = 0.1, accept: float = 16.0, precond_prec: int = 0, matvec_prec: int = 0):
+    """GMRES-IR.  Returns (X, [info dict per rhs], worst status).
+    precond_prec / matvec_prec: 1 = the inner GMRES's preconditioner / Arnoldi
+    product in fp32, 0 = fp64."""
     A = _f64(A)
     LU = _f64(LU)
     n = A.shape[0]
@@ -199,7 +202,7 @@ def solve_ir(A, LU, B, restart: int = 30, max_iters: int = 50, inner_tol: float 
     X = np.zeros((n, k), dtype=np.float64, order="F")
     info = (IRInfo * k)()
     rc = lib().oracle_solve_ir(n, _p(A), n, _p(LU), n, _p(B), n, _p(X), n, k, restart, max_iters,
-                               inner_tol, theta, accept, precond_prec, info)
+                               inner_tol, theta, accept, precond_prec, matvec_prec, info)
     if rc < 0:
         raise ValueError("oracle_solve_ir: bad arguments")
     infos = [dict(iters=i.iters, outer=i.outer, scaled_resid=i.scaled_resid, status=i.status)
@@ -209,6 +212,32 @@ def solve_ir(A, LU, B, restart: int = 30, max_iters: int = 50, inner_tol: float 
 
 def num_threads() -> int:
     return lib().oracle_num_threads()
+
+
+def set_num_threads(k: int) -> int:
+    """Threads of the oracle's parallel loops from now on; returns the number in effect."""
+    return lib().oracle_set_num_threads(int(k))
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo), or the machine type."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        info = ""
+    for key in ("model name", "Model Name", "Hardware"):
+        for line in info.splitlines():
+            if line.split(":")[0].strip() == key and ":" in line:
+                return line.split(":", 1)[1].strip()
+    parts = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            parts.setdefault(k.strip(), v.strip())
+    if "CPU implementer" in parts:
+        return f"{platform.machine()} (implementer {parts['CPU implementer']}, part {parts.get('CPU part', '?')})"
+    return platform.machine()
 
 
 def split_lu(LU):

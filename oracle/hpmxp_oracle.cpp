@@ -631,15 +631,15 @@ struct oracle_ir_info {
 // The inner loop of a cycle stops when the least-squares residual estimate
 // |g_{j+1}| <= beta * max(inner_tol, theta * accept / sr0), sr0 being the
 // scaled residual at the start of the cycle (theta = 0 disables the adaptive
-// term).  Arithmetic: fp64; with pprec 1 the operator of the inner GMRES
-// (preconditioner and matrix-vector product) is applied in fp32 while the
-// outer residual, orthogonalization, rotations and update stay fp64.
+// term).  Arithmetic: fp64; with pprec 1 the preconditioner of the inner
+// GMRES is applied in fp32, with mprec 1 its matrix-vector product A v_j, while
+// the outer residual, orthogonalization, rotations and update stay fp64.
 // Reading: "iterations" in the 50 cap are inner Arnoldi steps summed over
 // restarts.
 int oracle_solve_ir(int64_t n, const double* A, int64_t lda, const double* LU, int64_t ldlu,
                     const double* B, int64_t ldb, double* X, int64_t ldx, int64_t nrhs, int restart,
                     int max_iters, double inner_tol, double theta, double accept, int pprec,
-                    oracle_ir_info* info) {
+                    int mprec, oracle_ir_info* info) {
   if (n < 1 || restart < 1 || max_iters < 0) return -1;
   const double an = norm_inf_mat(n, A, lda);
   const int m = restart;
@@ -673,7 +673,7 @@ int oracle_solve_ir(int64_t n, const double* A, int64_t lda, const double* LU, i
         std::vector<double> Av(n);
         std::vector<double> zero(n, 0.0);
         // w = M^{-1} (A v_j): the residual routine with b = 0 gives -A v_j
-        if (pprec == 1) {
+        if (mprec == 1) {
           matvec_f32(n, A, lda, &V[(size_t)j * n], Av.data());
         } else {
           residual_vec(n, A, lda, &V[(size_t)j * n], zero.data(), Av.data());
@@ -729,6 +729,18 @@ int oracle_num_threads() {
 #ifdef _OPENMP
   return omp_get_max_threads();
 #else
+  return 1;
+#endif
+}
+
+// Threads used by the oracle's parallel loops from now on (k >= 1); returns
+// the number in effect afterwards.
+int oracle_set_num_threads(int k) {
+#ifdef _OPENMP
+  if (k >= 1) omp_set_num_threads(k);
+  return omp_get_max_threads();
+#else
+  (void)k;
   return 1;
 #endif
 }

@@ -152,8 +152,8 @@ class Solver:
         self.LU = ColMajor.empty(n, n, factor_storage_dtype(prec), self.device)
         self.x = ColMajor.empty(n, nrhs, torch.float64, self.device)
         self.fws = workspace(capi.hpmxp_factor_workspace(n, prec, nb), self.device)
-        # with the fp32 inner operator, room for its fp32 copy of A (half the bytes per product)
-        extra = capi.hpmxp_solve_workspace_a32(n) if self.params.precond_fp32 else 0
+        # with fp32 Arnoldi products, room for their fp32 copy of A (half the bytes per product)
+        extra = capi.hpmxp_solve_workspace_a32(n) if self.params.matvec_fp32 else 0
         self.sws = workspace(capi.hpmxp_solve_workspace(n, nrhs, self.params.restart) + extra, self.device)
 
     def factor(self, A: ColMajor, stream=None) -> ColMajor:

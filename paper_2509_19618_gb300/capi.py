@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: 
 class IRParams(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("theta", ctypes.c_double), ("accept", ctypes.c_double), ("precond_fp32", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("matvec_fp32", ctypes.c_int32)]
 
 
 class IRInfo(ctypes.Structure):
@@ -98,6 +98,7 @@ def load():
             "hpmxp_test_precond": ([i64, P, i64, i32, P, i64, P, i64, i64, i32, P, sz, P], i32),
             "hpmxp_test_arena": ([sz, ctypes.POINTER(i64), i32, ctypes.POINTER(i64)], i32),
             "hpmxp_test_fill_smem": ([ctypes.c_uint32, P], i32),
+            "hpmxp_test_set_wait_budget": ([ctypes.c_longlong, ctypes.c_ulonglong], i32),
             "hpmxp_request_footprint": ([ctypes.POINTER(Request)], sz),
             "hpmxp_executor_create": ([i32, i32, P, sz, ctypes.POINTER(P)], i32),
             "hpmxp_executor_submit": ([P, ctypes.POINTER(Request)], i32),
@@ -220,6 +221,10 @@ def hpmxp_test_precond(*args):
 
 def hpmxp_test_fill_smem(pattern: int, stream) -> int:
     return _call("hpmxp_test_fill_smem", pattern, stream)
+
+
+def hpmxp_test_set_wait_budget(polls: int, ns: int) -> int:
+    return _call("hpmxp_test_set_wait_budget", polls, ns)
 
 
 def hpmxp_test_arena(arena_bytes: int, ops: list[int]) -> list[int]:

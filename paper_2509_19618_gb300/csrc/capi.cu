@@ -3,7 +3,16 @@
 #include "internal.h"
 #include "../../include/hpmxp_testing.h"
 
+#include <atomic>
+
 namespace hpmxp {
+
+namespace {
+std::atomic<long long> g_wait_polls{kSpinLimit};
+std::atomic<unsigned long long> g_wait_ns{kWaitNs};
+}  // namespace
+
+WaitBudget wait_budget() { return WaitBudget{g_wait_polls.load(), g_wait_ns.load()}; }
 
 hpmxp_status status_from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return HPMXP_OK;
@@ -89,7 +98,7 @@ void hpmxp_ir_params_default(hpmxp_ir_params* p) {
   p->theta = 0.1;
   p->accept = 16.0;
   p->precond_fp32 = 0;
-  p->reserved = 0;
+  p->matvec_fp32 = 0;
 }
 
 size_t hpmxp_solve_workspace(int64_t n, int64_t nrhs, int restart) {
@@ -108,7 +117,8 @@ hpmxp_status hpmxp_solve_ir(int64_t n, const double* A, int64_t lda, const void*
   if (prm) p = *prm;
   if (n < 1 || n > kMaxN || !A || lda < n || !LU || ldlu < n || !b || ldb < n || !x || ldx < n || nrhs < 1 ||
       nrhs > 8 || !ws || !aligned(ws, 256) || !prec_ok(prec) || p.restart < 1 || p.restart > 64 ||
-      p.max_iters < 0 || !(p.accept > 0.0) || p.inner_tol < 0.0 || p.theta < 0.0)
+      p.max_iters < 0 || !(p.accept > 0.0) || p.inner_tol < 0.0 || p.theta < 0.0 ||
+      (p.precond_fp32 != 0 && p.precond_fp32 != 1) || (p.matvec_fp32 != 0 && p.matvec_fp32 != 1))
     return HPMXP_EINVAL;
   if (ws_bytes < solve_ws_bytes(n, nrhs, p.restart)) return HPMXP_ENOMEM;
   return solve_ir(n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs, p, info, ws, ws_bytes, (cudaStream_t)stream);
@@ -165,6 +175,18 @@ hpmxp_status hpmxp_test_precond(int64_t n, const void* LU, int64_t ldlu, int pre
   if (ws_bytes < solve_ws_bytes(n, nrhs, 1)) return HPMXP_ENOMEM;
   return precond_apply(n, LU, ldlu, prec == HPMXP_FP16 ? kFP16 : kBF16, v, ldv, z, ldz, nrhs, fp32, ws,
                        (cudaStream_t)stream);
+}
+
+hpmxp_status hpmxp_test_set_wait_budget(long long polls, unsigned long long ns) {
+  if (polls == 0 && ns == 0) {
+    g_wait_polls.store(kSpinLimit);
+    g_wait_ns.store(kWaitNs);
+    return HPMXP_OK;
+  }
+  if (polls < 1 || polls > kSpinLimit || ns > kWaitNs) return HPMXP_EINVAL;
+  g_wait_polls.store(polls);
+  g_wait_ns.store(ns);
+  return HPMXP_OK;
 }
 
 hpmxp_status hpmxp_test_fill_smem(uint32_t pattern, void* stream) {

@@ -22,9 +22,12 @@
 // variant keeps one accumulator per 128-deep K slice and folds them with the
 // per-tile scales in the epilogue.
 //
-// Every wait is bounded (kSpinLimit polls, kWaitNs of wall time); a wait that
-// runs out sets kErrTimeout in the status word, skips the remaining work and
-// still drains its copies and frees tensor memory before the CTA exits.
+// Every wait is bounded (a poll count and a global-timer limit passed in
+// TcParams); a wait that runs out sets kErrTimeout in the status word, skips
+// the remaining work and still drains its copies and tensor-core work (with
+// the default bound) and frees tensor memory before the CTA exits.  The four
+// warps of an epilogue group take each tile's go / give-up decision together,
+// so none of them is left waiting at the group's named barrier.
 #include "internal.h"
 
 #include <cudaTypedefs.h>
@@ -61,7 +64,7 @@ struct TileCfg {
   static constexpr int kAhead = kCBufs >= 2 ? kCBufs - 1 : 1;   // C prefetch distance (local tiles)
   static constexpr int kReadWait = kCBufs >= 2 ? kCBufs - 2 : 0; // stores allowed to be still reading
   static constexpr size_t kSmem = 1024 + (size_t)kStages * (kStageA + kStageB) + (size_t)kCBufs * kCTile +
-                                  8 * (2 * kStages + 4 + 2 * kCBufs) + 16;
+                                  8 * (2 * kStages + 5 + 2 * kCBufs) + 16;
 };
 // 227 KB of dynamic shared memory per CTA; two TI-column fp32 accumulators in
 // the 512 TMEM columns; a TMA box is at most 256 rows
@@ -91,13 +94,15 @@ __device__ inline bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity to complete.
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity to complete: at most
+// `polls` polls and `ns` nanoseconds (the defaults for the drain waits).
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, long long polls = kSpinLimit,
+                                 unsigned long long ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
-  for (long long i = 1; i < kSpinLimit; ++i) {
+  for (long long i = 1; i < polls; ++i) {
     if (mbar_try(bar, parity)) return true;
-    if ((i & 255) == 0 && global_ns() - t0 > kWaitNs) return false;
+    if ((i & 255) == 0 && global_ns() - t0 > ns) return false;
   }
   return false;
 }
@@ -118,6 +123,17 @@ __device__ inline void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;"
 __device__ inline void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ inline void epi_barrier(int group) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "n"(kEpiThreads) : "memory");
+}
+// True for every thread of the epilogue group when v is true for all of them
+// (a barrier of the group's four warps with an AND reduction).
+__device__ inline bool epi_all(int group, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(1 + group), "n"(kEpiThreads)
+      : "memory");
+  return r != 0;
 }
 
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -213,6 +229,8 @@ struct TcParams {
   const float* sA; int sa_ld;
   const float* sB; int sb_ld;
   uint32_t* status;
+  long long wait_polls;            // bound of the pipeline waits (the drain waits keep the defaults)
+  unsigned long long wait_ns;
 };
 
 // Two floats rounded to nearest even into one 32-bit word of 16-bit values (lo
@@ -244,7 +262,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   auto acc_full = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + b); };
   auto acc_empty = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + 2 + b); };
   auto c_full = [&](int b, int h) { return bar0 + 8u * (uint32_t)(2 * kStages + 4 + 2 * b + h); };
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4 + 2 * kCBufs);
+  const uint32_t mma_drain = bar0 + 8u * (uint32_t)(2 * kStages + 4 + 2 * kCBufs);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5 + 2 * kCBufs);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -258,6 +277,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_init(c_full(b, 0), 1);
       mbar_init(c_full(b, 1), 1);
     }
+    mbar_init(mma_drain, 1);
     fence_mbar_init();
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
@@ -286,7 +306,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int kb = 0; kb < p.nkb; ++kb, ++pos) {
           const int s = (int)(pos % kStages);
           const long long use = pos / kStages;
-          if (use > 0 && !mbar_wait(empty(s), (uint32_t)((use - 1) & 1))) { ok = false; break; }
+          if (use > 0 && !mbar_wait(empty(s), (uint32_t)((use - 1) & 1), p.wait_polls, p.wait_ns)) {
+            ok = false;
+            break;
+          }
           mbar_expect_tx(full(s), kStageA + kStageB);
           tma_load_2d(sOpA + s * kStageA, &tmB, kb * (kRowBytes / 2), j0, full(s));
           tma_load_2d(sOpB + s * kStageB, &tmA, kb * (kRowBytes / 2), i0, full(s));
@@ -305,12 +328,15 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       int local = 0;
       for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++local) {
         const int ab = local % p.nbuf, ause = local / p.nbuf;
-        if (ause > 0 && !mbar_wait(acc_empty(ab), (uint32_t)((ause - 1) & 1))) { ok = false; break; }
+        if (ause > 0 && !mbar_wait(acc_empty(ab), (uint32_t)((ause - 1) & 1), p.wait_polls, p.wait_ns)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         const uint32_t d0 = tmem + (uint32_t)ab * p.acc_cols;
         for (int kb = 0; kb < p.nkb; ++kb, ++pos) {
           const int s = (int)(pos % kStages);
-          if (!mbar_wait(full(s), (uint32_t)((pos / kStages) & 1))) { ok = false; break; }
+          if (!mbar_wait(full(s), (uint32_t)((pos / kStages) & 1), p.wait_polls, p.wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t d = d0 + (p.fp8 ? (uint32_t)(kb * TI) : 0u);
           for (int kk = 0; kk < 4; ++kk) {   // 4 MMAs of 32 bytes of K each
@@ -324,7 +350,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         tc_commit(acc_full(ab));
       }
-      if (!ok) atomicOr(p.status, kErrTimeout);
+      if (!ok) {
+        atomicOr(p.status, kErrTimeout);
+        // the MMAs issued before the wait ran out complete before TMEM is freed
+        tc_commit(mma_drain);
+        if (!mbar_wait(mma_drain, 0)) atomicOr(p.status, kErrTimeout);
+      }
     }
   } else {
     // epilogue: group g = (warp - 2) / 4 owns rows i0 + (TI/2) g .. + TI/2 - 1 of the
@@ -363,11 +394,13 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const int i0 = (t % p.tiles_i) * TI, j0 = (t / p.tiles_i) * kTJ;
       const int cb = local % kCBufs, ab = local % p.nbuf;
       bool w = true;
-      if (load_c) w = mbar_wait(c_full(cb, g), (uint32_t)((local / kCBufs) & 1));
-      if (leader) issued_c[cb] = -1;
-      w = w && mbar_wait(acc_full(ab), (uint32_t)((local / p.nbuf) & 1));
-      w = __all_sync(0xffffffffu, w);   // warp-uniform for tcgen05.ld
+      if (load_c) w = mbar_wait(c_full(cb, g), (uint32_t)((local / kCBufs) & 1), p.wait_polls, p.wait_ns);
+      w = w && mbar_wait(acc_full(ab), (uint32_t)((local / p.nbuf) & 1), p.wait_polls, p.wait_ns);
+      // one decision for the whole group (warp-uniform for tcgen05.ld, and no
+      // warp of the group left behind at its named barrier)
+      w = epi_all(g, w);
       if (!w) { ok = false; break; }
+      if (leader) issued_c[cb] = -1;
       tc_fence_after();
       const uint32_t lane_base = tmem + (uint32_t)ab * p.acc_cols + ((uint32_t)(32 * q) << 16) + (TI / 2) * g;
       float sc[4] = {1.0f, 1.0f, 1.0f, 1.0f};
@@ -549,6 +582,9 @@ cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
   p.R = (uint16_t*)g.R; p.ldr = g.ldr;
   p.sA = g.sA; p.sa_ld = g.sa_ld; p.sB = g.sB; p.sb_ld = g.sb_ld;
   p.status = g.status;
+  const WaitBudget wb = wait_budget();
+  p.wait_polls = wb.polls;
+  p.wait_ns = wb.ns;
   if (g.fp8) {
     if (TI != 128 || p.nkb > 4) return cudaErrorInvalidValue;   // one 128-column accumulator per slice
     p.acc_cols = (uint32_t)(TI * p.nkb);

@@ -6,7 +6,7 @@
 // steps by n along its row, so every write of a warp is one contiguous run of
 // a column (coalesced) and any tile of an arbitrarily large matrix is produced
 // independently.  The off-diagonal magnitudes of each row are summed exactly:
-// 64-bit per-thread partial sums (at most 2048 terms below 2^52 each) folded
+// 64-bit per-thread partial sums (at most 512 terms below 2^52 each) folded
 // into a 128-bit accumulator per row with carry-propagating atomics, which are
 // associative, so the diagonal is bit-for-bit independent of scheduling.
 #include "internal.h"

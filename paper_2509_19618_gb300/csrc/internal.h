@@ -27,10 +27,22 @@ enum : uint32_t {
 };
 
 // Bounds of every device-side wait: at most kSpinLimit polls and at most
-// kWaitNs nanoseconds of the global timer (checked every 256 polls).  A
+// kWaitNs nanoseconds of the global timer (checked every 64 or 256 polls).  A
 // legitimate wait here lasts microseconds to milliseconds.
 constexpr long long kSpinLimit = 1ll << 28;
 constexpr unsigned long long kWaitNs = 2000000000ull;
+
+// The bound of the waits whose running out is an error (a peer CTA that never
+// publishes, a pipeline stage that never fills) is passed to the kernels as
+// an argument: the defaults above, unless the test hook
+// hpmxp_test_set_wait_budget lowered it.  The waits with which a CTA drains
+// its own copies and tensor-core work before it exits always keep the
+// defaults, so a short budget cannot make a CTA leave work in flight.
+struct WaitBudget {
+  long long polls;
+  unsigned long long ns;
+};
+WaitBudget wait_budget();
 
 __device__ inline unsigned long long global_ns() {
   unsigned long long t;

@@ -375,7 +375,8 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
                                                       const double* __restrict__ v, int64_t ldv,
                                                       double* __restrict__ z, int64_t ldz,
                                                       unsigned long long* __restrict__ pub, int epoch,
-                                                      uint32_t* status) {
+                                                      uint32_t* status, long long wait_polls,
+                                                      unsigned long long wait_ns) {
   constexpr bool kInvInSmem = sizeof(T) == 4;   // the fp32 inverse (64 KB) is staged; the fp64 one stays in L2
   constexpr int W = kWords<T>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -469,7 +470,11 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
   // all copies issued by this CTA have landed (ready) / all but the latest group (ready_prev)
   auto ready = [&]() { cp_async_wait<0>(); __syncthreads(); };
   auto ready_prev = [&]() { cp_async_wait<1>(); __syncthreads(); };
-  // wait for the tagged words of block c and unpack them into dst
+  // wait for the tagged words of block c and unpack them into dst; a wait
+  // that runs out (at most wait_polls polls and wait_ns of the global timer)
+  // sets the timeout bit and the CTA's abort flag, and the other threads of
+  // the CTA stop polling once they see the flag
+  volatile int* abort_v = &abort_flag;
   auto receive = [&](const unsigned long long* src, int c, T* dst) {
     const unsigned long long* w = src + (size_t)c * kTB32 * K * W;
     const unsigned long long t0 = global_ns();
@@ -477,13 +482,13 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
       uint32_t bits[W];
 #pragma unroll
       for (int h = 0; h < W; ++h) {
-        unsigned long long word;
+        unsigned long long word = 0;
         for (long long it = 0;; ++it) {
           asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(word) : "l"(w + (size_t)t * W + h) : "memory");
           if ((int)(word >> 32) == epoch) break;
-          if (it > kSpinLimit || ((it & 63) == 63 && global_ns() - t0 > kWaitNs)) {
+          if (it >= wait_polls || ((it & 63) == 63 && (global_ns() - t0 > wait_ns || *abort_v))) {
             atomicOr(status, kErrTimeout);
-            abort_flag = 1;
+            *abort_v = 1;
             break;
           }
         }
@@ -987,7 +992,11 @@ cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt,
   // one value for every call: concurrent solves on other threads set the same cap
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPrecondSmem);
   if (e != cudaSuccess) return e;
-  void* args[] = {&n, (void*)&LU, &ld, &fmt, (void*)&dinv, (void*)&v, &ldv, &z, &ldz, &pub, &epoch, &status};
+  const WaitBudget wb = wait_budget();
+  long long polls = wb.polls;
+  unsigned long long ns = wb.ns;
+  void* args[] = {&n,   (void*)&LU, &ld,    &fmt,    (void*)&dinv, (void*)&v, &ldv, &z,
+                  &ldz, &pub,       &epoch, &status, &polls,       &ns};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(256), args, smem, st);
 }
 
@@ -1105,9 +1114,9 @@ struct Solver {
       if ((e = read_brief()) != cudaSuccess) return e;
       if (!any(&Brief::outer_active)) break;
       for (int j = 0; j < m && any(&Brief::cycle_active); ++j) {
-        // w = M^{-1} (A v_j); with the fp32 preconditioner the product is fp32 too
+        // w = M^{-1} (A v_j); the product in fp32 or fp64 as matvec_fp32 says
         if ((e = residual(n, K, A, lda, w.V + (int64_t)j * n, ldv_rhs(), nullptr, 0, w.tmp, n,
-                          prm.precond_fp32 ? 3 : 0, 0, w, st)) != cudaSuccess)
+                          prm.matvec_fp32 ? 3 : 0, 0, w, st)) != cudaSuccess)
           return e;
         if ((e = precond(w.tmp, n, w.w, n)) != cudaSuccess) return e;
         for (int i = 0; i <= j + 1; ++i)
@@ -1170,9 +1179,9 @@ hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, i
   s.B = b; s.ldb = ldb; s.X = x; s.ldx = ldx;
   s.prm = prm;
   s.w = carve_solve(ws, n, nrhs, prm.restart);
-  // room for the fp32 copy of A after the workspace proper: the fp32 operator's
+  // room for the fp32 copy of A after the workspace proper: the fp32 Arnoldi
   // products then read 4 instead of 8 bytes per entry
-  if (prm.precond_fp32 && ws_bytes >= s.w.bytes + solve_a32_bytes(n)) {
+  if (prm.matvec_fp32 && ws_bytes >= s.w.bytes + solve_a32_bytes(n)) {
     s.w.a32 = (float*)((char*)ws + s.w.bytes);
     s.w.ld32 = a32_ld(n);
   }

@@ -4,7 +4,7 @@ rounding (generator, cast, and the whole factorization on the SIMT reference
 engine); tolerance-based where tensor-core summation order differs (the
 default tcgen05 factorization, the refinement).
 
-Tolerances (derived in DESIGN.md):
+Tolerances:
   factors, tcgen05 engine:  ||LU_gpu - LU_orc||_F / ||LU_orc||_F <= 8 n u_low
                             (asserted tighter too: <= u_low)
   solution:                 scaled residual < 16, ||x_gpu - x_orc||_inf / ||x_orc||_inf <= 1e-10,
@@ -358,17 +358,18 @@ def test_solve_against_oracle(n, nb, prec, k):
 
 
 @pytest.mark.parametrize("n,nb,k", [(300, 128, 1), (1024, 128, 2), (2049, 512, 1), (4096, 512, 3)])
-def test_solve_fp32_operator_against_oracle(n, nb, k):
-    # inner GMRES operator (preconditioner and Arnoldi product) in fp32, same
-    # parameters on both sides
+@pytest.mark.parametrize("pp,mp", [(1, 1), (1, 0), (0, 1)])
+def test_solve_fp32_operator_against_oracle(n, nb, k, pp, mp):
+    # inner GMRES preconditioner (pp) and / or Arnoldi product (mp) in fp32,
+    # same parameters on both sides
     A, b = api.generate(n, seed=n + 3, nrhs=k, device=DEV)
     LU = api.factor(A, capi.BF16, nb)
-    x, info, st = api.solve_ir(A, LU, b, capi.BF16, api.ir_params(precond_fp32=1, inner_tol=1e-5))
+    x, info, st = api.solve_ir(A, LU, b, capi.BF16, api.ir_params(precond_fp32=pp, matvec_fp32=mp, inner_tol=1e-5))
     torch.cuda.synchronize()
     sr = api.residual(A, x, b)
     A_o, b_o = oracle.generate(n, n + 3, nrhs=k)
     LU_o, _ = oracle.factor(A_o, oracle.BF16, nb)
-    X_o, info_o, rc = oracle.solve_ir(A_o, LU_o, b_o, precond_prec=1, inner_tol=1e-5)
+    X_o, info_o, rc = oracle.solve_ir(A_o, LU_o, b_o, precond_prec=pp, matvec_prec=mp, inner_tol=1e-5)
     xg = to_np(x)
     assert st == capi.OK and rc == 0
     for c in range(k):
@@ -442,7 +443,7 @@ def test_fp32_copy_of_A_changes_no_bit(n, k):
     instead of A; the solution and the iteration counts are identical."""
     A, b = api.generate(n, seed=n + 1, nrhs=k, device=DEV)
     LU = api.factor(A, capi.BF16, 128)
-    p = api.ir_params(precond_fp32=1, inner_tol=1e-5)
+    p = api.ir_params(precond_fp32=1, matvec_fp32=1, inner_tol=1e-5)
     base = capi.hpmxp_solve_workspace(n, k, p.restart)
     outs = []
     for extra in (0, capi.hpmxp_solve_workspace_a32(n)):

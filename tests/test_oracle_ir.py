@@ -96,10 +96,11 @@ def test_exact_factors_need_no_refinement():
     assert rc == 0 and info[0]["outer"] == 0 and info[0]["iters"] == 0
 
 
-def test_fp32_preconditioner_option_converges():
+@pytest.mark.parametrize("pp,mp", [(1, 1), (1, 0), (0, 1)])
+def test_fp32_inner_operator_options_converge(pp, mp):
     A, b = oracle.generate(700, 3)
     LU, _ = oracle.factor(A, oracle.BF16, 256)
-    X, info, rc = oracle.solve_ir(A, LU, b, precond_prec=1)
+    X, info, rc = oracle.solve_ir(A, LU, b, precond_prec=pp, matvec_prec=mp)
     assert rc == 0 and oracle.scaled_residual(A, X, b)[0] < ACCEPT
 
 
