@@ -108,8 +108,9 @@ def test_solve_reports_timeout_then_recovers():
     s.factor(A)
     assert s.factor_status == capi.OK
     with short_budget():
-        _, _, st = s.solve(A, b)
-    assert st == capi.ETIMEOUT
+        with pytest.raises(capi.HpmxpError) as e:
+            s.solve(A, b)
+        assert e.value.status == capi.ETIMEOUT
     x, info, st = s.solve(A, b)
     torch.cuda.synchronize()
     assert st == capi.OK and api.residual(A, x, b)[0] < 16.0
