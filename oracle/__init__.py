@@ -81,6 +81,10 @@ def lib():
             L.oracle_generate_rows.restype = i32
             L.oracle_factor.argtypes = [i64, P, i64, i32, i32, i32, P, i64]
             L.oracle_factor.restype = i32
+            L.oracle_factor_scheme.argtypes = [i64, P, i64, i32, i32, i32, P, i64, i32]
+            L.oracle_factor_scheme.restype = i32
+            L.oracle_matvec_f32.argtypes = [i64, P, i64, P, P]
+            L.oracle_matvec_f32.restype = None
             L.oracle_precond.argtypes = [i64, P, i64, P, P, i32]; L.oracle_precond.restype = None
             L.oracle_residual_vec.argtypes = [i64, P, i64, P, P, P]
             L.oracle_residual_vec.restype = None
@@ -160,6 +164,27 @@ def factor(A, fmt: int = BF16, nb: int = 128, fmt_update: int | None = None) -> 
     if rc < 0:
         raise ValueError("oracle_factor: bad arguments")
     return LU, rc
+
+
+def factor_plain(A, fmt: int = BF16, nb: int = 128) -> tuple[np.ndarray, int]:
+    """The plain reading of Fig. 1: unblocked fp32 diagonal block of width nb,
+    fp32 forward / back substitution for the panels, no inverses."""
+    A = _f64(A)
+    n = A.shape[0]
+    LU = np.empty((n, n), dtype=np.float64, order="F")
+    rc = lib().oracle_factor_scheme(n, _p(A), n, fmt, fmt, nb, _p(LU), n, 1)
+    if rc < 0:
+        raise ValueError("oracle_factor_scheme: bad arguments")
+    return LU, rc
+
+
+def matvec_f32(A, v) -> np.ndarray:
+    """The inner GMRES's fp32 Arnoldi product A v (A truncated toward zero to fp32)."""
+    A = _f64(A)
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    w = np.empty_like(v)
+    lib().oracle_matvec_f32(A.shape[0], _p(A), A.shape[0], _p(v), _p(w))
+    return w
 
 
 def precond(LU, v, prec: int = 0) -> np.ndarray:

@@ -362,6 +362,72 @@ struct LowPrecLU {
       }
   }
 
+  // ------------------------------------------------------------------------
+  // Plain reading of Fig. 1 (no inverses): the nb x nb diagonal block is
+  // factored unblocked in fp32 as one block, and the panels are formed by
+  // fp32 forward / back substitution with the stored low-precision L11 / U11,
+  // each panel entry rounded to storage once.  Used to measure how far the
+  // method's inverse-based panels sit from the textbook substitution.
+  // ------------------------------------------------------------------------
+  bool getrf_plain(int64_t k, int64_t b) {
+    std::vector<T> a((size_t)b * b);
+    for (int64_t j = 0; j < b; ++j)
+      for (int64_t i = 0; i < b; ++i) a[i + j * b] = (T)at(k + i, k + j);
+    bool ok = true;
+    for (int64_t p = 0; p < b; ++p) {
+      const T piv = a[p + p * b];
+      if (!(std::isfinite((double)piv)) || piv == T(0)) ok = false;
+      for (int64_t i = p + 1; i < b; ++i) a[i + p * b] = a[i + p * b] / piv;
+      for (int64_t j = p + 1; j < b; ++j)
+        for (int64_t i = p + 1; i < b; ++i)
+          a[i + j * b] = fma_t<T>(-a[i + p * b], a[p + j * b], a[i + j * b]);
+    }
+    for (int64_t j = 0; j < b; ++j)
+      for (int64_t i = 0; i < b; ++i) at(k + i, k + j) = st((double)a[i + j * b]);
+    return ok;
+  }
+
+  // U12 = L11^{-1} A12, column by column: u_r = a_r - sum_{t<r} l_rt u_t in T,
+  // t ascending, then every u_r rounded to storage.
+  void trsm_row_plain(int64_t k, int64_t b, int64_t c0, int64_t c1) {
+    std::vector<T> u((size_t)b);
+    for (int64_t j = c0; j < c1; ++j) {
+      for (int64_t r = 0; r < b; ++r) {
+        T acc = (T)at(k + r, j);
+        for (int64_t t = 0; t < r; ++t) acc = fma_t<T>(-(T)at(k + r, k + t), u[t], acc);
+        u[r] = acc;
+      }
+      for (int64_t r = 0; r < b; ++r) at(k + r, j) = st((double)u[r]);
+    }
+  }
+
+  // L21 = A21 U11^{-1}, row by row: l_c = (a_c - sum_{t<c} l_t u_tc) / u_cc in
+  // T, t ascending, then every l_c rounded to storage.
+  void trsm_col_plain(int64_t k, int64_t b, int64_t r0, int64_t r1) {
+    std::vector<T> l((size_t)b);
+    for (int64_t i = r0; i < r1; ++i) {
+      for (int64_t c = 0; c < b; ++c) {
+        T acc = (T)at(i, k + c);
+        for (int64_t t = 0; t < c; ++t) acc = fma_t<T>(-l[t], (T)at(k + t, k + c), acc);
+        l[c] = acc / (T)at(k + c, k + c);
+      }
+      for (int64_t c = 0; c < b; ++c) at(i, k + c) = st((double)l[c]);
+    }
+  }
+
+  bool lu_plain(int NB) {
+    bool ok = true;
+    for (int64_t k = 0; k < n; k += NB) {
+      const int64_t b = std::min<int64_t>(NB, n - k);
+      ok = getrf_plain(k, b) && ok;
+      if (k + b >= n) break;
+      trsm_row_plain(k, b, k + b, n);
+      trsm_col_plain(k, b, k + b, n);
+      schur_update(k, b, n, true);
+    }
+    return ok;
+  }
+
   // Factor the square sub-matrix [k0, k0+size)^2 with update depth NB.
   bool lu_range(int64_t k0, int64_t size, int NB, bool top) {
     bool ok = true;
@@ -560,9 +626,22 @@ int oracle_generate_rows(int64_t n, uint64_t seed, double margin, int mode, cons
 // which also switches the arithmetic to fp64); fmt_update: 2 selects E4M3
 // operands for the Schur update, anything else the storage format.
 // Returns 0, 1 on a zero or non-finite pivot, -1 on bad arguments.
+int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
+                         double* LU, int64_t ldlu, int plain);
+
 int oracle_factor(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
                   double* LU, int64_t ldlu) {
+  return oracle_factor_scheme(n, A, lda, fmt, fmt_update, nb, LU, ldlu, 0);
+}
+
+// The factorization in the method's scheme (plain = 0, above) or in the plain
+// reading of Fig. 1 (plain = 1: unblocked fp32 diagonal block of width nb,
+// fp32 substitution panels, no inverses; no fp8 update; with FP64 storage the
+// arithmetic is fp64, the exact-arithmetic special case).
+int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
+                         double* LU, int64_t ldlu, int plain) {
   if (n < 1 || lda < n || ldlu < n || !(nb == 128 || nb == 256 || nb == 512)) return -1;
+  if (plain && fmt_update == FMT_E4M3) return -1;
   bool ok;
   if (fmt == FMT_FP64) {
     LowPrecLU<double> f;
@@ -572,7 +651,7 @@ int oracle_factor(int64_t n, const double* A, int64_t lda, int fmt, int fmt_upda
       for (int64_t i = 0; i < n; ++i) f.M[i + j * n] = A[i + j * lda];
     f.Linv.resize((size_t)(n + kBase - 1) / kBase);
     f.Uinv.resize(f.Linv.size());
-    ok = f.lu_range(0, n, nb, true);
+    ok = plain ? f.lu_plain(nb) : f.lu_range(0, n, nb, true);
     for (int64_t j = 0; j < n; ++j)
       for (int64_t i = 0; i < n; ++i) LU[i + j * ldlu] = f.M[i + j * n];
   } else {
@@ -583,11 +662,18 @@ int oracle_factor(int64_t n, const double* A, int64_t lda, int fmt, int fmt_upda
       for (int64_t i = 0; i < n; ++i) f.M[i + j * n] = round_fmt(A[i + j * lda], fmt);
     f.Linv.resize((size_t)(n + kBase - 1) / kBase);
     f.Uinv.resize(f.Linv.size());
-    ok = f.lu_range(0, n, nb, true);
+    ok = plain ? f.lu_plain(nb) : f.lu_range(0, n, nb, true);
     for (int64_t j = 0; j < n; ++j)
       for (int64_t i = 0; i < n; ++i) LU[i + j * ldlu] = f.M[i + j * n];
   }
   return ok ? 0 : 1;
+}
+
+// The fp32 Arnoldi product of the inner GMRES alone: w = A v with A truncated
+// toward zero to fp32, v rounded to fp32, fp32 fused multiply-adds, j
+// ascending (matvec_f32 above).
+void oracle_matvec_f32(int64_t n, const double* A, int64_t lda, const double* v, double* w) {
+  matvec_f32(n, A, lda, v, w);
 }
 
 // Apply the preconditioner z = U^{-1} L^{-1} v (prec 0: fp64, 1: fp32).
