@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--no-fp64-comparator", action="store_true",
                     help="skip the fp64 LU solve with partial pivoting (torch/cuSOLVER) of the same A")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the all-fp64 and all-fp32 inner-operator variants (timed over --steps each)")
+                    help="skip the variants: all-fp64 and all-fp32 inner operator, balanced (timed over --steps each)")
+    ap.add_argument("--balance", type=int, default=0,
+                    help="1: balance and scale A (hpmxp_balance) inside every timed solve")
     ap.add_argument("--serving-requests", type=int, default=600,
                     help="requests of the serving sub-record at 1000/s (a third of them at 100/s); 0: skip")
     ap.add_argument("--no-e2e", action="store_true")
@@ -456,7 +458,7 @@ def main():
                 "what": "torch.linalg.lu_factor + lu_solve (cuSOLVER, fp64, partial pivoting) on the same A, one run"}
         del Af, bf, LUf, piv, xf, xs
         torch.cuda.empty_cache()
-    solver = api.Solver(n, 1, prec, nb, device=dev, params=params)
+    solver = api.Solver(n, 1, prec, nb, device=dev, params=params, balance=bool(args.balance))
     if not args.no_variants:
         # room for the fp32 copy of A that the all-fp32 variant's Arnoldi products read
         solver.sws = api.workspace(capi.hpmxp_solve_workspace(n, 1, params.restart) + capi.hpmxp_solve_workspace_a32(n),
@@ -491,7 +493,7 @@ def main():
     capi.hpmxp_prof_enable(False)
     kinds = {"gemm_update": capi.PROF_GEMM, "gemm_panel": capi.PROF_GEMM_STORE, "gemv": capi.PROF_GEMV,
              "gemv32": capi.PROF_GEMV32, "precond": capi.PROF_PRECOND, "getrf": capi.PROF_GETRF,
-             "cast": capi.PROF_CAST, "panel_ops": capi.PROF_PANEL}
+             "cast": capi.PROF_CAST, "panel_ops": capi.PROF_PANEL, "balance": capi.PROF_BALANCE}
     prof = {k: capi.hpmxp_prof_read(v) for k, v in kinds.items()}
     # every launch of the tensor-core GEMM kernel (Schur updates and panel products)
     g = {f: prof["gemm_update"][f] + prof["gemm_panel"][f] for f in ("ms", "work", "launches")}
@@ -524,11 +526,15 @@ def main():
     # the same solve with other inner-operator precisions, over the same number of steps
     variants = {}
     if not args.no_variants:
-        keep = solver.params
-        for name, (pp, mp) in (("fp64_inner_operator", (0, 0)), ("fp32_inner_operator", (1, 1))):
-            if (pp, mp) == (keep.precond_fp32, keep.matvec_fp32):
+        keep, keep_bal = solver.params, solver.balance
+        x_head = solver.x.view().clone()
+        legs = [("fp64_inner_operator", (0, 0), keep_bal), ("fp32_inner_operator", (1, 1), keep_bal),
+                ("balanced" if not keep_bal else "unbalanced", (keep.precond_fp32, keep.matvec_fp32), not keep_bal)]
+        for name, (pp, mp), bal in legs:
+            if (pp, mp) == (keep.precond_fp32, keep.matvec_fp32) and bal == keep_bal:
                 continue
             solver.params = ir_params_for(args, pp, mp)
+            solver.balance = bal
             solver(A, b)
             t_v, res = time_solves(solver, A, b, args.steps, stream, dev)
             sr_v = float(api.residual(A, solver.x, b)[0])
@@ -537,8 +543,12 @@ def main():
                               "valid": bool(all(st == capi.OK for st, _ in res) and sr_v < 16.0),
                               "ir_iters": res[-1][1]["iters"], "ir_outer": res[-1][1]["outer"],
                               "what": operator_label(solver.params) +
-                                      f", inner tolerance {solver.params.inner_tol:g}"}
-        solver.params = keep
+                                      f", inner tolerance {solver.params.inner_tol:g}" +
+                                      (", balancing and scaling (hpmxp_balance) inside the timed step" if bal
+                                       else ", no balancing")}
+            if name in ("balanced", "unbalanced"):
+                variants[name]["x_bitwise_equal_to_headline"] = bool(torch.equal(solver.x.view(), x_head))
+        solver.params, solver.balance = keep, keep_bal
 
     # timed region 2: end to end through the public API with host buffers
     e2e = None
@@ -590,7 +600,7 @@ def main():
                            "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (A is %.1f GB)" % (8 * n * n / 1e9),
                            "precond_fp32": int(params.precond_fp32), "matvec_fp32": int(params.matvec_fp32),
-                           "inner_tol": params.inner_tol},
+                           "inner_tol": params.inner_tol, "balance": int(args.balance)},
                 "valid": bool(ok and sr < 16.0), "scaled_residual": sr,
                 "ir_iters": infos[-1][1]["iters"], "ir_outer": infos[-1][1]["outer"],
                 "ir_status": int(infos[-1][0]), "diag": args.diag, "margin": args.margin,

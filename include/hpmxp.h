@@ -137,6 +137,41 @@ hpmxp_status hpmxp_factor(int64_t n, const double* A, int64_t lda, int prec, int
                           int64_t ldlu, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Balancing and scaling (section "Algorithmic Framework": implementations may
+ * balance the input matrix with Theta(n^2) work, as the HPL harness does, and
+ * scale it so that its values fit the low-precision format; both are part of
+ * the timed solve and are undone at the end).
+ *
+ * hpmxp_balance computes power-of-two row and column scales of A:
+ *   rs_i = 2^-floor(log2 max_j |a_ij|),  cs_j = 2^-floor(log2 max_i |rs_i a_ij|),
+ * so that the largest magnitude of every row and column of diag(rs) A diag(cs)
+ * lies in [1, 2); then rs is multiplied by the format's scale, 2^12 for FP16
+ * (values up to 2^13 leave room below 65504 for the growth of the Schur
+ * complements and keep the small entries out of FP16's subnormal range), 1 for
+ * BF16 and FP8 (fp32's exponent range).  A zero or non-finite row or column
+ * gets scale 1.  Two passes over A (16 n^2 bytes); the result does not depend
+ * on the order of the reductions.
+ *   A        in, n x n fp64, lda >= n
+ *   prec     hpmxp_prec the factors will have
+ *   rs, cs   out, n fp64 each (device, distinct, 8-byte aligned)
+ *
+ * hpmxp_factor_scaled factors diag(rs) A diag(cs) (hpmxp_factor with the
+ * scales applied exactly, before the one rounding to the factor format);
+ * hpmxp_solve_ir_scaled refines x for the ORIGINAL A and b with those factors,
+ * using M^{-1} = diag(cs) U^{-1} L^{-1} diag(rs): the balancing is undone in
+ * every preconditioner application, and x, the residuals and the scaled
+ * residual are those of the input system.  rs and cs must both be given or
+ * both be NULL (no balancing: the plain calls).  Because the scales are powers
+ * of two, a BF16 factorization of a system whose values stay inside the
+ * fp32 normal range gives factors that are exact rescalings of the unbalanced
+ * ones, and the same x bit for bit. */
+hpmxp_status hpmxp_balance(int64_t n, const double* A, int64_t lda, int prec, double* rs, double* cs,
+                           void* stream);
+hpmxp_status hpmxp_factor_scaled(int64_t n, const double* A, int64_t lda, int prec, int nb, const double* rs,
+                                 const double* cs, void* LU, int64_t ldlu, void* ws, size_t ws_bytes,
+                                 void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* GMRES-based iterative refinement (section "Algorithmic Framework").
  *
  * x0 = U^{-1} L^{-1} b from the low-precision factors, then repeatedly
@@ -197,6 +232,11 @@ hpmxp_status hpmxp_solve_ir(int64_t n, const double* A, int64_t lda, const void*
                             int prec, const double* b, int64_t ldb, double* x, int64_t ldx,
                             int64_t nrhs, const hpmxp_ir_params* prm, hpmxp_ir_info* info,
                             void* ws, size_t ws_bytes, void* stream);
+/* hpmxp_solve_ir with the factors of diag(rs) A diag(cs) (see hpmxp_balance). */
+hpmxp_status hpmxp_solve_ir_scaled(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu,
+                                   int prec, const double* rs, const double* cs, const double* b, int64_t ldb,
+                                   double* x, int64_t ldx, int64_t nrhs, const hpmxp_ir_params* prm,
+                                   hpmxp_ir_info* info, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Backward-error check (section "Algorithmic Framework"): for every column c,
@@ -223,6 +263,7 @@ hpmxp_status hpmxp_residual(int64_t n, const double* A, int64_t lda, const doubl
  *   kind 5  fp64 -> 16-bit cast     work = 10 n^2 bytes per launch
  *   kind 6  panel operand kernels (column-panel pack, substitution operands)
  *   kind 7  tensor-core GEMM, panel products (C = sign A B^T)  work = 2 M N K flops
+ *   kind 8  balancing (hpmxp_balance)  work = 16 n^2 bytes of A per call
  * hpmxp_prof_read synchronizes the recorded events and returns the summed
  * event time, work and launch count of one kind since the last reset.
  * Returns HPMXP_EINVAL for a bad kind or NULL output.

@@ -81,7 +81,11 @@ def lib():
             L.oracle_generate_rows.restype = i32
             L.oracle_factor.argtypes = [i64, P, i64, i32, i32, i32, P, i64]
             L.oracle_factor.restype = i32
-            L.oracle_factor_scheme.argtypes = [i64, P, i64, i32, i32, i32, P, i64, i32]
+            L.oracle_factor_scheme.argtypes = [i64, P, i64, i32, i32, i32, P, i64, i32, P, P]
+            L.oracle_balance.argtypes = [i64, P, i64, i32, P, P]
+            L.oracle_balance.restype = None
+            L.oracle_precond_scaled.argtypes = [i64, P, i64, P, P, i32, P, P]
+            L.oracle_precond_scaled.restype = None
             L.oracle_factor_scheme.restype = i32
             L.oracle_matvec_f32.argtypes = [i64, P, i64, P, P]
             L.oracle_matvec_f32.restype = None
@@ -91,7 +95,7 @@ def lib():
             L.oracle_scaled_residual.argtypes = [i64, P, i64, P, i64, P, i64, i64, P]
             L.oracle_scaled_residual.restype = None
             L.oracle_solve_ir.argtypes = [i64, P, i64, P, i64, P, i64, P, i64, i64, i32, i32, d, d,
-                                          d, i32, i32, ctypes.POINTER(IRInfo)]
+                                          d, i32, i32, P, P, ctypes.POINTER(IRInfo)]
             L.oracle_solve_ir.restype = i32
             L.oracle_num_threads.argtypes = []; L.oracle_num_threads.restype = i32
             L.oracle_set_num_threads.argtypes = [i32]; L.oracle_set_num_threads.restype = i32
@@ -154,13 +158,36 @@ def generate_rows(n: int, seed: int, rows, margin: float = 1.0, mode: int = DOMI
     return out
 
 
-def factor(A, fmt: int = BF16, nb: int = 128, fmt_update: int | None = None) -> tuple[np.ndarray, int]:
-    """Packed LU factors (widened to fp64) and 0 / 1 (zero or non-finite pivot)."""
+def _scales(rs, cs):
+    if (rs is None) != (cs is None):
+        raise ValueError("give both balancing scales or neither")
+    if rs is None:
+        return None, None, None
+    rs = np.ascontiguousarray(np.asarray(rs, dtype=np.float64))
+    cs = np.ascontiguousarray(np.asarray(cs, dtype=np.float64))
+    return rs, cs, (_p(rs), _p(cs))
+
+
+def balance(A, fmt: int = BF16) -> tuple[np.ndarray, np.ndarray]:
+    """Power-of-two row / column balancing scales (rs, cs) of A for the format."""
+    A = _f64(A)
+    n = A.shape[0]
+    rs = np.empty(n, dtype=np.float64)
+    cs = np.empty(n, dtype=np.float64)
+    lib().oracle_balance(n, _p(A), n, fmt, _p(rs), _p(cs))
+    return rs, cs
+
+
+def factor(A, fmt: int = BF16, nb: int = 128, fmt_update: int | None = None, rs=None,
+           cs=None) -> tuple[np.ndarray, int]:
+    """Packed LU factors (widened to fp64) and 0 / 1 (zero or non-finite pivot);
+    with balancing scales, of diag(rs) A diag(cs)."""
     A = _f64(A)
     n = A.shape[0]
     LU = np.empty((n, n), dtype=np.float64, order="F")
-    rc = lib().oracle_factor(n, _p(A), n, fmt, fmt if fmt_update is None else fmt_update, nb,
-                             _p(LU), n)
+    rs, cs, ptrs = _scales(rs, cs)
+    rc = lib().oracle_factor_scheme(n, _p(A), n, fmt, fmt if fmt_update is None else fmt_update, nb,
+                                    _p(LU), n, 0, *(ptrs or (None, None)))
     if rc < 0:
         raise ValueError("oracle_factor: bad arguments")
     return LU, rc
@@ -172,7 +199,7 @@ def factor_plain(A, fmt: int = BF16, nb: int = 128) -> tuple[np.ndarray, int]:
     A = _f64(A)
     n = A.shape[0]
     LU = np.empty((n, n), dtype=np.float64, order="F")
-    rc = lib().oracle_factor_scheme(n, _p(A), n, fmt, fmt, nb, _p(LU), n, 1)
+    rc = lib().oracle_factor_scheme(n, _p(A), n, fmt, fmt, nb, _p(LU), n, 1, None, None)
     if rc < 0:
         raise ValueError("oracle_factor_scheme: bad arguments")
     return LU, rc
@@ -187,11 +214,12 @@ def matvec_f32(A, v) -> np.ndarray:
     return w
 
 
-def precond(LU, v, prec: int = 0) -> np.ndarray:
+def precond(LU, v, prec: int = 0, rs=None, cs=None) -> np.ndarray:
     LU = _f64(LU)
     v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
     z = np.empty_like(v)
-    lib().oracle_precond(LU.shape[0], _p(LU), LU.shape[0], _p(v), _p(z), prec)
+    rs, cs, ptrs = _scales(rs, cs)
+    lib().oracle_precond_scaled(LU.shape[0], _p(LU), LU.shape[0], _p(v), _p(z), prec, *(ptrs or (None, None)))
     return z
 
 
@@ -215,10 +243,12 @@ def scaled_residual(A, X, B) -> np.ndarray:
 
 
 def solve_ir(A, LU, B, restart: int = 30, max_iters: int = 50, inner_tol: float = 1e-12,
-             theta: float = 0.1, accept: float = 16.0, precond_prec: int = 0, matvec_prec: int = 0):
+             theta: float = 0.1, accept: float = 16.0, precond_prec: int = 0, matvec_prec: int = 0,
+             rs=None, cs=None):
     """GMRES-IR.  Returns (X, [info dict per rhs], worst status).
     precond_prec / matvec_prec: 1 = the inner GMRES's preconditioner / Arnoldi
-    product in fp32, 0 = fp64."""
+    product in fp32, 0 = fp64.  rs, cs: the balancing scales the factors LU
+    were computed with (both or neither)."""
     A = _f64(A)
     LU = _f64(LU)
     n = A.shape[0]
@@ -227,7 +257,8 @@ def solve_ir(A, LU, B, restart: int = 30, max_iters: int = 50, inner_tol: float 
     X = np.zeros((n, k), dtype=np.float64, order="F")
     info = (IRInfo * k)()
     rc = lib().oracle_solve_ir(n, _p(A), n, _p(LU), n, _p(B), n, _p(X), n, k, restart, max_iters,
-                               inner_tol, theta, accept, precond_prec, matvec_prec, info)
+                               inner_tol, theta, accept, precond_prec, matvec_prec,
+                               *(_scales(rs, cs)[2] or (None, None)), info)
     if rc < 0:
         raise ValueError("oracle_solve_ir: bad arguments")
     infos = [dict(iters=i.iters, outer=i.outer, scaled_resid=i.scaled_resid, status=i.status)

@@ -446,6 +446,38 @@ struct LowPrecLU {
 };
 
 // ---------------------------------------------------------------------------
+// Balancing and scaling (section "Algorithmic Framework": a Theta(n^2)
+// balancing borrowed from the HPL harness and a scaling into the range of the
+// low-precision format, both timed and undone at the end).  Reading: row then
+// column equilibration by powers of two, rs_i = 2^-floor(log2 max_j |a_ij|),
+// cs_j = 2^-floor(log2 max_i |rs_i a_ij|) (a zero or non-finite maximum gives
+// 1), then rs times the format's scale (2^12 for FP16, 1 otherwise).  The
+// factorization then works on diag(rs) A diag(cs), and the preconditioner is
+// M^{-1} = diag(cs) U^{-1} L^{-1} diag(rs), which undoes the balancing.
+// ---------------------------------------------------------------------------
+double inverse_power_of_two(double m) {
+  if (!(m > 0.0) || !std::isfinite(m)) return 1.0;
+  int e;
+  std::frexp(m, &e);   // m = f 2^e, f in [0.5, 1)
+  return std::ldexp(1.0, 1 - e);
+}
+
+void balance(int64_t n, const double* A, int64_t lda, int fmt, double* rs, double* cs) {
+  for (int64_t i = 0; i < n; ++i) {
+    double m = 0.0;
+    for (int64_t j = 0; j < n; ++j) m = std::max(m, std::fabs(A[i + j * lda]));
+    rs[i] = inverse_power_of_two(m);
+  }
+  for (int64_t j = 0; j < n; ++j) {
+    double m = 0.0;
+    for (int64_t i = 0; i < n; ++i) m = std::max(m, std::fabs(A[i + j * lda] * rs[i]));
+    cs[j] = inverse_power_of_two(m);
+  }
+  const double s = fmt == FMT_FP16 ? 4096.0 : 1.0;
+  for (int64_t i = 0; i < n; ++i) rs[i] *= s;
+}
+
+// ---------------------------------------------------------------------------
 // fp64 refinement helpers (section "Algorithmic Framework": GMRES with the
 // low-precision factors as a left preconditioner, fp64 working precision).
 // ---------------------------------------------------------------------------
@@ -627,19 +659,21 @@ int oracle_generate_rows(int64_t n, uint64_t seed, double margin, int mode, cons
 // operands for the Schur update, anything else the storage format.
 // Returns 0, 1 on a zero or non-finite pivot, -1 on bad arguments.
 int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
-                         double* LU, int64_t ldlu, int plain);
+                         double* LU, int64_t ldlu, int plain, const double* rs, const double* cs);
 
 int oracle_factor(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
                   double* LU, int64_t ldlu) {
-  return oracle_factor_scheme(n, A, lda, fmt, fmt_update, nb, LU, ldlu, 0);
+  return oracle_factor_scheme(n, A, lda, fmt, fmt_update, nb, LU, ldlu, 0, nullptr, nullptr);
 }
 
 // The factorization in the method's scheme (plain = 0, above) or in the plain
 // reading of Fig. 1 (plain = 1: unblocked fp32 diagonal block of width nb,
 // fp32 substitution panels, no inverses; no fp8 update; with FP64 storage the
 // arithmetic is fp64, the exact-arithmetic special case).
+// rs, cs (both or neither): factor diag(rs) A diag(cs) instead of A (the
+// powers of two are applied in fp64, exactly, before the one rounding).
 int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
-                         double* LU, int64_t ldlu, int plain) {
+                         double* LU, int64_t ldlu, int plain, const double* rs, const double* cs) {
   if (n < 1 || lda < n || ldlu < n || !(nb == 128 || nb == 256 || nb == 512)) return -1;
   if (plain && fmt_update == FMT_E4M3) return -1;
   bool ok;
@@ -648,7 +682,7 @@ int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int f
     f.n = n; f.fmt = fmt; f.fmt_update = FMT_FP64;
     f.M.resize((size_t)n * n);
     for (int64_t j = 0; j < n; ++j)
-      for (int64_t i = 0; i < n; ++i) f.M[i + j * n] = A[i + j * lda];
+      for (int64_t i = 0; i < n; ++i) f.M[i + j * n] = rs ? A[i + j * lda] * rs[i] * cs[j] : A[i + j * lda];
     f.Linv.resize((size_t)(n + kBase - 1) / kBase);
     f.Uinv.resize(f.Linv.size());
     ok = plain ? f.lu_plain(nb) : f.lu_range(0, n, nb, true);
@@ -659,7 +693,8 @@ int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int f
     f.n = n; f.fmt = fmt; f.fmt_update = fmt_update == FMT_E4M3 ? FMT_E4M3 : fmt;
     f.M.resize((size_t)n * n);
     for (int64_t j = 0; j < n; ++j)
-      for (int64_t i = 0; i < n; ++i) f.M[i + j * n] = round_fmt(A[i + j * lda], fmt);
+      for (int64_t i = 0; i < n; ++i)
+        f.M[i + j * n] = round_fmt(rs ? A[i + j * lda] * rs[i] * cs[j] : A[i + j * lda], fmt);
     f.Linv.resize((size_t)(n + kBase - 1) / kBase);
     f.Uinv.resize(f.Linv.size());
     ok = plain ? f.lu_plain(nb) : f.lu_range(0, n, nb, true);
@@ -680,6 +715,22 @@ void oracle_matvec_f32(int64_t n, const double* A, int64_t lda, const double* v,
 void oracle_precond(int64_t n, const double* LU, int64_t ld, const double* v, double* z, int prec) {
   if (prec == 1) precond_apply<float>(n, LU, ld, v, z);
   else precond_apply<double>(n, LU, ld, v, z);
+}
+
+// With the factors of diag(rs) A diag(cs): z = diag(cs) U^{-1} L^{-1} diag(rs) v
+// (rs, cs NULL: no balancing).
+void oracle_precond_scaled(int64_t n, const double* LU, int64_t ld, const double* v, double* z, int prec,
+                           const double* rs, const double* cs) {
+  if (!rs) { oracle_precond(n, LU, ld, v, z, prec); return; }
+  std::vector<double> w((size_t)n);
+  for (int64_t i = 0; i < n; ++i) w[i] = v[i] * rs[i];
+  oracle_precond(n, LU, ld, w.data(), z, prec);
+  for (int64_t i = 0; i < n; ++i) z[i] *= cs[i];
+}
+
+// Balancing scales of A for the format fmt (see balance above).
+void oracle_balance(int64_t n, const double* A, int64_t lda, int fmt, double* rs, double* cs) {
+  balance(n, A, lda, fmt, rs, cs);
 }
 
 void oracle_residual_vec(int64_t n, const double* A, int64_t lda, const double* x,
@@ -721,11 +772,13 @@ struct oracle_ir_info {
 // GMRES is applied in fp32, with mprec 1 its matrix-vector product A v_j, while
 // the outer residual, orthogonalization, rotations and update stay fp64.
 // Reading: "iterations" in the 50 cap are inner Arnoldi steps summed over
-// restarts.
+// restarts.  With bal_r, bal_c (the balancing scales rs, cs of the factors,
+// both or neither) the preconditioner is diag(cs) U^{-1} L^{-1} diag(rs) and everything else is in
+// the space of the input system.
 int oracle_solve_ir(int64_t n, const double* A, int64_t lda, const double* LU, int64_t ldlu,
                     const double* B, int64_t ldb, double* X, int64_t ldx, int64_t nrhs, int restart,
                     int max_iters, double inner_tol, double theta, double accept, int pprec,
-                    int mprec, oracle_ir_info* info) {
+                    int mprec, const double* bal_r, const double* bal_c, oracle_ir_info* info) {
   if (n < 1 || restart < 1 || max_iters < 0) return -1;
   const double an = norm_inf_mat(n, A, lda);
   const int m = restart;
@@ -736,7 +789,7 @@ int oracle_solve_ir(int64_t n, const double* A, int64_t lda, const double* LU, i
     const double* b = B + c * ldb;
     double* x = X + c * ldx;
     const double bn = norm_inf_vec(n, b);
-    oracle_precond(n, LU, ldlu, b, x, pprec);
+    oracle_precond_scaled(n, LU, ldlu, b, x, pprec, bal_r, bal_c);
     int iters = 0, outer = 0, status = 0;
     double sr = 0.0;
     for (;;) {
@@ -746,7 +799,7 @@ int oracle_solve_ir(int64_t n, const double* A, int64_t lda, const double* LU, i
       if (sr < accept) { status = 0; break; }
       if (iters >= max_iters) { status = 4; break; }
       ++outer;
-      oracle_precond(n, LU, ldlu, r.data(), z.data(), pprec);
+      oracle_precond_scaled(n, LU, ldlu, r.data(), z.data(), pprec, bal_r, bal_c);
       const double beta = std::sqrt(dot(n, z.data(), z.data()));
       if (!std::isfinite(beta) || beta == 0.0) { status = 5; break; }
       for (int64_t i = 0; i < n; ++i) V[i] = z[i] / beta;
@@ -765,7 +818,7 @@ int oracle_solve_ir(int64_t n, const double* A, int64_t lda, const double* LU, i
           residual_vec(n, A, lda, &V[(size_t)j * n], zero.data(), Av.data());
           for (int64_t i = 0; i < n; ++i) Av[i] = -Av[i];
         }
-        oracle_precond(n, LU, ldlu, Av.data(), w.data(), pprec);
+        oracle_precond_scaled(n, LU, ldlu, Av.data(), w.data(), pprec, bal_r, bal_c);
         for (int i = 0; i <= j; ++i) {            // modified Gram-Schmidt
           const double h = dot(n, w.data(), &V[(size_t)i * n]);
           H[i + j * (m + 1)] = h;

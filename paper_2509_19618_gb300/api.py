@@ -82,17 +82,36 @@ def factor_storage_dtype(prec: int):
     return torch.float16 if prec == capi.FP16 else torch.bfloat16
 
 
+def balance(A: ColMajor, prec: int = capi.BF16, scales: tuple | None = None, stream=None):
+    """Power-of-two balancing scales (rs, cs) of A for the factor format, as two
+    fp64 device tensors of n entries (hpmxp_balance)."""
+    n = A.rows
+    rs, cs = scales if scales is not None else (torch.empty(n, dtype=torch.float64, device=A.storage.device),
+                                                torch.empty(n, dtype=torch.float64, device=A.storage.device))
+    _check("hpmxp_balance", capi.hpmxp_balance(n, A.ptr, A.ld, prec, rs.data_ptr(), cs.data_ptr(),
+                                               stream_handle(stream)))
+    return rs, cs
+
+
+def _scale_ptrs(scales):
+    if scales is None:
+        return None, None
+    return scales[0].data_ptr(), scales[1].data_ptr()
+
+
 def factor(A: ColMajor, prec: int = capi.BF16, nb: int = 128, LU: ColMajor | None = None, ws=None,
-           stream=None, check: bool = True) -> ColMajor:
-    """Low-precision LU without pivoting of A; returns the packed factors.
+           stream=None, check: bool = True, scales: tuple | None = None) -> ColMajor:
+    """Low-precision LU without pivoting of A (of diag(rs) A diag(cs) with
+    scales = (rs, cs) from `balance`); returns the packed factors.
     With check=False a breakdown status is left in `factor.last_status` instead of raising."""
     n = A.rows
     if LU is None:
         LU = ColMajor.empty(n, n, factor_storage_dtype(prec), A.storage.device)
     if ws is None:
         ws = workspace(capi.hpmxp_factor_workspace(n, prec, nb), A.storage.device)
-    st = capi.hpmxp_factor(n, A.ptr, A.ld, prec, nb, LU.ptr, LU.ld, ws.data_ptr(), ws.numel(),
-                           stream_handle(stream))
+    rs, cs = _scale_ptrs(scales)
+    st = capi.hpmxp_factor_scaled(n, A.ptr, A.ld, prec, nb, rs, cs, LU.ptr, LU.ld, ws.data_ptr(), ws.numel(),
+                                  stream_handle(stream))
     factor.last_status = st
     if check or st not in (capi.OK, capi.EBREAKDOWN):
         _check("hpmxp_factor", st)
@@ -107,8 +126,9 @@ def ir_params(**kw) -> capi.IRParams:
 
 
 def solve_ir(A: ColMajor, LU: ColMajor, b: ColMajor, prec: int = capi.BF16, params: capi.IRParams | None = None,
-             x: ColMajor | None = None, ws=None, stream=None, check: bool = True):
-    """GMRES-IR; returns (x, [info dicts], status)."""
+             x: ColMajor | None = None, ws=None, stream=None, check: bool = True, scales: tuple | None = None):
+    """GMRES-IR (with the factors of the balanced matrix when scales = (rs, cs));
+    returns (x, [info dicts], status)."""
     n, k = A.rows, b.cols
     if x is None:
         x = ColMajor.empty(n, k, torch.float64, A.storage.device)
@@ -116,8 +136,9 @@ def solve_ir(A: ColMajor, LU: ColMajor, b: ColMajor, prec: int = capi.BF16, para
     if ws is None:
         ws = workspace(capi.hpmxp_solve_workspace(n, k, restart), A.storage.device)
     info = (capi.IRInfo * k)()
-    st = capi.hpmxp_solve_ir(n, A.ptr, A.ld, LU.ptr, LU.ld, prec, b.ptr, b.ld, x.ptr, x.ld, k, params, info,
-                             ws.data_ptr(), ws.numel(), stream_handle(stream))
+    rs, cs = _scale_ptrs(scales)
+    st = capi.hpmxp_solve_ir_scaled(n, A.ptr, A.ld, LU.ptr, LU.ld, prec, rs, cs, b.ptr, b.ld, x.ptr, x.ld, k,
+                                    params, info, ws.data_ptr(), ws.numel(), stream_handle(stream))
     infos = [dict(iters=i.iters, outer=i.outer, scaled_resid=i.scaled_resid, status=i.status) for i in info]
     if check and st not in (capi.OK, capi.ENOCONV, capi.EBREAKDOWN):
         _check("hpmxp_solve_ir", st)
@@ -145,8 +166,9 @@ class Solver:
     """Reusable device buffers for repeated solves of one shape (bench, serving)."""
 
     def __init__(self, n: int, nrhs: int = 1, prec: int = capi.BF16, nb: int = 128, device="cuda",
-                 params: capi.IRParams | None = None):
+                 params: capi.IRParams | None = None, balance: bool = False):
         self.n, self.nrhs, self.prec, self.nb = n, nrhs, prec, nb
+        self.balance = balance   # balancing and scaling as part of every solve (hpmxp_balance)
         self.params = params if params is not None else capi.hpmxp_ir_params_default()
         self.device = torch.device(device)
         self.LU = ColMajor.empty(n, n, factor_storage_dtype(prec), self.device)
@@ -155,14 +177,18 @@ class Solver:
         # with fp32 Arnoldi products, room for their fp32 copy of A (half the bytes per product)
         extra = capi.hpmxp_solve_workspace_a32(n) if self.params.matvec_fp32 else 0
         self.sws = workspace(capi.hpmxp_solve_workspace(n, nrhs, self.params.restart) + extra, self.device)
+        self.scales = (torch.empty(n, dtype=torch.float64, device=self.device),
+                       torch.empty(n, dtype=torch.float64, device=self.device))
 
     def factor(self, A: ColMajor, stream=None) -> ColMajor:
-        LU = factor(A, self.prec, self.nb, LU=self.LU, ws=self.fws, stream=stream, check=False)
+        sc = balance(A, self.prec, self.scales, stream) if self.balance else None
+        LU = factor(A, self.prec, self.nb, LU=self.LU, ws=self.fws, stream=stream, check=False, scales=sc)
         self.factor_status = factor.last_status
         return LU
 
     def solve(self, A: ColMajor, b: ColMajor, stream=None):
-        return solve_ir(A, self.LU, b, self.prec, self.params, x=self.x, ws=self.sws, stream=stream)
+        return solve_ir(A, self.LU, b, self.prec, self.params, x=self.x, ws=self.sws, stream=stream,
+                        scales=self.scales if self.balance else None)
 
     def __call__(self, A: ColMajor, b: ColMajor, stream=None):
         self.factor(A, stream)

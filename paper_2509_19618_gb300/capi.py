@@ -80,11 +80,15 @@ def load():
             "hpmxp_generate_noalloc": ([i64, u64, d, i32, P, i64, P, i64, i64, P], i32),
             "hpmxp_factor_workspace": ([i64, i32, i32], sz),
             "hpmxp_factor": ([i64, P, i64, i32, i32, P, i64, P, sz, P], i32),
+            "hpmxp_factor_scaled": ([i64, P, i64, i32, i32, P, P, P, i64, P, sz, P], i32),
+            "hpmxp_balance": ([i64, P, i64, i32, P, P, P], i32),
             "hpmxp_ir_params_default": ([ctypes.POINTER(IRParams)], None),
             "hpmxp_solve_workspace": ([i64, i64, i32], sz),
             "hpmxp_solve_workspace_a32": ([i64], sz),
             "hpmxp_solve_ir": ([i64, P, i64, P, i64, i32, P, i64, P, i64, i64, ctypes.POINTER(IRParams),
                                 ctypes.POINTER(IRInfo), P, sz, P], i32),
+            "hpmxp_solve_ir_scaled": ([i64, P, i64, P, i64, i32, P, P, P, i64, P, i64, i64,
+                                       ctypes.POINTER(IRParams), ctypes.POINTER(IRInfo), P, sz, P], i32),
             "hpmxp_residual_workspace": ([i64, i64], sz),
             "hpmxp_residual": ([i64, P, i64, P, i64, P, i64, i64, P, P, sz, P], i32),
             "hpmxp_test_gemm": ([i32, i32, i32, P, i64, P, i64, P, i64, P, i64, i32, ctypes.c_float, i32, i32,
@@ -155,6 +159,14 @@ def hpmxp_factor(n, A, lda, prec, nb, LU, ldlu, ws, ws_bytes, stream):
     return _call("hpmxp_factor", n, A, lda, prec, nb, LU, ldlu, ws, ws_bytes, stream)
 
 
+def hpmxp_factor_scaled(n, A, lda, prec, nb, rs, cs, LU, ldlu, ws, ws_bytes, stream):
+    return _call("hpmxp_factor_scaled", n, A, lda, prec, nb, rs, cs, LU, ldlu, ws, ws_bytes, stream)
+
+
+def hpmxp_balance(n, A, lda, prec, rs, cs, stream):
+    return _call("hpmxp_balance", n, A, lda, prec, rs, cs, stream)
+
+
 def hpmxp_ir_params_default() -> IRParams:
     p = IRParams()
     load().hpmxp_ir_params_default(ctypes.byref(p))
@@ -167,6 +179,12 @@ def hpmxp_solve_workspace(n, nrhs, restart):
 
 def hpmxp_solve_ir(n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs, params, info, ws, ws_bytes, stream):
     return _call("hpmxp_solve_ir", n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs,
+                 None if params is None else ctypes.byref(params), info, ws, ws_bytes, stream)
+
+
+def hpmxp_solve_ir_scaled(n, A, lda, LU, ldlu, prec, rs, cs, b, ldb, x, ldx, nrhs, params, info, ws, ws_bytes,
+                          stream):
+    return _call("hpmxp_solve_ir_scaled", n, A, lda, LU, ldlu, prec, rs, cs, b, ldb, x, ldx, nrhs,
                  None if params is None else ctypes.byref(params), info, ws, ws_bytes, stream)
 
 
@@ -194,9 +212,10 @@ def hpmxp_prof_reset():
     load().hpmxp_prof_reset()
 
 
-PROF_GEMM, PROF_GEMV, PROF_PRECOND, PROF_GETRF, PROF_GEMV32, PROF_CAST, PROF_PANEL, PROF_GEMM_STORE = range(8)
+PROF_GEMM, PROF_GEMV, PROF_PRECOND, PROF_GETRF, PROF_GEMV32, PROF_CAST, PROF_PANEL, PROF_GEMM_STORE, \
+    PROF_BALANCE = range(9)
 PROF_NAMES = {0: "gemm_update", 1: "gemv", 2: "precond", 3: "getrf", 4: "gemv32", 5: "cast", 6: "panel",
-              7: "gemm_panel"}
+              7: "gemm_panel", 8: "balance"}
 
 
 def hpmxp_prof_read(kind: int) -> dict:

@@ -30,7 +30,7 @@ hpmxp_status status_from_word(uint32_t w) {
 hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu, int prec,
                       const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs,
                       const hpmxp_ir_params& prm, hpmxp_ir_info* info, void* ws, size_t ws_bytes,
-                      cudaStream_t st);
+                      cudaStream_t st, const double* rs = nullptr, const double* cs = nullptr);
 hpmxp_status residual_check(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
                             const double* b, int64_t ldb, int64_t nrhs, double* out, void* ws, cudaStream_t st);
 
@@ -81,13 +81,27 @@ size_t hpmxp_factor_workspace(int64_t n, int prec, int nb) {
   return factor_ws_bytes(n, prec, nb);
 }
 
-hpmxp_status hpmxp_factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU, int64_t ldlu,
-                          void* ws, size_t ws_bytes, void* stream) {
+hpmxp_status hpmxp_factor_scaled(int64_t n, const double* A, int64_t lda, int prec, int nb, const double* rs,
+                                 const double* cs, void* LU, int64_t ldlu, void* ws, size_t ws_bytes,
+                                 void* stream) {
   if (n < 1 || n > kMaxN || !A || lda < n || !LU || ldlu < n || (ldlu % 8) != 0 || !aligned(LU, 16) || !ws ||
-      !aligned(ws, 256) || !prec_ok(prec) || !(nb == 128 || nb == 256 || nb == 512))
+      !aligned(ws, 256) || !prec_ok(prec) || !(nb == 128 || nb == 256 || nb == 512) || (!rs != !cs))
     return HPMXP_EINVAL;
   if (ws_bytes < factor_ws_bytes(n, prec, nb)) return HPMXP_ENOMEM;
-  return factor(n, A, lda, prec, nb, LU, ldlu, ws, ws_bytes, (cudaStream_t)stream);
+  return factor(n, A, lda, prec, nb, LU, ldlu, ws, ws_bytes, (cudaStream_t)stream, rs, cs);
+}
+
+hpmxp_status hpmxp_factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU, int64_t ldlu,
+                          void* ws, size_t ws_bytes, void* stream) {
+  return hpmxp_factor_scaled(n, A, lda, prec, nb, nullptr, nullptr, LU, ldlu, ws, ws_bytes, stream);
+}
+
+hpmxp_status hpmxp_balance(int64_t n, const double* A, int64_t lda, int prec, double* rs, double* cs,
+                           void* stream) {
+  if (n < 1 || n > kMaxN || !A || lda < n || !rs || !cs || rs == cs || !aligned(rs, 8) || !aligned(cs, 8) ||
+      !prec_ok(prec))
+    return HPMXP_EINVAL;
+  return status_from_cuda(launch_balance(n, A, lda, prec, rs, cs, (cudaStream_t)stream));
 }
 
 void hpmxp_ir_params_default(hpmxp_ir_params* p) {
@@ -112,6 +126,15 @@ hpmxp_status hpmxp_solve_ir(int64_t n, const double* A, int64_t lda, const void*
                             const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs,
                             const hpmxp_ir_params* prm, hpmxp_ir_info* info, void* ws, size_t ws_bytes,
                             void* stream) {
+  return hpmxp_solve_ir_scaled(n, A, lda, LU, ldlu, prec, nullptr, nullptr, b, ldb, x, ldx, nrhs, prm, info, ws,
+                               ws_bytes, stream);
+}
+
+hpmxp_status hpmxp_solve_ir_scaled(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu,
+                                   int prec, const double* rs, const double* cs, const double* b, int64_t ldb,
+                                   double* x, int64_t ldx, int64_t nrhs, const hpmxp_ir_params* prm,
+                                   hpmxp_ir_info* info, void* ws, size_t ws_bytes, void* stream) {
+  if (!rs != !cs) return HPMXP_EINVAL;
   hpmxp_ir_params p;
   hpmxp_ir_params_default(&p);
   if (prm) p = *prm;
@@ -121,7 +144,8 @@ hpmxp_status hpmxp_solve_ir(int64_t n, const double* A, int64_t lda, const void*
       (p.precond_fp32 != 0 && p.precond_fp32 != 1) || (p.matvec_fp32 != 0 && p.matvec_fp32 != 1))
     return HPMXP_EINVAL;
   if (ws_bytes < solve_ws_bytes(n, nrhs, p.restart)) return HPMXP_ENOMEM;
-  return solve_ir(n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs, p, info, ws, ws_bytes, (cudaStream_t)stream);
+  return solve_ir(n, A, lda, LU, ldlu, prec, b, ldb, x, ldx, nrhs, p, info, ws, ws_bytes, (cudaStream_t)stream, rs,
+                  cs);
 }
 
 size_t hpmxp_residual_workspace(int64_t n, int64_t nrhs) {

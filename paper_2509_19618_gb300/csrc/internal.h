@@ -117,10 +117,16 @@ cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st);
 int gemm_engine();
 
 // lu.cu
-cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st);
+// rs / cs (optional, NULL = 1): the cast converts diag(rs) A diag(cs)
+cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st,
+                        const double* rs = nullptr, const double* cs = nullptr);
+// power-of-two row / column equilibration and the format's scale into rs, cs (n each)
+cudaError_t launch_balance(int64_t n, const double* A, int64_t lda, int prec, double* rs, double* cs,
+                           cudaStream_t st);
 size_t factor_ws_bytes(int64_t n, int prec, int nb);
 hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU,
-                    int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st);
+                    int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st, const double* rs = nullptr,
+                    const double* cs = nullptr);
 
 // ir.cu
 size_t solve_ws_bytes(int64_t n, int64_t nrhs, int restart);
@@ -128,11 +134,12 @@ size_t solve_a32_bytes(int64_t n);   // optional fp32 copy of A after the solve 
 cudaError_t fill_smem(uint32_t pattern, cudaStream_t st);   // test support
 size_t residual_ws_bytes(int64_t n, int64_t nrhs);
 hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, const double* v, int64_t ldv,
-                           double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws, cudaStream_t st);
+                           double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws, cudaStream_t st,
+                           const double* rs = nullptr, const double* cs = nullptr);
 
 // prof.cu: launch counting and optional event timing (kinds below).
 enum ProfKind { kProfGemm = 0, kProfGemv = 1, kProfPrecond = 2, kProfGetrf = 3, kProfGemv32 = 4, kProfCast = 5,
-                kProfPanel = 6, kProfGemmStore = 7, kProfKinds = 8 };
+                kProfPanel = 6, kProfGemmStore = 7, kProfBalance = 8, kProfKinds = 9 };
 void count_launches(int k);
 bool prof_on();
 // Programmatic dependent launch.  A kernel launched by launch_pdl may start

@@ -376,7 +376,8 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
                                                       double* __restrict__ z, int64_t ldz,
                                                       unsigned long long* __restrict__ pub, int epoch,
                                                       uint32_t* status, long long wait_polls,
-                                                      unsigned long long wait_ns) {
+                                                      unsigned long long wait_ns, const double* __restrict__ rs,
+                                                      const double* __restrict__ cs) {
   constexpr bool kInvInSmem = sizeof(T) == 4;   // the fp32 inverse (64 KB) is staged; the fp64 one stays in L2
   constexpr int W = kWords<T>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -397,7 +398,9 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     for (int t = tid; t < kTB32 * K; t += 256) {
       const int ii = t % kTB32, r = t / kTB32;
       const int64_t i = (int64_t)(me + o * G) * kTB32 + ii;
-      acc[((size_t)o * kTB32 + ii) * K + r] = i < n ? (T)v[i + r * ldv] : (T)0;
+      // balanced factors (LU of diag(rs) A diag(cs)): M^{-1} v = diag(cs) U^{-1} L^{-1} diag(rs) v;
+      // rs and cs are powers of two, so the scalings are exact
+      acc[((size_t)o * kTB32 + ii) * K + r] = i < n ? (T)(rs ? v[i + r * ldv] * rs[i] : v[i + r * ldv]) : (T)0;
     }
   // abort_flag (and acc) must be written before any thread reads them: shared
   // memory starts with whatever the SM's previous block left there
@@ -535,7 +538,7 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
       if (backward) {
         const int ii = t / K, r = t % K;
         const int64_t i = (int64_t)c * kTB32 + ii;
-        if (i < n) z[i + r * ldz] = (double)zs[t];
+        if (i < n) z[i + r * ldz] = cs ? (double)zs[t] * cs[i] : (double)zs[t];
       }
     }
     __syncthreads();
@@ -987,7 +990,8 @@ size_t precond_smem(int64_t n, int K, int G) {
 template <class T, int K>
 cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt, const T* dinv, const double* v,
                              int64_t ldv, double* z, int64_t ldz, unsigned long long* pub, int epoch,
-                             uint32_t* status, int G, size_t smem, cudaStream_t st) {
+                             uint32_t* status, int G, size_t smem, cudaStream_t st, const double* rs,
+                             const double* cs) {
   auto kern = precond_kernel<T, K>;
   // one value for every call: concurrent solves on other threads set the same cap
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPrecondSmem);
@@ -995,25 +999,29 @@ cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt,
   const WaitBudget wb = wait_budget();
   long long polls = wb.polls;
   unsigned long long ns = wb.ns;
-  void* args[] = {&n,   (void*)&LU, &ld,    &fmt,    (void*)&dinv, (void*)&v, &ldv, &z,
-                  &ldz, &pub,       &epoch, &status, &polls,       &ns};
+  void* args[] = {&n,   (void*)&LU, &ld,    &fmt,    (void*)&dinv, (void*)&v, &ldv,       &z,
+                  &ldz, &pub,       &epoch, &status, &polls,       &ns,       (void*)&rs, (void*)&cs};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(256), args, smem, st);
 }
 
 template <class T>
 cudaError_t precond_launch(int K, int64_t n, const uint16_t* LU, int64_t ld, int fmt, const T* dinv,
                            const double* v, int64_t ldv, double* z, int64_t ldz, unsigned long long* pub,
-                           int epoch, uint32_t* status, int G, size_t smem, cudaStream_t st) {
+                           int epoch, uint32_t* status, int G, size_t smem, cudaStream_t st, const double* rs,
+                           const double* cs) {
+#define HPMXP_PRECOND_K(KK) \
+  precond_launch_k<T, KK>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st, rs, cs)
   switch (K) {
-    case 1: return precond_launch_k<T, 1>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 2: return precond_launch_k<T, 2>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 3: return precond_launch_k<T, 3>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 4: return precond_launch_k<T, 4>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 5: return precond_launch_k<T, 5>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 6: return precond_launch_k<T, 6>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    case 7: return precond_launch_k<T, 7>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
-    default: return precond_launch_k<T, 8>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st);
+    case 1: return HPMXP_PRECOND_K(1);
+    case 2: return HPMXP_PRECOND_K(2);
+    case 3: return HPMXP_PRECOND_K(3);
+    case 4: return HPMXP_PRECOND_K(4);
+    case 5: return HPMXP_PRECOND_K(5);
+    case 6: return HPMXP_PRECOND_K(6);
+    case 7: return HPMXP_PRECOND_K(7);
+    default: return HPMXP_PRECOND_K(8);
   }
+#undef HPMXP_PRECOND_K
 }
 
 template <class T>
@@ -1031,6 +1039,8 @@ struct Solver {
   int K, m;
   const double* A; int64_t lda;
   const uint16_t* LU; int64_t ldlu; int fmt;
+  const double* rs = nullptr;   // balancing of the factors (NULL: none)
+  const double* cs = nullptr;
   const double* B; int64_t ldb;
   double* X; int64_t ldx;
   hpmxp_ir_params prm;
@@ -1049,9 +1059,9 @@ struct Solver {
     unsigned long long* pub = (unsigned long long*)w.pub;
     cudaError_t e = prm.precond_fp32
                         ? precond_launch<float>(K, n, LU, ldlu, fmt, (const float*)w.dinv, v, ldv, z, ldz, pub,
-                                                epoch, w.status, G, psmem, st)
+                                                epoch, w.status, G, psmem, st, rs, cs)
                         : precond_launch<double>(K, n, LU, ldlu, fmt, (const double*)w.dinv, v, ldv, z, ldz, pub,
-                                                 epoch, w.status, G, psmem, st);
+                                                 epoch, w.status, G, psmem, st, rs, cs);
     prof_end(tok, kProfPrecond, 2.0 * (double)n * (double)n, st);
     count_launches(1);
     return e;
@@ -1171,11 +1181,12 @@ size_t residual_ws_bytes(int64_t n, int64_t nrhs) { return carve_solve(nullptr, 
 hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, int64_t ldlu, int prec,
                       const double* b, int64_t ldb, double* x, int64_t ldx, int64_t nrhs,
                       const hpmxp_ir_params& prm, hpmxp_ir_info* info, void* ws, size_t ws_bytes,
-                      cudaStream_t st) {
+                      cudaStream_t st, const double* rs, const double* cs) {
   Solver s;
   s.n = n; s.K = (int)nrhs; s.m = prm.restart;
   s.A = A; s.lda = lda;
   s.LU = (const uint16_t*)LU; s.ldlu = ldlu; s.fmt = prec == HPMXP_FP16 ? kFP16 : kBF16;
+  s.rs = rs; s.cs = cs;
   s.B = b; s.ldb = ldb; s.X = x; s.ldx = ldx;
   s.prm = prm;
   s.w = carve_solve(ws, n, nrhs, prm.restart);
@@ -1208,10 +1219,12 @@ hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, i
 }
 
 hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, const double* v, int64_t ldv,
-                           double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws, cudaStream_t st) {
+                           double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws, cudaStream_t st,
+                           const double* rs, const double* cs) {
   Solver s;
   s.n = n; s.K = (int)nrhs; s.m = 1;
   s.LU = (const uint16_t*)LU; s.ldlu = ldlu; s.fmt = fmt;
+  s.rs = rs; s.cs = cs;
   hpmxp_ir_params_default(&s.prm);
   s.prm.precond_fp32 = fp32;
   s.w = carve_solve(ws, n, nrhs, 1);

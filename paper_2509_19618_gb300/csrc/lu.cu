@@ -75,18 +75,23 @@ __device__ inline uint16_t f64_to_u16(double x, int fmt) {
   return fmt == kBF16 ? f64_to_f16bits<7, 127>(x) : f64_to_f16bits<10, 15>(x);
 }
 
-// A (fp64, column major) -> LU (16-bit, column major).  CTA (x, y) converts
-// rows 2048 y .. +2047 of column x; each thread 8 consecutive rows with four
-// 16-byte loads and one 16-byte store when aligned (LU is 16-byte aligned
-// with ldlu % 8 == 0), entry by entry otherwise.
+// A (fp64, column major) -> LU (16-bit, column major), optionally of the
+// balanced matrix diag(rs) A diag(cs) (rs, cs powers of two, so the fp64
+// products are exact and the one rounding is the cast's).  CTA (x, y)
+// converts rows 2048 y .. +2047 of column x; each thread 8 consecutive rows
+// with four 16-byte loads and one 16-byte store when aligned (LU is 16-byte
+// aligned with ldlu % 8 == 0), entry by entry otherwise.
 constexpr int kCastRows = 256 * 8;
 __global__ void __launch_bounds__(256) cast_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
-                                                   uint16_t* __restrict__ LU, int64_t ldlu, int fmt) {
+                                                   uint16_t* __restrict__ LU, int64_t ldlu, int fmt,
+                                                   const double* __restrict__ rs, const double* __restrict__ cs) {
   const int64_t j = blockIdx.x;
   const int64_t i = (int64_t)blockIdx.y * kCastRows + 8 * (int64_t)threadIdx.x;
   if (i >= n) return;
   const double* src = A + i + j * lda;
   uint16_t* dst = LU + i + j * ldlu;
+  const double cj = cs ? cs[j] : 1.0;
+  auto scaled = [&](double a, int64_t row) { return rs ? a * rs[row] * cj : a * cj; };
   if (i + 8 <= n && (((uintptr_t)src) & 15) == 0) {
     double2 v[4];
 #pragma unroll
@@ -94,11 +99,100 @@ __global__ void __launch_bounds__(256) cast_kernel(int64_t n, const double* __re
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      w[k] = (uint32_t)f64_to_u16(v[k].x, fmt) | ((uint32_t)f64_to_u16(v[k].y, fmt) << 16);
+      w[k] = (uint32_t)f64_to_u16(scaled(v[k].x, i + 2 * k), fmt) |
+             ((uint32_t)f64_to_u16(scaled(v[k].y, i + 2 * k + 1), fmt) << 16);
     *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
   } else {
-    for (int k = 0; k < 8 && i + k < n; ++k) dst[k] = f64_to_u16(src[k], fmt);
+    for (int k = 0; k < 8 && i + k < n; ++k) dst[k] = f64_to_u16(scaled(src[k], i + k), fmt);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Balancing and scaling (section "Algorithmic Framework": a Theta(n^2)
+// balancing of the input borrowed from the HPL harness, and a scaling that
+// makes the values fit the low-precision format, both timed and undone).
+// Power-of-two row then column equilibration: rs_i = 2^-floor(log2 max_j
+// |a_ij|), cs_j = 2^-floor(log2 max_i |rs_i a_ij|), so every row and column of
+// diag(rs) A diag(cs) has its largest magnitude in [1, 2); then rs *= 2^k,
+// the format's scale (k = 12 for FP16, whose range ends at 65504 and whose
+// normal range at 2^-14; 0 for BF16, which has fp32's range).  Maxima are
+// taken on the bit patterns of non-negative doubles (ordered like the values),
+// so any reduction order gives the same bits.
+// ---------------------------------------------------------------------------
+constexpr int kBalRows = 512;        // rows per CTA of the row pass (256 threads x 2)
+constexpr int kBalChunk = 1024;      // columns per CTA of the row pass
+
+__device__ inline unsigned long long abs_bits(double a) {
+  return (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+}
+
+// pass 1: rmax[i] = max_j |a_ij| as a bit pattern (rmax zeroed first)
+__global__ void __launch_bounds__(256) row_absmax_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
+                                                         unsigned long long* __restrict__ rmax) {
+  const int64_t i = (int64_t)blockIdx.x * kBalRows + 2 * threadIdx.x;
+  if (i >= n) return;
+  const int64_t j0 = (int64_t)blockIdx.y * kBalChunk, j1 = min(j0 + (int64_t)kBalChunk, n);
+  const bool two = i + 1 < n;
+  const bool vec = two && ((((uintptr_t)(A + i)) & 15) == 0) && ((lda & 1) == 0);
+  unsigned long long m0 = 0, m1 = 0;
+  const double* col = A + i + j0 * lda;
+  int64_t j = j0;
+  if (vec) {
+    for (; j + 4 <= j1; j += 4) {
+      double2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldcs(reinterpret_cast<const double2*>(col + (int64_t)u * lda));
+      col += 4 * lda;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        m0 = max(m0, abs_bits(v[u].x));
+        m1 = max(m1, abs_bits(v[u].y));
+      }
+    }
+  }
+  for (; j < j1; ++j, col += lda) {
+    m0 = max(m0, abs_bits(col[0]));
+    if (two) m1 = max(m1, abs_bits(col[1]));
+  }
+  atomicMax(rmax + i, m0);
+  if (two) atomicMax(rmax + i + 1, m1);
+}
+
+// 2^-floor(log2 m) for a finite m > 0, else 1 (a zero or non-finite row or
+// column is left unscaled)
+__device__ inline double pow2_inverse(double m) {
+  if (!(m > 0.0) || !isfinite(m)) return 1.0;
+  int e;
+  frexp(m, &e);                       // m = f 2^e, f in [0.5, 1): floor(log2 m) = e - 1
+  return ldexp(1.0, 1 - e);
+}
+
+// rmax bits -> rs_i (in place); the format scale is applied after the column pass
+__global__ void row_scale_kernel(int64_t n, double* rs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rs[i] = pow2_inverse(rs[i]);
+}
+
+// pass 2: one CTA per column: cs_j = 2^-floor(log2 max_i |rs_i a_ij|)
+__global__ void __launch_bounds__(256) col_scale_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
+                                                        const double* __restrict__ rs, double* __restrict__ cs) {
+  __shared__ unsigned long long wmax[8];
+  const int64_t j = blockIdx.x;
+  const double* col = A + j * lda;
+  unsigned long long m = 0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) m = max(m, abs_bits(__ldcs(col + i) * rs[i]));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = max(m, wmax[w]);
+    cs[j] = pow2_inverse(__longlong_as_double((long long)m));
+  }
+}
+
+__global__ void format_scale_kernel(int64_t n, double* rs, double s) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rs[i] *= s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1089,10 +1183,11 @@ SideStream& side_stream(int dev) {
   return s;
 }
 
-cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st) {
+cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st,
+                        const double* rs, const double* cs) {
   void* tok = prof_begin(st);
   cast_kernel<<<dim3((unsigned)n, (unsigned)cdiv<int64_t>(n, kCastRows)), 256, 0, st>>>(n, A, lda, (uint16_t*)out,
-                                                                                    ldo, fmt);
+                                                                                    ldo, fmt, rs, cs);
   prof_end(tok, kProfCast, 10.0 * (double)n * (double)n, st);
   count_launches(1);
   return cudaGetLastError();
@@ -1100,8 +1195,28 @@ cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int6
 
 size_t factor_ws_bytes(int64_t n, int prec, int nb) { return carve(nullptr, n, prec, nb).bytes; }
 
+cudaError_t launch_balance(int64_t n, const double* A, int64_t lda, int prec, double* rs, double* cs,
+                           cudaStream_t st) {
+  void* tok = prof_begin(st);
+  cudaError_t e = cudaMemsetAsync(rs, 0, sizeof(double) * (size_t)n, st);
+  if (e != cudaSuccess) return e;
+  dim3 g1((unsigned)cdiv<int64_t>(n, kBalRows), (unsigned)cdiv<int64_t>(n, kBalChunk));
+  row_absmax_kernel<<<g1, 256, 0, st>>>(n, A, lda, reinterpret_cast<unsigned long long*>(rs));
+  row_scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, rs);
+  col_scale_kernel<<<(unsigned)n, 256, 0, st>>>(n, A, lda, rs, cs);
+  const double s = prec == HPMXP_FP16 ? 4096.0 : 1.0;
+  if (s != 1.0) {
+    format_scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, rs, s);
+    count_launches(1);
+  }
+  prof_end(tok, kProfBalance, 16.0 * (double)n * (double)n, st);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
 hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU,
-                    int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st) {
+                    int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st, const double* rs,
+                    const double* cs) {
   static std::atomic<int> attr_dev{-1};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1118,7 +1233,7 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
   f.w = carve(ws, n, prec, nb);
   f.st = st;
   f.check(cudaMemsetAsync(f.w.status, 0, sizeof(uint32_t), st));
-  f.check(launch_cast(n, A, lda, LU, ldlu, f.fmt, st));
+  f.check(launch_cast(n, A, lda, LU, ldlu, f.fmt, st, rs, cs));
   if (const char* om = getenv("HPMXP_OVERLAP_MIN")) f.overlap_min = atoll(om);
   // the largest far part is n - 2 nb (first step); below overlap_min the
   // schedule never uses the side stream, so it is not taken (concurrent
