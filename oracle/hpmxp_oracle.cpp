@@ -450,28 +450,42 @@ struct LowPrecLU {
 // balancing borrowed from the HPL harness and a scaling into the range of the
 // low-precision format, both timed and undone at the end).  Reading: row then
 // column equilibration by powers of two, rs_i = 2^-floor(log2 max_j |a_ij|),
-// cs_j = 2^-floor(log2 max_i |rs_i a_ij|) (a zero or non-finite maximum gives
-// 1), then rs times the format's scale (2^12 for FP16, 1 otherwise).  The
-// factorization then works on diag(rs) A diag(cs), and the preconditioner is
+// cs_j = 2^-floor(log2 max_i |rs_i a_ij|), the logarithms taken exactly (as
+// integers, so no product can under- or overflow); a row or column that holds
+// a non-finite entry, or only zeros, gets 1; then rs times the format's scale
+// (2^12 for FP16, 1 otherwise).  The factorization then works on
+// diag(rs) A diag(cs), and the preconditioner is
 // M^{-1} = diag(cs) U^{-1} L^{-1} diag(rs), which undoes the balancing.
 // ---------------------------------------------------------------------------
-double inverse_power_of_two(double m) {
-  if (!(m > 0.0) || !std::isfinite(m)) return 1.0;
+int floor_log2(double a) {   // finite a != 0
   int e;
-  std::frexp(m, &e);   // m = f 2^e, f in [0.5, 1)
-  return std::ldexp(1.0, 1 - e);
+  std::frexp(std::fabs(a), &e);   // |a| = f 2^e, f in [0.5, 1)
+  return e - 1;
 }
 
 void balance(int64_t n, const double* A, int64_t lda, int fmt, double* rs, double* cs) {
   for (int64_t i = 0; i < n; ++i) {
-    double m = 0.0;
-    for (int64_t j = 0; j < n; ++j) m = std::max(m, std::fabs(A[i + j * lda]));
-    rs[i] = inverse_power_of_two(m);
+    bool bad = false, any = false;
+    int m = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      const double a = A[i + j * lda];
+      if (!std::isfinite(a)) bad = true;
+      else if (a != 0.0) { m = any ? std::max(m, floor_log2(a)) : floor_log2(a); any = true; }
+    }
+    rs[i] = (bad || !any) ? 1.0 : std::ldexp(1.0, -m);
   }
   for (int64_t j = 0; j < n; ++j) {
-    double m = 0.0;
-    for (int64_t i = 0; i < n; ++i) m = std::max(m, std::fabs(A[i + j * lda] * rs[i]));
-    cs[j] = inverse_power_of_two(m);
+    bool bad = false, any = false;
+    int m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double a = A[i + j * lda];
+      if (!std::isfinite(a)) { bad = true; continue; }
+      if (a == 0.0) continue;
+      const int l = floor_log2(a) + floor_log2(rs[i]);
+      m = any ? std::max(m, l) : l;
+      any = true;
+    }
+    cs[j] = (bad || !any) ? 1.0 : std::ldexp(1.0, -m);
   }
   const double s = fmt == FMT_FP16 ? 4096.0 : 1.0;
   for (int64_t i = 0; i < n; ++i) rs[i] *= s;

@@ -75,6 +75,29 @@ __device__ inline uint16_t f64_to_u16(double x, int fmt) {
   return fmt == kBF16 ? f64_to_f16bits<7, 127>(x) : f64_to_f16bits<10, 15>(x);
 }
 
+// Exponent k of a power of two 2^k (a normal fp64 value).
+__device__ inline int pow2_exponent(double s) {
+  return (int)(((unsigned long long)__double_as_longlong(s) >> 52) & 0x7ff) - 1023;
+}
+
+// f64_to_u16(x * 2^k) with integer operations only: the scaling moves the
+// exponent field (exact for normal x whose scaled value stays normal; below
+// fp64's normal range the value is far below every 16-bit format's smallest
+// subnormal and rounds to a signed zero, above it the result is infinite);
+// zeros, fp64 subnormals, infinities and NaNs take the fp64 multiply, which is
+// exact or IEEE there too.  GB300's fp64 rate is low enough that one fp64
+// multiply per entry would cost as much as reading the matrix.
+__device__ inline uint16_t f64_to_u16_pow2(double x, int k, int fmt) {
+  if (k == 0) return f64_to_u16(x, fmt);
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0 || e == 0x7ff) return f64_to_u16(x * ldexp(1.0, k), fmt);
+  const int e2 = e + k;
+  if (e2 <= 0) return f64_to_u16(__longlong_as_double((long long)(u & 0x8000000000000000ull)), fmt);
+  if (e2 >= 0x7ff) return f64_to_u16(__longlong_as_double((long long)((u & 0x8000000000000000ull) | 0x7ff0000000000000ull)), fmt);
+  return f64_to_u16(__longlong_as_double((long long)((u & ~(0x7ffull << 52)) | ((unsigned long long)e2 << 52))), fmt);
+}
+
 // A (fp64, column major) -> LU (16-bit, column major), optionally of the
 // balanced matrix diag(rs) A diag(cs) (rs, cs powers of two, so the fp64
 // products are exact and the one rounding is the cast's).  CTA (x, y)
@@ -90,8 +113,11 @@ __global__ void __launch_bounds__(256) cast_kernel(int64_t n, const double* __re
   if (i >= n) return;
   const double* src = A + i + j * lda;
   uint16_t* dst = LU + i + j * ldlu;
-  const double cj = cs ? cs[j] : 1.0;
-  auto scaled = [&](double a, int64_t row) { return rs ? a * rs[row] * cj : a * cj; };
+  // exponents of the power-of-two scales of this column and of the thread's rows
+  const int kc = cs ? pow2_exponent(cs[j]) : 0;
+  int kr[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) kr[k] = (rs && i + k < n) ? kc + pow2_exponent(rs[i + k]) : kc;
   if (i + 8 <= n && (((uintptr_t)src) & 15) == 0) {
     double2 v[4];
 #pragma unroll
@@ -99,11 +125,11 @@ __global__ void __launch_bounds__(256) cast_kernel(int64_t n, const double* __re
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      w[k] = (uint32_t)f64_to_u16(scaled(v[k].x, i + 2 * k), fmt) |
-             ((uint32_t)f64_to_u16(scaled(v[k].y, i + 2 * k + 1), fmt) << 16);
+      w[k] = (uint32_t)f64_to_u16_pow2(v[k].x, kr[2 * k], fmt) |
+             ((uint32_t)f64_to_u16_pow2(v[k].y, kr[2 * k + 1], fmt) << 16);
     *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
   } else {
-    for (int k = 0; k < 8 && i + k < n; ++k) dst[k] = f64_to_u16(scaled(src[k], i + k), fmt);
+    for (int k = 0; k < 8 && i + k < n; ++k) dst[k] = f64_to_u16_pow2(src[k], kr[k], fmt);
   }
 }
 
@@ -113,11 +139,14 @@ __global__ void __launch_bounds__(256) cast_kernel(int64_t n, const double* __re
 // makes the values fit the low-precision format, both timed and undone).
 // Power-of-two row then column equilibration: rs_i = 2^-floor(log2 max_j
 // |a_ij|), cs_j = 2^-floor(log2 max_i |rs_i a_ij|), so every row and column of
-// diag(rs) A diag(cs) has its largest magnitude in [1, 2); then rs *= 2^k,
-// the format's scale (k = 12 for FP16, whose range ends at 65504 and whose
-// normal range at 2^-14; 0 for BF16, which has fp32's range).  Maxima are
-// taken on the bit patterns of non-negative doubles (ordered like the values),
-// so any reduction order gives the same bits.
+// diag(rs) A diag(cs) has its largest magnitude in [1, 2); a row or column
+// with a non-finite entry, or only zeros, gets scale 1; then rs *= 2^k, the
+// format's scale (k = 12 for FP16, whose range ends at 65504 and whose normal
+// range at 2^-14; 0 for BF16, which has fp32's range).  Row maxima are taken
+// on the bit patterns of non-negative doubles (ordered like the values, NaN
+// and infinity above every finite value); the column pass needs only
+// floor(log2 |rs_i a_ij|) = floor(log2 |a_ij|) + log2 rs_i, an integer max:
+// no fp64 arithmetic per entry, and any reduction order gives the same bits.
 // ---------------------------------------------------------------------------
 constexpr int kBalRows = 512;        // rows per CTA of the row pass (256 threads x 2)
 constexpr int kBalChunk = 1024;      // columns per CTA of the row pass
@@ -167,6 +196,19 @@ __device__ inline double pow2_inverse(double m) {
   return ldexp(1.0, 1 - e);
 }
 
+// floor(log2 |a|) for a finite nonzero a; kZeroLog for 0, kBadLog for inf / NaN
+constexpr int kZeroLog = -100000, kBadLog = 100000;
+__device__ inline int floor_log2_abs(double a) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0x7ff) return kBadLog;
+  if (e != 0) return e - 1023;
+  if ((u & 0x000fffffffffffffull) == 0) return kZeroLog;
+  int f;
+  frexp(a, &f);                      // fp64 subnormal
+  return f - 1;
+}
+
 // rmax bits -> rs_i (in place); the format scale is applied after the column pass
 __global__ void row_scale_kernel(int64_t n, double* rs) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -176,17 +218,20 @@ __global__ void row_scale_kernel(int64_t n, double* rs) {
 // pass 2: one CTA per column: cs_j = 2^-floor(log2 max_i |rs_i a_ij|)
 __global__ void __launch_bounds__(256) col_scale_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
                                                         const double* __restrict__ rs, double* __restrict__ cs) {
-  __shared__ unsigned long long wmax[8];
+  __shared__ int wmax[8];
   const int64_t j = blockIdx.x;
   const double* col = A + j * lda;
-  unsigned long long m = 0;
-  for (int64_t i = threadIdx.x; i < n; i += 256) m = max(m, abs_bits(__ldcs(col + i) * rs[i]));
+  int m = kZeroLog;
+  for (int64_t i = threadIdx.x; i < n; i += 256) {
+    const int l = floor_log2_abs(__ldcs(col + i));
+    m = max(m, l >= kBadLog ? kBadLog : (l <= kZeroLog ? kZeroLog : l + pow2_exponent(rs[i])));
+  }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < 8; ++w) m = max(m, wmax[w]);
-    cs[j] = pow2_inverse(__longlong_as_double((long long)m));
+    cs[j] = (m == kZeroLog || m == kBadLog) ? 1.0 : ldexp(1.0, -m);
   }
 }
 
