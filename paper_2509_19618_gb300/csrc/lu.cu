@@ -41,15 +41,26 @@ constexpr int kB = 128;         // base (sub-)block width
 // definition on the bit pattern (exponent rebias, 45- or 42-bit round-off with
 // ties to even, subnormal quantum for tiny values, overflow to infinity).
 // ---------------------------------------------------------------------------
+// With k != 0 the value converted is x * 2^k (a power-of-two balancing
+// scale): the scaling only moves the exponent, so it is one integer add here;
+// an fp64-subnormal x (far below every 16-bit format) is scaled by an fp64
+// multiply first.
 template <int kMant, int kBias>
-__device__ inline uint16_t f64_to_f16bits(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+__device__ inline uint16_t f64_to_f16bits(double x, int k = 0) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0 && k != 0 && (u << 1) != 0) {
+    u = (unsigned long long)__double_as_longlong(x * ldexp(1.0, k));
+    e = (int)((u >> 52) & 0x7ff);
+    k = 0;
+  }
   const uint32_t sign = (uint32_t)(u >> 63) << 15;
-  const int e = (int)((u >> 52) & 0x7ff);
   const unsigned long long m = u & ((1ull << 52) - 1);
   constexpr int kExpBits = 15 - kMant;
   constexpr uint32_t kInf = ((1u << kExpBits) - 1) << kMant;
   if (e == 0x7ff) return (uint16_t)(sign | kInf | (m ? (1u << (kMant - 1)) : 0u));
+  if (e == 0) return (uint16_t)sign;            // zero; fp64 subnormals are far below the 16-bit ones
+  e += k;                                       // exponent of x * 2^k (may leave fp64's range: handled below)
   const int E = e - 1023 + kBias;             // biased target exponent
   if (E >= (1 << kExpBits) - 1) return (uint16_t)(sign | kInf);
   if (E >= 1) {
@@ -60,14 +71,13 @@ __device__ inline uint16_t f64_to_f16bits(double x) {
     if (rem > half || (rem == half && (keep & 1))) r += 1;   // may carry into the exponent / infinity
     return (uint16_t)(sign | r);
   }
-  if (e == 0) return (uint16_t)sign;            // fp64 subnormals are far below the 16-bit ones
-  // target subnormal: value = mf 2^(e-1075) = k * 2^(1 - kBias - kMant)
+  // target subnormal: value = mf 2^(e-1075) = q * 2^(1 - kBias - kMant)
   const unsigned long long mf = m | (1ull << 52);
   const int s = 1075 - e - (kBias - 1 + kMant);  // right shift taking mf to units of the quantum
   if (s > 63) return (uint16_t)sign;
-  const unsigned long long k = mf >> s, rem = mf & ((1ull << s) - 1), half = 1ull << (s - 1);
-  uint32_t r = (uint32_t)k;
-  if (rem > half || (rem == half && (k & 1))) r += 1;
+  const unsigned long long q = mf >> s, rem = mf & ((1ull << s) - 1), half = 1ull << (s - 1);
+  uint32_t r = (uint32_t)q;
+  if (rem > half || (rem == half && (q & 1))) r += 1;
   return (uint16_t)(sign | r);
 }
 
@@ -80,22 +90,11 @@ __device__ inline int pow2_exponent(double s) {
   return (int)(((unsigned long long)__double_as_longlong(s) >> 52) & 0x7ff) - 1023;
 }
 
-// f64_to_u16(x * 2^k) with integer operations only: the scaling moves the
-// exponent field (exact for normal x whose scaled value stays normal; below
-// fp64's normal range the value is far below every 16-bit format's smallest
-// subnormal and rounds to a signed zero, above it the result is infinite);
-// zeros, fp64 subnormals, infinities and NaNs take the fp64 multiply, which is
-// exact or IEEE there too.  GB300's fp64 rate is low enough that one fp64
-// multiply per entry would cost as much as reading the matrix.
+// f64_to_u16(x * 2^k): the power-of-two scale is an exponent add inside the
+// conversion (GB300's fp64 rate is low enough that one fp64 multiply per
+// entry would cost as much as reading the matrix).
 __device__ inline uint16_t f64_to_u16_pow2(double x, int k, int fmt) {
-  if (k == 0) return f64_to_u16(x, fmt);
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((u >> 52) & 0x7ff);
-  if (e == 0 || e == 0x7ff) return f64_to_u16(x * ldexp(1.0, k), fmt);
-  const int e2 = e + k;
-  if (e2 <= 0) return f64_to_u16(__longlong_as_double((long long)(u & 0x8000000000000000ull)), fmt);
-  if (e2 >= 0x7ff) return f64_to_u16(__longlong_as_double((long long)((u & 0x8000000000000000ull) | 0x7ff0000000000000ull)), fmt);
-  return f64_to_u16(__longlong_as_double((long long)((u & ~(0x7ffull << 52)) | ((unsigned long long)e2 << 52))), fmt);
+  return fmt == kBF16 ? f64_to_f16bits<7, 127>(x, k) : f64_to_f16bits<10, 15>(x, k);
 }
 
 // A (fp64, column major) -> LU (16-bit, column major), optionally of the
@@ -167,13 +166,13 @@ __global__ void __launch_bounds__(256) row_absmax_kernel(int64_t n, const double
   const double* col = A + i + j0 * lda;
   int64_t j = j0;
   if (vec) {
-    for (; j + 4 <= j1; j += 4) {
-      double2 v[4];
+    for (; j + 8 <= j1; j += 8) {   // eight 16-byte loads in flight per thread
+      double2 v[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = __ldcs(reinterpret_cast<const double2*>(col + (int64_t)u * lda));
-      col += 4 * lda;
+      for (int u = 0; u < 8; ++u) v[u] = __ldcs(reinterpret_cast<const double2*>(col + (int64_t)u * lda));
+      col += 8 * lda;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         m0 = max(m0, abs_bits(v[u].x));
         m1 = max(m1, abs_bits(v[u].y));
       }
@@ -215,23 +214,39 @@ __global__ void row_scale_kernel(int64_t n, double* rs) {
   if (i < n) rs[i] = pow2_inverse(rs[i]);
 }
 
-// pass 2: one CTA per column: cs_j = 2^-floor(log2 max_i |rs_i a_ij|)
+// pass 2: kBalCols columns per CTA (each row's rs read once for all of
+// them): cs_j = 2^-floor(log2 max_i |rs_i a_ij|)
+constexpr int kBalCols = 8;
 __global__ void __launch_bounds__(256) col_scale_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
                                                         const double* __restrict__ rs, double* __restrict__ cs) {
-  __shared__ int wmax[8];
-  const int64_t j = blockIdx.x;
-  const double* col = A + j * lda;
-  int m = kZeroLog;
+  __shared__ int wmax[8][kBalCols];
+  const int64_t j0 = (int64_t)blockIdx.x * kBalCols;
+  const int nc = (int)min((int64_t)kBalCols, n - j0);
+  int m[kBalCols];
+#pragma unroll
+  for (int c = 0; c < kBalCols; ++c) m[c] = kZeroLog;
   for (int64_t i = threadIdx.x; i < n; i += 256) {
-    const int l = floor_log2_abs(__ldcs(col + i));
-    m = max(m, l >= kBadLog ? kBadLog : (l <= kZeroLog ? kZeroLog : l + pow2_exponent(rs[i])));
+    const int er = pow2_exponent(rs[i]);
+    double a[kBalCols];
+#pragma unroll
+    for (int c = 0; c < kBalCols; ++c) a[c] = c < nc ? __ldcs(A + i + (j0 + c) * lda) : 0.0;
+#pragma unroll
+    for (int c = 0; c < kBalCols; ++c) {
+      const int l = floor_log2_abs(a[c]);
+      m[c] = max(m[c], l >= kBadLog ? kBadLog : (l <= kZeroLog ? kZeroLog : l + er));
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+#pragma unroll
+  for (int c = 0; c < kBalCols; ++c) {
+    for (int o = 16; o > 0; o >>= 1) m[c] = max(m[c], __shfl_xor_sync(0xffffffffu, m[c], o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5][c] = m[c];
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < 8; ++w) m = max(m, wmax[w]);
-    cs[j] = (m == kZeroLog || m == kBadLog) ? 1.0 : ldexp(1.0, -m);
+  if (threadIdx.x < nc) {
+    const int c = threadIdx.x;
+    int mm = wmax[0][c];
+    for (int w = 1; w < 8; ++w) mm = max(mm, wmax[w][c]);
+    cs[j0 + c] = (mm == kZeroLog || mm == kBadLog) ? 1.0 : ldexp(1.0, -mm);
   }
 }
 
@@ -1248,7 +1263,7 @@ cudaError_t launch_balance(int64_t n, const double* A, int64_t lda, int prec, do
   dim3 g1((unsigned)cdiv<int64_t>(n, kBalRows), (unsigned)cdiv<int64_t>(n, kBalChunk));
   row_absmax_kernel<<<g1, 256, 0, st>>>(n, A, lda, reinterpret_cast<unsigned long long*>(rs));
   row_scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, rs);
-  col_scale_kernel<<<(unsigned)n, 256, 0, st>>>(n, A, lda, rs, cs);
+  col_scale_kernel<<<(unsigned)cdiv<int64_t>(n, kBalCols), 256, 0, st>>>(n, A, lda, rs, cs);
   const double s = prec == HPMXP_FP16 ? 4096.0 : 1.0;
   if (s != 1.0) {
     format_scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, rs, s);
