@@ -100,35 +100,38 @@ __device__ inline uint16_t f64_to_u16_pow2(double x, int k, int fmt) {
 // A (fp64, column major) -> LU (16-bit, column major), optionally of the
 // balanced matrix diag(rs) A diag(cs) (rs, cs powers of two, so the fp64
 // products are exact and the one rounding is the cast's).  CTA (x, y)
-// converts rows 2048 y .. +2047 of column x; each thread 8 consecutive rows
-// with four 16-byte loads and one 16-byte store when aligned (LU is 16-byte
-// aligned with ldlu % 8 == 0), entry by entry otherwise.
+// converts rows 2048 y .. +2047 of columns kCastCols x .. +kCastCols-1; each
+// thread 8 consecutive rows (their scale exponents read once for all the
+// columns) with four 16-byte loads and one 16-byte store per column when
+// aligned (LU is 16-byte aligned with ldlu % 8 == 0), entry by entry otherwise.
 constexpr int kCastRows = 256 * 8;
+constexpr int kCastCols = 4;
 __global__ void __launch_bounds__(256) cast_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
                                                    uint16_t* __restrict__ LU, int64_t ldlu, int fmt,
                                                    const double* __restrict__ rs, const double* __restrict__ cs) {
-  const int64_t j = blockIdx.x;
   const int64_t i = (int64_t)blockIdx.y * kCastRows + 8 * (int64_t)threadIdx.x;
   if (i >= n) return;
-  const double* src = A + i + j * lda;
-  uint16_t* dst = LU + i + j * ldlu;
-  // exponents of the power-of-two scales of this column and of the thread's rows
-  const int kc = cs ? pow2_exponent(cs[j]) : 0;
-  int kr[8];
+  int er[8];   // exponents of the power-of-two row scales of the thread's rows
 #pragma unroll
-  for (int k = 0; k < 8; ++k) kr[k] = (rs && i + k < n) ? kc + pow2_exponent(rs[i + k]) : kc;
-  if (i + 8 <= n && (((uintptr_t)src) & 15) == 0) {
-    double2 v[4];
+  for (int k = 0; k < 8; ++k) er[k] = (rs && i + k < n) ? pow2_exponent(rs[i + k]) : 0;
+  const int64_t jend = min((int64_t)(blockIdx.x + 1) * kCastCols, n);
+  for (int64_t j = (int64_t)blockIdx.x * kCastCols; j < jend; ++j) {
+    const double* src = A + i + j * lda;
+    uint16_t* dst = LU + i + j * ldlu;
+    const int kc = cs ? pow2_exponent(cs[j]) : 0;
+    if (i + 8 <= n && (((uintptr_t)src) & 15) == 0) {
+      double2 v[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = __ldcs(reinterpret_cast<const double2*>(src) + k);
-    uint32_t w[4];
+      for (int k = 0; k < 4; ++k) v[k] = __ldcs(reinterpret_cast<const double2*>(src) + k);
+      uint32_t w[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      w[k] = (uint32_t)f64_to_u16_pow2(v[k].x, kr[2 * k], fmt) |
-             ((uint32_t)f64_to_u16_pow2(v[k].y, kr[2 * k + 1], fmt) << 16);
-    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-  } else {
-    for (int k = 0; k < 8 && i + k < n; ++k) dst[k] = f64_to_u16_pow2(src[k], kr[k], fmt);
+      for (int k = 0; k < 4; ++k)
+        w[k] = (uint32_t)f64_to_u16_pow2(v[k].x, kc + er[2 * k], fmt) |
+               ((uint32_t)f64_to_u16_pow2(v[k].y, kc + er[2 * k + 1], fmt) << 16);
+      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+      for (int k = 0; k < 8 && i + k < n; ++k) dst[k] = f64_to_u16_pow2(src[k], kc + er[k], fmt);
+    }
   }
 }
 
@@ -1246,8 +1249,8 @@ SideStream& side_stream(int dev) {
 cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int64_t ldo, int fmt, cudaStream_t st,
                         const double* rs, const double* cs) {
   void* tok = prof_begin(st);
-  cast_kernel<<<dim3((unsigned)n, (unsigned)cdiv<int64_t>(n, kCastRows)), 256, 0, st>>>(n, A, lda, (uint16_t*)out,
-                                                                                    ldo, fmt, rs, cs);
+  cast_kernel<<<dim3((unsigned)cdiv<int64_t>(n, kCastCols), (unsigned)cdiv<int64_t>(n, kCastRows)), 256, 0, st>>>(
+      n, A, lda, (uint16_t*)out, ldo, fmt, rs, cs);
   prof_end(tok, kProfCast, 10.0 * (double)n * (double)n, st);
   count_launches(1);
   return cudaGetLastError();
