@@ -55,8 +55,11 @@ typedef enum { HPMXP_BF16 = 0, HPMXP_FP16 = 1, HPMXP_FP8_E4M3 = 2 } hpmxp_prec;
  * diagonal-scaling discussion of section "Experimental Results"). */
 typedef enum {
   HPMXP_DIAG_DOMINANT = 0, /* a_ii = sum_{j!=i} |a_ij| + margin: strictly row diagonally dominant */
-  HPMXP_DIAG_SQRTN = 1,    /* a_ii = r_ii + sign(r_ii) sqrt(n): the sqrt(n) scaling the paper recommends */
-  HPMXP_DIAG_NONE = 2      /* raw uniform entries, no diagonal scaling */
+  HPMXP_DIAG_SQRTN = 1,    /* a_ii = r_ii + sign(r_ii) c sqrt(n) with c = margin: the sqrt(n) scaling the
+                              paper recommends (c = 1), and its 5/8 sqrt(n) curve (c = 0.625) */
+  HPMXP_DIAG_NONE = 2,     /* raw uniform entries, no diagonal scaling */
+  HPMXP_DIAG_DEPARTURE = 3 /* a_ii = rho sum_{j!=i} |a_ij| with rho = margin > 0: a controlled departure
+                              from diagonal dominance (rho < 1), weak dominance at rho = 1 */
 } hpmxp_diag;
 
 /* Human-readable name of a status code (static storage; never NULL). */
@@ -74,9 +77,11 @@ int hpmxp_version(void);
  * after t+1 steps, reached by skip-ahead.  The top 52 bits u of a state give
  * the value (2u + 1 - 2^52) 2^-53, uniform in (-0.5, 0.5) and never 0.
  * Entry A(i,j) is draw i + j*n, b(i,r) is draw n*n + i + r*n.  The diagonal is
- * then replaced as `diag_mode` says; for DOMINANT the off-diagonal magnitudes
- * are summed exactly in 128-bit integer arithmetic and a_ii =
- * fl(fl(S_i) 2^-53 + margin), so the result is bit-for-bit reproducible.
+ * then replaced as `diag_mode` says; for DOMINANT and DEPARTURE the
+ * off-diagonal magnitudes are summed exactly in 128-bit integer arithmetic and
+ * a_ii = fl(fl(S_i) 2^-53 + margin) (DOMINANT) or fl(fl(S_i) 2^-53 margin)
+ * (DEPARTURE); SQRTN gives fl(r_ii + sign(r_ii) fl(margin fl(sqrt(n)))); so the
+ * result is bit-for-bit reproducible.  DEPARTURE needs margin > 0.
  *
  *   n        1 <= n <= 131072
  *   A        out, n x n fp64, column major, lda >= n
@@ -249,6 +254,36 @@ size_t hpmxp_residual_workspace(int64_t n, int64_t nrhs);
 hpmxp_status hpmxp_residual(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
                             const double* b, int64_t ldb, int64_t nrhs, double* scaled_resid,
                             void* ws, size_t ws_bytes, void* stream);
+
+/* r = b - A x for every column, fp64 (the refinement's residual kernels):
+ *   r   out, n x nrhs fp64 (ldr >= n); the other arguments as hpmxp_residual. */
+hpmxp_status hpmxp_residual_vector(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
+                                   const double* b, int64_t ldb, int64_t nrhs, double* r, int64_t ldr, void* ws,
+                                   size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* FP64 LU without pivoting, for the study of section "Experimental Results"
+ * (Figs. 2-4: the largest pivot and the residual norms of 64-bit LU with and
+ * without partial pivoting on matrices with and without diagonal scaling).
+ *
+ * hpmxp_lu_f64 factors A in place, A = L U (unit-lower L below the diagonal,
+ * U on and above), right-looking with block width 64, fp64 arithmetic in the
+ * plain order: unblocked diagonal blocks (l = a / pivot, then one fused
+ * multiply-add per update, pivots ascending), panels by substitution (terms
+ * ascending, one division per L entry), trailing update one fp64 accumulation
+ * over the 64 terms in ascending order per entry.  Returns HPMXP_EBREAKDOWN on
+ * a zero or non-finite pivot (the factors then hold what was computed).
+ *   A    in/out, n x n fp64, lda >= n
+ *   ws   scratch of hpmxp_lu_f64_workspace(n) bytes (256-byte aligned)
+ * Synchronizes `stream`.
+ *
+ * hpmxp_lu_solve_f64 overwrites B (n x nrhs, 1 <= nrhs <= 64) with
+ * U^{-1} L^{-1} B for those factors (64-row blocks: substitution in the
+ * diagonal block, a fp64 product into the rows after it). */
+size_t hpmxp_lu_f64_workspace(int64_t n);
+hpmxp_status hpmxp_lu_f64(int64_t n, double* A, int64_t lda, void* ws, size_t ws_bytes, void* stream);
+hpmxp_status hpmxp_lu_solve_f64(int64_t n, const double* LU, int64_t ld, double* B, int64_t ldb, int64_t nrhs,
+                                void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Measurement support (the paper has no counterpart; used by the benchmark).

@@ -6,7 +6,8 @@ import this package; the solver library never does, and the oracle shares no
 code with it.
 
 Formats: 0 BF16, 1 FP16, 2 E4M3, 3 FP32, 4 FP64 (identity).
-Diagonal modes: 0 DOMINANT (row absolute sum + margin), 1 SQRTN, 2 NONE.
+Diagonal modes: 0 DOMINANT (row absolute sum + margin), 1 SQRTN (margin sqrt(n)), 2 NONE,
+3 DEPARTURE (margin times the row absolute sum).
 Status codes returned by ``solve_ir``: 0 ok, 4 no convergence, 5 breakdown.
 """
 from __future__ import annotations
@@ -26,7 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 BF16, FP16, E4M3, FP32, FP64 = 0, 1, 2, 3, 4
-DOMINANT, SQRTN, NONE = 0, 1, 2
+DOMINANT, SQRTN, NONE, DEPARTURE = 0, 1, 2, 3
 
 
 def _cpu_has_fma() -> bool:
@@ -195,7 +196,8 @@ def factor(A, fmt: int = BF16, nb: int = 128, fmt_update: int | None = None, rs=
 
 def factor_plain(A, fmt: int = BF16, nb: int = 128) -> tuple[np.ndarray, int]:
     """The plain reading of Fig. 1: unblocked fp32 diagonal block of width nb,
-    fp32 forward / back substitution for the panels, no inverses."""
+    fp32 forward / back substitution for the panels, no inverses.  With
+    fmt = FP64 the arithmetic is fp64 (nb 64 allowed: the fp64 study's LU)."""
     A = _f64(A)
     n = A.shape[0]
     LU = np.empty((n, n), dtype=np.float64, order="F")

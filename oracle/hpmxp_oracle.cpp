@@ -120,20 +120,26 @@ inline double q_to_value(int64_t q) { return std::ldexp((double)q, -53); }
 // (the compiler's conversion follows the IEEE default rounding mode).
 inline double u128_to_double(u128 v) { return (double)v; }
 
-enum DiagMode { DIAG_DOMINANT = 0, DIAG_SQRTN = 1, DIAG_NONE = 2 };
+enum DiagMode { DIAG_DOMINANT = 0, DIAG_SQRTN = 1, DIAG_NONE = 2, DIAG_DEPARTURE = 3 };
 
 // Diagonal of row i from its exact off-diagonal magnitude sum S (an integer
 // number of 2^-53 units), the raw draw q_ii and the mode.
 //  * DOMINANT: a_ii = fl(fl(S) * 2^-53 + margin): the row's absolute sum plus
 //    the margin, so A is strictly row diagonally dominant by `margin`.
-//  * SQRTN: a_ii = fl(q_ii 2^-53 + sign(q_ii) * fl(sqrt(n))), the sqrt(n)
-//    diagonal scaling the experiments section recommends.
+//  * SQRTN: a_ii = fl(q_ii 2^-53 + sign(q_ii) * fl(c * fl(sqrt(n)))) with
+//    c = margin: the sqrt(n) diagonal scaling the experiments section
+//    recommends (c = 1) and its 5/8 sqrt(n) curve (c = 5/8).
 //  * NONE: the raw draw (uniform entries without diagonal scaling).
+//  * DEPARTURE: a_ii = fl(fl(S) * 2^-53 * rho), rho = margin: the "departure
+//    from diagonal dominance" of section "Matrix Generation", whose formula
+//    the paper does not print; reading: the diagonal is the fraction rho of
+//    the row's off-diagonal absolute sum (rho < 1 departs from dominance).
 double diag_value(int mode, u128 S, int64_t q_ii, double margin, int64_t n) {
   switch (mode) {
     case DIAG_DOMINANT: return std::ldexp(u128_to_double(S), -53) + margin;
+    case DIAG_DEPARTURE: return std::ldexp(u128_to_double(S), -53) * margin;
     case DIAG_SQRTN: {
-      const double r = std::sqrt((double)n);
+      const double r = margin * std::sqrt((double)n);
       return q_to_value(q_ii) + (q_ii > 0 ? r : -r);
     }
     default: return q_to_value(q_ii);
@@ -619,6 +625,7 @@ double oracle_draw_value(uint64_t seed, uint64_t t) {
 int oracle_generate(int64_t n, uint64_t seed, double margin, int mode, double* A, int64_t lda,
                     double* b, int64_t ldb, int64_t nrhs) {
   if (n < 1 || lda < n || (nrhs > 0 && ldb < n) || n > (int64_t(1) << 17)) return -1;
+  if (mode < DIAG_DOMINANT || mode > DIAG_DEPARTURE || (mode == DIAG_DEPARTURE && !(margin > 0.0))) return -1;
   std::vector<u128> S((size_t)n, 0);
   std::vector<int64_t> qd((size_t)n, 0);
   uint64_t s = seed;
@@ -644,6 +651,7 @@ int oracle_generate(int64_t n, uint64_t seed, double margin, int mode, double* A
 int oracle_generate_rows(int64_t n, uint64_t seed, double margin, int mode, const int64_t* rows,
                          int64_t nrows, double* out) {
   if (n < 1 || n > (int64_t(1) << 17)) return -1;
+  if (mode < DIAG_DOMINANT || mode > DIAG_DEPARTURE || (mode == DIAG_DEPARTURE && !(margin > 0.0))) return -1;
   uint64_t an, cn;
   lcg_jump((uint64_t)n, &an, &cn);
   for (int64_t r = 0; r < nrows; ++r) {
@@ -683,12 +691,13 @@ int oracle_factor(int64_t n, const double* A, int64_t lda, int fmt, int fmt_upda
 // The factorization in the method's scheme (plain = 0, above) or in the plain
 // reading of Fig. 1 (plain = 1: unblocked fp32 diagonal block of width nb,
 // fp32 substitution panels, no inverses; no fp8 update; with FP64 storage the
-// arithmetic is fp64, the exact-arithmetic special case).
+// arithmetic is fp64, the exact-arithmetic special case; nb may also be 64,
+// the block width of the fp64 study factorization).
 // rs, cs (both or neither): factor diag(rs) A diag(cs) instead of A (the
 // powers of two are applied in fp64, exactly, before the one rounding).
 int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
                          double* LU, int64_t ldlu, int plain, const double* rs, const double* cs) {
-  if (n < 1 || lda < n || ldlu < n || !(nb == 128 || nb == 256 || nb == 512)) return -1;
+  if (n < 1 || lda < n || ldlu < n || !(nb == 128 || nb == 256 || nb == 512 || (plain && nb == 64))) return -1;
   if (plain && fmt_update == FMT_E4M3) return -1;
   bool ok;
   if (fmt == FMT_FP64) {

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libhpmxp.so")
-SOURCES = ["gen.cu", "lu.cu", "gemm_tc.cu", "ir.cu", "capi.cu", "prof.cu", "serve.cu"]
+SOURCES = ["gen.cu", "lu.cu", "gemm_tc.cu", "ir.cu", "capi.cu", "prof.cu", "serve.cu", "study.cu"]
 HEADERS = ["internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -21,7 +21,7 @@ _lib = None
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ETIMEOUT, EINVALID = range(8)
 BF16, FP16, FP8_E4M3 = 0, 1, 2
-DIAG_DOMINANT, DIAG_SQRTN, DIAG_NONE = 0, 1, 2
+DIAG_DOMINANT, DIAG_SQRTN, DIAG_NONE, DIAG_DEPARTURE = 0, 1, 2, 3
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN",
                 6: "ETIMEOUT", 7: "EINVALID"}
 
@@ -91,6 +91,10 @@ def load():
                                        ctypes.POINTER(IRParams), ctypes.POINTER(IRInfo), P, sz, P], i32),
             "hpmxp_residual_workspace": ([i64, i64], sz),
             "hpmxp_residual": ([i64, P, i64, P, i64, P, i64, i64, P, P, sz, P], i32),
+            "hpmxp_residual_vector": ([i64, P, i64, P, i64, P, i64, i64, P, i64, P, sz, P], i32),
+            "hpmxp_lu_f64_workspace": ([i64], sz),
+            "hpmxp_lu_f64": ([i64, P, i64, P, sz, P], i32),
+            "hpmxp_lu_solve_f64": ([i64, P, i64, P, i64, i64, P], i32),
             "hpmxp_test_gemm": ([i32, i32, i32, P, i64, P, i64, P, i64, P, i64, i32, ctypes.c_float, i32, i32,
                                  P, i32, P, i32, i32, P, P], i32),
             "hpmxp_test_cast": ([i64, P, i64, i32, P, i64, P], i32),
@@ -198,6 +202,22 @@ def hpmxp_residual_workspace(n, nrhs):
 
 def hpmxp_residual(n, A, lda, x, ldx, b, ldb, nrhs, out, ws, ws_bytes, stream):
     return _call("hpmxp_residual", n, A, lda, x, ldx, b, ldb, nrhs, out, ws, ws_bytes, stream)
+
+
+def hpmxp_residual_vector(n, A, lda, x, ldx, b, ldb, nrhs, r, ldr, ws, ws_bytes, stream):
+    return _call("hpmxp_residual_vector", n, A, lda, x, ldx, b, ldb, nrhs, r, ldr, ws, ws_bytes, stream)
+
+
+def hpmxp_lu_f64_workspace(n):
+    return _call("hpmxp_lu_f64_workspace", n)
+
+
+def hpmxp_lu_f64(n, A, lda, ws, ws_bytes, stream):
+    return _call("hpmxp_lu_f64", n, A, lda, ws, ws_bytes, stream)
+
+
+def hpmxp_lu_solve_f64(n, LU, ld, B, ldb, nrhs, stream):
+    return _call("hpmxp_lu_solve_f64", n, LU, ld, B, ldb, nrhs, stream)
 
 
 def hpmxp_launch_count() -> int:

@@ -33,6 +33,9 @@ hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, i
                       cudaStream_t st, const double* rs = nullptr, const double* cs = nullptr);
 hpmxp_status residual_check(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
                             const double* b, int64_t ldb, int64_t nrhs, double* out, void* ws, cudaStream_t st);
+hpmxp_status residual_vector(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
+                             const double* b, int64_t ldb, int64_t nrhs, double* r, int64_t ldr, void* ws,
+                             cudaStream_t st);
 
 }  // namespace hpmxp
 
@@ -68,7 +71,8 @@ hpmxp_status hpmxp_generate(int64_t n, uint64_t seed, double margin, int diag_mo
                             double* b, int64_t ldb, int64_t nrhs, void* ws, size_t ws_bytes, void* stream) {
   if (n < 1 || n > kMaxN || !A || lda < n || nrhs < 0 || (nrhs > 0 && (!b || ldb < n)) || !ws)
     return HPMXP_EINVAL;
-  if (diag_mode < HPMXP_DIAG_DOMINANT || diag_mode > HPMXP_DIAG_NONE) return HPMXP_EINVAL;
+  if (diag_mode < HPMXP_DIAG_DOMINANT || diag_mode > HPMXP_DIAG_DEPARTURE) return HPMXP_EINVAL;
+  if (diag_mode == HPMXP_DIAG_DEPARTURE && !(margin > 0.0)) return HPMXP_EINVAL;
   if (!aligned(ws, 16)) return HPMXP_EINVAL;
   if (ws_bytes < hpmxp_generate_workspace(n)) return HPMXP_ENOMEM;
   cudaError_t e = launch_generate(n, seed, margin, diag_mode, A, lda, b, ldb, nrhs, (unsigned long long*)ws,
@@ -161,6 +165,37 @@ hpmxp_status hpmxp_residual(int64_t n, const double* A, int64_t lda, const doubl
     return HPMXP_EINVAL;
   if (ws_bytes < residual_ws_bytes(n, nrhs)) return HPMXP_ENOMEM;
   return residual_check(n, A, lda, x, ldx, b, ldb, nrhs, scaled_resid, ws, (cudaStream_t)stream);
+}
+
+hpmxp_status hpmxp_residual_vector(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
+                                   const double* b, int64_t ldb, int64_t nrhs, double* r, int64_t ldr, void* ws,
+                                   size_t ws_bytes, void* stream) {
+  if (n < 1 || n > kMaxN || !A || lda < n || !x || ldx < n || !b || ldb < n || !r || ldr < n || nrhs < 1 ||
+      nrhs > 8 || !ws || !aligned(ws, 256))
+    return HPMXP_EINVAL;
+  if (ws_bytes < residual_ws_bytes(n, nrhs)) return HPMXP_ENOMEM;
+  return residual_vector(n, A, lda, x, ldx, b, ldb, nrhs, r, ldr, ws, (cudaStream_t)stream);
+}
+
+size_t hpmxp_lu_f64_workspace(int64_t n) { return n < 1 ? 0 : 256; }
+
+hpmxp_status hpmxp_lu_f64(int64_t n, double* A, int64_t lda, void* ws, size_t ws_bytes, void* stream) {
+  if (n < 1 || n > kMaxN || !A || lda < n || !ws || !aligned(ws, 256)) return HPMXP_EINVAL;
+  if (ws_bytes < hpmxp_lu_f64_workspace(n)) return HPMXP_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* status = (uint32_t*)ws;
+  cudaError_t e = cudaMemsetAsync(status, 0, 4, st);
+  if (e == cudaSuccess) e = lu_f64(n, A, lda, status, st);
+  uint32_t word = 0;
+  if (e == cudaSuccess) e = read_to_host(&word, status, 4, st);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  return status_from_word(word);
+}
+
+hpmxp_status hpmxp_lu_solve_f64(int64_t n, const double* LU, int64_t ld, double* B, int64_t ldb, int64_t nrhs,
+                                void* stream) {
+  if (n < 1 || n > kMaxN || !LU || ld < n || !B || ldb < n || nrhs < 1 || nrhs > 64) return HPMXP_EINVAL;
+  return status_from_cuda(lu_solve_f64(n, LU, ld, B, ldb, nrhs, (cudaStream_t)stream));
 }
 
 // ---------------------------------------------------------------------------

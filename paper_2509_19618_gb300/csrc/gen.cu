@@ -87,20 +87,24 @@ __global__ void __launch_bounds__(kRows) gen_matrix_kernel(int64_t n, uint64_t s
   if (part) atomic_add_u128(sums + 2 * i, part);
 }
 
-// Phase 2: the diagonal (section "Matrix Generation"; the sqrt(n) variant from
-// section "Experimental Results").
+// Phase 2: the diagonal (section "Matrix Generation": diagonal dominance and
+// its "departure"; the c sqrt(n) variants from section "Experimental Results").
+//   DOMINANT   a_ii = fl(fl(S_i) 2^-53 + margin)
+//   SQRTN      a_ii = fl(q_ii 2^-53 + sign(q_ii) fl(margin fl(sqrt(n))))   (margin = c)
+//   NONE       a_ii = q_ii 2^-53
+//   DEPARTURE  a_ii = fl(fl(S_i) 2^-53 margin)                            (margin = rho)
 __global__ void gen_diag_kernel(int64_t n, uint64_t seed, double margin, int mode, double* A,
                                 int64_t lda, const unsigned long long* sums) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double v;
-  if (mode == HPMXP_DIAG_DOMINANT) {
+  if (mode == HPMXP_DIAG_DOMINANT || mode == HPMXP_DIAG_DEPARTURE) {
     const double S = u128_to_f64(sums[2 * i + 1], sums[2 * i]);
-    v = __dadd_rn(S * 0x1p-53, margin);
+    v = mode == HPMXP_DIAG_DOMINANT ? __dadd_rn(S * 0x1p-53, margin) : __dmul_rn(S * 0x1p-53, margin);
   } else {
     const Affine p = lcg_power((uint64_t)(i + i * n) + 1);
     const int64_t q = state_q(p.a * seed + p.c);
-    const double r = __dsqrt_rn((double)n);
+    const double r = __dmul_rn(margin, __dsqrt_rn((double)n));
     v = mode == HPMXP_DIAG_SQRTN ? __dadd_rn(q_value(q), q > 0 ? r : -r) : q_value(q);
   }
   A[i + i * lda] = v;
@@ -192,7 +196,8 @@ extern "C" hpmxp_status hpmxp_generate_noalloc(int64_t n, uint64_t seed, double 
   using namespace hpmxp;
   if (n > kNoallocMaxN) return HPMXP_ENOMEM;
   if (n < 1 || !A || lda < n || nrhs < 0 || (nrhs > 0 && (!b || ldb < n))) return HPMXP_EINVAL;
-  if (diag_mode < HPMXP_DIAG_DOMINANT || diag_mode > HPMXP_DIAG_NONE) return HPMXP_EINVAL;
+  if (diag_mode < HPMXP_DIAG_DOMINANT || diag_mode > HPMXP_DIAG_DEPARTURE) return HPMXP_EINVAL;
+  if (diag_mode == HPMXP_DIAG_DEPARTURE && !(margin > 0.0)) return HPMXP_EINVAL;
   unsigned long long* sums = nullptr;
   cudaError_t e = row_sums_address(&sums);
   if (e != cudaSuccess) return status_from_cuda(e);

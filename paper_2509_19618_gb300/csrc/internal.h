@@ -128,6 +128,11 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
                     int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st, const double* rs = nullptr,
                     const double* cs = nullptr);
 
+// study.cu: fp64 LU without pivoting (block 64, in place) and its solves
+cudaError_t lu_f64(int64_t n, double* A, int64_t ld, uint32_t* status, cudaStream_t st);
+cudaError_t lu_solve_f64(int64_t n, const double* LU, int64_t ld, double* X, int64_t ldx, int64_t nrhs,
+                         cudaStream_t st);
+
 // ir.cu
 size_t solve_ws_bytes(int64_t n, int64_t nrhs, int restart);
 size_t solve_a32_bytes(int64_t n);   // optional fp32 copy of A after the solve workspace

@@ -1237,6 +1237,16 @@ hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, con
   return status_from_word(word);
 }
 
+// r = b - A x (fp64, the refinement's residual kernels), every column.
+hpmxp_status residual_vector(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
+                             const double* b, int64_t ldb, int64_t nrhs, double* r, int64_t ldr, void* ws,
+                             cudaStream_t st) {
+  SolveWs w = carve_solve(ws, n, nrhs, 1);
+  cudaError_t e = cudaMemsetAsync(w.st, 0, sizeof(RhsState) * kMaxK, st);
+  if (e == cudaSuccess) e = residual(n, (int)nrhs, A, lda, x, ldx, b, ldb, r, ldr, 0, 0, w, st);
+  return status_from_cuda(e);
+}
+
 hpmxp_status residual_check(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
                             const double* b, int64_t ldb, int64_t nrhs, double* out, void* ws, cudaStream_t st) {
   SolveWs w = carve_solve(ws, n, nrhs, 1);

@@ -86,7 +86,7 @@ bool request_ok(const hpmxp_request& r) {
   if (!(nb == 128 || nb == 256 || nb == 512)) return false;
   if ((r.A == nullptr) != (r.b == nullptr)) return false;
   if (r.A && (r.lda < r.n || r.ldb < r.n)) return false;
-  if (!r.A && (r.diag_mode < HPMXP_DIAG_DOMINANT || r.diag_mode > HPMXP_DIAG_NONE)) return false;
+  if (!r.A && (r.diag_mode < HPMXP_DIAG_DOMINANT || r.diag_mode > HPMXP_DIAG_DEPARTURE)) return false;
   if (r.x && r.ldx < r.n) return false;
   const hpmxp_ir_params& p = r.params;
   if (p.restart < 1 || p.restart > 64 || p.max_iters < 0) return false;

@@ -61,10 +61,12 @@ class engine:
 # generator: integer work, bit-exact
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [1, 2, 3, 127, 128, 129, 600, 1000])
-@pytest.mark.parametrize("mode", [capi.DIAG_DOMINANT, capi.DIAG_SQRTN, capi.DIAG_NONE])
-def test_generator_bit_exact(n, mode):
-    A, b = api.generate(n, seed=1234 + n, margin=1.5, diag=mode, nrhs=3, device=DEV)
-    A_o, b_o = oracle.generate(n, 1234 + n, margin=1.5, mode=mode, nrhs=3)
+@pytest.mark.parametrize("mode,margin", [(capi.DIAG_DOMINANT, 1.5), (capi.DIAG_SQRTN, 1.0), (capi.DIAG_SQRTN, 0.625),
+                                         (capi.DIAG_NONE, 1.0), (capi.DIAG_DEPARTURE, 0.9),
+                                         (capi.DIAG_DEPARTURE, 1.0)])
+def test_generator_bit_exact(n, mode, margin):
+    A, b = api.generate(n, seed=1234 + n, margin=margin, diag=mode, nrhs=3, device=DEV)
+    A_o, b_o = oracle.generate(n, 1234 + n, margin=margin, mode=mode, nrhs=3)
     assert np.array_equal(to_np(A), A_o)
     assert np.array_equal(to_np(b), b_o)
 

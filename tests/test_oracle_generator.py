@@ -122,3 +122,35 @@ def test_rows_by_skip_ahead_match_full_generation():
 def test_bad_arguments():
     with pytest.raises(ValueError):
         oracle.generate(0, 1)
+
+
+@pytest.mark.parametrize("n,rho", [(2, 1.0), (64, 0.9), (257, 0.5), (300, 1.25)])
+def test_departure_from_dominance_exact(n, rho):
+    """DEPARTURE: a_ii = fl(fl(S_i) 2^-53 rho), S_i the exact off-diagonal sum
+    of |q_ij| (section "Matrix Generation", departure from diagonal dominance)."""
+    A, _ = oracle.generate(n, 12, margin=rho, mode=oracle.DEPARTURE)
+    D, _ = oracle.generate(n, 12, margin=1.0)
+    for i in range(n):
+        S = sum(abs(int(round(A[i, j] * 2.0**53))) for j in range(n) if j != i)
+        assert A[i, i] == (float(S) * 2.0**-53) * rho
+        exact = Fraction(S, 2**53) * Fraction(rho)      # rho times the exact off-diagonal sum
+        assert abs(Fraction(A[i, i]) - exact) <= 2 * Fraction(np.spacing(A[i, i]))
+    # the off-diagonal entries are those of every other mode
+    mask = ~np.eye(n, dtype=bool)
+    assert np.array_equal(A[mask], D[mask])
+
+
+@pytest.mark.parametrize("c", [1.0, 0.625])
+def test_sqrtn_coefficient(c):
+    n = 333
+    A, _ = oracle.generate(n, 5, margin=c, mode=oracle.SQRTN)
+    N, _ = oracle.generate(n, 5, mode=oracle.NONE)
+    r = c * np.sqrt(float(n))
+    for i in range(n):
+        q = N[i, i]
+        assert A[i, i] == q + (r if q > 0 else -r)
+
+
+def test_departure_rejects_nonpositive_ratio():
+    with pytest.raises(ValueError):
+        oracle.generate(10, 1, margin=0.0, mode=oracle.DEPARTURE)

@@ -152,7 +152,7 @@ def test_method_within_bound_of_plain_substitution_reading(n, nb):
     assert rc_m == 0 and rc_p == 0 and abs(i_m[0]["iters"] - i_p[0]["iters"]) <= 1
 
 
-@pytest.mark.parametrize("n,nb", [(3, 128), (300, 128), (700, 256), (1100, 512)])
+@pytest.mark.parametrize("n,nb", [(3, 128), (300, 128), (700, 256), (1100, 512), (300, 64), (130, 64)])
 def test_plain_reading_exact_arithmetic_is_doolittle(n, nb):
     from test_oracle_lu import doolittle
     A, _ = oracle.generate(n, 5)
