@@ -48,8 +48,20 @@ typedef enum {
 /* Low-precision format of the factorization (section "Algorithmic Framework":
  * the factors must be at least FP16-accurate; BF16 has FP32's exponent range).
  * HPMXP_FP8_E4M3 keeps BF16 factors and runs only the trailing-matrix (Schur)
- * update on OCP E4M3 operands with fp32 per-128x128-tile scales. */
-typedef enum { HPMXP_BF16 = 0, HPMXP_FP16 = 1, HPMXP_FP8_E4M3 = 2 } hpmxp_prec;
+ * update on OCP E4M3 operands with fp32 per-128x128-tile scales.
+ * HPMXP_BF16_TRAIL32 / HPMXP_FP16_TRAIL32 follow Fig. 1 with a 32-bit trailing
+ * matrix: the Schur updates (16-bit operands, fp32 accumulation) are
+ * accumulated into an fp32 copy of the matrix, and a block column / row is
+ * rounded to the 16-bit format only once, when it becomes the panel; the
+ * factors are BF16 / FP16 as with HPMXP_BF16 / HPMXP_FP16, which the solve
+ * accepts for them too. */
+typedef enum {
+  HPMXP_BF16 = 0,
+  HPMXP_FP16 = 1,
+  HPMXP_FP8_E4M3 = 2,
+  HPMXP_BF16_TRAIL32 = 3,
+  HPMXP_FP16_TRAIL32 = 4
+} hpmxp_prec;
 
 /* Diagonal of the generated matrix (section "Matrix Generation" and the
  * diagonal-scaling discussion of section "Experimental Results"). */
@@ -131,9 +143,12 @@ hpmxp_status hpmxp_generate_noalloc(int64_t n, uint64_t seed, double margin, int
  *
  *   A        in, n x n fp64, lda >= n (not modified)
  *   prec     hpmxp_prec
- *   LU       out, n x n 16-bit (BF16 for HPMXP_BF16 and HPMXP_FP8_E4M3, FP16 for
- *            HPMXP_FP16), column major; unit-lower L below the diagonal, U on
- *            and above it.  ldlu >= n, ldlu % 8 == 0, LU 16-byte aligned.
+ *   LU       out, n x n 16-bit (BF16 for HPMXP_BF16, HPMXP_FP8_E4M3 and
+ *            HPMXP_BF16_TRAIL32, FP16 for HPMXP_FP16 and HPMXP_FP16_TRAIL32),
+ *            column major; unit-lower L below the diagonal, U on and above it.
+ *            ldlu >= n, ldlu % 8 == 0, LU 16-byte aligned.
+ * The TRAIL32 formats take 4 n^2 bytes more workspace (the fp32 matrix) and
+ * run without the look-ahead schedule.
  *   ws       scratch of hpmxp_factor_workspace(n, prec, nb) bytes
  * Returns HPMXP_EBREAKDOWN when a pivot is zero or not finite (the factors are
  * then unusable). */

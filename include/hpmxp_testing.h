@@ -19,7 +19,8 @@ extern "C" {
  * Fig. 1: low-precision operands, fp32 accumulation).
  *   A      M x K, K-major 16-bit (A(i,k) at A[i*lda + k]); 8-bit E4M3 when fp8
  *   B      N x K, K-major (B(j,k) at B[j*ldb + k])
- *   C      M x N column major 16-bit: mode 0 C = st(C - A B^T); mode 1 C = st(sign * A B^T)
+ *   C      M x N column major 16-bit: mode 0 C = st(C - A B^T); mode 1 C = st(sign * A B^T);
+ *          mode 2: C fp32 (ldc in floats), C = fl32(C - A B^T) (16-bit operands only, R NULL)
  *   R      optional row-major copy of the mode-1 result (may be NULL)
  *   fmt    0 BF16, 1 FP16 (operands of the 16-bit kinds, and C / R)
  *   fp8    1: E4M3 operands with fp32 scales sA[(i/128)*sa_ld + g], sB[(j/128)*sb_ld + g]

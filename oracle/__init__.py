@@ -82,7 +82,7 @@ def lib():
             L.oracle_generate_rows.restype = i32
             L.oracle_factor.argtypes = [i64, P, i64, i32, i32, i32, P, i64]
             L.oracle_factor.restype = i32
-            L.oracle_factor_scheme.argtypes = [i64, P, i64, i32, i32, i32, P, i64, i32, P, P]
+            L.oracle_factor_scheme.argtypes = [i64, P, i64, i32, i32, i32, P, i64, i32, P, P, i32]
             L.oracle_balance.argtypes = [i64, P, i64, i32, P, P]
             L.oracle_balance.restype = None
             L.oracle_precond_scaled.argtypes = [i64, P, i64, P, P, i32, P, P]
@@ -180,15 +180,16 @@ def balance(A, fmt: int = BF16) -> tuple[np.ndarray, np.ndarray]:
 
 
 def factor(A, fmt: int = BF16, nb: int = 128, fmt_update: int | None = None, rs=None,
-           cs=None) -> tuple[np.ndarray, int]:
+           cs=None, trail32: bool = False) -> tuple[np.ndarray, int]:
     """Packed LU factors (widened to fp64) and 0 / 1 (zero or non-finite pivot);
-    with balancing scales, of diag(rs) A diag(cs)."""
+    with balancing scales, of diag(rs) A diag(cs); trail32: Fig. 1 with a
+    32-bit trailing matrix (fp32 Schur results, panels rounded to fmt once)."""
     A = _f64(A)
     n = A.shape[0]
     LU = np.empty((n, n), dtype=np.float64, order="F")
     rs, cs, ptrs = _scales(rs, cs)
     rc = lib().oracle_factor_scheme(n, _p(A), n, fmt, fmt if fmt_update is None else fmt_update, nb,
-                                    _p(LU), n, 0, *(ptrs or (None, None)))
+                                    _p(LU), n, 0, *(ptrs or (None, None)), int(trail32))
     if rc < 0:
         raise ValueError("oracle_factor: bad arguments")
     return LU, rc
@@ -201,7 +202,7 @@ def factor_plain(A, fmt: int = BF16, nb: int = 128) -> tuple[np.ndarray, int]:
     A = _f64(A)
     n = A.shape[0]
     LU = np.empty((n, n), dtype=np.float64, order="F")
-    rc = lib().oracle_factor_scheme(n, _p(A), n, fmt, fmt, nb, _p(LU), n, 1, None, None)
+    rc = lib().oracle_factor_scheme(n, _p(A), n, fmt, fmt, nb, _p(LU), n, 1, None, None, 0)
     if rc < 0:
         raise ValueError("oracle_factor_scheme: bad arguments")
     return LU, rc

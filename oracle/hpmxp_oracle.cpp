@@ -180,6 +180,8 @@ struct LowPrecLU {
   int64_t n;
   int fmt;                  // storage format of factors and trailing matrix
   int fmt_update;           // operand format of the Schur update (FMT_E4M3 = fp8 variant)
+  bool trail32 = false;     // 32-bit trailing matrix: top-level Schur results stay fp32, a block
+                            // column / row is rounded to fmt once, when it becomes the panel
   std::vector<double> M;    // working matrix, column major, ld = n
   // inverses of the 128-wide diagonal sub-blocks, indexed by block start / 128
   std::vector<std::vector<double>> Linv, Uinv;  // column major, ld = 128
@@ -308,13 +310,24 @@ struct LowPrecLU {
   // storage format even in the FP8 variant.
   void schur_update(int64_t k, int64_t b, int64_t e, bool top) {
     if (top && fmt_update == FMT_E4M3) { schur_update_fp8(k, b, e); return; }
+    const bool keep32 = top && trail32;
 #pragma omp parallel for schedule(static)
     for (int64_t j = k + b; j < e; ++j)
       for (int64_t i = k + b; i < e; ++i) {
         T acc = T(0);
         for (int64_t p = k; p < k + b; ++p) acc = fma_t<T>((T)at(i, p), (T)at(p, j), acc);
-        at(i, j) = st((double)((T)at(i, j) - acc));
+        const double v = (double)((T)at(i, j) - acc);
+        at(i, j) = keep32 ? round_fmt(v, FMT_FP32) : st(v);
       }
+  }
+
+  // 32-bit trailing matrix: block column [k, e) x [k, k+b) and block row
+  // [k, k+b) x [k+b, e) rounded to the storage format when they become the panel
+  void round_panel(int64_t k, int64_t b, int64_t e) {
+    for (int64_t j = k; j < k + b; ++j)
+      for (int64_t i = k; i < e; ++i) at(i, j) = st(at(i, j));
+    for (int64_t j = k + b; j < e; ++j)
+      for (int64_t i = k; i < k + b; ++i) at(i, j) = st(at(i, j));
   }
 
   // FP8 variant of (iii): the operands L21 and U12 are quantized per 128x128
@@ -440,6 +453,7 @@ struct LowPrecLU {
     const int64_t e = k0 + size;
     for (int64_t k = k0; k < e; k += NB) {
       const int64_t b = std::min<int64_t>(NB, e - k);
+      if (top && trail32) round_panel(k, b, e);
       if (b <= kBase) ok = getrf_base(k, b) && ok;
       else ok = lu_range(k, b, kBase, false) && ok;
       if (k + b >= e) break;
@@ -681,11 +695,11 @@ int oracle_generate_rows(int64_t n, uint64_t seed, double margin, int mode, cons
 // operands for the Schur update, anything else the storage format.
 // Returns 0, 1 on a zero or non-finite pivot, -1 on bad arguments.
 int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
-                         double* LU, int64_t ldlu, int plain, const double* rs, const double* cs);
+                         double* LU, int64_t ldlu, int plain, const double* rs, const double* cs, int trail32);
 
 int oracle_factor(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
                   double* LU, int64_t ldlu) {
-  return oracle_factor_scheme(n, A, lda, fmt, fmt_update, nb, LU, ldlu, 0, nullptr, nullptr);
+  return oracle_factor_scheme(n, A, lda, fmt, fmt_update, nb, LU, ldlu, 0, nullptr, nullptr, 0);
 }
 
 // The factorization in the method's scheme (plain = 0, above) or in the plain
@@ -695,8 +709,13 @@ int oracle_factor(int64_t n, const double* A, int64_t lda, int fmt, int fmt_upda
 // the block width of the fp64 study factorization).
 // rs, cs (both or neither): factor diag(rs) A diag(cs) instead of A (the
 // powers of two are applied in fp64, exactly, before the one rounding).
+// trail32 (method scheme, 16-bit fmt, no fp8 update): Fig. 1 with a 32-bit
+// trailing matrix: the input rounded to fp32, the top-level Schur results
+// kept in fp32, each block column / row rounded to fmt when it becomes the
+// panel.
 int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int fmt_update, int nb,
-                         double* LU, int64_t ldlu, int plain, const double* rs, const double* cs) {
+                         double* LU, int64_t ldlu, int plain, const double* rs, const double* cs, int trail32) {
+  if (trail32 && (plain || fmt == FMT_FP64 || fmt_update == FMT_E4M3)) return -1;
   if (n < 1 || lda < n || ldlu < n || !(nb == 128 || nb == 256 || nb == 512 || (plain && nb == 64))) return -1;
   if (plain && fmt_update == FMT_E4M3) return -1;
   bool ok;
@@ -714,10 +733,11 @@ int oracle_factor_scheme(int64_t n, const double* A, int64_t lda, int fmt, int f
   } else {
     LowPrecLU<float> f;
     f.n = n; f.fmt = fmt; f.fmt_update = fmt_update == FMT_E4M3 ? FMT_E4M3 : fmt;
+    f.trail32 = trail32 != 0;
     f.M.resize((size_t)n * n);
     for (int64_t j = 0; j < n; ++j)
       for (int64_t i = 0; i < n; ++i)
-        f.M[i + j * n] = round_fmt(rs ? A[i + j * lda] * rs[i] * cs[j] : A[i + j * lda], fmt);
+        f.M[i + j * n] = round_fmt(rs ? A[i + j * lda] * rs[i] * cs[j] : A[i + j * lda], trail32 ? FMT_FP32 : fmt);
     f.Linv.resize((size_t)(n + kBase - 1) / kBase);
     f.Uinv.resize(f.Linv.size());
     ok = plain ? f.lu_plain(nb) : f.lu_range(0, n, nb, true);

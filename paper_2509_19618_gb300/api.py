@@ -79,7 +79,7 @@ def generate(n: int, seed: int = 1, margin: float = 1.0, diag: int = capi.DIAG_D
 
 
 def factor_storage_dtype(prec: int):
-    return torch.float16 if prec == capi.FP16 else torch.bfloat16
+    return torch.float16 if prec in (capi.FP16, capi.FP16_TRAIL32) else torch.bfloat16
 
 
 def balance(A: ColMajor, prec: int = capi.BF16, scales: tuple | None = None, stream=None):

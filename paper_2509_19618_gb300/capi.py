@@ -20,7 +20,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ETIMEOUT, EINVALID = range(8)
-BF16, FP16, FP8_E4M3 = 0, 1, 2
+BF16, FP16, FP8_E4M3, BF16_TRAIL32, FP16_TRAIL32 = 0, 1, 2, 3, 4
 DIAG_DOMINANT, DIAG_SQRTN, DIAG_NONE, DIAG_DEPARTURE = 0, 1, 2, 3
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN",
                 6: "ETIMEOUT", 7: "EINVALID"}

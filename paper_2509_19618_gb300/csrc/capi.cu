@@ -44,7 +44,7 @@ using namespace hpmxp;
 namespace {
 constexpr int64_t kMaxN = int64_t(1) << 17;
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-bool prec_ok(int p) { return p == HPMXP_BF16 || p == HPMXP_FP16 || p == HPMXP_FP8_E4M3; }
+bool prec_ok(int p) { return p >= HPMXP_BF16 && p <= HPMXP_FP16_TRAIL32; }
 }  // namespace
 
 extern "C" {
@@ -205,13 +205,15 @@ hpmxp_status hpmxp_test_gemm(int M, int N, int K, const void* A, int64_t lda, co
                              void* C, int64_t ldc, void* R, int64_t ldr, int mode, float sign, int fmt,
                              int fp8, const float* sA, int sa_ld, const float* sB, int sb_ld, int engine,
                              uint32_t* status, void* stream) {
+  const int c32 = mode == 2;   // fp32 C, subtract mode
+  if (c32) mode = kEpiSub;
   if (M < 0 || N < 0 || K <= 0 || (K % 128) || !A || !B || !status || (mode == kEpiSub && !C) ||
       (mode != kEpiSub && mode != kEpiStore) || (fmt != kBF16 && fmt != kFP16) ||
-      (fp8 && (!sA || !sB || K > 512)) || (!C && !R))
+      (fp8 && (!sA || !sB || K > 512)) || (!C && !R) || (c32 && (R || fp8)))
     return HPMXP_EINVAL;
   GemmArgs g{};
   g.M = M; g.N = N; g.K = K; g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
-  g.R = R; g.ldr = ldr; g.mode = mode; g.sign = sign; g.fmt = fmt; g.fp8 = fp8;
+  g.R = R; g.ldr = ldr; g.mode = mode; g.sign = sign; g.fmt = fmt; g.fp8 = fp8; g.c32 = c32;
   g.sA = sA; g.sa_ld = sa_ld; g.sB = sB; g.sb_ld = sb_ld; g.status = status;
   cudaError_t e = engine == 1 ? gemm_simt(g, (cudaStream_t)stream) : gemm_tc(g, (cudaStream_t)stream);
   return status_from_cuda(e);
@@ -221,7 +223,7 @@ hpmxp_status hpmxp_test_cast(int64_t n, const double* A, int64_t lda, int prec, 
                              void* stream) {
   if (n < 1 || !A || lda < n || !out || ldo < n || (ldo % 8) || !aligned(out, 16) || !prec_ok(prec))
     return HPMXP_EINVAL;
-  return status_from_cuda(launch_cast(n, A, lda, out, ldo, prec == HPMXP_FP16 ? kFP16 : kBF16,
+  return status_from_cuda(launch_cast(n, A, lda, out, ldo, fmt_of(prec),
                                       (cudaStream_t)stream));
 }
 
@@ -232,7 +234,7 @@ hpmxp_status hpmxp_test_precond(int64_t n, const void* LU, int64_t ldlu, int pre
       !ws || !aligned(ws, 256) || !prec_ok(prec))
     return HPMXP_EINVAL;
   if (ws_bytes < solve_ws_bytes(n, nrhs, 1)) return HPMXP_ENOMEM;
-  return precond_apply(n, LU, ldlu, prec == HPMXP_FP16 ? kFP16 : kBF16, v, ldv, z, ldz, nrhs, fp32, ws,
+  return precond_apply(n, LU, ldlu, fmt_of(prec), v, ldv, z, ldz, nrhs, fp32, ws,
                        (cudaStream_t)stream);
 }
 

@@ -44,7 +44,7 @@ namespace {
 constexpr int kTJ = 128;                      // output columns per tile (MMA M, TMEM lanes)
 constexpr int kRowBytes = 128;                // K bytes per operand row per stage (one swizzle atom)
 constexpr int kStageA = kTJ * kRowBytes;      // MMA A operand: rows j (16 KiB)
-constexpr int kCBox = kTJ * 128;              // one C box: 64 rows x 128 columns (16 KiB)
+constexpr int kCBox = kTJ * 128;              // one C box: 128 bytes of rows x 128 columns (16 KiB)
 constexpr int kEpiGroups = 2;                 // epilogue groups, one per half of the tile's rows
 constexpr int kEpiThreads = 128;              // threads per epilogue group (one warp per TMEM lane quarter)
 constexpr int kThreads = 64 + kEpiGroups * kEpiThreads;
@@ -52,15 +52,18 @@ constexpr int kThreads = 64 + kEpiGroups * kEpiThreads;
 // Tile height TI (output rows i per tile = MMA N): 128, or 256 for the large
 // 16-bit products, where every operand byte an SM receives feeds twice the
 // flops (the SM's operand intake is what bounds this kernel at K >= 256).
-template <int TI>
+// CB: bytes per C element, 2 (the 16-bit factor storage) or 4 (an fp32
+// trailing matrix: C = fl32(C - acc), 128-row tiles only).
+template <int TI, int CB = 2>
 struct TileCfg {
   static constexpr int kStages = TI == 128 ? 4 : 3;
   static constexpr int kStageB = TI * kRowBytes;            // MMA B operand: rows i (16 or 32 KiB)
-  static constexpr int kBoxes = TI / 128;                   // 64-row C boxes per epilogue group
-  static constexpr int kCTile = kEpiGroups * kBoxes * kCBox;  // 32 or 64 KiB
+  static constexpr int kBoxRows = 128 / CB;                 // rows of one 128-byte C box: 64 or 32
+  static constexpr int kBoxes = TI / 2 / kBoxRows;          // C boxes per epilogue group
+  static constexpr int kCTile = kEpiGroups * kBoxes * kCBox;  // 32, 64 KiB (16-bit) or 64 KiB (fp32)
   // C tile buffers: with three, one is in the epilogue, one being stored and
-  // one loading; the 256-row tile has room for one only
-  static constexpr int kCBufs = TI == 128 ? 3 : 1;
+  // one loading; the 256-row and the fp32 tiles have room for one only
+  static constexpr int kCBufs = (TI == 128 && CB == 2) ? 3 : 1;
   static constexpr int kAhead = kCBufs >= 2 ? kCBufs - 1 : 1;   // C prefetch distance (local tiles)
   static constexpr int kReadWait = kCBufs >= 2 ? kCBufs - 2 : 0; // stores allowed to be still reading
   static constexpr size_t kSmem = 1024 + (size_t)kStages * (kStageA + kStageB) + (size_t)kCBufs * kCTile +
@@ -68,7 +71,8 @@ struct TileCfg {
 };
 // 227 KB of dynamic shared memory per CTA; two TI-column fp32 accumulators in
 // the 512 TMEM columns; a TMA box is at most 256 rows
-static_assert(TileCfg<128>::kSmem <= 232448 && TileCfg<256>::kSmem <= 232448, "shared memory per CTA");
+static_assert(TileCfg<128>::kSmem <= 232448 && TileCfg<256>::kSmem <= 232448 && TileCfg<128, 4>::kSmem <= 232448,
+              "shared memory per CTA");
 template <int TI>
 constexpr bool tile_fits() { return 2 * TI <= 512 && TI <= 256 && TI % 128 == 0; }
 static_assert(tile_fits<128>() && tile_fits<256>(), "two accumulators in TMEM, one TMA box per stage");
@@ -242,13 +246,14 @@ __device__ inline uint32_t pack16x2(float lo, float hi, int fmt) {
   return r;
 }
 
-template <int TI>
+template <int TI, int CB>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmC, TcParams p) {
-  using Cfg = TileCfg<TI>;
+  using Cfg = TileCfg<TI, CB>;
   constexpr int kStages = Cfg::kStages, kStageB = Cfg::kStageB, kCTile = Cfg::kCTile, kCBufs = Cfg::kCBufs;
-  constexpr int kBoxes = Cfg::kBoxes;
+  constexpr int kBoxes = Cfg::kBoxes, kBoxRows = Cfg::kBoxRows;
+  constexpr int kSegs = TI / 128;   // 64-row segments of an epilogue group's TI/2 rows
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);   // swizzle atoms need 1024-byte alignment
@@ -378,7 +383,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_expect_tx(c_full(b, g), kBoxes * kCBox);
 #pragma unroll
       for (int h = 0; h < kBoxes; ++h)
-        tma_load_2d(sC + b * kCTile + (g * kBoxes + h) * kCBox, &tmC, ii0 + (TI / 2) * g + 64 * h, jj0,
+        tma_load_2d(sC + b * kCTile + (g * kBoxes + h) * kCBox, &tmC, ii0 + (TI / 2) * g + kBoxRows * h, jj0,
                     c_full(b, g));
     };
     if (leader && load_c) {       // prefetch the C of the first kAhead local tiles
@@ -412,7 +417,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       // leader waited for it before it reached this barrier)
       if (kCBufs == 1 && p.has_c && !load_c) epi_barrier(g);
 #pragma unroll 1
-      for (int h = 0; h < kBoxes; ++h) {
+      for (int h = 0; h < kSegs; ++h) {   // 64-row segments of the group's rows
         const uint32_t lane_addr = lane_base + 64u * h;
         float acc[64];
         {
@@ -431,12 +436,30 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int v = 0; v < 64; ++v) acc[v] = __uint_as_float(r[v]);
           }
         }
-        if (h == kBoxes - 1) {
+        if (h == kSegs - 1) {
           // accumulator buffer free for the MMA warp as soon as it is in registers
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(acc_empty(ab));
         }
+        if constexpr (CB == 4) {
+          // fp32 C: two 32-row boxes; rows 32 q + 4 c8 .. +3 of column j in chunk c8 of box q
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const uint32_t row_addr = sC + cb * kCTile + (g * kBoxes + 2 * h + q) * kCBox + jl * 128;
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) {
+              const uint32_t ad = row_addr + ((c8 ^ (jl & 7)) << 4);
+              float cf[4];
+              asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                           : "=f"(cf[0]), "=f"(cf[1]), "=f"(cf[2]), "=f"(cf[3]) : "r"(ad) : "memory");
+#pragma unroll
+              for (int v = 0; v < 4; ++v) cf[v] = __fsub_rn(cf[v], acc[32 * q + 4 * c8 + v]);
+              asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                           ::"r"(ad), "f"(cf[0]), "f"(cf[1]), "f"(cf[2]), "f"(cf[3]) : "memory");
+            }
+          }
+        } else {
         // rows i0 + (TI/2) g + 64 h + 8 ch .. +7 of column j: eight 16-byte chunks of the swizzled box
         const uint32_t cbox = sC + cb * kCTile + (g * kBoxes + h) * kCBox;
         const uint32_t row_addr = cbox + jl * 128;
@@ -470,6 +493,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
           }
         }
+        }
       }
       if (p.has_c) {
         fence_async_smem();
@@ -477,7 +501,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (leader) {
 #pragma unroll
           for (int h = 0; h < kBoxes; ++h)
-            tma_store_2d(&tmC, i0 + (TI / 2) * g + 64 * h, j0, sC + cb * kCTile + (g * kBoxes + h) * kCBox);
+            tma_store_2d(&tmC, i0 + (TI / 2) * g + kBoxRows * h, j0, sC + cb * kCTile + (g * kBoxes + h) * kCBox);
           bulk_commit();
           // the stores issued kCBufs - 1 tiles ago (one buffer: this tile's)
           // have finished reading their buffer, which now receives the C of
@@ -523,11 +547,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D map over 16-bit units: `rows` rows of `inner` units, consecutive rows
-// `ld_bytes` apart, box = box_inner x box_rows, 128-byte swizzle, zero fill
-// outside the matrix.
+// 2-D map over 16-bit (or, with u32, 32-bit) units: `rows` rows of `inner`
+// units, consecutive rows `ld_bytes` apart, box = box_inner x box_rows,
+// 128-byte swizzle, zero fill outside the matrix.
 bool make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows, uint64_t ld_bytes,
-              uint32_t box_inner, uint32_t box_rows) {
+              uint32_t box_inner, uint32_t box_rows, bool u32 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
   if (((uintptr_t)base & 15) || (ld_bytes & 15) || inner == 0 || rows == 0) return false;
@@ -535,7 +559,8 @@ bool make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows, 
   cuuint64_t strides[1] = {ld_bytes};
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t es[2] = {1, 1};
-  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides, box, es,
+  return fn(tm, u32 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base),
+            dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -556,9 +581,11 @@ int num_sms() {
 
 namespace {
 
-template <int TI>
+template <int TI, int CB = 2>
 cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
-  using Cfg = TileCfg<TI>;
+  using Cfg = TileCfg<TI, CB>;
+  static_assert(CB == 2 || TI == 128, "fp32 C on 128-row tiles only");
+  if (CB == 4 && (g.mode != kEpiSub || g.R || !g.C)) return cudaErrorInvalidValue;
   const int esz = g.fp8 ? 1 : 2;
   const uint64_t kbytes = (uint64_t)g.K * esz;
   if (kbytes % kRowBytes) return cudaErrorInvalidValue;
@@ -569,8 +596,8 @@ cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
   TcParams p{};
   p.has_c = g.C != nullptr;
   if (p.has_c) {
-    // column-major C: inner = rows; box = 64 rows x 128 columns
-    if (!make_map(&tc, g.C, (uint64_t)g.M, (uint64_t)g.N, (uint64_t)g.ldc * 2, 64, kTJ))
+    // column-major C: inner = rows; box = 128 bytes of rows (64 16-bit or 32 fp32) x 128 columns
+    if (!make_map(&tc, g.C, (uint64_t)g.M, (uint64_t)g.N, (uint64_t)g.ldc * CB, Cfg::kBoxRows, kTJ, CB == 4))
       return cudaErrorInvalidValue;
   } else {
     tc = ta;   // never dereferenced
@@ -600,7 +627,7 @@ cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured_for.load() != dev) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<TI, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg::kSmem);
     if (e != cudaSuccess) return e;
     configured_for.store(dev);
@@ -609,7 +636,7 @@ cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
   const double flops = 2.0 * g.M * (double)g.N * g.K;
   void* tok = prof_begin(st);
   const cudaError_t e =
-      launch_pdl(gemm_tc_kernel<TI>, dim3(grid), dim3(kThreads), Cfg::kSmem, st, ta, tb, tc, p);
+      launch_pdl(gemm_tc_kernel<TI, CB>, dim3(grid), dim3(kThreads), Cfg::kSmem, st, ta, tb, tc, p);
   prof_end(tok, g.mode == kEpiSub ? kProfGemm : kProfGemmStore, flops, st);
   count_launches(1);
   return e;
@@ -628,6 +655,7 @@ bool wide_tiles_enabled() {
 
 cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (g.c32) return g.fp8 ? cudaErrorInvalidValue : gemm_tc_tiles<128, 4>(g, st);
   // 256-row tiles for the 16-bit products that fill them (M >= 256) and have
   // enough depth (K >= 256) for one C buffer to keep up
   if (!g.fp8 && g.M >= 256 && g.K >= 256 && wide_tiles_enabled()) return gemm_tc_tiles<256>(g, st);

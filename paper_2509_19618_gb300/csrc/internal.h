@@ -58,6 +58,9 @@ __host__ __device__ inline T round_up(T a, T b) { return cdiv(a, b) * b; }
 
 // 16-bit storage formats of the factors.
 enum Fmt16 { kBF16 = 0, kFP16 = 1 };
+// Storage format of the factors of a precision (hpmxp_prec).
+inline int fmt_of(int prec) { return (prec == HPMXP_FP16 || prec == HPMXP_FP16_TRAIL32) ? kFP16 : kBF16; }
+inline bool trail32_of(int prec) { return prec == HPMXP_BF16_TRAIL32 || prec == HPMXP_FP16_TRAIL32; }
 
 __device__ inline float ld16(const uint16_t* p, int fmt) {
   const uint16_t h = *p;
@@ -90,6 +93,7 @@ cudaError_t launch_generate(int64_t n, uint64_t seed, double margin, int mode, d
 // K a multiple of 128 (128-deep fp8 slices for the E4M3 kind).
 // Epilogue (`mode`):
 //   kEpiSub    C(i,j) = st(C(i,j) - acc)    C column major 16-bit, in place
+//              (fp32 C with c32: C(i,j) = fl32(C(i,j) - acc), the fp32-stored trailing matrix)
 //   kEpiStore  C(i,j) = st(sign * acc)      C column major (C may be NULL)
 //              and, if R != NULL, R(i,j) = same value, R row major (R[i*ldr + j])
 enum EpiMode { kEpiSub = 0, kEpiStore = 1 };
@@ -109,6 +113,7 @@ struct GemmArgs {
   const float* sB; int sb_ld;
   uint32_t* status;
   int max_ctas;         // 0: one CTA per SM; else at most this many (leaves SMs for concurrent work)
+  int c32;              // 1: C is fp32 column major (ldc in elements), mode kEpiSub: C = fl32(C - acc)
 };
 cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st);
 cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st);

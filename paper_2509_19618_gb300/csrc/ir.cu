@@ -1185,7 +1185,7 @@ hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, i
   Solver s;
   s.n = n; s.K = (int)nrhs; s.m = prm.restart;
   s.A = A; s.lda = lda;
-  s.LU = (const uint16_t*)LU; s.ldlu = ldlu; s.fmt = prec == HPMXP_FP16 ? kFP16 : kBF16;
+  s.LU = (const uint16_t*)LU; s.ldlu = ldlu; s.fmt = fmt_of(prec);
   s.rs = rs; s.cs = cs;
   s.B = b; s.ldb = ldb; s.X = x; s.ldx = ldx;
   s.prm = prm;

@@ -136,6 +136,37 @@ __global__ void __launch_bounds__(256) cast_kernel(int64_t n, const double* __re
 }
 
 // ---------------------------------------------------------------------------
+// 32-bit trailing matrix (Fig. 1 with 32-bit storage of the matrix being
+// updated): A (fp64, optionally balanced by powers of two) -> W (fp32, round
+// to nearest even), and a region of W -> the 16-bit factor array when it
+// becomes a panel (one rounding, nearest even).
+// ---------------------------------------------------------------------------
+__device__ inline double times_pow2(double x, int k) {   // x * 2^k, an exponent add for normal x
+  if (k == 0) return x;
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0 || e == 0x7ff || e + k <= 0 || e + k >= 0x7ff) return x * ldexp(1.0, k);
+  return __longlong_as_double((long long)(u + ((unsigned long long)(int64_t)k << 52)));
+}
+
+__global__ void __launch_bounds__(256) cast32_kernel(int64_t n, const double* __restrict__ A, int64_t lda,
+                                                     float* __restrict__ W, int64_t ldw,
+                                                     const double* __restrict__ rs, const double* __restrict__ cs) {
+  const int64_t j = blockIdx.x;   // column (grid x holds up to 2^31 - 1)
+  const int64_t i = (int64_t)blockIdx.y * 256 + threadIdx.x;
+  if (i >= n) return;
+  const int k = (rs ? pow2_exponent(rs[i]) : 0) + (cs ? pow2_exponent(cs[j]) : 0);
+  W[i + j * ldw] = __double2float_rn(times_pow2(__ldcs(A + i + j * lda), k));
+}
+
+__global__ void __launch_bounds__(256) round32_kernel(int64_t rows, int64_t cols, const float* __restrict__ W,
+                                                      int64_t ldw, uint16_t* __restrict__ LU, int64_t ld, int fmt) {
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= rows) return;
+  for (int64_t j = blockIdx.y; j < cols; j += gridDim.y) LU[i + j * ld] = f32_to_u16(W[i + j * ldw], fmt);
+}
+
+// ---------------------------------------------------------------------------
 // Balancing and scaling (section "Algorithmic Framework": a Theta(n^2)
 // balancing of the input borrowed from the HPL harness, and a scaling that
 // makes the values fit the low-precision format, both timed and undone).
@@ -817,6 +848,11 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs g, int sub_m, i
       for (int c = 0; c < 4; ++c) {
         const int64_t i = m0 + ty * 4 + a, j = n0 + tx * 4 + c;
         if (i >= g.M || j >= g.N) continue;
+        if (g.c32) {   // fp32 trailing matrix: one fp32 subtraction, no rounding to 16 bits
+          float* cf = (float*)g.C + i + j * g.ldc;
+          *cf = __fsub_rn(*cf, acc[t][a][c]);
+          continue;
+        }
         uint16_t* cp = g.C ? (uint16_t*)g.C + i + j * g.ldc : nullptr;
         float v;
         if (g.mode == kEpiSub) v = __fsub_rn(u16_to_f32(*cp, g.fmt), acc[t][a][c]);
@@ -889,6 +925,8 @@ struct FactorWs {
   uint8_t* Uq[2];    // fp8 row panel, n x NB bytes (K-major per column)
   float* sL[2];      // fp8 scales, (n/128) x 4
   float* sU[2];
+  float* W32;        // fp32 trailing matrix (TRAIL32 precisions), ld = ldw
+  int64_t ldw;
   size_t bytes;
 };
 
@@ -914,6 +952,10 @@ FactorWs carve(void* base, int64_t n, int prec, int NB) {
       w.sU[q] = (float*)take(sizeof(float) * (nr / kB) * 4);
     }
   }
+  if (trail32_of(prec)) {
+    w.ldw = round_up<int64_t>(n, 8);
+    w.W32 = (float*)take(sizeof(float) * (size_t)w.ldw * (size_t)n);
+  }
   w.bytes = off;
   return w;
 }
@@ -923,6 +965,21 @@ struct Factorizer {
   uint16_t* LU;
   int64_t ld;
   int fmt, prec, NB, engine;
+  bool trail32 = false;   // Schur updates into the fp32 matrix w.W32; panels rounded from it
+
+  // TRAIL32: block column [k, n) x [k, k+b) and block row [k, k+b) x [k+b, n)
+  // of the fp32 matrix take their one rounding into the factor array
+  void round_panel(int64_t k, int64_t b) {
+    const float* W = w.W32;
+    const int64_t ldw = w.ldw;
+    round32_kernel<<<dim3((unsigned)cdiv<int64_t>(n - k, 256), (unsigned)std::min<int64_t>(b, 65535)), 256, 0, st>>>(
+        n - k, b, W + k + k * ldw, ldw, at(k, k), ld, fmt);
+    if (n - k - b > 0)
+      round32_kernel<<<dim3((unsigned)cdiv<int64_t>(b, 256), (unsigned)std::min<int64_t>(n - k - b, 1024)), 256, 0,
+                       st>>>(b, n - k - b, W + k + (k + b) * ldw, ldw, at(k, k + b), ld, fmt);
+    count_launches(2);
+    check(cudaGetLastError());
+  }
   FactorWs w;
   cudaStream_t st;
   cudaError_t err = cudaSuccess;
@@ -1084,6 +1141,7 @@ struct Factorizer {
       uint16_t* Lp = w.Lp[par];
       const int panel_ctas = overlap && far_pending && cap_panels ? reserve : 0;
       const int64_t m = n - (k + b);
+      if (trail32) round_panel(k, b);
       // (i) diagonal block.  Beside it on st3 (after each inner step's own
       // work there): W_s and Z_s of the sub-blocks 0 < s < nsub - 1
       for (int s = 0; s < nsub; ++s) {
@@ -1159,7 +1217,14 @@ struct Factorizer {
         } else {
           g.A = Lp + r0 * NB; g.B = at(k, k + b + c0);
         }
-        g.C = at(k + b + r0, k + b + c0); g.ldc = ld;
+        if (trail32) {   // into the fp32 matrix, no rounding to 16 bits
+          g.C = w.W32 + (k + b + r0) + (k + b + c0) * w.ldw;
+          g.ldc = w.ldw;
+          g.c32 = 1;
+        } else {
+          g.C = at(k + b + r0, k + b + c0);
+          g.ldc = ld;
+        }
         g.max_ctas = max_ctas;
         gemm(g);
       };
@@ -1267,7 +1332,7 @@ cudaError_t launch_balance(int64_t n, const double* A, int64_t lda, int prec, do
   row_absmax_kernel<<<g1, 256, 0, st>>>(n, A, lda, reinterpret_cast<unsigned long long*>(rs));
   row_scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, rs);
   col_scale_kernel<<<(unsigned)cdiv<int64_t>(n, kBalCols), 256, 0, st>>>(n, A, lda, rs, cs);
-  const double s = prec == HPMXP_FP16 ? 4096.0 : 1.0;
+  const double s = fmt_of(prec) == kFP16 ? 4096.0 : 1.0;
   if (s != 1.0) {
     format_scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, rs, s);
     count_launches(1);
@@ -1291,18 +1356,29 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
   }
   Factorizer f;
   f.n = n; f.LU = (uint16_t*)LU; f.ld = ldlu;
-  f.prec = prec; f.fmt = prec == HPMXP_FP16 ? kFP16 : kBF16;
+  f.prec = prec; f.fmt = fmt_of(prec);
+  f.trail32 = trail32_of(prec);
   f.NB = nb; f.engine = gemm_engine();
   f.w = carve(ws, n, prec, nb);
   f.st = st;
   f.check(cudaMemsetAsync(f.w.status, 0, sizeof(uint32_t), st));
-  f.check(launch_cast(n, A, lda, LU, ldlu, f.fmt, st, rs, cs));
+  if (f.trail32) {
+    void* tok = prof_begin(st);
+    cast32_kernel<<<dim3((unsigned)n, (unsigned)cdiv<int64_t>(n, 256)), 256, 0, st>>>(n, A, lda, f.w.W32, f.w.ldw,
+                                                                                      rs, cs);
+    prof_end(tok, kProfCast, 12.0 * (double)n * (double)n, st);
+    count_launches(1);
+    f.check(cudaGetLastError());
+  } else {
+    f.check(launch_cast(n, A, lda, LU, ldlu, f.fmt, st, rs, cs));
+  }
   if (const char* om = getenv("HPMXP_OVERLAP_MIN")) f.overlap_min = atoll(om);
   // the largest far part is n - 2 nb (first step); below overlap_min the
   // schedule never uses the side stream, so it is not taken (concurrent
   // factorizations of small systems on other streams then do not serialize)
   std::unique_lock<std::mutex> lk;
-  if (n - 2 * (int64_t)nb >= std::max<int64_t>(f.overlap_min, 1) && getenv("HPMXP_NO_LOOKAHEAD") == nullptr) {
+  if (!f.trail32 && n - 2 * (int64_t)nb >= std::max<int64_t>(f.overlap_min, 1) &&
+      getenv("HPMXP_NO_LOOKAHEAD") == nullptr) {
     SideStream& ss = side_stream(dev);
     if (ss.ok) {
       lk = std::unique_lock<std::mutex>(ss.mu);

@@ -81,7 +81,7 @@ int pick_nb(const hpmxp_request& r) { return r.nb ? r.nb : (r.n < 4096 ? 128 : 2
 
 bool request_ok(const hpmxp_request& r) {
   if (r.n < 1 || r.n > (int64_t(1) << 17) || r.nrhs < 1 || r.nrhs > kMaxRhs) return false;
-  if (!(r.prec == HPMXP_BF16 || r.prec == HPMXP_FP16 || r.prec == HPMXP_FP8_E4M3)) return false;
+  if (!(r.prec >= HPMXP_BF16 && r.prec <= HPMXP_FP16_TRAIL32)) return false;
   const int nb = pick_nb(r);
   if (!(nb == 128 || nb == 256 || nb == 512)) return false;
   if ((r.A == nullptr) != (r.b == nullptr)) return false;

@@ -146,9 +146,10 @@ class MethodLU:
     over [W_s | Linv_ss] (rows) or [Z_s ; Uinv_ss] (columns); Schur update one
     fp32 accumulation over the panel width, rounded once into storage."""
 
-    def __init__(self, A, nb: int, fp8_update: bool = False, store=bf16):
+    def __init__(self, A, nb: int, fp8_update: bool = False, store=bf16, trail32: bool = False):
         self.st = store                 # rounding to the storage format (bf16; f32 to expose fp32 rounding points)
-        self.M = store(np.asarray(A, dtype=F64))
+        self.trail32 = trail32          # 32-bit trailing matrix: top-level Schur results kept in fp32
+        self.M = f32(np.asarray(A, dtype=F64)) if trail32 else store(np.asarray(A, dtype=F64))
         self.n = self.M.shape[0]
         self.nb = nb
         self.fp8 = fp8_update
@@ -241,7 +242,7 @@ class MethodLU:
             acc = np.zeros((m, m), dtype=F32)
             for p in range(b):
                 acc = fmaf(L[:, p].astype(F32)[:, None], U[p, :].astype(F32)[None, :], acc)
-        M[k + b:e, k + b:e] = self.st((C - acc).astype(F64))
+        M[k + b:e, k + b:e] = (C - acc).astype(F64) if (top and self.trail32) else self.st((C - acc).astype(F64))
 
     @staticmethod
     def fp8_product(L, U) -> np.ndarray:
@@ -284,6 +285,9 @@ class MethodLU:
         e = k0 + size
         for k in range(k0, e, NB):
             b = min(NB, e - k)
+            if top and self.trail32:    # the block column and row take their one rounding to storage
+                self.M[k:e, k:k + b] = self.st(self.M[k:e, k:k + b])
+                self.M[k:k + b, k + b:e] = self.st(self.M[k:k + b, k + b:e])
             if b <= BASE:
                 self.getrf_base(k, b)
             else:
@@ -295,5 +299,5 @@ class MethodLU:
             self.schur(k, b, e, top)
 
 
-def method_lu(A, nb: int, fp8_update: bool = False, store=bf16) -> np.ndarray:
-    return MethodLU(A, nb, fp8_update, store).run()
+def method_lu(A, nb: int, fp8_update: bool = False, store=bf16, trail32: bool = False) -> np.ndarray:
+    return MethodLU(A, nb, fp8_update, store, trail32).run()

@@ -128,6 +128,42 @@ def test_blocked_lu_rederived_fp32_storage(n, nb, fp8):
 
 
 # ---------------------------------------------------------------------------
+# 32-bit trailing matrix (Fig. 1 with fp32 storage of the matrix being updated)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,nb", [(300, 128), (456, 256), (520, 128)])
+def test_trail32_rederived(n, nb):
+    A, _ = oracle.generate(n, 22)
+    LU, rc = oracle.factor(A, oracle.BF16, nb, trail32=True)
+    assert rc == 0
+    assert np.array_equal(LU, R.method_lu(A, nb, trail32=True))
+
+
+def test_trail32_without_schur_steps_is_the_method_on_the_fp32_input():
+    # nb >= n: no top-level Schur update, so the only difference from the
+    # method is the input's rounding to fp32 first
+    A, _ = oracle.generate(300, 23)
+    LU, _ = oracle.factor(A, oracle.BF16, 512, trail32=True)
+    want, _ = oracle.factor(oracle.round_to(A, oracle.FP32), oracle.BF16, 512)
+    assert np.array_equal(LU, want)
+
+
+@pytest.mark.parametrize("fmt", [oracle.BF16, oracle.FP16])
+def test_trail32_error_bounds_and_refinement(fmt):
+    n = 900
+    A, b = oracle.generate(n, 24)
+    LU, rc = oracle.factor(A, fmt, 256, trail32=True)
+    assert rc == 0 and np.array_equal(oracle.round_to(LU, fmt), LU)
+    L, U = oracle.split_lu(LU)
+    u = 2.0**-8 if fmt == oracle.BF16 else 2.0**-11
+    assert np.linalg.norm(L @ U - A) / np.linalg.norm(A) <= u
+    X, info, rc = oracle.solve_ir(A, LU, b)
+    assert rc == 0 and oracle.scaled_residual(A, X, b)[0] < 16
+    # it differs from rounding the trailing matrix at every step
+    LU16, _ = oracle.factor(A, fmt, 256)
+    assert not np.array_equal(LU, LU16)
+
+
+# ---------------------------------------------------------------------------
 # the method's scheme against the plain reading of Fig. 1
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [700, 1100])
