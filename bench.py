@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "HPL-MxP TFLOP/s (2n^3/3 + 3n^2/2 per solve) at scaled residual < 16"
-PREC = {"bf16": 0, "fp16": 1, "fp8": 2}
+PREC = {"bf16": 0, "fp16": 1, "fp8": 2, "bf16t32": 3, "fp16t32": 4}
 
 
 def hpl_ops(n: int) -> float:
@@ -176,10 +176,10 @@ IR_KW = {}   # refinement parameters of the GPU arm, mirrored by the oracle legs
 def oracle_solve_timed(n: int, seed: int, prec: str, nb: int):
     import oracle
     A, b = oracle.generate(n, seed)
-    fmt = oracle.FP16 if prec == "fp16" else oracle.BF16
+    fmt = oracle.FP16 if prec in ("fp16", "fp16t32") else oracle.BF16
     upd = oracle.E4M3 if prec == "fp8" else None
     t0 = time.perf_counter()
-    LU, _ = oracle.factor(A, fmt, nb, fmt_update=upd)
+    LU, _ = oracle.factor(A, fmt, nb, fmt_update=upd, trail32=prec.endswith("t32"))
     X, info, rc = oracle.solve_ir(A, LU, b, **IR_KW)
     dt = time.perf_counter() - t0
     return dt, info[0], rc
