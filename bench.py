@@ -347,6 +347,31 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+GEMM_SRC = os.path.join(ROOT, "paper_2509_19618_gb300", "csrc", "gemm_tc.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gemm_tc_kernel_traffic_n32768_bf16_nb512.md")
+
+
+def measured_gemm_traffic(n: int, nb: int, prec: str):
+    """DRAM bytes per gemm_tc_kernel launch over one solve, from the committed
+    ncu summary of that workload, or None when there is none for this
+    workload or the kernel's source has changed since it was captured."""
+    import hashlib
+    if (n, nb, prec) != (32768, 512, "bf16") or not os.path.exists(TRAFFIC_FILE):
+        return None
+    fields = {}
+    for line in open(TRAFFIC_FILE):
+        if line.startswith("traffic_") and ":" in line:
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    sha = hashlib.sha256(open(GEMM_SRC, "rb").read()).hexdigest()[:16]
+    if fields.get("traffic_kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return float(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def ir_params_for(args, precond_fp32: int, matvec_fp32: int):
     from paper_2509_19618_gb300 import capi
     p = capi.hpmxp_ir_params_default()
@@ -496,7 +521,7 @@ def main():
              "cast": capi.PROF_CAST, "panel_ops": capi.PROF_PANEL, "balance": capi.PROF_BALANCE}
     prof = {k: capi.hpmxp_prof_read(v) for k, v in kinds.items()}
     # every launch of the tensor-core GEMM kernel (Schur updates and panel products)
-    g = {f: prof["gemm_update"][f] + prof["gemm_panel"][f] for f in ("ms", "work", "launches")}
+    g = {f: prof["gemm_update"][f] + prof["gemm_panel"][f] for f in ("ms", "work", "launches", "bytes")}
     bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     dom_ms_launch = g["ms"] / max(g["launches"], 1)
@@ -510,7 +535,9 @@ def main():
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops_sustained" if peaks
                                 else "of fallback 1.7 PF/s") + (" x2 nominal fp8/bf16 ratio" if prec == 2 else ""),
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": measured_gemm_traffic(n, nb, args.prec),
+                "algorithmic_bytes_per_launch": g["bytes"] / max(g["launches"], 1),
                 "whole_solve": {"t_roof_ms": t_roof * 1e3, "t_meas_ms": t_step * 1e3, "frac": t_roof / t_step,
                                 "what": "T_roof = 2/3 n^3 / tensor peak + 10 n^2 (iters + 1) bytes / HBM peak"},
                 "per_kind_ms_per_solve": {k: v["ms"] for k, v in prof.items()},

@@ -325,6 +325,10 @@ unsigned long long hpmxp_launch_count(void);
 void hpmxp_prof_enable(int on);
 void hpmxp_prof_reset(void);
 int hpmxp_prof_read(int kind, double* total_ms, double* total_work, long long* launches);
+/* Algorithmic DRAM bytes recorded for a kind since the last reset (the GEMM
+ * kinds 0 and 7: operands once, C read and / or written once; 0 for the
+ * others), for comparison with the bytes a profiler measures. */
+int hpmxp_prof_read_bytes(int kind, double* total_bytes);
 int hpmxp_prof_timeline(double* out, int max_spans);
 
 #ifdef __cplusplus

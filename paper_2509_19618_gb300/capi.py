@@ -102,6 +102,7 @@ def load():
             "hpmxp_prof_enable": ([i32], None),
             "hpmxp_prof_reset": ([], None),
             "hpmxp_prof_read": ([i32, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)], i32),
+            "hpmxp_prof_read_bytes": ([i32, ctypes.POINTER(d)], i32),
             "hpmxp_prof_timeline": ([P, i32], i32),
             "hpmxp_test_precond": ([i64, P, i64, i32, P, i64, P, i64, i64, i32, P, sz, P], i32),
             "hpmxp_test_arena": ([sz, ctypes.POINTER(i64), i32, ctypes.POINTER(i64)], i32),
@@ -243,7 +244,9 @@ def hpmxp_prof_read(kind: int) -> dict:
     st = load().hpmxp_prof_read(kind, ctypes.byref(ms), ctypes.byref(work), ctypes.byref(cnt))
     if st != OK:
         raise HpmxpError("hpmxp_prof_read", st)
-    return dict(ms=ms.value, work=work.value, launches=cnt.value)
+    by = ctypes.c_double()
+    load().hpmxp_prof_read_bytes(kind, ctypes.byref(by))
+    return dict(ms=ms.value, work=work.value, launches=cnt.value, bytes=by.value)
 
 
 def hpmxp_test_gemm(*args):

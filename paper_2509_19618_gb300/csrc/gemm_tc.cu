@@ -634,10 +634,15 @@ cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
   }
   const int grid = std::min(p.ntiles, g.max_ctas > 0 ? std::min(g.max_ctas, num_sms()) : num_sms());
   const double flops = 2.0 * g.M * (double)g.N * g.K;
+  // algorithmic DRAM bytes: both operands once, C read (subtract mode) and
+  // written once, the optional row-major copy written once
+  const double mn = (double)g.M * (double)g.N;
+  const double bytes = ((double)g.M + (double)g.N) * (double)g.K * esz +
+                       (p.has_c ? mn * CB * (g.mode == kEpiSub ? 2.0 : 1.0) : 0.0) + (g.R ? mn * 2.0 : 0.0);
   void* tok = prof_begin(st);
   const cudaError_t e =
       launch_pdl(gemm_tc_kernel<TI, CB>, dim3(grid), dim3(kThreads), Cfg::kSmem, st, ta, tb, tc, p);
-  prof_end(tok, g.mode == kEpiSub ? kProfGemm : kProfGemmStore, flops, st);
+  prof_end(tok, g.mode == kEpiSub ? kProfGemm : kProfGemmStore, flops, st, bytes);
   count_launches(1);
   return e;
 }

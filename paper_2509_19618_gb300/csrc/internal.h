@@ -179,7 +179,9 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 void* prof_begin(cudaStream_t st);
-void prof_end(void* token, int kind, double work, cudaStream_t st);
+// work: the kind's unit (flops or bytes, see hpmxp.h); bytes: algorithmic DRAM
+// bytes of the launch where the kind records them (the GEMM kinds)
+void prof_end(void* token, int kind, double work, cudaStream_t st, double bytes = 0.0);
 
 cudaError_t host_wait(cudaStream_t st);   // waits for `st` (spinning unless HPMXP_BLOCKING_WAIT=1)
 cudaError_t read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t st);   // + host_wait

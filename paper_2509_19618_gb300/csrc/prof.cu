@@ -30,7 +30,7 @@ std::atomic<int> g_enabled{0};
 struct Span {
   cudaEvent_t a, b;
   int kind;
-  double work;
+  double work, bytes;
 };
 
 std::mutex g_mu;
@@ -42,7 +42,7 @@ struct Interval {
 };
 std::vector<Interval> g_timeline;     // resolved spans, in recording order
 constexpr size_t kMaxTimeline = size_t(1) << 20;
-double g_ms[kProfKinds], g_work[kProfKinds];
+double g_ms[kProfKinds], g_work[kProfKinds], g_bytes[kProfKinds];
 long long g_count[kProfKinds];
 std::vector<cudaEvent_t> g_pool;
 
@@ -63,6 +63,7 @@ void resolve_locked() {
     if (cudaEventSynchronize(s.b) == cudaSuccess && cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
       g_ms[s.kind] += ms;
       g_work[s.kind] += s.work;
+      g_bytes[s.kind] += s.bytes;
       g_count[s.kind] += 1;
       float t0 = 0.0f;
       if (g_origin && g_timeline.size() < kMaxTimeline && cudaEventElapsedTime(&t0, g_origin, s.a) == cudaSuccess)
@@ -150,12 +151,12 @@ void* prof_begin(cudaStream_t st) {
   return (void*)a;
 }
 
-void prof_end(void* token, int kind, double work, cudaStream_t st) {
+void prof_end(void* token, int kind, double work, cudaStream_t st, double bytes) {
   if (!token) return;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t b = take_event();
   cudaEventRecord(b, st);
-  g_open.push_back(Span{(cudaEvent_t)token, b, kind, work});
+  g_open.push_back(Span{(cudaEvent_t)token, b, kind, work, bytes});
   if (g_open.size() > 4096) resolve_locked();
 }
 
@@ -172,7 +173,7 @@ void hpmxp_prof_enable(int on) { g_enabled.store(on ? 1 : 0); }
 void hpmxp_prof_reset(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   resolve_locked();
-  for (int k = 0; k < kProfKinds; ++k) { g_ms[k] = 0.0; g_work[k] = 0.0; g_count[k] = 0; }
+  for (int k = 0; k < kProfKinds; ++k) { g_ms[k] = 0.0; g_work[k] = 0.0; g_bytes[k] = 0.0; g_count[k] = 0; }
   if (g_origin) g_pool.push_back(g_origin);
   g_origin = nullptr;
   g_timeline.clear();
@@ -190,6 +191,14 @@ int hpmxp_prof_timeline(double* out, int max_spans) {
     }
   }
   return (int)g_timeline.size();
+}
+
+int hpmxp_prof_read_bytes(int kind, double* total_bytes) {
+  if (kind < 0 || kind >= kProfKinds || !total_bytes) return HPMXP_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  resolve_locked();
+  *total_bytes = g_bytes[kind];
+  return HPMXP_OK;
 }
 
 int hpmxp_prof_read(int kind, double* total_ms, double* total_work, long long* launches) {
