@@ -259,6 +259,53 @@ hpmxp_status hpmxp_solve_ir_scaled(int64_t n, const double* A, int64_t lda, cons
                                    hpmxp_ir_info* info, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batches of independent systems of different sizes (the same method per
+ * system, section "Algorithmic Framework"; batching many small systems is this
+ * library's serving use, the paper has one large system per run).
+ *
+ * Each hpmxp_problem names one system's caller-owned device buffers.  The
+ * batched calls run all systems in lockstep with Schur-update depth 128: one
+ * grouped launch per stage serves every system that is still active (one CTA
+ * per system's diagonal block; one tensor-core launch walking all systems'
+ * tiles for each of the row-panel, column-panel and Schur products), so a
+ * batch of B systems of order up to N takes about 5 N / 128 launches instead
+ * of 5 sum_b n_b / 128.  Each system's factors are bit-for-bit those of
+ * hpmxp_factor(n_b, ..., nb = 128) of it alone (the same kernels compute every
+ * tile).  Formats: HPMXP_BF16 and HPMXP_FP16. */
+typedef struct {
+  int64_t n;            /* order, 1..131072 */
+  const double* A;      /* n x n fp64, column major, lda >= n */
+  int64_t lda;
+  void* LU;             /* factors, n x n 16-bit, ldlu >= n, ldlu % 8 == 0, 16-byte aligned */
+  int64_t ldlu;
+  const double* b;      /* right-hand sides, n x nrhs (the solve only) */
+  int64_t ldb;
+  double* x;            /* solutions, n x nrhs (the solve only) */
+  int64_t ldx;
+  int64_t nrhs;         /* 1..8 (the solve only) */
+} hpmxp_problem;
+
+/* probs: host array of `count` descriptors.  status: host, count entries (may
+ * be NULL): each system's status (HPMXP_EBREAKDOWN for a zero or non-finite
+ * pivot).  Returns HPMXP_OK when every system factored, else the first
+ * failure.  Synchronizes `stream`. */
+size_t hpmxp_factor_batched_workspace(const hpmxp_problem* probs, int count, int prec);
+hpmxp_status hpmxp_factor_batched(const hpmxp_problem* probs, int count, int prec, hpmxp_status* status, void* ws,
+                                  size_t ws_bytes, void* stream);
+
+/* GMRES-IR of every system with its factors from hpmxp_factor_batched (or
+ * hpmxp_factor), the parameters of hpmxp_solve_ir shared by all.  The systems
+ * advance in lockstep: one host decision point per refinement phase for the
+ * whole batch (each system's kernels on one of the library's streams, so small
+ * systems run side by side), instead of one per system.  info: host, sum of
+ * nrhs entries in problem order (may be NULL).  Returns HPMXP_OK when every
+ * right-hand side of every system met the threshold, else the first failure.
+ * Synchronizes `stream`. */
+size_t hpmxp_solve_ir_batched_workspace(const hpmxp_problem* probs, int count, int restart);
+hpmxp_status hpmxp_solve_ir_batched(const hpmxp_problem* probs, int count, int prec, const hpmxp_ir_params* prm,
+                                    hpmxp_ir_info* info, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Backward-error check (section "Algorithmic Framework"): for every column c,
  * scaled_resid[c] = ||A x_c - b_c||_inf / ((||A||_inf ||x_c||_inf + ||b_c||_inf) n eps)
  * with eps = 2^-53, all in fp64.  The solution is valid when it is < 16.

@@ -156,6 +156,50 @@ def residual(A: ColMajor, x: ColMajor, b: ColMajor, stream=None) -> np.ndarray:
     return np.array(out[:], dtype=np.float64)
 
 
+def _problem(A: ColMajor, LU: ColMajor, b: ColMajor | None = None, x: ColMajor | None = None) -> capi.Problem:
+    p = capi.Problem()
+    p.n, p.A, p.lda, p.LU, p.ldlu = A.rows, A.ptr, A.ld, LU.ptr, LU.ld
+    if b is not None:
+        p.b, p.ldb, p.x, p.ldx, p.nrhs = b.ptr, b.ld, x.ptr, x.ld, b.cols
+    return p
+
+
+def factor_batched(As: list, prec: int = capi.BF16, LUs: list | None = None, stream=None, check: bool = True):
+    """Factors every system of the list in one batched call (depth 128, grouped
+    kernels); returns (factors, per-system statuses)."""
+    dev = As[0].storage.device
+    if LUs is None:
+        LUs = [ColMajor.empty(A.rows, A.rows, factor_storage_dtype(prec), dev) for A in As]
+    probs = [_problem(A, LU) for A, LU in zip(As, LUs)]
+    ws = workspace(capi.hpmxp_factor_batched_workspace(probs, prec), dev)
+    st, per = capi.hpmxp_factor_batched(probs, prec, ws.data_ptr(), ws.numel(), stream_handle(stream))
+    if check and st not in (capi.OK, capi.EBREAKDOWN):
+        _check("hpmxp_factor_batched", st)
+    return LUs, per
+
+
+def solve_ir_batched(As: list, LUs: list, bs: list, prec: int = capi.BF16, params: capi.IRParams | None = None,
+                     xs: list | None = None, stream=None, check: bool = True):
+    """GMRES-IR of every system in lockstep; returns (solutions, [per-system info lists], status)."""
+    dev = As[0].storage.device
+    if xs is None:
+        xs = [ColMajor.empty(A.rows, b.cols, torch.float64, dev) for A, b in zip(As, bs)]
+    probs = [_problem(A, LU, b, x) for A, LU, b, x in zip(As, LUs, bs, xs)]
+    restart = params.restart if params is not None else 30
+    ws = workspace(capi.hpmxp_solve_ir_batched_workspace(probs, restart), dev)
+    total = sum(b.cols for b in bs)
+    info = (capi.IRInfo * total)()
+    st = capi.hpmxp_solve_ir_batched(probs, prec, params, info, ws.data_ptr(), ws.numel(), stream_handle(stream))
+    if check and st not in (capi.OK, capi.ENOCONV, capi.EBREAKDOWN):
+        _check("hpmxp_solve_ir_batched", st)
+    infos, off = [], 0
+    for b in bs:
+        infos.append([dict(iters=i.iters, outer=i.outer, scaled_resid=i.scaled_resid, status=i.status)
+                      for i in info[off:off + b.cols]])
+        off += b.cols
+    return xs, infos, st
+
+
 def hpl_mxp_ops(n: int, nrhs: int = 1) -> float:
     """Canonical operation count (section "Algorithmic Framework"): 2/3 n^3 + 3/2 n^2
     for one right-hand side; with k right-hand sides the solves count 2 k n^2."""

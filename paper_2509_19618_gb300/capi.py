@@ -37,6 +37,12 @@ class IRInfo(ctypes.Structure):
                 ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("LU", ctypes.c_void_p),
+                ("ldlu", ctypes.c_int64), ("b", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("x", ctypes.c_void_p),
+                ("ldx", ctypes.c_int64), ("nrhs", ctypes.c_int64)]
+
+
 class Request(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64), ("n", ctypes.c_int64), ("nrhs", ctypes.c_int64), ("prec", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("b", ctypes.c_void_p),
@@ -81,6 +87,11 @@ def load():
             "hpmxp_factor_workspace": ([i64, i32, i32], sz),
             "hpmxp_factor": ([i64, P, i64, i32, i32, P, i64, P, sz, P], i32),
             "hpmxp_factor_scaled": ([i64, P, i64, i32, i32, P, P, P, i64, P, sz, P], i32),
+            "hpmxp_factor_batched_workspace": ([ctypes.POINTER(Problem), i32, i32], sz),
+            "hpmxp_factor_batched": ([ctypes.POINTER(Problem), i32, i32, ctypes.POINTER(i32), P, sz, P], i32),
+            "hpmxp_solve_ir_batched_workspace": ([ctypes.POINTER(Problem), i32, i32], sz),
+            "hpmxp_solve_ir_batched": ([ctypes.POINTER(Problem), i32, i32, ctypes.POINTER(IRParams),
+                                        ctypes.POINTER(IRInfo), P, sz, P], i32),
             "hpmxp_balance": ([i64, P, i64, i32, P, P, P], i32),
             "hpmxp_ir_params_default": ([ctypes.POINTER(IRParams)], None),
             "hpmxp_solve_workspace": ([i64, i64, i32], sz),
@@ -166,6 +177,30 @@ def hpmxp_factor(n, A, lda, prec, nb, LU, ldlu, ws, ws_bytes, stream):
 
 def hpmxp_factor_scaled(n, A, lda, prec, nb, rs, cs, LU, ldlu, ws, ws_bytes, stream):
     return _call("hpmxp_factor_scaled", n, A, lda, prec, nb, rs, cs, LU, ldlu, ws, ws_bytes, stream)
+
+
+def hpmxp_factor_batched_workspace(probs, prec):
+    arr = (Problem * len(probs))(*probs)
+    return _call("hpmxp_factor_batched_workspace", arr, len(probs), prec)
+
+
+def hpmxp_factor_batched(probs, prec, ws, ws_bytes, stream):
+    """Returns (status, [per-system status])."""
+    arr = (Problem * len(probs))(*probs)
+    per = (ctypes.c_int * len(probs))()
+    st = _call("hpmxp_factor_batched", arr, len(probs), prec, per, ws, ws_bytes, stream)
+    return st, list(per)
+
+
+def hpmxp_solve_ir_batched_workspace(probs, restart):
+    arr = (Problem * len(probs))(*probs)
+    return _call("hpmxp_solve_ir_batched_workspace", arr, len(probs), restart)
+
+
+def hpmxp_solve_ir_batched(probs, prec, params, info, ws, ws_bytes, stream):
+    arr = (Problem * len(probs))(*probs)
+    return _call("hpmxp_solve_ir_batched", arr, len(probs), prec, None if params is None else ctypes.byref(params),
+                 info, ws, ws_bytes, stream)
 
 
 def hpmxp_balance(n, A, lda, prec, rs, cs, stream):

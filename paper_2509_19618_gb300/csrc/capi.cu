@@ -33,6 +33,9 @@ hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, i
                       cudaStream_t st, const double* rs = nullptr, const double* cs = nullptr);
 hpmxp_status residual_check(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
                             const double* b, int64_t ldb, int64_t nrhs, double* out, void* ws, cudaStream_t st);
+size_t solve_batched_ws_bytes(const hpmxp_problem* probs, int count, int restart);
+hpmxp_status solve_ir_batched(const hpmxp_problem* probs, int count, int prec, const hpmxp_ir_params& prm,
+                              hpmxp_ir_info* info, void* ws, cudaStream_t caller);
 hpmxp_status residual_vector(int64_t n, const double* A, int64_t lda, const double* x, int64_t ldx,
                              const double* b, int64_t ldb, int64_t nrhs, double* r, int64_t ldr, void* ws,
                              cudaStream_t st);
@@ -98,6 +101,54 @@ hpmxp_status hpmxp_factor_scaled(int64_t n, const double* A, int64_t lda, int pr
 hpmxp_status hpmxp_factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU, int64_t ldlu,
                           void* ws, size_t ws_bytes, void* stream) {
   return hpmxp_factor_scaled(n, A, lda, prec, nb, nullptr, nullptr, LU, ldlu, ws, ws_bytes, stream);
+}
+
+namespace {
+bool batch_problem_ok(const hpmxp_problem& q, bool solve) {
+  if (q.n < 1 || q.n > kMaxN || !q.A || q.lda < q.n || !q.LU || q.ldlu < q.n || (q.ldlu % 8) || !aligned(q.LU, 16))
+    return false;
+  if (solve && (!q.b || q.ldb < q.n || !q.x || q.ldx < q.n || q.nrhs < 1 || q.nrhs > 8)) return false;
+  return true;
+}
+}  // namespace
+
+size_t hpmxp_factor_batched_workspace(const hpmxp_problem* probs, int count, int prec) {
+  if (!probs || count < 1 || !(prec == HPMXP_BF16 || prec == HPMXP_FP16)) return 0;
+  for (int q = 0; q < count; ++q)
+    if (probs[q].n < 1 || probs[q].n > kMaxN) return 0;
+  return factor_batched_ws_bytes(probs, count);
+}
+
+hpmxp_status hpmxp_factor_batched(const hpmxp_problem* probs, int count, int prec, hpmxp_status* status, void* ws,
+                                  size_t ws_bytes, void* stream) {
+  if (!probs || count < 1 || !(prec == HPMXP_BF16 || prec == HPMXP_FP16) || !ws || !aligned(ws, 256))
+    return HPMXP_EINVAL;
+  for (int q = 0; q < count; ++q)
+    if (!batch_problem_ok(probs[q], false)) return HPMXP_EINVAL;
+  if (ws_bytes < factor_batched_ws_bytes(probs, count)) return HPMXP_ENOMEM;
+  return factor_batched(probs, count, prec, status, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+size_t hpmxp_solve_ir_batched_workspace(const hpmxp_problem* probs, int count, int restart) {
+  if (!probs || count < 1 || restart < 1 || restart > 64) return 0;
+  for (int q = 0; q < count; ++q)
+    if (probs[q].n < 1 || probs[q].n > kMaxN || probs[q].nrhs < 1 || probs[q].nrhs > 8) return 0;
+  return solve_batched_ws_bytes(probs, count, restart);
+}
+
+hpmxp_status hpmxp_solve_ir_batched(const hpmxp_problem* probs, int count, int prec, const hpmxp_ir_params* prm,
+                                    hpmxp_ir_info* info, void* ws, size_t ws_bytes, void* stream) {
+  hpmxp_ir_params p;
+  hpmxp_ir_params_default(&p);
+  if (prm) p = *prm;
+  if (!probs || count < 1 || !prec_ok(prec) || !ws || !aligned(ws, 256) || p.restart < 1 || p.restart > 64 ||
+      p.max_iters < 0 || !(p.accept > 0.0) || p.inner_tol < 0.0 || p.theta < 0.0 ||
+      (p.precond_fp32 != 0 && p.precond_fp32 != 1) || (p.matvec_fp32 != 0 && p.matvec_fp32 != 1))
+    return HPMXP_EINVAL;
+  for (int q = 0; q < count; ++q)
+    if (!batch_problem_ok(probs[q], true)) return HPMXP_EINVAL;
+  if (ws_bytes < solve_batched_ws_bytes(probs, count, p.restart)) return HPMXP_ENOMEM;
+  return solve_ir_batched(probs, count, prec, p, info, ws, (cudaStream_t)stream);
 }
 
 hpmxp_status hpmxp_balance(int64_t n, const double* A, int64_t lda, int prec, double* rs, double* cs,

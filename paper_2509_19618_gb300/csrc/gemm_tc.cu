@@ -246,10 +246,22 @@ __device__ inline uint32_t pack16x2(float lo, float hi, int fmt) {
   return r;
 }
 
+// Where tile t of the launch is: its product's tensor maps, its output origin
+// and that product's bounds (one product, or the items of a grouped launch).
+struct TileLoc {
+  const CUtensorMap* a;
+  const CUtensorMap* b;
+  const CUtensorMap* c;
+  int i0, j0, M, N;
+  uint16_t* R;
+  int64_t ldr;
+};
+
 template <int TI, int CB>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const __grid_constant__ CUtensorMap tmC, TcParams p) {
+               const __grid_constant__ CUtensorMap tmC, TcParams p, const GemmGroupItem* __restrict__ items,
+               int nitems) {
   using Cfg = TileCfg<TI, CB>;
   constexpr int kStages = Cfg::kStages, kStageB = Cfg::kStageB, kCTile = Cfg::kCTile, kCBufs = Cfg::kCBufs;
   constexpr int kBoxes = Cfg::kBoxes, kBoxRows = Cfg::kBoxRows;
@@ -272,6 +284,37 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+  // tile t -> its product (grouped launch: the last item starting at or before t)
+  auto locate = [&](int t) {
+    TileLoc L;
+    if (items == nullptr) {
+      L.a = &tmA; L.b = &tmB; L.c = &tmC;
+      L.i0 = (t % p.tiles_i) * TI; L.j0 = (t / p.tiles_i) * kTJ;
+      L.M = p.M; L.N = p.N; L.R = p.R; L.ldr = p.ldr;
+    } else {
+      int lo = 0, hi = nitems - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+      }
+      const GemmGroupItem& g = items[lo];
+      const int lt = t - g.tile_begin;
+      L.a = reinterpret_cast<const CUtensorMap*>(g.maps[0]);
+      L.b = reinterpret_cast<const CUtensorMap*>(g.maps[1]);
+      L.c = reinterpret_cast<const CUtensorMap*>(g.maps[2]);
+      L.i0 = (lt % g.tiles_i) * TI; L.j0 = (lt / g.tiles_i) * kTJ;
+      L.M = g.M; L.N = g.N; L.R = (uint16_t*)g.R; L.ldr = g.ldr;
+    }
+    return L;
+  };
+  // the items' tensor maps were written to global memory before the launch:
+  // acquire them for the tensor-map proxy before the first TMA through them
+  auto acquire_maps = [&](int which) {
+    for (int it = 0; items != nullptr && it < nitems; ++it)
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)items[it].maps[which])
+                   : "memory");
+  };
+
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(full(s), 1); mbar_init(empty(s), 1); }
     for (int b = 0; b < 2; ++b) {
@@ -284,9 +327,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     mbar_init(mma_drain, 1);
     fence_mbar_init();
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
-    if (p.has_c) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmC) : "memory");
+    if (items == nullptr) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+      if (p.has_c) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmC) : "memory");
+    }
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), p.ncols);
@@ -306,8 +351,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       // operand ring: stage s holds K bytes [128 kb, +128) of the tile's rows j (A) and rows i (B)
       long long pos = 0;   // ring position over all tiles of this CTA
       bool ok = true;
+      acquire_maps(0);
+      acquire_maps(1);
       for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-        const int i0 = (t % p.tiles_i) * TI, j0 = (t / p.tiles_i) * kTJ;
+        const TileLoc L = locate(t);
+        const int i0 = L.i0, j0 = L.j0;
         for (int kb = 0; kb < p.nkb; ++kb, ++pos) {
           const int s = (int)(pos % kStages);
           const long long use = pos / kStages;
@@ -316,8 +364,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             break;
           }
           mbar_expect_tx(full(s), kStageA + kStageB);
-          tma_load_2d(sOpA + s * kStageA, &tmB, kb * (kRowBytes / 2), j0, full(s));
-          tma_load_2d(sOpB + s * kStageB, &tmA, kb * (kRowBytes / 2), i0, full(s));
+          tma_load_2d(sOpA + s * kStageA, L.b, kb * (kRowBytes / 2), j0, full(s));
+          tma_load_2d(sOpB + s * kStageB, L.a, kb * (kRowBytes / 2), i0, full(s));
         }
       }
       if (!ok) atomicOr(p.status, kErrTimeout);
@@ -379,13 +427,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     int issued_c[kCBufs];         // local tile whose C load is outstanding in each buffer
     for (int b = 0; b < kCBufs; ++b) issued_c[b] = -1;
     auto load_c_tile = [&](int tt, int b) {   // this group's boxes of tile tt's C into buffer b
-      const int ii0 = (tt % p.tiles_i) * TI, jj0 = (tt / p.tiles_i) * kTJ;
+      const TileLoc Lc = locate(tt);
       mbar_expect_tx(c_full(b, g), kBoxes * kCBox);
 #pragma unroll
       for (int h = 0; h < kBoxes; ++h)
-        tma_load_2d(sC + b * kCTile + (g * kBoxes + h) * kCBox, &tmC, ii0 + (TI / 2) * g + kBoxRows * h, jj0,
+        tma_load_2d(sC + b * kCTile + (g * kBoxes + h) * kCBox, Lc.c, Lc.i0 + (TI / 2) * g + kBoxRows * h, Lc.j0,
                     c_full(b, g));
     };
+    if (leader && p.has_c) acquire_maps(2);
     if (leader && load_c) {       // prefetch the C of the first kAhead local tiles
       int local = 0;
       for (int t = blockIdx.x; t < p.ntiles && local < Cfg::kAhead; t += gridDim.x, ++local) {
@@ -396,7 +445,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     bool ok = true;
     int local = 0;
     for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++local) {
-      const int i0 = (t % p.tiles_i) * TI, j0 = (t / p.tiles_i) * kTJ;
+      const TileLoc L = locate(t);
+      const int i0 = L.i0, j0 = L.j0;
       const int cb = local % kCBufs, ab = local % p.nbuf;
       bool w = true;
       if (load_c) w = mbar_wait(c_full(cb, g), (uint32_t)((local / kCBufs) & 1), p.wait_polls, p.wait_ns);
@@ -485,11 +535,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           if (p.has_c)
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
                          ::"r"(ad), "r"(outw[0]), "r"(outw[1]), "r"(outw[2]), "r"(outw[3]) : "memory");
-          if (p.R && j < p.N) {
+          if (L.R && j < L.N) {
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
               const int64_t i = (int64_t)i0 + (TI / 2) * g + 64 * h + 8 * ch + v;
-              if (i < p.M) p.R[i * p.ldr + j] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
+              if (i < L.M) L.R[i * L.ldr + j] = (uint16_t)((outw[v >> 1] >> ((v & 1) * 16)) & 0xffffu);
             }
           }
         }
@@ -501,7 +551,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (leader) {
 #pragma unroll
           for (int h = 0; h < kBoxes; ++h)
-            tma_store_2d(&tmC, i0 + (TI / 2) * g + kBoxRows * h, j0, sC + cb * kCTile + (g * kBoxes + h) * kCBox);
+            tma_store_2d(L.c, i0 + (TI / 2) * g + kBoxRows * h, j0, sC + cb * kCTile + (g * kBoxes + h) * kCBox);
           bulk_commit();
           // the stores issued kCBufs - 1 tiles ago (one buffer: this tile's)
           // have finished reading their buffer, which now receives the C of
@@ -641,11 +691,81 @@ cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
                        (p.has_c ? mn * CB * (g.mode == kEpiSub ? 2.0 : 1.0) : 0.0) + (g.R ? mn * 2.0 : 0.0);
   void* tok = prof_begin(st);
   const cudaError_t e =
-      launch_pdl(gemm_tc_kernel<TI, CB>, dim3(grid), dim3(kThreads), Cfg::kSmem, st, ta, tb, tc, p);
+      launch_pdl(gemm_tc_kernel<TI, CB>, dim3(grid), dim3(kThreads), Cfg::kSmem, st, ta, tb, tc, p,
+                 (const GemmGroupItem*)nullptr, 0);
   prof_end(tok, g.mode == kEpiSub ? kProfGemm : kProfGemmStore, flops, st, bytes);
   count_launches(1);
   return e;
 }
+
+}  // namespace
+
+bool gemm_group_encode(const GemmArgs* gs, int count, GemmGroupItem* items, int* total_tiles) {
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  int tiles = 0;
+  for (int c = 0; c < count; ++c) {
+    const GemmArgs& g = gs[c];
+    if (g.fp8 || g.c32 || g.K <= 0 || g.K >= 256 || (g.K % 128) || g.K != gs[0].K || g.mode != gs[0].mode ||
+        (!g.R) != (!gs[0].R) || !g.C || g.M <= 0 || g.N <= 0)
+      return false;
+    const uint64_t kbytes = (uint64_t)g.K * 2;
+    CUtensorMap* ta = reinterpret_cast<CUtensorMap*>(items[c].maps[0]);
+    CUtensorMap* tb = reinterpret_cast<CUtensorMap*>(items[c].maps[1]);
+    CUtensorMap* tc = reinterpret_cast<CUtensorMap*>(items[c].maps[2]);
+    if (!make_map(ta, g.A, kbytes / 2, (uint64_t)g.M, (uint64_t)g.lda * 2, kRowBytes / 2, 128) ||
+        !make_map(tb, g.B, kbytes / 2, (uint64_t)g.N, (uint64_t)g.ldb * 2, kRowBytes / 2, kTJ) ||
+        !make_map(tc, g.C, (uint64_t)g.M, (uint64_t)g.N, (uint64_t)g.ldc * 2, 64, kTJ))
+      return false;
+    items[c].M = g.M;
+    items[c].N = g.N;
+    items[c].tiles_i = cdiv(g.M, 128);
+    items[c].tile_begin = tiles;
+    items[c].R = g.R;
+    items[c].ldr = g.ldr;
+    tiles += items[c].tiles_i * cdiv(g.N, kTJ);
+  }
+  *total_tiles = tiles;
+  return true;
+}
+
+cudaError_t gemm_tc_grouped(const GemmArgs& g, const GemmGroupItem* dev_items, int nitems, int total_tiles,
+                            cudaStream_t st, double flops, double bytes) {
+  using Cfg = TileCfg<128, 2>;
+  if (nitems <= 0 || total_tiles <= 0) return cudaSuccess;
+  TcParams p{};
+  p.has_c = 1;
+  p.nkb = (int)((uint64_t)g.K * 2 / kRowBytes);
+  p.tiles_i = 1;
+  p.ntiles = total_tiles;
+  p.mode = g.mode; p.sign = g.sign; p.fmt = g.fmt; p.fp8 = 0;
+  p.status = g.status;
+  const WaitBudget wb = wait_budget();
+  p.wait_polls = wb.polls;
+  p.wait_ns = wb.ns;
+  p.acc_cols = 128;
+  p.nbuf = 2;
+  p.ncols = 256;
+  static std::atomic<int> configured_for{-1};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_for.load() != dev) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    configured_for.store(dev);
+  }
+  const int grid = std::min(total_tiles, g.max_ctas > 0 ? std::min(g.max_ctas, num_sms()) : num_sms());
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));   // the items' maps are used instead
+  void* tok = prof_begin(st);
+  const cudaError_t e = launch_pdl(gemm_tc_kernel<128, 2>, dim3(grid), dim3(kThreads), Cfg::kSmem, st, none, none,
+                                   none, p, dev_items, nitems);
+  prof_end(tok, g.mode == kEpiSub ? kProfGemm : kProfGemmStore, flops, st, bytes);
+  count_launches(1);
+  return e;
+}
+
+namespace {
 
 // HPMXP_GEMM_TILE=128 keeps every product on the 128-row tile.
 bool wide_tiles_enabled() {

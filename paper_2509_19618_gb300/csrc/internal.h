@@ -117,6 +117,26 @@ struct GemmArgs {
 };
 cudaError_t gemm_tc(const GemmArgs& g, cudaStream_t st);
 cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st);
+
+// Grouped launches of the tensor-core engine: several independent products of
+// the same kind (same mode, sign, format and K, 16-bit operands, K < 256 so
+// all take 128-row tiles, R given for all or none) in ONE launch, the
+// persistent CTAs walking the concatenated tile lists.  One item per product,
+// in device memory (its tensor maps are read from there by the TMA unit).
+struct alignas(128) GemmGroupItem {
+  unsigned char maps[3][128];   // CUtensorMap of A, B and C
+  int M, N, tiles_i, tile_begin;
+  void* R;
+  int64_t ldr;
+};
+// Encodes the items of `count` products into `items` (host memory); returns
+// false if they cannot share a launch.  *total_tiles receives the tile count.
+bool gemm_group_encode(const GemmArgs* gs, int count, GemmGroupItem* items, int* total_tiles);
+// Launches the grouped product: proto carries the shared fields (mode, sign,
+// fmt, K, status, max_ctas), dev_items the encoded items copied to the device;
+// flops and bytes (the items' total) only feed the optional event timing.
+cudaError_t gemm_tc_grouped(const GemmArgs& proto, const GemmGroupItem* dev_items, int nitems, int total_tiles,
+                            cudaStream_t st, double flops = 0.0, double bytes = 0.0);
 // Returns the engine selected for the factorization (0 = tcgen05, 1 = SIMT
 // validation engine, chosen by HPMXP_GEMM_ENGINE=simt for parity tests).
 int gemm_engine();
@@ -129,6 +149,9 @@ cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int6
 cudaError_t launch_balance(int64_t n, const double* A, int64_t lda, int prec, double* rs, double* cs,
                            cudaStream_t st);
 size_t factor_ws_bytes(int64_t n, int prec, int nb);
+size_t factor_batched_ws_bytes(const hpmxp_problem* probs, int count);
+hpmxp_status factor_batched(const hpmxp_problem* probs, int count, int prec, hpmxp_status* status, void* ws,
+                            size_t ws_bytes, cudaStream_t st);
 hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, void* LU,
                     int64_t ldlu, void* ws, size_t ws_bytes, cudaStream_t st, const double* rs = nullptr,
                     const double* cs = nullptr);

@@ -23,6 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 namespace hpmxp {
@@ -1214,6 +1215,226 @@ hpmxp_status solve_ir(int64_t n, const double* A, int64_t lda, const void* LU, i
       info[r].reserved = 0;
     }
     if (s.brief[r].status != HPMXP_OK && worst == HPMXP_OK) worst = s.brief[r].status;
+  }
+  return (hpmxp_status)worst;
+}
+
+// ---------------------------------------------------------------------------
+// Batched GMRES-IR: every system's refinement as a state machine (the phases
+// of Solver::run), advanced in lockstep.  Each round issues every active
+// system's next phase on its stream (systems spread over a pool of streams,
+// so small systems' kernels run side by side) with an asynchronous copy of its
+// brief, then waits once per system and decides every next phase on the host:
+// one host decision point per phase for the whole batch.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kPoolStreams = 8;
+
+struct StreamPool {
+  std::mutex mu;
+  bool ok = false;
+  cudaStream_t st[kPoolStreams] = {};
+  cudaEvent_t ev[kPoolStreams] = {};
+};
+
+StreamPool& stream_pool(int dev) {
+  static StreamPool tab[64];
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  StreamPool& p = tab[dev & 63];
+  if (!p.ok) {
+    bool good = true;
+    for (int i = 0; i < kPoolStreams && good; ++i)
+      good = cudaStreamCreateWithFlags(&p.st[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p.ev[i], cudaEventDisableTiming) == cudaSuccess;
+    p.ok = good;
+  }
+  return p;
+}
+
+enum Phase { kResid, kCycle, kArnoldi, kDone };
+
+struct BatchItem {
+  Solver s;
+  Phase ph = kResid;
+  int j = 0;            // next Arnoldi step
+  bool first = true;    // the first residual also takes ||A||
+  bool finish = false;  // cycle_finish + update to issue before the next residual
+  cudaEvent_t ev = nullptr;
+  Brief* host = nullptr;   // pinned copy of the brief
+};
+
+size_t batch_solve_bytes(const hpmxp_problem* probs, int count, int restart) {
+  size_t b = 0;
+  for (int q = 0; q < count; ++q) b += round_up<size_t>(solve_ws_bytes(probs[q].n, probs[q].nrhs, restart), 256);
+  return b;
+}
+}  // namespace
+
+size_t solve_batched_ws_bytes(const hpmxp_problem* probs, int count, int restart) {
+  return batch_solve_bytes(probs, count, restart);
+}
+
+hpmxp_status solve_ir_batched(const hpmxp_problem* probs, int count, int prec, const hpmxp_ir_params& prm,
+                              hpmxp_ir_info* info, void* ws, cudaStream_t caller) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  StreamPool& pool = stream_pool(dev);
+  if (!pool.ok) return HPMXP_ECUDA;
+  std::lock_guard<std::mutex> lk(pool.mu);   // one batched solve drives a device's pool at a time
+  // pinned briefs and per-system events, kept by the calling thread
+  struct HostSide {
+    Brief* pinned = nullptr;
+    size_t cap = 0;
+    std::vector<cudaEvent_t> ev;
+    ~HostSide() {
+      if (pinned) cudaFreeHost(pinned);
+      for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    }
+  };
+  thread_local HostSide hs;
+  const size_t need = (size_t)count * kMaxK;
+  if (hs.cap < need) {
+    if (hs.pinned) cudaFreeHost(hs.pinned);
+    hs.pinned = nullptr;
+    hs.cap = 0;
+    if ((e = cudaMallocHost(&hs.pinned, sizeof(Brief) * need)) != cudaSuccess) return status_from_cuda(e);
+    hs.cap = need;
+  }
+  while ((int)hs.ev.size() < count) {
+    cudaEvent_t x;
+    if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess) return status_from_cuda(e);
+    hs.ev.push_back(x);
+  }
+  std::vector<BatchItem> it((size_t)count);
+  char* base = (char*)ws;
+  for (int q = 0; q < count; ++q) {
+    Solver& s = it[q].s;
+    s.n = probs[q].n; s.K = (int)probs[q].nrhs; s.m = prm.restart;
+    s.A = probs[q].A; s.lda = probs[q].lda;
+    s.LU = (const uint16_t*)probs[q].LU; s.ldlu = probs[q].ldlu; s.fmt = fmt_of(prec);
+    s.B = probs[q].b; s.ldb = probs[q].ldb; s.X = probs[q].x; s.ldx = probs[q].ldx;
+    s.prm = prm;
+    s.w = carve_solve(base, s.n, s.K, prm.restart);
+    base += round_up<size_t>(s.w.bytes, 256);
+    s.st = pool.st[q % kPoolStreams];
+    it[q].ev = hs.ev[q];
+    it[q].host = hs.pinned + (size_t)q * kMaxK;
+  }
+  // fork from the caller's stream
+  cudaEvent_t fork_ev = pool.ev[0];
+  if ((e = cudaEventRecord(fork_ev, caller)) != cudaSuccess) return status_from_cuda(e);
+  for (int i = 0; i < kPoolStreams && i < count; ++i)
+    if ((e = cudaStreamWaitEvent(pool.st[i], fork_ev, 0)) != cudaSuccess) return status_from_cuda(e);
+  for (int q = 0; q < count && e == cudaSuccess; ++q) {
+    Solver& s = it[q].s;
+    if ((e = s.setup()) == cudaSuccess) e = s.precond(s.B, s.ldb, s.X, s.ldx);   // x0 = U^{-1} L^{-1} b
+  }
+  auto any = [](const BatchItem& b, int Brief::*f) {
+    for (int r = 0; r < b.s.K; ++r)
+      if (b.host[r].*f) return true;
+    return false;
+  };
+  int active = count;
+  while (active > 0 && e == cudaSuccess) {
+    // issue every active system's next phase
+    for (int q = 0; q < count && e == cudaSuccess; ++q) {
+      BatchItem& b = it[q];
+      if (b.ph == kDone) continue;
+      Solver& s = b.s;
+      const SolveParams sp{s.K, s.m, s.prm.max_iters, s.prm.inner_tol, s.prm.theta, s.prm.accept, s.n};
+      const cudaStream_t st = s.st;
+      if (b.finish) {
+        cycle_finish_kernel<<<1, 32, 0, st>>>(sp, s.w.st);
+        update_kernel<<<(unsigned)cdiv<int64_t>(s.n, 256), 256, 0, st>>>(s.n, s.K, s.X, s.ldx, s.w.V, s.n,
+                                                                         s.ldv_rhs(), s.w.st);
+        count_launches(2);
+        b.finish = false;
+      }
+      if (b.ph == kResid) {
+        e = residual(s.n, s.K, s.A, s.lda, s.X, s.ldx, s.B, s.ldb, s.w.r, s.n, b.first ? 1 : 0, 1, s.w, st);
+        check_kernel<<<1, 32, 0, st>>>(sp, s.w.st, s.w.brief, b.first ? 1 : 0);
+        count_launches(1);
+        b.first = false;
+      } else if (b.ph == kCycle) {
+        e = s.precond(s.w.r, s.n, s.w.tmp, s.n);
+        norm2_kernel<<<kRedBlocks, 256, 0, st>>>(s.n, s.K, s.w.tmp, s.n, s.w.st, s.w.partials, s.w.counter);
+        cycle_start_kernel<<<1, 32, 0, st>>>(sp, s.w.st, s.w.brief);
+        scale_kernel<<<(unsigned)cdiv<int64_t>(s.n, 256), 256, 0, st>>>(s.n, s.K, s.w.tmp, s.n, s.w.V, s.ldv_rhs(),
+                                                                         s.w.st, 0);
+        count_launches(3);
+      } else {   // Arnoldi step j
+        const int j = b.j;
+        e = residual(s.n, s.K, s.A, s.lda, s.w.V + (int64_t)j * s.n, s.ldv_rhs(), nullptr, 0, s.w.tmp, s.n,
+                     s.prm.matvec_fp32 ? 3 : 0, 0, s.w, st);
+        if (e == cudaSuccess) e = s.precond(s.w.tmp, s.n, s.w.w, s.n);
+        for (int i = 0; i <= j + 1; ++i)
+          mgs_kernel<<<kRedBlocks, 256, 0, st>>>(s.n, s.K, s.m, j, i, s.w.w, s.n, s.w.V, s.n, s.ldv_rhs(), s.w.st,
+                                                 s.w.partials, s.w.counter);
+        givens_kernel<<<1, 32, 0, st>>>(sp, j, s.w.st, s.w.brief);
+        scale_kernel<<<(unsigned)cdiv<int64_t>(s.n, 256), 256, 0, st>>>(s.n, s.K, s.w.w, s.n,
+                                                                         s.w.V + (int64_t)(j + 1) * s.n,
+                                                                         s.ldv_rhs(), s.w.st, 1);
+        count_launches(j + 4);
+      }
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b.host, s.w.brief, sizeof(Brief) * s.K, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaEventRecord(b.ev, st);
+    }
+    if (e != cudaSuccess) break;
+    // one decision point for the batch
+    for (int q = 0; q < count && e == cudaSuccess; ++q) {
+      BatchItem& b = it[q];
+      if (b.ph == kDone) continue;
+      if ((e = cudaEventSynchronize(b.ev)) != cudaSuccess) break;
+      if (b.ph == kResid) {
+        b.ph = any(b, &Brief::outer_active) ? kCycle : kDone;
+      } else if (b.ph == kCycle) {
+        if (!any(b, &Brief::outer_active)) {
+          b.ph = kDone;
+        } else if (any(b, &Brief::cycle_active) && b.s.m > 0) {
+          b.ph = kArnoldi;
+          b.j = 0;
+        } else {
+          b.finish = true;
+          b.ph = kResid;
+        }
+      } else {
+        b.j += 1;
+        if (!(b.j < b.s.m && any(b, &Brief::cycle_active))) {
+          b.finish = true;
+          b.ph = kResid;
+        }
+      }
+      if (b.ph == kDone) --active;
+    }
+  }
+  // join back to the caller's stream
+  for (int i = 0; i < kPoolStreams && i < count; ++i) {
+    cudaEventRecord(pool.ev[i], pool.st[i]);
+    cudaStreamWaitEvent(caller, pool.ev[i], 0);
+  }
+  if (e != cudaSuccess) return status_from_cuda(e);
+  int worst = HPMXP_OK;
+  int64_t off = 0;
+  for (int q = 0; q < count; ++q) {
+    BatchItem& b = it[q];
+    uint32_t word = 0;
+    if ((e = read_to_host(&word, b.s.w.status, 4, caller)) != cudaSuccess) return status_from_cuda(e);
+    if (word && worst == HPMXP_OK) worst = status_from_word(word);
+    for (int r = 0; r < b.s.K; ++r) {
+      if (info) {
+        info[off + r].iters = b.host[r].iters;
+        info[off + r].outer = b.host[r].outer;
+        info[off + r].scaled_resid = b.host[r].sr;
+        info[off + r].status = b.host[r].status;
+        info[off + r].reserved = 0;
+      }
+      if (b.host[r].status != HPMXP_OK && worst == HPMXP_OK) worst = b.host[r].status;
+    }
+    off += b.s.K;
   }
   return (hpmxp_status)worst;
 }

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 namespace hpmxp {
 namespace {
@@ -395,17 +396,15 @@ __device__ inline void store16(float* p, const float (&v)[kPW]) {
     *reinterpret_cast<float4*>(p + 4 * m) = make_float4(v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
 }
 
-__global__ void __launch_bounds__(kGetrfThreads)
-getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_t* __restrict__ linv,
-                  int64_t ldl, uint16_t* __restrict__ uinvT, int64_t ldu, uint32_t* status) {
+__device__ __forceinline__ void getrf_block(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt,
+                                            uint16_t* __restrict__ linv, int64_t ldl, uint16_t* __restrict__ uinvT,
+                                            int64_t ldu, uint32_t* status) {
   extern __shared__ float sm[];
   float* a = sm;                  // a[j * kP + i] = D(i, j); later the stored L and U
   float* x = sm + kB * kP;        // X = L^{-1}, x[c * kP + r] = X(r, c)
   float* y = sm + 2 * kB * kP;    // Y = U^{-1}, y[c * kP + r] = Y(r, c)
   float* urow = sm + 3 * kB * kP; // [2][kPW] pivot row of the current panel step
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  pdl_wait();      // may start while the previous kernel of the stream finishes
-  pdl_trigger();
 
   // a full block whose columns start on 16-byte boundaries moves 8 entries
   // (16 bytes) per access
@@ -663,19 +662,44 @@ getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_
   }
 }
 
+__global__ void __launch_bounds__(kGetrfThreads)
+getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_t* __restrict__ linv,
+                  int64_t ldl, uint16_t* __restrict__ uinvT, int64_t ldu, uint32_t* status) {
+  pdl_wait();      // may start while the previous kernel of the stream finishes
+  pdl_trigger();
+  getrf_block(b, D, ldd, fmt, linv, ldl, uinvT, ldu, status);
+}
+
+// Grouped diagonal blocks: CTA t factors task t's block (batched
+// factorization: one launch for the current block of every problem).
+struct GetrfTask {
+  uint16_t* D;
+  int64_t ldd;
+  uint16_t* linv;
+  int64_t ldl;
+  uint16_t* uinvT;
+  int64_t ldu;
+  uint32_t* status;
+  int b;
+};
+__global__ void __launch_bounds__(kGetrfThreads) getrf_grouped_kernel(const GetrfTask* __restrict__ tasks, int fmt) {
+  pdl_wait();
+  pdl_trigger();
+  const GetrfTask t = tasks[blockIdx.x];
+  getrf_block(t.b, t.D, t.ldd, fmt, t.linv, t.ldl, t.uinvT, t.ldu, t.status);
+}
+
 // Column-major block (rows x cols at src, lds) -> row-major (dst[i*ldd + j]),
 // through 64 x 64 tiles in shared memory (t[j][i], rows padded to 144 bytes).
 // A whole tile with 16-byte aligned columns and rows moves by 16-byte loads
 // (8 rows of one column) and 16-byte stores (8 columns of one row); the
 // gathers in between read 32 consecutive rows per warp (no bank conflicts).
 constexpr int kPackT = 64, kPackPad = 72;
-__global__ void __launch_bounds__(256) pack_rows_kernel(int64_t rows, int cols, const uint16_t* __restrict__ src,
-                                                        int64_t lds, uint16_t* __restrict__ dst, int64_t ldd) {
+__device__ __forceinline__ void pack_tile(int64_t rows, int cols, const uint16_t* __restrict__ src, int64_t lds,
+                                          uint16_t* __restrict__ dst, int64_t ldd, int64_t bx, int by) {
   __shared__ __align__(16) uint16_t t[kPackT][kPackPad];
-  pdl_wait();
-  pdl_trigger();
-  const int64_t i0 = (int64_t)blockIdx.x * kPackT;
-  const int j0 = blockIdx.y * kPackT;
+  const int64_t i0 = bx * kPackT;
+  const int j0 = by * kPackT;
   const bool whole = i0 + kPackT <= rows && j0 + kPackT <= cols && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
                      (lds & 7) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 && (ldd & 7) == 0;
   if (whole) {
@@ -703,6 +727,38 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(int64_t rows, int cols, 
       if (i0 + i < rows && j0 + j < cols) dst[(i0 + i) * ldd + j0 + j] = t[j][i];
     }
   }
+}
+
+__global__ void __launch_bounds__(256) pack_rows_kernel(int64_t rows, int cols, const uint16_t* __restrict__ src,
+                                                        int64_t lds, uint16_t* __restrict__ dst, int64_t ldd) {
+  pdl_wait();
+  pdl_trigger();
+  pack_tile(rows, cols, src, lds, dst, ldd, blockIdx.x, blockIdx.y);
+}
+
+// Grouped column-panel packs (batched factorization): the CTAs walk the
+// concatenated 64 x 64 tile lists of the tasks.
+struct PackTask {
+  const uint16_t* src;
+  int64_t lds;
+  uint16_t* dst;
+  int64_t ldd;
+  int64_t rows;
+  int cols, tile_begin;
+};
+__global__ void __launch_bounds__(256) pack_grouped_kernel(const PackTask* __restrict__ tasks, int ntasks) {
+  pdl_wait();
+  pdl_trigger();
+  const int t = blockIdx.x;
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  const PackTask& k = tasks[lo];
+  const int lt = t - k.tile_begin;
+  const int64_t tr = cdiv<int64_t>(k.rows, kPackT);
+  pack_tile(k.rows, k.cols, k.src, k.lds, k.dst, k.ldd, lt % tr, (int)(lt / tr));
 }
 
 // W_s = st(-Linv_ss L_{s,0:s}) into the first ws columns of the row-major
@@ -1322,6 +1378,220 @@ cudaError_t launch_cast(int64_t n, const double* A, int64_t lda, void* out, int6
 }
 
 size_t factor_ws_bytes(int64_t n, int prec, int nb) { return carve(nullptr, n, prec, nb).bytes; }
+
+// ---------------------------------------------------------------------------
+// Batched factorization: every system in lockstep at depth 128, one grouped
+// launch per stage for all active systems.  Per step k (block width b = 128):
+// getrf of each diagonal block (one CTA each), U12 = Linv A12 (grouped
+// tcgen05, in place), pack of A21 (grouped), L21 = A21 Uinv with its
+// row-major copy (grouped), A22 -= L21 U12 (grouped).  The same tiles as
+// hpmxp_factor at nb = 128 without look-ahead, so the same bits.
+// ---------------------------------------------------------------------------
+namespace {
+struct BatchLayout {
+  uint32_t* status;        // count + 1 words: one per system, the last for the GEMM launches
+  uint16_t** Lp;           // per system: packed column panel, row major, round_up(n, 128) x 128
+  uint16_t** Aop;          // per system: Linv (K-major operand, 128 x 128)
+  uint16_t** Bop;          // per system: Uinv^T
+  GemmGroupItem* items;
+  GetrfTask* getrf;
+  PackTask* pack;
+  size_t bytes;
+};
+
+struct BatchCounts { int64_t items = 0, getrf = 0, pack = 0; };
+
+BatchCounts batch_counts(const hpmxp_problem* probs, int count) {
+  BatchCounts c;
+  for (int q = 0; q < count; ++q) {
+    const int64_t steps = cdiv<int64_t>(probs[q].n, kB);
+    c.getrf += steps;
+    c.pack += steps - 1;
+    c.items += 3 * (steps - 1);
+  }
+  return c;
+}
+
+BatchLayout carve_batch(void* base, const hpmxp_problem* probs, int count, std::vector<uint16_t*>* ptrs) {
+  BatchLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? (char*)base + off : nullptr;
+    off += round_up<size_t>(bytes, 256);
+    return p;
+  };
+  L.status = (uint32_t*)take(sizeof(uint32_t) * (count + 1));
+  if (ptrs) ptrs->assign(3 * (size_t)count, nullptr);
+  for (int q = 0; q < count; ++q) {
+    const int64_t nr = round_up<int64_t>(probs[q].n, kB);
+    uint16_t* lp = (uint16_t*)take(sizeof(uint16_t) * nr * kB);
+    uint16_t* ao = (uint16_t*)take(sizeof(uint16_t) * kB * kB);
+    uint16_t* bo = (uint16_t*)take(sizeof(uint16_t) * kB * kB);
+    if (ptrs) { (*ptrs)[3 * q] = lp; (*ptrs)[3 * q + 1] = ao; (*ptrs)[3 * q + 2] = bo; }
+  }
+  const BatchCounts c = batch_counts(probs, count);
+  L.items = (GemmGroupItem*)take(sizeof(GemmGroupItem) * std::max<int64_t>(c.items, 1));
+  L.getrf = (GetrfTask*)take(sizeof(GetrfTask) * std::max<int64_t>(c.getrf, 1));
+  L.pack = (PackTask*)take(sizeof(PackTask) * std::max<int64_t>(c.pack, 1));
+  L.bytes = off;
+  return L;
+}
+}  // namespace
+
+size_t factor_batched_ws_bytes(const hpmxp_problem* probs, int count) {
+  return carve_batch(nullptr, probs, count, nullptr).bytes;
+}
+
+hpmxp_status factor_batched(const hpmxp_problem* probs, int count, int prec, hpmxp_status* status_out, void* ws,
+                            size_t ws_bytes, cudaStream_t st) {
+  (void)ws_bytes;
+  const int fmt = fmt_of(prec);
+  std::vector<uint16_t*> ptr;
+  const BatchLayout W = carve_batch(ws, probs, count, &ptr);
+  int64_t nmax = 0;
+  for (int q = 0; q < count; ++q) nmax = std::max(nmax, probs[q].n);
+  const int64_t steps = cdiv<int64_t>(nmax, kB);
+  const bool simt = gemm_engine() == 1;
+  auto at = [&](int q, int64_t i, int64_t j) { return (uint16_t*)probs[q].LU + i + j * probs[q].ldlu; };
+
+  // the whole plan, host side: per step the getrf tasks, pack tasks and the
+  // three products' items, each step's part contiguous
+  std::vector<GetrfTask> gt;
+  std::vector<PackTask> pt;
+  std::vector<GemmGroupItem> items;
+  std::vector<GemmArgs> all_args;   // the products themselves (SIMT engine; flop counts)
+  struct Step { int64_t g0, ng, p0, np, ptiles, u0, nu, tu, l0, nl, tl, s0, ns, ts; double fu, fl, fs; };
+  std::vector<Step> plan(steps);
+  GemmArgs proto{};
+  proto.K = kB; proto.fmt = fmt; proto.status = W.status + count;
+  for (int64_t s = 0; s < steps; ++s) {
+    const int64_t k = s * kB;
+    Step& S = plan[s];
+    S = Step{};
+    S.g0 = gt.size();
+    for (int q = 0; q < count; ++q) {
+      const int64_t n = probs[q].n;
+      if (n <= k) continue;
+      GetrfTask t{};
+      t.b = (int)std::min<int64_t>(kB, n - k);
+      t.D = at(q, k, k); t.ldd = probs[q].ldlu;
+      t.linv = ptr[3 * q + 1]; t.ldl = kB;
+      t.uinvT = ptr[3 * q + 2]; t.ldu = kB;
+      t.status = W.status + q;
+      gt.push_back(t);
+    }
+    S.ng = (int64_t)gt.size() - S.g0;
+    // products of the systems with a trailing part
+    std::vector<GemmArgs> U, Lg, Sg;
+    S.p0 = pt.size();
+    int ptiles = 0;
+    for (int q = 0; q < count; ++q) {
+      const int64_t n = probs[q].n, m = n - k - kB;
+      if (m <= 0) continue;
+      const int64_t ld = probs[q].ldlu;
+      PackTask pk{};
+      pk.src = at(q, k + kB, k); pk.lds = ld; pk.dst = ptr[3 * q]; pk.ldd = kB; pk.rows = m; pk.cols = kB;
+      pk.tile_begin = ptiles;
+      ptiles += (int)(cdiv<int64_t>(m, kPackT) * cdiv(kB, kPackT));
+      pt.push_back(pk);
+      GemmArgs u = proto;   // U12 = st(Linv A12), in place
+      u.M = kB; u.N = (int)m; u.A = ptr[3 * q + 1]; u.lda = kB; u.B = at(q, k, k + kB); u.ldb = ld;
+      u.C = at(q, k, k + kB); u.ldc = ld; u.mode = kEpiStore; u.sign = 1.0f;
+      U.push_back(u);
+      GemmArgs l = proto;   // L21 = st(A21 Uinv), column major into LU and row major over the packed copy
+      l.M = (int)m; l.N = kB; l.A = ptr[3 * q]; l.lda = kB; l.B = ptr[3 * q + 2]; l.ldb = kB;
+      l.C = at(q, k + kB, k); l.ldc = ld; l.R = ptr[3 * q]; l.ldr = kB; l.mode = kEpiStore; l.sign = 1.0f;
+      Lg.push_back(l);
+      GemmArgs t = proto;   // A22 <- st(A22 - L21 U12)
+      t.M = (int)m; t.N = (int)m; t.A = ptr[3 * q]; t.lda = kB; t.B = at(q, k, k + kB); t.ldb = ld;
+      t.C = at(q, k + kB, k + kB); t.ldc = ld; t.mode = kEpiSub;
+      Sg.push_back(t);
+    }
+    S.np = (int64_t)pt.size() - S.p0;
+    S.ptiles = ptiles;
+    auto add = [&](std::vector<GemmArgs>& v, int64_t& first, int64_t& num, int64_t& tiles, double& flops) {
+      first = items.size();
+      num = v.size();
+      tiles = 0;
+      flops = 0.0;
+      if (v.empty()) return true;
+      items.resize(items.size() + v.size());
+      int tt = 0;
+      if (!gemm_group_encode(v.data(), (int)v.size(), items.data() + first, &tt)) return false;
+      tiles = tt;
+      for (const GemmArgs& g : v) flops += 2.0 * g.M * (double)g.N * g.K;
+      all_args.insert(all_args.end(), v.begin(), v.end());
+      return true;
+    };
+    if (!add(U, S.u0, S.nu, S.tu, S.fu) || !add(Lg, S.l0, S.nl, S.tl, S.fl) || !add(Sg, S.s0, S.ns, S.ts, S.fs))
+      return HPMXP_EINVAL;
+  }
+  // one copy of the plan into the workspace
+  cudaError_t e = cudaMemsetAsync(W.status, 0, sizeof(uint32_t) * (count + 1), st);
+  if (e == cudaSuccess && !gt.empty())
+    e = cudaMemcpyAsync(W.getrf, gt.data(), sizeof(GetrfTask) * gt.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !pt.empty())
+    e = cudaMemcpyAsync(W.pack, pt.data(), sizeof(PackTask) * pt.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpyAsync(W.items, items.data(), sizeof(GemmGroupItem) * items.size(), cudaMemcpyHostToDevice, st);
+  for (int q = 0; q < count && e == cudaSuccess; ++q)
+    e = launch_cast(probs[q].n, probs[q].A, probs[q].lda, probs[q].LU, probs[q].ldlu, fmt, st);
+  static std::atomic<int> attr_dev{-1};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (e == cudaSuccess && attr_dev.load() != dev) {
+    e = cudaFuncSetAttribute(getrf_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGetrfSmem);
+    if (e == cudaSuccess) attr_dev.store(dev);
+  }
+  size_t ai = 0;   // index into all_args (SIMT engine)
+  auto run_products = [&](int64_t first, int64_t num, int64_t tiles, double flops, const GemmArgs& kind) {
+    if (num == 0 || e != cudaSuccess) return;
+    if (simt) {
+      for (int64_t c = 0; c < num && e == cudaSuccess; ++c) e = gemm_simt(all_args[ai + c], st);
+    } else {
+      double bytes = 0.0;
+      for (int64_t c = 0; c < num; ++c) {
+        const GemmArgs& g = all_args[ai + c];
+        bytes += ((double)g.M + g.N) * g.K * 2.0 + (double)g.M * g.N * 2.0 * (kind.mode == kEpiSub ? 2.0 : 1.0) +
+                 (g.R ? (double)g.M * g.N * 2.0 : 0.0);
+      }
+      e = gemm_tc_grouped(kind, W.items + first, (int)num, (int)tiles, st, flops, bytes);
+    }
+    ai += num;
+  };
+  for (int64_t s = 0; s < steps && e == cudaSuccess; ++s) {
+    const Step& S = plan[s];
+    void* tok = prof_begin(st);
+    e = launch_pdl(getrf_grouped_kernel, dim3((unsigned)S.ng), dim3(kGetrfThreads), kGetrfSmem, st,
+                   (const GetrfTask*)(W.getrf + S.g0), fmt);
+    prof_end(tok, kProfGetrf, (double)S.ng * kB * kB * kB * 2.0, st);
+    count_launches(1);
+    if (S.np == 0) continue;
+    GemmArgs ku = proto; ku.mode = kEpiStore; ku.sign = 1.0f;
+    GemmArgs ks = proto; ks.mode = kEpiSub;
+    run_products(S.u0, S.nu, S.tu, S.fu, ku);
+    if (e == cudaSuccess) {
+      void* tk = prof_begin(st);
+      e = launch_pdl(pack_grouped_kernel, dim3((unsigned)S.ptiles), dim3(256), 0, st,
+                     (const PackTask*)(W.pack + S.p0), (int)S.np);
+      prof_end(tk, kProfPanel, 0.0, st);
+      count_launches(1);
+    }
+    run_products(S.l0, S.nl, S.tl, S.fl, ku);
+    run_products(S.s0, S.ns, S.ts, S.fs, ks);
+  }
+  if (e != cudaSuccess) return status_from_cuda(e);
+  std::vector<uint32_t> words((size_t)count + 1);
+  e = read_to_host(words.data(), W.status, sizeof(uint32_t) * (count + 1), st);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  hpmxp_status first = status_from_word(words[count]);
+  for (int q = 0; q < count; ++q) {
+    const hpmxp_status sq = words[count] ? status_from_word(words[count]) : status_from_word(words[q]);
+    if (status_out) status_out[q] = sq;
+    if (first == HPMXP_OK) first = sq;
+  }
+  return first;
+}
 
 cudaError_t launch_balance(int64_t n, const double* A, int64_t lda, int prec, double* rs, double* cs,
                            cudaStream_t st) {
