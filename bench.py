@@ -66,6 +66,8 @@ def parse():
                     help="1: balance and scale A (hpmxp_balance) inside every timed solve")
     ap.add_argument("--serving-requests", type=int, default=600,
                     help="requests of the serving sub-record at 1000/s (a third of them at 100/s); 0: skip")
+    ap.add_argument("--serving-batch", type=int, default=16, help="serving: requests per batch in batch mode")
+    ap.add_argument("--serving-batch-workers", type=int, default=4, help="serving: workers in batch mode")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
@@ -425,6 +427,21 @@ def serving_record(args, dev, params) -> dict:
                                 "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "mean_queue_ms": sm["mean_queue_ms"],
                                 "tflops": sm["tflops"], "valid": sm["valid"], "failed": sm["failed"],
                                 "mean_ir_iters": sm["mean_iters"], "max_scaled_residual": sm["max_scaled_resid"]})
+    # batch mode: each worker runs up to `serving_batch` queued requests through the batched
+    # entry points (grouped factorization kernels, lockstep refinement)
+    out["batched"] = []
+    with serve.Executor(workers=args.serving_batch_workers, arena_bytes=int(args.arena_gb * (1 << 30)), device=dev,
+                        batch=args.serving_batch) as exb:
+        serve.run_stream(exb, warm, PREC[args.prec], params)
+        for rate, count in ((1000.0, args.serving_requests), (100.0, max(1, args.serving_requests // 3))):
+            specs = serve.request_stream(count, rate, stream_seed=2509)
+            comps = serve.run_stream(exb, specs, PREC[args.prec], params)
+            sm = serve.summarize(specs, comps)
+            out["batched"].append({"rate": rate, "requests": count, "systems_per_s": sm["systems_per_s"],
+                                   "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"],
+                                   "mean_queue_ms": sm["mean_queue_ms"], "tflops": sm["tflops"],
+                                   "valid": sm["valid"], "failed": sm["failed"],
+                                   "workers": args.serving_batch_workers, "max_batch": args.serving_batch})
     sub = serve.request_stream(max(1, args.serving_requests // 3), 0.0, stream_seed=2509)
     with serve.Executor(workers=1, arena_bytes=int(args.arena_gb * (1 << 30)), device=dev) as ex1:
         c1 = serve.run_stream(ex1, sub, PREC[args.prec], params, one_at_a_time=True)

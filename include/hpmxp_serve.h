@@ -69,6 +69,17 @@ size_t hpmxp_request_footprint(const hpmxp_request* r);
 hpmxp_status hpmxp_executor_create(int device, int workers, void* arena, size_t arena_bytes,
                                    hpmxp_executor** out);
 
+/* The same executor in batch mode: each worker takes the request at the head
+ * of the queue and the ones queued right after it (up to max_batch, 1..256,
+ * in arrival order, as many as fit the arena together) and runs them as one
+ * batch through hpmxp_factor_batched and hpmxp_solve_ir_batched (grouped
+ * kernels, lockstep refinement); requests in HPMXP_BF16 / HPMXP_FP16 with nb 0
+ * or 128 (batches use depth 128) and equal refinement parameters share a
+ * batch, any other runs alone.  Every request of a batch completes when the
+ * batch does; max_batch = 1 is the plain executor. */
+hpmxp_status hpmxp_executor_create_batched(int device, int workers, int max_batch, void* arena, size_t arena_bytes,
+                                           hpmxp_executor** out);
+
 /* Queues a copy of *r and returns at once.  HPMXP_EINVAL: bad request;
  * HPMXP_ENOMEM: its footprint exceeds the whole arena (it could never run).
  * Caller buffers named by the request must stay valid until its completion. */

@@ -121,6 +121,7 @@ def load():
             "hpmxp_test_set_wait_budget": ([ctypes.c_longlong, ctypes.c_ulonglong], i32),
             "hpmxp_request_footprint": ([ctypes.POINTER(Request)], sz),
             "hpmxp_executor_create": ([i32, i32, P, sz, ctypes.POINTER(P)], i32),
+            "hpmxp_executor_create_batched": ([i32, i32, i32, P, sz, ctypes.POINTER(P)], i32),
             "hpmxp_executor_submit": ([P, ctypes.POINTER(Request)], i32),
             "hpmxp_executor_poll": ([P, ctypes.POINTER(Completion), i32, i32], i32),
             "hpmxp_executor_outstanding": ([P], i64),
@@ -322,6 +323,13 @@ def hpmxp_executor_create(device: int, workers: int, arena: int, arena_bytes: in
     """Returns (status, handle)."""
     h = ctypes.c_void_p()
     st = load().hpmxp_executor_create(device, workers, arena, arena_bytes, ctypes.byref(h))
+    return st, h
+
+
+def hpmxp_executor_create_batched(device: int, workers: int, max_batch: int, arena: int, arena_bytes: int):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    st = load().hpmxp_executor_create_batched(device, workers, max_batch, arena, arena_bytes, ctypes.byref(h))
     return st, h
 
 

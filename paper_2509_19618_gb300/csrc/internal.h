@@ -162,6 +162,7 @@ cudaError_t lu_solve_f64(int64_t n, const double* LU, int64_t ld, double* X, int
                          cudaStream_t st);
 
 // ir.cu
+size_t solve_batched_ws_bytes(const hpmxp_problem* probs, int count, int restart);
 size_t solve_ws_bytes(int64_t n, int64_t nrhs, int restart);
 size_t solve_a32_bytes(int64_t n);   // optional fp32 copy of A after the solve workspace
 cudaError_t fill_smem(uint32_t pattern, cudaStream_t st);   // test support

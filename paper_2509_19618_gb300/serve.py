@@ -73,14 +73,21 @@ def make_request(spec: Spec, prec: int = capi.BF16, nb: int = 0, params: capi.IR
 class Executor:
     """Owns the device arena (torch-allocated, once) and the native executor."""
 
-    def __init__(self, workers: int = 8, arena_bytes: int = 16 << 30, device=None):
+    def __init__(self, workers: int = 8, arena_bytes: int = 16 << 30, device=None, batch: int = 1):
+        """batch > 1: batch mode (hpmxp_executor_create_batched): each worker runs up
+        to `batch` queued requests at once through the batched entry points."""
         dev = torch.device(device if device is not None else "cuda")
         index = dev.index if dev.index is not None else torch.cuda.current_device()
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
         torch.cuda.synchronize(dev)
-        st, h = capi.hpmxp_executor_create(index, workers, self.arena.data_ptr(), int(arena_bytes))
+        if batch > 1:
+            st, h = capi.hpmxp_executor_create_batched(index, workers, batch, self.arena.data_ptr(),
+                                                       int(arena_bytes))
+        else:
+            st, h = capi.hpmxp_executor_create(index, workers, self.arena.data_ptr(), int(arena_bytes))
         if st != capi.OK:
             raise capi.HpmxpError("hpmxp_executor_create", st)
+        self.batch = batch
         self.h = h
         self.workers = workers
         self._buf = (capi.Completion * 256)()

@@ -98,3 +98,27 @@ def test_open_loop_stream_with_arrivals():
     _check_valid(comps)
     summ = serve.summarize(specs, comps)
     assert summ["valid"] and summ["requests"] == 30 and summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_batched_executor_equals_plain_executor(mixed):
+    """Batch mode (grouped factorization, lockstep refinement, several requests
+    per worker at once) gives bit-for-bit the x of the plain executor: every
+    request here has n < 4096, so both factor at depth 128 with the same tiles."""
+    specs, xs, comps = mixed
+    xsb = _xs(specs)
+    with serve.Executor(workers=2, arena_bytes=1 << 30, device=DEV, batch=8) as ex:
+        compsb = serve.run_stream(ex, specs, xs=xsb)
+    torch.cuda.synchronize()
+    _check_valid(compsb)
+    for s, c, cb in zip(specs, comps, compsb):
+        assert torch.equal(xs[s.id][:, : s.n], xsb[s.id][:, : s.n]), s
+        assert [i["iters"] for i in c["info"]] == [i["iters"] for i in cb["info"]]
+
+
+def test_batched_executor_with_an_arena_for_one_request():
+    specs = _specs(count=6, seed=3)
+    xs = _xs(specs)
+    big = max(capi.hpmxp_request_footprint(serve.make_request(s)) for s in specs)
+    with serve.Executor(workers=2, arena_bytes=int(big * 1.6), device=DEV, batch=8) as ex:
+        comps = serve.run_stream(ex, specs, xs=xs)
+    _check_valid(comps)
