@@ -66,8 +66,8 @@ def parse():
                     help="1: balance and scale A (hpmxp_balance) inside every timed solve")
     ap.add_argument("--serving-requests", type=int, default=600,
                     help="requests of the serving sub-record at 1000/s (a third of them at 100/s); 0: skip")
-    ap.add_argument("--serving-batch", type=int, default=16, help="serving: requests per batch in batch mode")
-    ap.add_argument("--serving-batch-workers", type=int, default=4, help="serving: workers in batch mode")
+    ap.add_argument("--serving-batch", type=int, default=64, help="serving: requests per batch in batch mode")
+    ap.add_argument("--serving-batch-workers", type=int, default=2, help="serving: workers in batch mode")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
