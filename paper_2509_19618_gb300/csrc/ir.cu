@@ -356,6 +356,44 @@ __global__ void __launch_bounds__(128) diag_inv_kernel(int64_t n, const uint16_t
 template <class T>
 size_t diag_inv_smem() { return sizeof(float) * kTB32 * 130 + sizeof(T) * kTB32 * 129; }
 
+// Chain blocks of the fp64 preconditioner, once per solve: forward
+// P_c = Linv_c L(c, c-1) (c >= 1), backward Q_c = Uinv_c U(c, c+1) (c <= nb-2),
+// fp64 products of the fp64 inverses and the 16-bit factor tiles (terms t
+// ascending).  out[((which * nb + c) * 128 + j) * 128 + i] = P(i, j).  With
+// them the wavefront's dependent step is one product: z_{c+1} = y_{c+1} -
+// P_{c+1} z_c, y_{c+1} = Linv_{c+1} (v_{c+1} - sum_{k<c} L(c+1,k) z_k) being
+// known before z_c is.
+__global__ void __launch_bounds__(256) chain_blocks_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
+                                                           int fmt, const double* __restrict__ dinv,
+                                                           double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char cb_raw[];
+  float* tile = reinterpret_cast<float*>(cb_raw);   // tile[t * 128 + j] = T(t, j)
+  const int nb = (int)cdiv<int64_t>(n, kTB32);
+  const int c = blockIdx.x, which = blockIdx.y, tid = threadIdx.x;
+  const int nbr = which == 0 ? c - 1 : c + 1;   // block column of the neighbour tile
+  if (nbr < 0 || nbr >= nb) return;
+  const int64_t r0 = (int64_t)c * kTB32, c0 = (int64_t)nbr * kTB32;
+  for (int idx = tid; idx < kTB32 * kTB32; idx += 256) {
+    const int t = idx % kTB32, j = idx / kTB32;   // coalesced over t (column major source)
+    const bool in = r0 + t < n && c0 + j < n;
+    tile[t * kTB32 + j] = in ? u16_to_f32(LU[r0 + t + (c0 + j) * ld], fmt) : 0.0f;
+  }
+  __syncthreads();
+  const double* inv = dinv + ((int64_t)which * nb + c) * kTB32 * kTB32;
+  const int i = tid % kTB32, jh = (tid / kTB32) * 64;
+  double acc[64];
+#pragma unroll
+  for (int q = 0; q < 64; ++q) acc[q] = 0.0;
+  for (int t = 0; t < kTB32; ++t) {
+    const double a = inv[(int64_t)t * kTB32 + i];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) acc[q] = __fma_rn(a, (double)tile[t * kTB32 + jh + q], acc[q]);
+  }
+  double* o = out + ((int64_t)which * nb + c) * kTB32 * kTB32;
+#pragma unroll
+  for (int q = 0; q < 64; ++q) o[(int64_t)(jh + q) * kTB32 + i] = acc[q];
+}
+
 // words of one published value
 template <class T> constexpr int kWords = sizeof(T) / 4;
 
@@ -373,6 +411,7 @@ __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" 
 template <class T, int K>
 __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
                                                       int fmt, const T* __restrict__ dinv,
+                                                      const double* __restrict__ pch,
                                                       const double* __restrict__ v, int64_t ldv,
                                                       double* __restrict__ z, int64_t ldz,
                                                       unsigned long long* __restrict__ pub, int epoch,
@@ -391,6 +430,7 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
   T* zc = acc + (size_t)nown * kTB32 * K;                         // [128][K] block c
   T* zs = zc + kTB32 * K;                                         // [128][K] block being solved
   T* part = zs + kTB32 * K;                                       // [2][128][K]
+  T* ys = part + 2 * kTB32 * K;                                   // [128][K] y of the next block (fp64)
   __shared__ int abort_flag;
   if (tid == 0) abort_flag = 0;
   unsigned long long* fpub = pub;
@@ -435,6 +475,15 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
         cp_async16((uint32_t)__cvta_generic_to_shared(ti + chunk * 4), src + chunk * 4, 16);
       }
     } else {
+      const int ii = tid % kTB32, h = tid / kTB32;
+#pragma unroll
+      for (int q = 0; q < 64; ++q) invr[q] = __ldcg(src + (h * 64 + q) * kTB32 + ii);
+    }
+  };
+  // fp64: the chain block P (which 0) / Q (which 1) of block cb into the same registers
+  auto fetch_chain = [&](int which, int cb) {
+    if constexpr (!kInvInSmem) {
+      const double* src = pch + ((int64_t)which * nb + cb) * kTB32 * kTB32;
       const int ii = tid % kTB32, h = tid / kTB32;
 #pragma unroll
       for (int q = 0; q < 64; ++q) invr[q] = __ldcg(src + (h * 64 + q) * kTB32 + ii);
@@ -503,25 +552,33 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     }
     __syncthreads();
   };
-  // zs = Tinv acc_o, stored back into acc_o and published (backward: also into z)
-  auto solve = [&](int o, int c, bool backward, unsigned long long* dst) {
+  // fp64: out = M w (or from - M w) with M in the invr registers (thread: row ii,
+  // columns h*64 .. h*64+63), the two column halves summed through `part`
+  auto reg_product = [&](const T* w, T* out, const T* from) {
+    const int ii = tid % kTB32, h = tid / kTB32;
+    T sr[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) sr[r] = (T)0;
+#pragma unroll
+    for (int q = 0; q < 64; ++q)
+#pragma unroll
+      for (int r = 0; r < K; ++r) sr[r] = fma_t<T>(invr[kInvInSmem ? 0 : q], w[(h * 64 + q) * K + r], sr[r]);
+#pragma unroll
+    for (int r = 0; r < K; ++r) part[(h * kTB32 + ii) * K + r] = sr[r];
+    __syncthreads();
+    for (int t = tid; t < kTB32 * K; t += 256) {
+      const T tot = part[t] + part[kTB32 * K + t];
+      out[t] = from ? from[t] - tot : tot;
+    }
+    __syncthreads();
+  };
+  // zs = Tinv acc_o (or, with chain, zs as computed by the caller), stored back
+  // into acc_o and published (backward: also into z)
+  auto solve = [&](int o, int c, bool backward, unsigned long long* dst, bool chained = false) {
     T* a = acc + (size_t)o * kTB32 * K;
-    if constexpr (kInvInSmem) {
-      product(nullptr, reinterpret_cast<const T*>(ti), a, zs, false);
-    } else {
-      const int ii = tid % kTB32, h = tid / kTB32;
-      T sr[K];
-#pragma unroll
-      for (int r = 0; r < K; ++r) sr[r] = (T)0;
-#pragma unroll
-      for (int q = 0; q < 64; ++q)
-#pragma unroll
-        for (int r = 0; r < K; ++r) sr[r] = fma_t<T>(invr[q], a[(h * 64 + q) * K + r], sr[r]);
-#pragma unroll
-      for (int r = 0; r < K; ++r) part[(h * kTB32 + ii) * K + r] = sr[r];
-      __syncthreads();
-      for (int t = tid; t < kTB32 * K; t += 256) zs[t] = part[t] + part[kTB32 * K + t];
-      __syncthreads();
+    if (!chained) {
+      if constexpr (kInvInSmem) product(nullptr, reinterpret_cast<const T*>(ti), a, zs, false);
+      else reg_product(a, zs, nullptr);
     }
     unsigned long long* wd = dst + (size_t)c * kTB32 * K * W;
     for (int t = tid; t < kTB32 * K; t += 256) {
@@ -594,7 +651,18 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
       if (nown == 0 || last <= c) continue;
     }
     const int skip = next_mine ? (c + 1) / G : -1;
-    if (next_mine) { fetch_tile(0, c + 1, c); fetch_inv(0, c + 1); }
+    if (next_mine) {
+      if constexpr (kInvInSmem) {
+        fetch_tile(0, c + 1, c);
+        fetch_inv(0, c + 1);
+      } else {
+        // fp64: y = Linv_{c+1} acc_{c+1} before z_c is awaited (acc_{c+1} has every
+        // term but z_c's), then the chain block P_{c+1} into the registers
+        fetch_inv(0, c + 1);
+        reg_product(acc + (size_t)skip * kTB32 * K, ys, nullptr);
+        fetch_chain(0, c + 1);
+      }
+    }
     const int npre = prefetch_updates(c, true, skip);
     cp_async_commit();
     if (c % G == me) {
@@ -605,8 +673,13 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     }
     ready();
     if (next_mine) {
-      product(tl, nullptr, zc, acc + (size_t)skip * kTB32 * K, true);
-      solve(skip, c + 1, false, fpub);
+      if constexpr (kInvInSmem) {
+        product(tl, nullptr, zc, acc + (size_t)skip * kTB32 * K, true);
+        solve(skip, c + 1, false, fpub);
+      } else {
+        reg_product(zc, zs, ys);   // z_{c+1} = y_{c+1} - P_{c+1} z_c
+        solve(skip, c + 1, false, fpub, true);
+      }
     }
     stream_updates(c, true, skip, npre);
   }
@@ -623,7 +696,16 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     const bool next_mine = c - 1 >= 0 && (c - 1) % G == me;
     if (c % G != me && (nown == 0 || me >= c)) continue;
     const int skip = next_mine ? (c - 1) / G : -1;
-    if (next_mine) { fetch_tile(0, c - 1, c); fetch_inv(1, c - 1); }
+    if (next_mine) {
+      if constexpr (kInvInSmem) {
+        fetch_tile(0, c - 1, c);
+        fetch_inv(1, c - 1);
+      } else {
+        fetch_inv(1, c - 1);
+        reg_product(acc + (size_t)skip * kTB32 * K, ys, nullptr);
+        fetch_chain(1, c - 1);
+      }
+    }
     const int npre = prefetch_updates(c, false, skip);
     cp_async_commit();
     if (c % G == me) {
@@ -634,8 +716,13 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     }
     ready();
     if (next_mine) {
-      product(tl, nullptr, zc, acc + (size_t)skip * kTB32 * K, true);
-      solve(skip, c - 1, true, bpub);
+      if constexpr (kInvInSmem) {
+        product(tl, nullptr, zc, acc + (size_t)skip * kTB32 * K, true);
+        solve(skip, c - 1, true, bpub);
+      } else {
+        reg_product(zc, zs, ys);   // z_{c-1} = y_{c-1} - Q_{c-1} z_c
+        solve(skip, c - 1, true, bpub, true);
+      }
     }
     stream_updates(c, false, skip, npre);
   }
@@ -876,6 +963,7 @@ struct SolveWs {
   void* RS;          // nchunk x n (fp64 size)
   void* pub;         // 2 sweeps x round_up(n, 128) x K values x (1 or 2) 8-byte tagged words
   void* dinv;        // 2 x nb128 x 128 x 128 inverted diagonal blocks (float or double)
+  double* pch;       // 2 x nb128 x 128 x 128 chain blocks of the fp64 preconditioner
   float* a32;        // optional fp32 copy of A (ld32), written by the first residual, NULL if none
   int64_t ld32;
   size_t bytes;
@@ -918,6 +1006,7 @@ SolveWs carve_solve(void* base, int64_t n, int64_t K, int m) {
   w.RS = take(sizeof(double) * nchunk * n);
   w.pub = take(pub_bytes(n, K));
   w.dinv = take(sizeof(double) * 2 * round_up<int64_t>(n, kTB32) * kTB32);
+  w.pch = (double*)take(sizeof(double) * 2 * round_up<int64_t>(n, kTB32) * kTB32);
   w.bytes = off;
   return w;
 }
@@ -985,11 +1074,12 @@ size_t precond_smem(int64_t n, int K, int G) {
   const int nown = cdiv(nb, G);
   const size_t inv = sizeof(T) == 4 ? sizeof(float) * kTB32 * kTB32 : 0;
   return sizeof(uint16_t) * 3 * kTB32 * kTB32 + inv +
-         sizeof(T) * ((size_t)nown * kTB32 * K + 2 * kTB32 * K + 2 * kTB32 * K) + 64;
+         sizeof(T) * ((size_t)nown * kTB32 * K + 2 * kTB32 * K + 2 * kTB32 * K + kTB32 * K) + 64;
 }
 
 template <class T, int K>
-cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt, const T* dinv, const double* v,
+cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt, const T* dinv, const double* pch,
+                             const double* v,
                              int64_t ldv, double* z, int64_t ldz, unsigned long long* pub, int epoch,
                              uint32_t* status, int G, size_t smem, cudaStream_t st, const double* rs,
                              const double* cs) {
@@ -1000,18 +1090,18 @@ cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt,
   const WaitBudget wb = wait_budget();
   long long polls = wb.polls;
   unsigned long long ns = wb.ns;
-  void* args[] = {&n,   (void*)&LU, &ld,    &fmt,    (void*)&dinv, (void*)&v, &ldv,       &z,
-                  &ldz, &pub,       &epoch, &status, &polls,       &ns,       (void*)&rs, (void*)&cs};
+  void* args[] = {&n,  (void*)&LU, &ld,     &fmt,   (void*)&dinv, (void*)&pch, (void*)&v,  &ldv, &z,
+                  &ldz, &pub,      &epoch, &status, &polls,      &ns,         (void*)&rs, (void*)&cs};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(256), args, smem, st);
 }
 
 template <class T>
 cudaError_t precond_launch(int K, int64_t n, const uint16_t* LU, int64_t ld, int fmt, const T* dinv,
-                           const double* v, int64_t ldv, double* z, int64_t ldz, unsigned long long* pub,
+                           const double* pch, const double* v, int64_t ldv, double* z, int64_t ldz, unsigned long long* pub,
                            int epoch, uint32_t* status, int G, size_t smem, cudaStream_t st, const double* rs,
                            const double* cs) {
 #define HPMXP_PRECOND_K(KK) \
-  precond_launch_k<T, KK>(n, LU, ld, fmt, dinv, v, ldv, z, ldz, pub, epoch, status, G, smem, st, rs, cs)
+  precond_launch_k<T, KK>(n, LU, ld, fmt, dinv, pch, v, ldv, z, ldz, pub, epoch, status, G, smem, st, rs, cs)
   switch (K) {
     case 1: return HPMXP_PRECOND_K(1);
     case 2: return HPMXP_PRECOND_K(2);
@@ -1059,10 +1149,10 @@ struct Solver {
     void* tok = prof_begin(st);
     unsigned long long* pub = (unsigned long long*)w.pub;
     cudaError_t e = prm.precond_fp32
-                        ? precond_launch<float>(K, n, LU, ldlu, fmt, (const float*)w.dinv, v, ldv, z, ldz, pub,
-                                                epoch, w.status, G, psmem, st, rs, cs)
-                        : precond_launch<double>(K, n, LU, ldlu, fmt, (const double*)w.dinv, v, ldv, z, ldz, pub,
-                                                 epoch, w.status, G, psmem, st, rs, cs);
+                        ? precond_launch<float>(K, n, LU, ldlu, fmt, (const float*)w.dinv, nullptr, v, ldv, z, ldz,
+                                                pub, epoch, w.status, G, psmem, st, rs, cs)
+                        : precond_launch<double>(K, n, LU, ldlu, fmt, (const double*)w.dinv, w.pch, v, ldv, z, ldz,
+                                                 pub, epoch, w.status, G, psmem, st, rs, cs);
     prof_end(tok, kProfPrecond, 2.0 * (double)n * (double)n, st);
     count_launches(1);
     return e;
@@ -1091,6 +1181,15 @@ struct Solver {
     e = prm.precond_fp32 ? diag_inv_launch<float>(n, LU, ldlu, fmt, w.dinv, st)
                          : diag_inv_launch<double>(n, LU, ldlu, fmt, w.dinv, st);
     if (e != cudaSuccess) return e;
+    if (!prm.precond_fp32) {
+      constexpr size_t kChainSmem = sizeof(float) * kTB32 * kTB32;
+      e = cudaFuncSetAttribute(chain_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmem);
+      if (e != cudaSuccess) return e;
+      chain_blocks_kernel<<<dim3((unsigned)cdiv<int64_t>(n, kTB32), 2), 256, kChainSmem, st>>>(
+          n, LU, ldlu, fmt, (const double*)w.dinv, w.pch);
+      count_launches(1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if ((e = cudaMemsetAsync(w.st, 0, sizeof(RhsState) * kMaxK, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.counter, 0, 256, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.status, 0, 4, st)) != cudaSuccess) return e;
