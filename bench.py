@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=32768)
-    ap.add_argument("--nb", type=int, default=0, help="Schur update depth; 0 = autotune over 128/256/512")
+    ap.add_argument("--nb", type=int, default=0, help="Schur update depth; 0 = autotune nb over 128/256/512 with the GEMM tile and reserved SMs")
     ap.add_argument("--prec", default="bf16", choices=list(PREC))
     ap.add_argument("--precond-fp32", type=int, default=1,
                     help="1: the preconditioner U^-1 L^-1 of the inner GMRES applied in fp32 (default), 0: fp64")
@@ -478,7 +478,14 @@ def main():
     diag = {"dominant": capi.DIAG_DOMINANT, "sqrtn": capi.DIAG_SQRTN, "none": capi.DIAG_NONE}[args.diag]
     A, b = api.generate(n, seed=args.seed, margin=args.margin, diag=diag, device=dev)   # untimed (not timed by the paper)
     params = ir_params_for(args, args.precond_fp32, args.matvec_fp32)
-    nb = args.nb or autotune.pick_nb(n, prec, A, device=dev)
+    if args.nb:
+        schedule = {"nb": args.nb, **capi.hpmxp_get_tuning(), "source": "--nb flag, library defaults"}
+        nb = args.nb
+    else:
+        choice = autotune.tune(n, prec, A, device=dev)
+        nb = choice.nb
+        schedule = {"nb": nb, "gemm_tile": choice.gemm_tile, "reserve_sms": choice.reserve_sms,
+                    "source": "autotune (nb x GEMM tile x reserved SMs)"}
     fp64 = None
     if not args.no_fp64_comparator and rank == 0:
         # same system, fp64 LU with partial pivoting + solve (cuSOLVER through torch), one run after one warm-up
@@ -644,7 +651,7 @@ def main():
                            "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (A is %.1f GB)" % (8 * n * n / 1e9),
                            "precond_fp32": int(params.precond_fp32), "matvec_fp32": int(params.matvec_fp32),
-                           "inner_tol": params.inner_tol, "balance": int(args.balance)},
+                           "inner_tol": params.inner_tol, "balance": int(args.balance), "schedule": schedule},
                 "valid": bool(ok and sr < 16.0), "scaled_residual": sr,
                 "ir_iters": infos[-1][1]["iters"], "ir_outer": infos[-1][1]["outer"],
                 "ir_status": int(infos[-1][0]), "diag": args.diag, "margin": args.margin,

@@ -348,6 +348,28 @@ hpmxp_status hpmxp_lu_solve_f64(int64_t n, const double* LU, int64_t ld, double*
                                 void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Schedule tuning of the factorization (this library's knobs; the paper has
+ * no counterpart).  Process-wide, read by every factorization started
+ * afterwards; a field of 0 keeps the built-in choice.  The autotuner
+ * (autotune.py) searches them together with nb.
+ *   gemm_tile     tile height of the 16-bit products with M, K >= 256: 128 or 256
+ *                 (0: 256)
+ *   reserve_sms   SMs kept free of the far Schur update for the next panel chain
+ *                 in the look-ahead schedule (0: SMs / 16, at least 4)
+ *   overlap_min   smallest far-update order run concurrently with the next panel
+ *                 chain (0: 8192)
+ * Environment variables HPMXP_GEMM_TILE, HPMXP_RESERVE_SMS and
+ * HPMXP_OVERLAP_MIN, when set, take precedence (they fix a setting for
+ * experiments).  Returns HPMXP_EINVAL for values out of range. */
+typedef struct {
+  int32_t gemm_tile;
+  int32_t reserve_sms;
+  int64_t overlap_min;
+} hpmxp_tuning;
+hpmxp_status hpmxp_set_tuning(const hpmxp_tuning* t);
+void hpmxp_get_tuning(hpmxp_tuning* t);
+
+/* ------------------------------------------------------------------------ */
 /* Measurement support (the paper has no counterpart; used by the benchmark).
  * hpmxp_launch_count: kernels this library has launched since it was loaded.
  * hpmxp_prof_enable(1) makes the library record a CUDA event pair around

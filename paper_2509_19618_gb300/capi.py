@@ -37,6 +37,10 @@ class IRInfo(ctypes.Structure):
                 ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("gemm_tile", ctypes.c_int32), ("reserve_sms", ctypes.c_int32), ("overlap_min", ctypes.c_int64)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("LU", ctypes.c_void_p),
                 ("ldlu", ctypes.c_int64), ("b", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("x", ctypes.c_void_p),
@@ -110,6 +114,8 @@ def load():
                                  P, i32, P, i32, i32, P, P], i32),
             "hpmxp_test_cast": ([i64, P, i64, i32, P, i64, P], i32),
             "hpmxp_launch_count": ([], ctypes.c_ulonglong),
+            "hpmxp_set_tuning": ([ctypes.POINTER(Tuning)], i32),
+            "hpmxp_get_tuning": ([ctypes.POINTER(Tuning)], None),
             "hpmxp_prof_enable": ([i32], None),
             "hpmxp_prof_reset": ([], None),
             "hpmxp_prof_read": ([i32, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)], i32),
@@ -255,6 +261,17 @@ def hpmxp_lu_f64(n, A, lda, ws, ws_bytes, stream):
 
 def hpmxp_lu_solve_f64(n, LU, ld, B, ldb, nrhs, stream):
     return _call("hpmxp_lu_solve_f64", n, LU, ld, B, ldb, nrhs, stream)
+
+
+def hpmxp_set_tuning(gemm_tile: int = 0, reserve_sms: int = 0, overlap_min: int = 0) -> int:
+    t = Tuning(gemm_tile, reserve_sms, overlap_min)
+    return load().hpmxp_set_tuning(ctypes.byref(t))
+
+
+def hpmxp_get_tuning() -> dict:
+    t = Tuning()
+    load().hpmxp_get_tuning(ctypes.byref(t))
+    return dict(gemm_tile=t.gemm_tile, reserve_sms=t.reserve_sms, overlap_min=t.overlap_min)
 
 
 def hpmxp_launch_count() -> int:

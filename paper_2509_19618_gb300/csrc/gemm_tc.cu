@@ -767,14 +767,9 @@ cudaError_t gemm_tc_grouped(const GemmArgs& g, const GemmGroupItem* dev_items, i
 
 namespace {
 
-// HPMXP_GEMM_TILE=128 keeps every product on the 128-row tile.
-bool wide_tiles_enabled() {
-  static const bool on = [] {
-    const char* e = getenv("HPMXP_GEMM_TILE");
-    return !(e && strcmp(e, "128") == 0);
-  }();
-  return on;
-}
+// A tile height of 128 (hpmxp_set_tuning or HPMXP_GEMM_TILE=128) keeps every
+// product on the 128-row tile.
+bool wide_tiles_enabled() { return tuning().gemm_tile != 128; }
 
 }  // namespace
 

@@ -186,6 +186,9 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 #endif
 bool pdl_enabled();   // HPMXP_PDL=0 turns it off (every launch_pdl becomes a plain launch)
+// Schedule tuning (hpmxp_set_tuning, environment overrides applied): the
+// effective values, 0 = built-in choice.
+hpmxp_tuning tuning();
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                        Args&&... args) {

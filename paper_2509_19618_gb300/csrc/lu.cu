@@ -1642,7 +1642,8 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
   } else {
     f.check(launch_cast(n, A, lda, LU, ldlu, f.fmt, st, rs, cs));
   }
-  if (const char* om = getenv("HPMXP_OVERLAP_MIN")) f.overlap_min = atoll(om);
+  const hpmxp_tuning tune = tuning();
+  if (tune.overlap_min > 0) f.overlap_min = tune.overlap_min;
   // the largest far part is n - 2 nb (first step); below overlap_min the
   // schedule never uses the side stream, so it is not taken (concurrent
   // factorizations of small systems on other streams then do not serialize)
@@ -1663,7 +1664,7 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
       f.evW2 = ss.evW2;
       cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
       f.reserve = std::max(4, f.sms / 16);
-      if (const char* rv = getenv("HPMXP_RESERVE_SMS")) f.reserve = std::max(1, std::min(f.sms - 1, atoi(rv)));
+      if (tune.reserve_sms > 0) f.reserve = std::max(1, std::min(f.sms - 1, tune.reserve_sms));
       if (const char* cp = getenv("HPMXP_CAP_PANELS")) f.cap_panels = cp[0] != '0';
     }
   }

@@ -14,6 +14,25 @@
 
 namespace hpmxp {
 
+namespace {
+std::atomic<int> g_tile{0}, g_reserve{0};
+std::atomic<long long> g_overlap{0};
+}  // namespace
+
+// The tile override is read once (the value is consulted per GEMM launch);
+// the two schedule overrides are read per factorization.
+hpmxp_tuning tuning() {
+  static const int env_tile = [] {
+    const char* e = getenv("HPMXP_GEMM_TILE");
+    return e ? atoi(e) : 0;
+  }();
+  hpmxp_tuning t{g_tile.load(), g_reserve.load(), g_overlap.load()};
+  if (env_tile) t.gemm_tile = env_tile;
+  if (const char* e = getenv("HPMXP_RESERVE_SMS")) t.reserve_sms = atoi(e);
+  if (const char* e = getenv("HPMXP_OVERLAP_MIN")) t.overlap_min = atoll(e);
+  return t;
+}
+
 bool pdl_enabled() {
   static const bool on = [] {
     const char* e = getenv("HPMXP_PDL");
@@ -167,6 +186,20 @@ using namespace hpmxp;
 extern "C" {
 
 unsigned long long hpmxp_launch_count(void) { return g_launches.load(); }
+
+hpmxp_status hpmxp_set_tuning(const hpmxp_tuning* t) {
+  if (!t || !(t->gemm_tile == 0 || t->gemm_tile == 128 || t->gemm_tile == 256) || t->reserve_sms < 0 ||
+      t->reserve_sms > 1024 || t->overlap_min < 0)
+    return HPMXP_EINVAL;
+  g_tile.store(t->gemm_tile);
+  g_reserve.store(t->reserve_sms);
+  g_overlap.store(t->overlap_min);
+  return HPMXP_OK;
+}
+
+void hpmxp_get_tuning(hpmxp_tuning* t) {
+  if (t) *t = hpmxp_tuning{g_tile.load(), g_reserve.load(), g_overlap.load()};
+}
 
 void hpmxp_prof_enable(int on) { g_enabled.store(on ? 1 : 0); }
 

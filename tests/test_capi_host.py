@@ -78,3 +78,35 @@ def test_python_modules_import():
     import importlib
     for m in ("paper_2509_19618_gb300.api", "paper_2509_19618_gb300.autotune", "bench"):
         importlib.import_module(m)
+
+
+def test_schedule_tuning_set_get(lib):
+    old = capi.hpmxp_get_tuning()
+    try:
+        assert capi.hpmxp_set_tuning(128, 20, 4096) == capi.OK
+        assert capi.hpmxp_get_tuning() == dict(gemm_tile=128, reserve_sms=20, overlap_min=4096)
+        # tile heights other than 0/128/256 and negative counts are refused and change nothing
+        for bad in ((64, 0, 0), (512, 0, 0), (0, -1, 0), (0, 0, -5), (0, 5000, 0)):
+            assert capi.hpmxp_set_tuning(*bad) == capi.EINVAL
+        assert capi.hpmxp_get_tuning() == dict(gemm_tile=128, reserve_sms=20, overlap_min=4096)
+    finally:
+        assert capi.hpmxp_set_tuning(old["gemm_tile"], old["reserve_sms"], old["overlap_min"]) == capi.OK
+
+
+def test_autotune_search_space():
+    from paper_2509_19618_gb300 import autotune
+    sms = 152
+    big = autotune.candidates(32768, capi.BF16, sms)
+    # nb x tile x reserve where the look-ahead schedule runs
+    assert len(big) == 3 * 2 * 3
+    assert {c.reserve_sms for c in big} == {max(4, sms // d) for d in autotune.RESERVE_DIVISORS}
+    assert {c.gemm_tile for c in big} == {128, 256}
+    # below the look-ahead threshold the reserve has no effect and is not searched
+    small = autotune.candidates(4096, capi.BF16, sms)
+    assert len(small) == 3 * 2 and {c.reserve_sms for c in small} == {0}
+    # the fp32-trailing variants run without look-ahead
+    assert {c.reserve_sms for c in autotune.candidates(32768, capi.BF16_TRAIL32, sms)} == {0}
+    # FP8 products stay on one tile height
+    assert {c.gemm_tile for c in autotune.candidates(32768, capi.FP8_E4M3, sms)} == {0}
+    # nb larger than the matrix is skipped (below 128 the smallest depth stays)
+    assert {c.nb for c in autotune.candidates(200, capi.BF16, sms)} == {128}
