@@ -353,12 +353,13 @@ GEMM_SRC = os.path.join(ROOT, "paper_2509_19618_gb300", "csrc", "gemm_tc.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gemm_tc_kernel_traffic_n32768_bf16_nb512.md")
 
 
-def measured_gemm_traffic(n: int, nb: int, prec: str):
+def measured_gemm_traffic(n: int, nb: int, prec: str, gemm_tile: int):
     """DRAM bytes per gemm_tc_kernel launch over one solve, from the committed
-    ncu summary of that workload, or None when there is none for this
-    workload or the kernel's source has changed since it was captured."""
+    ncu summary of that workload (the library's default 256-row tile), or None
+    when there is none for this workload and schedule or the kernel's source
+    has changed since it was captured."""
     import hashlib
-    if (n, nb, prec) != (32768, 512, "bf16") or not os.path.exists(TRAFFIC_FILE):
+    if (n, nb, prec) != (32768, 512, "bf16") or gemm_tile not in (0, 256) or not os.path.exists(TRAFFIC_FILE):
         return None
     fields = {}
     for line in open(TRAFFIC_FILE):
@@ -560,7 +561,7 @@ def main():
                 "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops_sustained" if peaks
                                 else "of fallback 1.7 PF/s") + (" x2 nominal fp8/bf16 ratio" if prec == 2 else ""),
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": measured_gemm_traffic(n, nb, args.prec),
+                "traffic": measured_gemm_traffic(n, nb, args.prec, schedule["gemm_tile"]),
                 "algorithmic_bytes_per_launch": g["bytes"] / max(g["launches"], 1),
                 "whole_solve": {"t_roof_ms": t_roof * 1e3, "t_meas_ms": t_step * 1e3, "frac": t_roof / t_step,
                                 "what": "T_roof = 2/3 n^3 / tensor peak + 10 n^2 (iters + 1) bytes / HBM peak"},
