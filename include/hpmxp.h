@@ -358,13 +358,20 @@ hpmxp_status hpmxp_lu_solve_f64(int64_t n, const double* LU, int64_t ld, double*
  *                 in the look-ahead schedule (0: SMs / 16, at least 4)
  *   overlap_min   smallest far-update order run concurrently with the next panel
  *                 chain (0: 8192)
- * Environment variables HPMXP_GEMM_TILE, HPMXP_RESERVE_SMS and
- * HPMXP_OVERLAP_MIN, when set, take precedence (they fix a setting for
+ *   sm_budget     most SMs that one call's persistent tensor-core GEMM grid and
+ *                 cooperative preconditioner grid take (0: all).  For many
+ *                 solves sharing the GPU: a smaller grid leaves SMs free for the
+ *                 other solves' latency-bound kernels.  The request executor
+ *                 sets its own value for its workers (hpmxp_serve.h).
+ * Environment variables HPMXP_GEMM_TILE, HPMXP_RESERVE_SMS, HPMXP_OVERLAP_MIN
+ * and HPMXP_SM_BUDGET, when set, take precedence (they fix a setting for
  * experiments).  Returns HPMXP_EINVAL for values out of range. */
 typedef struct {
   int32_t gemm_tile;
   int32_t reserve_sms;
   int64_t overlap_min;
+  int32_t sm_budget;
+  int32_t reserved;   /* 0 */
 } hpmxp_tuning;
 hpmxp_status hpmxp_set_tuning(const hpmxp_tuning* t);
 void hpmxp_get_tuning(hpmxp_tuning* t);

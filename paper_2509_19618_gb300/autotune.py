@@ -35,7 +35,10 @@ class Choice:
     reserve_sms: int = 0
 
     def apply(self) -> None:
-        api._check("hpmxp_set_tuning", capi.hpmxp_set_tuning(self.gemm_tile, self.reserve_sms, 0))
+        """Set the tile height and reserve; the other knobs keep their values."""
+        t = capi.hpmxp_get_tuning()
+        t.update(gemm_tile=self.gemm_tile, reserve_sms=self.reserve_sms)
+        api._check("hpmxp_set_tuning", capi.hpmxp_set_tuning(**t))
 
 
 def _key(n: int, prec: int, device) -> str:

@@ -38,7 +38,8 @@ class IRInfo(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("gemm_tile", ctypes.c_int32), ("reserve_sms", ctypes.c_int32), ("overlap_min", ctypes.c_int64)]
+    _fields_ = [("gemm_tile", ctypes.c_int32), ("reserve_sms", ctypes.c_int32), ("overlap_min", ctypes.c_int64),
+                ("sm_budget", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -263,15 +264,16 @@ def hpmxp_lu_solve_f64(n, LU, ld, B, ldb, nrhs, stream):
     return _call("hpmxp_lu_solve_f64", n, LU, ld, B, ldb, nrhs, stream)
 
 
-def hpmxp_set_tuning(gemm_tile: int = 0, reserve_sms: int = 0, overlap_min: int = 0) -> int:
-    t = Tuning(gemm_tile, reserve_sms, overlap_min)
+def hpmxp_set_tuning(gemm_tile: int = 0, reserve_sms: int = 0, overlap_min: int = 0, sm_budget: int = 0,
+                     reserved: int = 0) -> int:
+    t = Tuning(gemm_tile, reserve_sms, overlap_min, sm_budget, reserved)
     return load().hpmxp_set_tuning(ctypes.byref(t))
 
 
 def hpmxp_get_tuning() -> dict:
     t = Tuning()
     load().hpmxp_get_tuning(ctypes.byref(t))
-    return dict(gemm_tile=t.gemm_tile, reserve_sms=t.reserve_sms, overlap_min=t.overlap_min)
+    return dict(gemm_tile=t.gemm_tile, reserve_sms=t.reserve_sms, overlap_min=t.overlap_min, sm_budget=t.sm_budget)
 
 
 def hpmxp_launch_count() -> int:

@@ -627,6 +627,12 @@ int num_sms() {
   return sms;
 }
 
+// persistent grid size: the SM count, or the calling thread's SM budget
+int grid_cap() {
+  const int b = sm_budget();
+  return b > 0 ? std::min(b, num_sms()) : num_sms();
+}
+
 }  // namespace
 
 namespace {
@@ -682,7 +688,7 @@ cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     configured_for.store(dev);
   }
-  const int grid = std::min(p.ntiles, g.max_ctas > 0 ? std::min(g.max_ctas, num_sms()) : num_sms());
+  const int grid = std::min(p.ntiles, g.max_ctas > 0 ? std::min(g.max_ctas, grid_cap()) : grid_cap());
   const double flops = 2.0 * g.M * (double)g.N * g.K;
   // algorithmic DRAM bytes: both operands once, C read (subtract mode) and
   // written once, the optional row-major copy written once
@@ -754,7 +760,7 @@ cudaError_t gemm_tc_grouped(const GemmArgs& g, const GemmGroupItem* dev_items, i
     if (e != cudaSuccess) return e;
     configured_for.store(dev);
   }
-  const int grid = std::min(total_tiles, g.max_ctas > 0 ? std::min(g.max_ctas, num_sms()) : num_sms());
+  const int grid = std::min(total_tiles, g.max_ctas > 0 ? std::min(g.max_ctas, grid_cap()) : grid_cap());
   CUtensorMap none;
   memset(&none, 0, sizeof(none));   // the items' maps are used instead
   void* tok = prof_begin(st);

@@ -189,6 +189,14 @@ bool pdl_enabled();   // HPMXP_PDL=0 turns it off (every launch_pdl becomes a pl
 // Schedule tuning (hpmxp_set_tuning, environment overrides applied): the
 // effective values, 0 = built-in choice.
 hpmxp_tuning tuning();
+// SMs one call's persistent / cooperative grids may take, 0 = all: the calling
+// thread's own value (SmBudgetScope) if set, else the process-wide tuning.
+int sm_budget();
+struct SmBudgetScope {
+  explicit SmBudgetScope(int sms);
+  ~SmBudgetScope();
+  int prev;
+};
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                        Args&&... args) {

@@ -1174,8 +1174,16 @@ struct Solver {
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     // one CTA per SM at most: a cooperative launch keeps all of them resident
     const int nb = (int)cdiv<int64_t>(n, kTB32);
-    G = std::max(1, std::min(nb, sms));
-    psmem = prm.precond_fp32 ? precond_smem<float>(n, K, G) : precond_smem<double>(n, K, G);
+    // one CTA per owned share of block rows; an SM budget takes fewer CTAs as
+    // long as their shares still fit in shared memory
+    const int budget = sm_budget();
+    const int gmax = std::max(1, std::min(nb, sms));
+    G = std::max(1, std::min(gmax, budget > 0 ? budget : gmax));
+    auto smem_for = [&](int g) {
+      return prm.precond_fp32 ? precond_smem<float>(n, K, g) : precond_smem<double>(n, K, g);
+    };
+    while (G < gmax && smem_for(G) > kMaxPrecondSmem) ++G;
+    psmem = smem_for(G);
     if (psmem > kMaxPrecondSmem) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(w.pub, 0, pub_bytes(n, K), st)) != cudaSuccess) return e;
     e = prm.precond_fp32 ? diag_inv_launch<float>(n, LU, ldlu, fmt, w.dinv, st)

@@ -975,8 +975,8 @@ struct FactorWs {
   uint32_t* status;
   uint16_t* Lp[2];   // packed column panel, row major, n x NB, by step parity
   uint16_t* Li;      // packed inner column panel, row major, NB x 128
-  uint16_t* Aop;     // 4 row-panel operands [W_s | Linv_ss], 128 x NB each
-  uint16_t* Bop;     // 4 column-panel operands [Z_s^T | Uinv_ss^T], 128 x NB each
+  uint16_t* Aop[2];  // 4 row-panel operands [W_s | Linv_ss], 128 x NB each, by step parity
+  uint16_t* Bop[2];  // 4 column-panel operands [Z_s^T | Uinv_ss^T], 128 x NB each, by step parity
   uint8_t* Lq[2];    // fp8 column panel, n x NB bytes, by step parity
   uint8_t* Uq[2];    // fp8 row panel, n x NB bytes (K-major per column)
   float* sL[2];      // fp8 scales, (n/128) x 4
@@ -998,8 +998,10 @@ FactorWs carve(void* base, int64_t n, int prec, int NB) {
   w.status = (uint32_t*)take(256);
   for (int q = 0; q < 2; ++q) w.Lp[q] = (uint16_t*)take(sizeof(uint16_t) * nr * NB);
   w.Li = (uint16_t*)take(sizeof(uint16_t) * (size_t)NB * kB);
-  w.Aop = (uint16_t*)take(sizeof(uint16_t) * 4 * kB * NB);
-  w.Bop = (uint16_t*)take(sizeof(uint16_t) * 4 * kB * NB);
+  for (int q = 0; q < 2; ++q) {
+    w.Aop[q] = (uint16_t*)take(sizeof(uint16_t) * 4 * kB * NB);
+    w.Bop[q] = (uint16_t*)take(sizeof(uint16_t) * 4 * kB * NB);
+  }
   if (prec == HPMXP_FP8_E4M3) {
     for (int q = 0; q < 2; ++q) {
       w.Lq[q] = (uint8_t*)take((size_t)nr * NB);
@@ -1041,8 +1043,12 @@ struct Factorizer {
   cudaError_t err = cudaSuccess;
 
   uint16_t* at(int64_t i, int64_t j) const { return LU + i + j * ld; }
-  uint16_t* aop(int s) const { return w.Aop + (size_t)s * kB * NB; }
-  uint16_t* bop(int s) const { return w.Bop + (size_t)s * kB * NB; }
+  // the substitution operands of the current step's diagonal block (double
+  // buffered by step parity: the look-ahead schedule's tail panels of step k
+  // still read them while step k+1's diagonal block writes its own)
+  int par = 0;
+  uint16_t* aop(int s) const { return w.Aop[par] + (size_t)s * kB * NB; }
+  uint16_t* bop(int s) const { return w.Bop[par] + (size_t)s * kB * NB; }
 
   void check(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
 
@@ -1127,18 +1133,10 @@ struct Factorizer {
     gemm(t);
   }
 
-  // Look-ahead schedule.  Step k's Schur update is split into "near" (the
-  // next block's column and row, on the caller's stream `st`) and "far" (the
-  // rest, on the side stream `st2`).  Step k+1's diagonal block and panels run
-  // on `st` while far(k) runs on `st2`; near(k+1) waits for far(k).  far(k)
-  // is a persistent grid held `reserve` SMs below the SM count, so the panel
-  // chain always finds free SMs; the panel products themselves are not capped
-  // and spread over every SM that far(k) has released.  Buffers read by far(k)
-  // are double buffered by step parity.
-  cudaStream_t st2 = nullptr;
-  cudaEvent_t evP = nullptr, evF = nullptr;
+  // Side streams of the look-ahead schedule (run_lookahead) and their events
+  cudaStream_t st2 = nullptr, st4 = nullptr;
+  cudaEvent_t evP = nullptr, evF = nullptr, evD = nullptr, evT = nullptr;
   int reserve = 0, sms = 0;
-  bool cap_panels = false;  // panel products limited to `reserve` CTAs while far(k) runs
   // The row-panel (U12) and column-panel (L21) substitution chains depend on
   // nothing of each other: with a third stream the L21 chain runs on st3
   // between a fork and a join on `st`.
@@ -1184,137 +1182,233 @@ struct Factorizer {
     f();
     st = keep;
   }
-  int64_t overlap_min = 8192;   // smallest far(k) trailing size run concurrently
+  int64_t overlap_min = 8192;   // look-ahead only when the first step's trailing part is this wide
+
+  // Diagonal block of step k (width b): getrf of each 128 sub-block and the
+  // inner steps between them; beside it on stw the W_s / Z_s of the middle
+  // sub-blocks (the last sub-block's are made by the caller).
+  void diagonal_block(int64_t k, int64_t b, int64_t m, int panel_ctas) {
+    const int nsub = (int)cdiv<int64_t>(b, kB);
+    for (int s = 0; s < nsub; ++s) {
+      const int64_t kk = k + (int64_t)s * kB;
+      getrf_base(kk, (int)std::min<int64_t>(kB, k + b - kk), s);
+      if (nsub > 1 && s + 1 < nsub) {
+        inner_step(kk, s, k + b, panel_ctas);
+        if (s > 0 && m > 0) make_wz(k, s);   // they feed only the panel chains
+      }
+    }
+  }
+
+  // One row-panel (U12 = [W_s | Linv_ss] [U12_{0:s}; A12_s]) and one
+  // column-panel product of sub-block s, over columns [c0, c0 + N) of the
+  // block row and rows [r0, r0 + M) of the block column (offsets from k + b).
+  void u_panel(int64_t k, int64_t b, int s, int64_t c0, int64_t N, int max_ctas) {
+    GemmArgs u{};
+    u.M = kB; u.N = (int)N; u.K = (s + 1) * kB;
+    u.A = aop(s); u.lda = NB;
+    u.B = at(k, k + b + c0); u.ldb = ld;
+    u.C = at(k + (int64_t)s * kB, k + b + c0); u.ldc = ld;
+    u.mode = kEpiStore; u.sign = 1.0f;
+    u.max_ctas = max_ctas;
+    gemm(u);
+  }
+  void l_panel(int64_t k, int64_t b, int s, uint16_t* Lp, int64_t r0, int64_t M, int max_ctas) {
+    GemmArgs l{};   // L21 column major into LU, row major over the packed copy
+    l.M = (int)M; l.N = kB; l.K = (s + 1) * kB;
+    l.A = Lp + r0 * NB; l.lda = NB;
+    l.B = bop(s); l.ldb = NB;
+    l.C = at(k + b + r0, k + (int64_t)s * kB); l.ldc = ld;
+    l.R = Lp + r0 * NB + (int64_t)s * kB; l.ldr = NB;
+    l.mode = kEpiStore; l.sign = 1.0f;
+    l.max_ctas = max_ctas;
+    gemm(l);
+  }
+
+  // FP8: per-tile E4M3 copies and scales of L21 rows [r0, r0 + M) and of U12
+  // columns [c0, c0 + N) (tiles never straddle r0 or c0, multiples of 128)
+  void quant_rows(int64_t b, int par_, const uint16_t* Lp, int64_t r0, int64_t M) {
+    if (M <= 0) return;
+    quant_tile_kernel<<<dim3((unsigned)cdiv<int64_t>(M, kB), (unsigned)cdiv<int64_t>(b, kB)), 256, 0, st>>>(
+        Lp + r0 * NB, NB, 1, M, (int)b, fmt, w.Lq[par_] + r0 * NB, NB, w.sL[par_] + (r0 / kB) * 4, 4);
+    count_launches(1);
+    check(cudaGetLastError());
+  }
+  void quant_cols(int64_t k, int64_t b, int par_, int64_t c0, int64_t N) {
+    if (N <= 0) return;
+    quant_tile_kernel<<<dim3((unsigned)cdiv<int64_t>(N, kB), (unsigned)cdiv<int64_t>(b, kB)), 256, 0, st>>>(
+        at(k, k + b + c0), ld, 0, N, (int)b, fmt, w.Uq[par_] + c0 * NB, NB, w.sU[par_] + (c0 / kB) * 4, 4);
+    count_launches(1);
+    check(cudaGetLastError());
+  }
+
+  // Schur update of step k (depth b) on rows [r0, r0 + M) x columns [c0, c0 + N)
+  // of the trailing matrix (offsets from k + b): A22 <- st(A22 - L21 U12)
+  void schur_part(int64_t k, int64_t b, int par_, const uint16_t* Lp, int64_t r0, int64_t M, int64_t c0,
+                  int64_t N, int max_ctas) {
+    if (M <= 0 || N <= 0) return;
+    GemmArgs g{};
+    g.M = (int)M; g.N = (int)N; g.K = (int)b;
+    g.mode = kEpiSub;
+    if (prec == HPMXP_FP8_E4M3) {
+      g.fp8 = 1;
+      g.lda = NB; g.ldb = NB;
+      g.sa_ld = 4; g.sb_ld = 4;
+      g.A = w.Lq[par_] + r0 * NB; g.B = w.Uq[par_] + c0 * NB;
+      g.sA = w.sL[par_] + (r0 / kB) * 4; g.sB = w.sU[par_] + (c0 / kB) * 4;
+    } else {
+      g.lda = NB; g.ldb = ld;
+      g.A = Lp + r0 * NB; g.B = at(k, k + b + c0);
+    }
+    if (trail32) {   // into the fp32 matrix, no rounding to 16 bits
+      g.C = w.W32 + (k + b + r0) + (k + b + c0) * w.ldw;
+      g.ldc = w.ldw;
+      g.c32 = 1;
+    } else {
+      g.C = at(k + b + r0, k + b + c0);
+      g.ldc = ld;
+    }
+    g.max_ctas = max_ctas;
+    gemm(g);
+  }
+
+  template <class F>
+  void on_st2(F&& f) {
+    cudaStream_t keep = st;
+    st = st2;
+    f();
+    st = keep;
+  }
 
   void run() {
-    const bool overlap = st2 != nullptr;
+    if (st2) { run_lookahead(); return; }
     int step = 0;
-    bool far_pending = false;
     for (int64_t k = 0; k < n && err == cudaSuccess; k += NB, ++step) {
       const int64_t b = std::min<int64_t>(NB, n - k);
       const int nsub = (int)cdiv<int64_t>(b, kB);
-      const int par = step & 1;
+      par = step & 1;
       uint16_t* Lp = w.Lp[par];
-      const int panel_ctas = overlap && far_pending && cap_panels ? reserve : 0;
       const int64_t m = n - (k + b);
       if (trail32) round_panel(k, b);
-      // (i) diagonal block.  Beside it on st3 (after each inner step's own
-      // work there): W_s and Z_s of the sub-blocks 0 < s < nsub - 1
-      for (int s = 0; s < nsub; ++s) {
-        const int64_t kk = k + (int64_t)s * kB;
-        getrf_base(kk, (int)std::min<int64_t>(kB, k + b - kk), s);
-        if (nsub > 1 && s + 1 < nsub) {
-          inner_step(kk, s, k + b, panel_ctas);
-          if (s > 0 && m > 0) make_wz(k, s);   // they feed only the panel chains below
-        }
-      }
+      diagonal_block(k, b, m, 0);
       if (m <= 0) break;
-      // (ii) row panel U12 (on st) and column panel L21 (on st3 when there is
-      // one), block substitution over s; the chains meet before the update.
-      // The last sub-block's W_s / Z_s head its own chain's last product.
+      // row panel U12 (on st) and column panel L21 (on st3 when there is one),
+      // block substitution over s; the chains meet before the update.  The
+      // last sub-block's W_s / Z_s head its own chain's last product.
       join();
       join_wz();
       fork();
       on_st3([&] { pack(m, (int)b, at(k + b, k), Lp, NB); });
       for (int s = 0; s < nsub; ++s) {
-        const int64_t s0 = k + (int64_t)s * kB;
         if (s > 0 && s == nsub - 1) make_w(k, s);
-        GemmArgs u{};
-        u.M = kB; u.N = (int)m; u.K = (s + 1) * kB;
-        u.A = aop(s); u.lda = NB;
-        u.B = at(k, k + b); u.ldb = ld;
-        u.C = at(s0, k + b); u.ldc = ld;
-        u.mode = kEpiStore; u.sign = 1.0f;
-        u.max_ctas = panel_ctas;
-        gemm(u);
+        u_panel(k, b, s, 0, m, 0);
         on_st3([&] {
           if (s > 0 && s == nsub - 1) make_z(k, s);
-          GemmArgs l{};
-          l.M = (int)m; l.N = kB; l.K = (s + 1) * kB;
-          l.A = Lp; l.lda = NB;
-          l.B = bop(s); l.ldb = NB;
-          l.C = at(k + b, s0); l.ldc = ld;
-          l.R = Lp + s * kB; l.ldr = NB;
-          l.mode = kEpiStore; l.sign = 1.0f;
-          l.max_ctas = panel_ctas;
-          gemm(l);
+          l_panel(k, b, s, Lp, 0, m, 0);
         });
       }
       join();
-      // (iii) Schur update of depth b: A22 <- st(A22 - L21 U12)
-      GemmArgs t{};
-      t.K = (int)b;
-      t.mode = kEpiSub;
-      const uint8_t* qL = nullptr;
-      const uint8_t* qU = nullptr;
       if (prec == HPMXP_FP8_E4M3) {
-        const int ng = nsub;
-        quant_tile_kernel<<<dim3((unsigned)cdiv<int64_t>(m, kB), ng), 256, 0, st>>>(
-            Lp, NB, 1, m, (int)b, fmt, w.Lq[par], NB, w.sL[par], 4);
-        quant_tile_kernel<<<dim3((unsigned)cdiv<int64_t>(m, kB), ng), 256, 0, st>>>(
-            at(k, k + b), ld, 0, m, (int)b, fmt, w.Uq[par], NB, w.sU[par], 4);
-        count_launches(2);
-        check(cudaGetLastError());
-        t.fp8 = 1;
-        t.lda = NB; t.ldb = NB;
-        t.sa_ld = 4; t.sb_ld = 4;
-        qL = w.Lq[par];
-        qU = w.Uq[par];
-      } else {
-        t.lda = NB; t.ldb = ld;
+        quant_rows(b, par, Lp, 0, m);
+        quant_cols(k, b, par, 0, m);
       }
-      // operand views for rows [r0, r0+M) of L21 and columns [c0, c0+N) of U12 (offsets from k+b)
-      auto part = [&](int64_t r0, int64_t M, int64_t c0, int64_t N, int max_ctas) {
-        GemmArgs g = t;
-        g.M = (int)M; g.N = (int)N;
-        if (g.fp8) {
-          g.A = qL + r0 * NB; g.B = qU + c0 * NB;
-          g.sA = w.sL[par] + (r0 / kB) * 4; g.sB = w.sU[par] + (c0 / kB) * 4;
-        } else {
-          g.A = Lp + r0 * NB; g.B = at(k, k + b + c0);
-        }
-        if (trail32) {   // into the fp32 matrix, no rounding to 16 bits
-          g.C = w.W32 + (k + b + r0) + (k + b + c0) * w.ldw;
-          g.ldc = w.ldw;
-          g.c32 = 1;
-        } else {
-          g.C = at(k + b + r0, k + b + c0);
-          g.ldc = ld;
-        }
-        g.max_ctas = max_ctas;
-        gemm(g);
-      };
-      if (!overlap) {
-        part(0, m, 0, m, 0);
-        continue;
+      schur_part(k, b, par, Lp, 0, m, 0, m, 0);
+    }
+    join_wz();
+  }
+
+  // Look-ahead schedule.  The critical path of step k is the diagonal block,
+  // then the "head" of the panels (the U12 columns and L21 rows of the next
+  // diagonal block, b1 = min(NB, m) wide), then the update of the next
+  // diagonal block alone, all on `st` (with the L21 head on st3).  The rest
+  // runs beside it: the panels' "tail" (columns / rows past b1) on st4 as
+  // soon as the diagonal block's operands exist (beside step k-1's far part
+  // on st2), then on st2 the rest of the next block row and column ("near",
+  // recorded as evN: step k+1's panels read it) and the far part of the
+  // update (recorded as evF: step k+1's next-diagonal update reads it).  The
+  // side streams' grids are held `reserve` SMs below the SM count, so the
+  // critical chain always finds free SMs.  The packed L21 rows, the FP8
+  // copies and the substitution operands read off the critical path are
+  // double buffered by step parity: a buffer of parity p is written again two
+  // steps later, after `st` has waited for evF of the step between, which
+  // st2 records only after it has waited for that step's tails (evT).
+  cudaEvent_t evN = nullptr;
+  void run_lookahead() {
+    const int cap = std::max(1, sms - reserve);
+    bool prev = false;   // st2 holds work of the previous step (evN, evF recorded)
+    int step = 0;
+    for (int64_t k = 0; k < n && err == cudaSuccess; k += NB, ++step) {
+      const int64_t b = std::min<int64_t>(NB, n - k);
+      const int nsub = (int)cdiv<int64_t>(b, kB);
+      par = step & 1;
+      uint16_t* Lp = w.Lp[par];
+      const int64_t m = n - (k + b);
+      // (i) diagonal block k: updated in full by step k-1's critical path
+      diagonal_block(k, b, m, 0);
+      if (m <= 0) break;
+      join();
+      join_wz();
+      if (nsub > 1) {   // the last sub-block's W_s / Z_s, read by head and tail
+        fork();
+        make_w(k, nsub - 1);
+        on_st3([&] { make_z(k, nsub - 1); });
+        join();
       }
-      const int64_t b1 = std::min<int64_t>(NB, m);   // next diagonal block
-      if (far_pending) check(cudaStreamWaitEvent(st, evF, 0));
-      // near(k): the next block's column (all rows) and its row (remaining
-      // columns), on every SM, before far(k) is released
-      part(0, m, 0, b1, 0);
-      if (m > b1) part(0, b1, b1, m - b1, 0);
-      // far(k) on the side stream, held below the SM count so that step k+1's
-      // diagonal block and panels (on `reserve` SMs) overlap it; for small
-      // trailing matrices the panels would be starved, so no overlap there
-      const int64_t mf = m - b1;
-      if (mf > 0 && mf >= overlap_min) {
-        check(cudaEventRecord(evP, st));
+      // block row / column k, written by step k-1's near part
+      if (prev) check(cudaStreamWaitEvent(st, evN, 0));
+      const int64_t b1 = std::min<int64_t>(NB, m), mt = m - b1;
+      // (ii) tail of the panels on st4
+      if (mt > 0) {
+        check(cudaEventRecord(evD, st));
+        check(cudaStreamWaitEvent(st4, evD, 0));
+        cudaStream_t keep = st;
+        st = st4;
+        pack(mt, (int)b, at(k + b + b1, k), Lp + b1 * NB, NB);
+        for (int s = 0; s < nsub; ++s) {
+          u_panel(k, b, s, b1, mt, cap);
+          l_panel(k, b, s, Lp, b1, mt, cap);
+        }
+        if (prec == HPMXP_FP8_E4M3) {
+          quant_rows(b, par, Lp, b1, mt);
+          quant_cols(k, b, par, b1, mt);
+        }
+        st = keep;
+        check(cudaEventRecord(evT, st4));
+      }
+      // (iii) head of the panels
+      fork();
+      on_st3([&] { pack(b1, (int)b, at(k + b, k), Lp, NB); });
+      for (int s = 0; s < nsub; ++s) {
+        u_panel(k, b, s, 0, b1, 0);
+        on_st3([&] { l_panel(k, b, s, Lp, 0, b1, 0); });
+      }
+      join();
+      if (prec == HPMXP_FP8_E4M3) {
+        quant_rows(b, par, Lp, 0, b1);
+        quant_cols(k, b, par, 0, b1);
+      }
+      // (iv) the next diagonal block, after step k-1's far part (it lies there)
+      if (prev) check(cudaStreamWaitEvent(st, evF, 0));
+      if (mt > 0) check(cudaEventRecord(evP, st));   // heads (and their FP8 copies) done
+      schur_part(k, b, par, Lp, 0, b1, 0, b1, 0);
+      // (v) near and far parts on st2, after the heads and the tails
+      if (mt > 0) {
         check(cudaStreamWaitEvent(st2, evP, 0));
-        {
-          cudaStream_t keep = st;
-          st = st2;
-          part(b1, mf, b1, mf, sms - reserve);
-          st = keep;
-        }
-        check(cudaEventRecord(evF, st2));
-        far_pending = true;
+        check(cudaStreamWaitEvent(st2, evT, 0));
+        on_st2([&] {
+          schur_part(k, b, par, Lp, b1, mt, 0, b1, cap);   // next block column below the diagonal block
+          schur_part(k, b, par, Lp, 0, b1, b1, mt, cap);   // next block row right of it
+          check(cudaEventRecord(evN, st2));
+          schur_part(k, b, par, Lp, b1, mt, b1, mt, cap);  // far
+          check(cudaEventRecord(evF, st2));
+        });
+        prev = true;
       } else {
-        if (mf > 0) part(b1, mf, b1, mf, 0);
-        far_pending = false;
+        prev = false;   // nothing past the next diagonal block
       }
     }
-    if (overlap && far_pending) check(cudaStreamWaitEvent(st, evF, 0));
+    // every side-stream launch precedes the last event recorded on st2
+    check(cudaEventRecord(evP, st2));
+    check(cudaStreamWaitEvent(st, evP, 0));
     join_wz();
   }
 };
@@ -1339,10 +1433,12 @@ cudaError_t gemm_simt(const GemmArgs& g, cudaStream_t st) {
 struct SideStream {
   std::mutex mu;   // one look-ahead factorization enqueues on this device at a time
   bool ok = false;
-  cudaStream_t st = nullptr;    // far part of the Schur update
+  cudaStream_t st = nullptr;    // near and far parts of the Schur update
+  cudaStream_t st4 = nullptr;   // tails of the panels
   cudaStream_t st3 = nullptr;   // column-panel (L21) chain, beside the row-panel chain
   cudaStream_t stw = nullptr;   // W_s / Z_s of the diagonal block, lowest priority
-  cudaEvent_t evP = nullptr, evF = nullptr, evS = nullptr, evJ = nullptr, evW = nullptr, evW2 = nullptr;
+  cudaEvent_t evP = nullptr, evF = nullptr, evN = nullptr, evD = nullptr, evT = nullptr, evS = nullptr,
+              evJ = nullptr, evW = nullptr, evW2 = nullptr;
 };
 
 SideStream& side_stream(int dev) {
@@ -1356,10 +1452,14 @@ SideStream& side_stream(int dev) {
     if (cudaStreamCreateWithPriority(&s.st, cudaStreamNonBlocking, lo) == cudaSuccess &&
         cudaStreamCreateWithPriority(&s.st3, cudaStreamNonBlocking, hi) == cudaSuccess &&
         cudaStreamCreateWithPriority(&s.stw, cudaStreamNonBlocking, lo) == cudaSuccess &&
+        cudaStreamCreateWithPriority(&s.st4, cudaStreamNonBlocking, lo) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s.evD, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s.evT, cudaEventDisableTiming) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evW, cudaEventDisableTiming) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evW2, cudaEventDisableTiming) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evP, cudaEventDisableTiming) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evF, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s.evN, cudaEventDisableTiming) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evS, cudaEventDisableTiming) == cudaSuccess &&
         cudaEventCreateWithFlags(&s.evJ, cudaEventDisableTiming) == cudaSuccess)
       s.ok = true;
@@ -1657,6 +1757,10 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
       f.st3 = ss.st3;
       f.evP = ss.evP;
       f.evF = ss.evF;
+      f.evN = ss.evN;
+      f.st4 = ss.st4;
+      f.evD = ss.evD;
+      f.evT = ss.evT;
       f.evS = ss.evS;
       f.evJ = ss.evJ;
       f.stw = ss.stw;
@@ -1665,7 +1769,6 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
       cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
       f.reserve = std::max(4, f.sms / 16);
       if (tune.reserve_sms > 0) f.reserve = std::max(1, std::min(f.sms - 1, tune.reserve_sms));
-      if (const char* cp = getenv("HPMXP_CAP_PANELS")) f.cap_panels = cp[0] != '0';
     }
   }
   f.run();

@@ -15,9 +15,23 @@
 namespace hpmxp {
 
 namespace {
-std::atomic<int> g_tile{0}, g_reserve{0};
+std::atomic<int> g_tile{0}, g_reserve{0}, g_budget{0};
 std::atomic<long long> g_overlap{0};
+thread_local int t_budget = 0;
 }  // namespace
+
+SmBudgetScope::SmBudgetScope(int sms) : prev(t_budget) { t_budget = sms; }
+SmBudgetScope::~SmBudgetScope() { t_budget = prev; }
+
+int sm_budget() {
+  static const int env_budget = [] {
+    const char* e = getenv("HPMXP_SM_BUDGET");
+    return e ? atoi(e) : 0;
+  }();
+  if (t_budget > 0) return t_budget;
+  if (env_budget > 0) return env_budget;
+  return g_budget.load();
+}
 
 // The tile override is read once (the value is consulted per GEMM launch);
 // the two schedule overrides are read per factorization.
@@ -26,7 +40,7 @@ hpmxp_tuning tuning() {
     const char* e = getenv("HPMXP_GEMM_TILE");
     return e ? atoi(e) : 0;
   }();
-  hpmxp_tuning t{g_tile.load(), g_reserve.load(), g_overlap.load()};
+  hpmxp_tuning t{g_tile.load(), g_reserve.load(), g_overlap.load(), g_budget.load(), 0};
   if (env_tile) t.gemm_tile = env_tile;
   if (const char* e = getenv("HPMXP_RESERVE_SMS")) t.reserve_sms = atoi(e);
   if (const char* e = getenv("HPMXP_OVERLAP_MIN")) t.overlap_min = atoll(e);
@@ -189,16 +203,17 @@ unsigned long long hpmxp_launch_count(void) { return g_launches.load(); }
 
 hpmxp_status hpmxp_set_tuning(const hpmxp_tuning* t) {
   if (!t || !(t->gemm_tile == 0 || t->gemm_tile == 128 || t->gemm_tile == 256) || t->reserve_sms < 0 ||
-      t->reserve_sms > 1024 || t->overlap_min < 0)
+      t->reserve_sms > 1024 || t->overlap_min < 0 || t->sm_budget < 0 || t->sm_budget > 1024 || t->reserved != 0)
     return HPMXP_EINVAL;
   g_tile.store(t->gemm_tile);
   g_reserve.store(t->reserve_sms);
   g_overlap.store(t->overlap_min);
+  g_budget.store(t->sm_budget);
   return HPMXP_OK;
 }
 
 void hpmxp_get_tuning(hpmxp_tuning* t) {
-  if (t) *t = hpmxp_tuning{g_tile.load(), g_reserve.load(), g_overlap.load()};
+  if (t) *t = hpmxp_tuning{g_tile.load(), g_reserve.load(), g_overlap.load(), g_budget.load(), 0};
 }
 
 void hpmxp_prof_enable(int on) { g_enabled.store(on ? 1 : 0); }

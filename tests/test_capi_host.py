@@ -83,14 +83,16 @@ def test_python_modules_import():
 def test_schedule_tuning_set_get(lib):
     old = capi.hpmxp_get_tuning()
     try:
-        assert capi.hpmxp_set_tuning(128, 20, 4096) == capi.OK
-        assert capi.hpmxp_get_tuning() == dict(gemm_tile=128, reserve_sms=20, overlap_min=4096)
-        # tile heights other than 0/128/256 and negative counts are refused and change nothing
-        for bad in ((64, 0, 0), (512, 0, 0), (0, -1, 0), (0, 0, -5), (0, 5000, 0)):
+        assert capi.hpmxp_set_tuning(128, 20, 4096, 40) == capi.OK
+        want = dict(gemm_tile=128, reserve_sms=20, overlap_min=4096, sm_budget=40)
+        assert capi.hpmxp_get_tuning() == want
+        # tile heights other than 0/128/256, negative counts and a nonzero reserved field are
+        # refused and change nothing
+        for bad in ((64, 0, 0), (512, 0, 0), (0, -1, 0), (0, 0, -5), (0, 5000, 0), (0, 0, 0, -1), (0, 0, 0, 0, 1)):
             assert capi.hpmxp_set_tuning(*bad) == capi.EINVAL
-        assert capi.hpmxp_get_tuning() == dict(gemm_tile=128, reserve_sms=20, overlap_min=4096)
+        assert capi.hpmxp_get_tuning() == want
     finally:
-        assert capi.hpmxp_set_tuning(old["gemm_tile"], old["reserve_sms"], old["overlap_min"]) == capi.OK
+        assert capi.hpmxp_set_tuning(**old) == capi.OK
 
 
 def test_autotune_search_space():

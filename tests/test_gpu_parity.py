@@ -229,21 +229,28 @@ def test_factor_simt_engine_bit_exact(n, nb, prec):
     assert bad.size == 0, (bad[:5], got[tuple(bad[0])], LU_o[tuple(bad[0])])
 
 
-@pytest.mark.parametrize("n,nb", [(1031, 128), (1300, 256), (1700, 512)])
-def test_factor_lookahead_schedule_bit_exact(n, nb, monkeypatch):
-    # two-stream look-ahead forced on at small sizes: any missing dependency
-    # between the near/far parts of the Schur update would change bits
+@pytest.mark.parametrize("n,nb,prec", [(1031, 128, capi.BF16), (1300, 256, capi.BF16), (1700, 512, capi.BF16),
+                                       (1300, 512, capi.BF16), (1031, 128, capi.FP8_E4M3),
+                                       (1700, 512, capi.FP8_E4M3), (1300, 512, capi.FP16)])
+def test_factor_lookahead_schedule_bit_exact(n, nb, prec, monkeypatch):
+    # look-ahead forced on at small sizes: any missing dependency between the
+    # critical path (diagonal block, panel heads, next diagonal block) and the
+    # side stream (panel tails, near and far parts, split FP8 quantization)
+    # would change bits; n = 1300, nb = 512 ends with a narrower next block
     monkeypatch.setenv("HPMXP_OVERLAP_MIN", "128")
     A_o, _ = oracle.generate(n, 77)
     A = api.ColMajor.from_tensor(torch.from_numpy(A_o), DEV)
     with engine("simt"):
-        LU = api.factor(A, capi.BF16, nb)
+        LU = api.factor(A, prec, nb)
     torch.cuda.synchronize()
-    LU_o, _ = oracle.factor(A_o, oracle.BF16, nb)
+    if prec == capi.FP8_E4M3:
+        LU_o, _ = oracle.factor(A_o, oracle.BF16, nb, fmt_update=oracle.E4M3)
+    else:
+        LU_o, _ = oracle.factor(A_o, ORC_FMT[prec], nb)
     assert np.array_equal(to_np(LU), LU_o)
-    LU2 = api.factor(A, capi.BF16, nb)   # tensor cores, same schedule
+    LU2 = api.factor(A, prec, nb)   # tensor cores, same schedule
     torch.cuda.synchronize()
-    assert np.linalg.norm(to_np(LU2) - LU_o) / np.linalg.norm(LU_o) <= 2.0**-8
+    assert np.linalg.norm(to_np(LU2) - LU_o) / np.linalg.norm(LU_o) <= U_LOW[prec]
 
 
 @pytest.mark.parametrize("n,nb", [(300, 128), (700, 256), (1000, 512), (1500, 512)])

@@ -23,7 +23,7 @@ DEV = torch.device("cuda:0")
 def restore_tuning():
     old = capi.hpmxp_get_tuning()
     yield
-    assert capi.hpmxp_set_tuning(old["gemm_tile"], old["reserve_sms"], old["overlap_min"]) == capi.OK
+    assert capi.hpmxp_set_tuning(**old) == capi.OK
 
 
 def factors(A, prec, nb):
@@ -57,3 +57,24 @@ def test_autotune_applies_a_candidate(tmp_path, monkeypatch):
     # the second call recalls the cached choice without searching
     monkeypatch.setattr(autotune, "_time", lambda *a, **k: pytest.fail("searched again"))
     assert autotune.tune(n, capi.BF16, A, device=DEV) == choice
+
+
+@pytest.mark.parametrize("budget", [1, 7, 40])
+def test_sm_budget_keeps_results_bit_identical(budget):
+    """A smaller persistent GEMM grid and a smaller cooperative preconditioner
+    grid (each CTA then owns more block rows) change neither the factors nor x:
+    every block row still receives its terms in the same order."""
+    n, k, nb = 3000, 3, 128
+    A, b = api.generate(n, seed=21, nrhs=k, device=DEV)
+    p = api.ir_params(precond_fp32=1, inner_tol=1e-5)
+    outs = []
+    for sm in (0, budget):
+        assert capi.hpmxp_set_tuning(0, 0, 0, sm) == capi.OK
+        LU = api.factor(A, capi.BF16, nb)
+        x, infos, st = api.solve_ir(A, LU, b, capi.BF16, p)
+        torch.cuda.synchronize(DEV)
+        assert st == capi.OK
+        outs.append((LU.view().float().cpu().numpy(), x.view().cpu().numpy(), [i["iters"] for i in infos]))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
