@@ -396,21 +396,14 @@ __device__ inline void store16(float* p, const float (&v)[kPW]) {
     *reinterpret_cast<float4*>(p + 4 * m) = make_float4(v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
 }
 
-__device__ __forceinline__ void getrf_block(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt,
-                                            uint16_t* __restrict__ linv, int64_t ldl, uint16_t* __restrict__ uinvT,
-                                            int64_t ldu, uint32_t* status) {
-  extern __shared__ float sm[];
-  float* a = sm;                  // a[j * kP + i] = D(i, j); later the stored L and U
-  float* x = sm + kB * kP;        // X = L^{-1}, x[c * kP + r] = X(r, c)
-  float* y = sm + 2 * kB * kP;    // Y = U^{-1}, y[c * kP + r] = Y(r, c)
-  float* urow = sm + 3 * kB * kP; // [2][kPW] pivot row of the current panel step
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// The pieces of the diagonal-block kernels.  `a` holds the block in fp32
+// (pitch kP, zero outside b x b); x = L^{-1}, y = U^{-1} (x[c * kP + r] = X(r, c)).
 
-  // a full block whose columns start on 16-byte boundaries moves 8 entries
-  // (16 bytes) per access
-  const bool vec = b == kB && (reinterpret_cast<uintptr_t>(D) & 15) == 0 && (ldd & 7) == 0;
+// a <- D (16-bit, column major), zero outside b x b; threads tid .. of nt
+__device__ __forceinline__ void load_block(float* a, const uint16_t* __restrict__ D, int64_t ldd, int b, int fmt,
+                                           bool vec, int tid, int nt) {
   if (vec) {
-    for (int v = tid; v < kB * kB / 8; v += kGetrfThreads) {
+    for (int v = tid; v < kB * kB / 8; v += nt) {
       const int i = 8 * (v % (kB / 8)), j = v / (kB / 8);
       const uint4 w = *reinterpret_cast<const uint4*>(D + i + (int64_t)j * ldd);
       const uint32_t h[4] = {w.x, w.y, w.z, w.w};
@@ -424,13 +417,17 @@ __device__ __forceinline__ void getrf_block(int b, uint16_t* __restrict__ D, int
       *reinterpret_cast<float4*>(&a[j * kP + i + 4]) = make_float4(f[4], f[5], f[6], f[7]);
     }
   } else {
-    for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    for (int idx = tid; idx < kB * kB; idx += nt) {
       const int i = idx % kB, j = idx / kB;
       a[j * kP + i] = (i < b && j < b) ? u16_to_f32(D[i + (int64_t)j * ldd], fmt) : 0.0f;
     }
   }
-  __syncthreads();
+}
 
+// LU without pivoting of a (b x b) in fp32, in place; kGetrfThreads threads.
+// A zero or non-finite pivot sets kErrPivot.
+__device__ __forceinline__ void lu_block(float* a, float* urow, int b, uint32_t* status) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   bool bad = false;
   // (a) panel: rows p0..b-1 (one per lane of warps 0-3), columns p0..p0+pw-1
   auto eliminate = [&](int p0, int pw) {
@@ -500,10 +497,14 @@ __device__ __forceinline__ void getrf_block(int b, uint16_t* __restrict__ D, int
   }
   if (bad && tid == 0) atomicOr(status, kErrPivot);
 
-  // round into storage and keep the stored values for the inverses; X = I,
-  // Y = diag(1 / stored U)
+}
+
+// D <- round(a); a <- the stored values (the factors' exact fp32 values);
+// with x / y given also X = I and Y = diag(1 / stored U)
+__device__ __forceinline__ void round_block(float* a, uint16_t* __restrict__ D, int64_t ldd, int b, int fmt,
+                                            bool vec, float* x, float* y, int tid, int nt) {
   if (vec) {
-    for (int v = tid; v < kB * kB / 8; v += kGetrfThreads) {
+    for (int v = tid; v < kB * kB / 8; v += nt) {
       const int i = 8 * (v % (kB / 8)), j = v / (kB / 8);
       float f[8];
       const float4 f0 = *reinterpret_cast<const float4*>(&a[j * kP + i]);
@@ -522,13 +523,17 @@ __device__ __forceinline__ void getrf_block(int b, uint16_t* __restrict__ D, int
       *reinterpret_cast<uint4*>(D + i + (int64_t)j * ldd) = make_uint4(h[0], h[1], h[2], h[3]);
       *reinterpret_cast<float4*>(&a[j * kP + i]) = make_float4(f[0], f[1], f[2], f[3]);
       *reinterpret_cast<float4*>(&a[j * kP + i + 4]) = make_float4(f[4], f[5], f[6], f[7]);
-      *reinterpret_cast<float4*>(&x[j * kP + i]) = make_float4(xs[0], xs[1], xs[2], xs[3]);
-      *reinterpret_cast<float4*>(&x[j * kP + i + 4]) = make_float4(xs[4], xs[5], xs[6], xs[7]);
-      *reinterpret_cast<float4*>(&y[j * kP + i]) = make_float4(ys[0], ys[1], ys[2], ys[3]);
-      *reinterpret_cast<float4*>(&y[j * kP + i + 4]) = make_float4(ys[4], ys[5], ys[6], ys[7]);
+      if (x) {
+        *reinterpret_cast<float4*>(&x[j * kP + i]) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+        *reinterpret_cast<float4*>(&x[j * kP + i + 4]) = make_float4(xs[4], xs[5], xs[6], xs[7]);
+      }
+      if (y) {
+        *reinterpret_cast<float4*>(&y[j * kP + i]) = make_float4(ys[0], ys[1], ys[2], ys[3]);
+        *reinterpret_cast<float4*>(&y[j * kP + i + 4]) = make_float4(ys[4], ys[5], ys[6], ys[7]);
+      }
     }
   } else {
-    for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
+    for (int idx = tid; idx < kB * kB; idx += nt) {
       const int i = idx % kB, j = idx / kB;
       float v = 0.0f;
       if (i < b && j < b) {
@@ -537,137 +542,211 @@ __device__ __forceinline__ void getrf_block(int b, uint16_t* __restrict__ D, int
         v = u16_to_f32(h, fmt);
       }
       a[j * kP + i] = v;
-      x[j * kP + i] = (i == j && i < b) ? 1.0f : 0.0f;
-      y[j * kP + i] = (i == j && i < b) ? __fdiv_rn(1.0f, v) : 0.0f;
-    }
-  }
-  __syncthreads();
-
-  if (warp < 8) {
-    // ---- X = L^{-1}, 16-row blocks top-down; group barrier id 2 (256 threads)
-    const int gt = tid;   // 0..255
-    for (int t0 = 0; t0 < b; t0 += kPW) {
-      const int t1 = min(t0 + kPW, b);
-      // rows t0..t1-1, every column c < t1: within-block terms t = t0 .. r-1 in
-      // ascending order; X(t, c) = 0 for t < c, so those terms are exact no-ops
-      // and each entry sees the same operations as the plain recurrence
-      for (int c = gt; c < t1; c += 256) {
-        float col[kPW];
-        if (t1 - t0 == kPW) {
-          load16(col, &x[c * kP + t0]);
-#pragma unroll
-          for (int q = 0; q < kPW - 1; ++q) {
-            float lq[kPW];   // column t0 + q of L, rows t0 .. t0 + 15
-            load16(lq, &a[(t0 + q) * kP + t0]);
-#pragma unroll
-            for (int r = q + 1; r < kPW; ++r) col[r] = __fmaf_rn(-lq[r], col[q], col[r]);
-          }
-          store16(&x[c * kP + t0], col);
-        } else {
-#pragma unroll
-          for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? x[c * kP + t0 + r] : 0.0f;
-#pragma unroll
-          for (int q = 0; q < kPW - 1; ++q) {
-#pragma unroll
-            for (int r = q + 1; r < kPW; ++r)
-              if (t0 + r < t1) col[r] = __fmaf_rn(-a[(t0 + q) * kP + t0 + r], col[q], col[r]);
-          }
-#pragma unroll
-          for (int r = 0; r < kPW; ++r)
-            if (t0 + r < t1) x[c * kP + t0 + r] = col[r];
-        }
-      }
-      named_sync(2, 256);
-      // rows t1..b-1, columns 0..t1-1: add -L(r, t) X(t, c) for t = t0..t1-1 ascending
-      if (t1 < b) rank_update<false>(x, a, x, t1, b, 0, t1, t0, t1, -1.0f, warp, 8, lane);
-      named_sync(2, 256);
-    }
-  } else {
-    // ---- Y = U^{-1}, 16-row blocks bottom-up; group barrier id 3 (256 threads)
-    const int gt = tid - 256;
-    const int nblk = (b + kPW - 1) / kPW;
-    for (int bi = nblk - 1; bi >= 0; --bi) {
-      const int t0 = bi * kPW, t1 = min(t0 + kPW, b);
-      // rows t1-1 down to t0, every column c >= t0, right-looking: finalize row
-      // t0+q (divide, unless it is the diagonal or below it), then add its term
-      // to the rows above it; terms come in descending t, rows t > c carry 0
-      for (int c = t0 + gt; c < b; c += 256) {
-        float col[kPW];
-        if (t1 - t0 == kPW) {
-          load16(col, &y[c * kP + t0]);
-          // uq = column rq of U, rows t0 .. t0 + 15 (uq[q] = U(rq, rq)); the
-          // next column is fetched while this one is applied
-          float uq[kPW], un[kPW];
-          load16(uq, &a[(t0 + kPW - 1) * kP + t0]);
-#pragma unroll
-          for (int q = kPW - 1; q >= 0; --q) {
-            const int rq = t0 + q;
-            if (q > 0) load16(un, &a[(rq - 1) * kP + t0]);
-            if (rq < c) col[q] = __fdiv_rn(-col[q], uq[q]);
-#pragma unroll
-            for (int r = 0; r < q; ++r) col[r] = __fmaf_rn(uq[r], col[q], col[r]);
-            if (q > 0) {
-#pragma unroll
-              for (int r = 0; r < kPW; ++r) uq[r] = un[r];
-            }
-          }
-          store16(&y[c * kP + t0], col);
-        } else {
-#pragma unroll
-          for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? y[c * kP + t0 + r] : 0.0f;
-#pragma unroll
-          for (int q = kPW - 1; q >= 0; --q) {
-            const int rq = t0 + q;
-            if (rq < t1 && rq < c) col[q] = __fdiv_rn(-col[q], a[rq * kP + rq]);
-#pragma unroll
-            for (int r = 0; r < q; ++r)
-              if (rq < t1) col[r] = __fmaf_rn(a[rq * kP + t0 + r], col[q], col[r]);
-          }
-#pragma unroll
-          for (int r = 0; r < kPW; ++r)
-            if (t0 + r < t1) y[c * kP + t0 + r] = col[r];
-        }
-      }
-      named_sync(3, 256);
-      // rows 0..t0-1, columns t0..b-1: add U(r, t) Y(t, c) for t = t1-1 down to t0
-      if (t0 > 0) rank_update<true>(y, a, y, 0, t0, t0, b, t0, t1, 1.0f, warp - 8, 8, lane);
-      named_sync(3, 256);
-    }
-  }
-  __syncthreads();
-  // Linv[p][t] = X(p, t), UinvT[p][t] = Y(t, p), rounded; zero outside b x b
-  if ((reinterpret_cast<uintptr_t>(linv) & 15) == 0 && (ldl & 7) == 0 &&
-      (reinterpret_cast<uintptr_t>(uinvT) & 15) == 0 && (ldu & 7) == 0) {
-    for (int v = tid; v < kB * kB / 8; v += kGetrfThreads) {
-      const int t0 = 8 * (v % (kB / 8)), pp = v / (kB / 8);
-      uint32_t hl[4], hu[4];
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const bool in = pp < b && t0 + m < b;
-        const uint16_t l = in ? f32_to_u16(x[(t0 + m) * kP + pp], fmt) : (uint16_t)0;
-        const uint16_t u = in ? f32_to_u16(y[pp * kP + t0 + m], fmt) : (uint16_t)0;
-        if (m & 1) { hl[m >> 1] |= (uint32_t)l << 16; hu[m >> 1] |= (uint32_t)u << 16; }
-        else { hl[m >> 1] = l; hu[m >> 1] = u; }
-      }
-      *reinterpret_cast<uint4*>(linv + (int64_t)pp * ldl + t0) = make_uint4(hl[0], hl[1], hl[2], hl[3]);
-      *reinterpret_cast<uint4*>(uinvT + (int64_t)pp * ldu + t0) = make_uint4(hu[0], hu[1], hu[2], hu[3]);
-    }
-  } else {
-    for (int idx = tid; idx < kB * kB; idx += kGetrfThreads) {
-      const int t = idx % kB, pp = idx / kB;
-      const bool in = pp < b && t < b;
-      linv[(int64_t)pp * ldl + t] = in ? f32_to_u16(x[t * kP + pp], fmt) : (uint16_t)0;
-      uinvT[(int64_t)pp * ldu + t] = in ? f32_to_u16(y[pp * kP + t], fmt) : (uint16_t)0;
+      if (x) x[j * kP + i] = (i == j && i < b) ? 1.0f : 0.0f;
+      if (y) y[j * kP + i] = (i == j && i < b) ? __fdiv_rn(1.0f, v) : 0.0f;
     }
   }
 }
 
+// X = I and Y = diag(1 / a_ii) for a block whose a already holds stored values
+__device__ __forceinline__ void init_inverse(float* m, const float* a, int b, bool upper, int tid, int nt) {
+  for (int idx = tid; idx < kB * kB; idx += nt) {
+    const int i = idx % kB, j = idx / kB;
+    m[j * kP + i] = (i == j && i < b) ? (upper ? __fdiv_rn(1.0f, a[j * kP + i]) : 1.0f) : 0.0f;
+  }
+}
+
+// X = L^{-1} (unit lower part of a), 16-row blocks top-down, by the NT
+// threads gt = 0 .. NT-1 (warps gw) of one group with barrier BAR.  The
+// result does not depend on NT: every entry takes its terms in one order.
+template <int NT, int BAR>
+__device__ __forceinline__ void inv_lower(float* x, const float* a, int b, int gt, int gw, int lane) {
+  for (int t0 = 0; t0 < b; t0 += kPW) {
+    const int t1 = min(t0 + kPW, b);
+    // rows t0..t1-1, every column c < t1: within-block terms t = t0 .. r-1 in
+    // ascending order; X(t, c) = 0 for t < c, so those terms are exact no-ops
+    // and each entry sees the same operations as the plain recurrence
+    for (int c = gt; c < t1; c += NT) {
+      float col[kPW];
+      if (t1 - t0 == kPW) {
+        load16(col, &x[c * kP + t0]);
+#pragma unroll
+        for (int q = 0; q < kPW - 1; ++q) {
+          float lq[kPW];   // column t0 + q of L, rows t0 .. t0 + 15
+          load16(lq, &a[(t0 + q) * kP + t0]);
+#pragma unroll
+          for (int r = q + 1; r < kPW; ++r) col[r] = __fmaf_rn(-lq[r], col[q], col[r]);
+        }
+        store16(&x[c * kP + t0], col);
+      } else {
+#pragma unroll
+        for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? x[c * kP + t0 + r] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < kPW - 1; ++q) {
+#pragma unroll
+          for (int r = q + 1; r < kPW; ++r)
+            if (t0 + r < t1) col[r] = __fmaf_rn(-a[(t0 + q) * kP + t0 + r], col[q], col[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kPW; ++r)
+          if (t0 + r < t1) x[c * kP + t0 + r] = col[r];
+      }
+    }
+    named_sync(BAR, NT);
+    // rows t1..b-1, columns 0..t1-1: add -L(r, t) X(t, c) for t = t0..t1-1 ascending
+    if (t1 < b) rank_update<false>(x, a, x, t1, b, 0, t1, t0, t1, -1.0f, gw, NT / 32, lane);
+    named_sync(BAR, NT);
+  }
+}
+
+// Y = U^{-1} (upper part of a, Y's diagonal preset to 1 / U(r, r)), 16-row
+// blocks bottom-up, by the NT threads of one group with barrier BAR
+template <int NT, int BAR>
+__device__ __forceinline__ void inv_upper(float* y, const float* a, int b, int gt, int gw, int lane) {
+  const int nblk = (b + kPW - 1) / kPW;
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int t0 = bi * kPW, t1 = min(t0 + kPW, b);
+    // rows t1-1 down to t0, every column c >= t0, right-looking: finalize row
+    // t0+q (divide, unless it is the diagonal or below it), then add its term
+    // to the rows above it; terms come in descending t, rows t > c carry 0
+    for (int c = t0 + gt; c < b; c += NT) {
+      float col[kPW];
+      if (t1 - t0 == kPW) {
+        load16(col, &y[c * kP + t0]);
+        // uq = column rq of U, rows t0 .. t0 + 15 (uq[q] = U(rq, rq)); the
+        // next column is fetched while this one is applied
+        float uq[kPW], un[kPW];
+        load16(uq, &a[(t0 + kPW - 1) * kP + t0]);
+#pragma unroll
+        for (int q = kPW - 1; q >= 0; --q) {
+          const int rq = t0 + q;
+          if (q > 0) load16(un, &a[(rq - 1) * kP + t0]);
+          if (rq < c) col[q] = __fdiv_rn(-col[q], uq[q]);
+#pragma unroll
+          for (int r = 0; r < q; ++r) col[r] = __fmaf_rn(uq[r], col[q], col[r]);
+          if (q > 0) {
+#pragma unroll
+            for (int r = 0; r < kPW; ++r) uq[r] = un[r];
+          }
+        }
+        store16(&y[c * kP + t0], col);
+      } else {
+#pragma unroll
+        for (int r = 0; r < kPW; ++r) col[r] = (t0 + r < t1) ? y[c * kP + t0 + r] : 0.0f;
+#pragma unroll
+        for (int q = kPW - 1; q >= 0; --q) {
+          const int rq = t0 + q;
+          if (rq < t1 && rq < c) col[q] = __fdiv_rn(-col[q], a[rq * kP + rq]);
+#pragma unroll
+          for (int r = 0; r < q; ++r)
+            if (rq < t1) col[r] = __fmaf_rn(a[rq * kP + t0 + r], col[q], col[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kPW; ++r)
+          if (t0 + r < t1) y[c * kP + t0 + r] = col[r];
+      }
+    }
+    named_sync(BAR, NT);
+    // rows 0..t0-1, columns t0..b-1: add U(r, t) Y(t, c) for t = t1-1 down to t0
+    if (t0 > 0) rank_update<true>(y, a, y, 0, t0, t0, b, t0, t1, 1.0f, gw, NT / 32, lane);
+    named_sync(BAR, NT);
+  }
+}
+
+// Linv[p][t] = X(p, t) and UinvT[p][t] = Y(t, p), rounded; zero outside b x b
+__device__ __forceinline__ void store_inverse(const float* m, bool upper, int b, int fmt, uint16_t* __restrict__ out,
+                                              int64_t ldo, int tid, int nt) {
+  if ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && (ldo & 7) == 0) {
+    for (int v = tid; v < kB * kB / 8; v += nt) {
+      const int t0 = 8 * (v % (kB / 8)), pp = v / (kB / 8);
+      uint32_t h[4];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const bool in = pp < b && t0 + q < b;
+        const uint16_t e = in ? f32_to_u16(upper ? m[pp * kP + t0 + q] : m[(t0 + q) * kP + pp], fmt) : (uint16_t)0;
+        if (q & 1) h[q >> 1] |= (uint32_t)e << 16; else h[q >> 1] = e;
+      }
+      *reinterpret_cast<uint4*>(out + (int64_t)pp * ldo + t0) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+  } else {
+    for (int idx = tid; idx < kB * kB; idx += nt) {
+      const int t = idx % kB, pp = idx / kB;
+      const bool in = pp < b && t < b;
+      out[(int64_t)pp * ldo + t] = in ? f32_to_u16(upper ? m[pp * kP + t] : m[t * kP + pp], fmt) : (uint16_t)0;
+    }
+  }
+}
+
+__device__ __forceinline__ bool block_vec(int b, const uint16_t* D, int64_t ldd) {
+  return b == kB && (reinterpret_cast<uintptr_t>(D) & 15) == 0 && (ldd & 7) == 0;
+}
+
+// The whole diagonal block in one CTA: LU, then L^{-1} (warps 0-7) beside
+// U^{-1} (warps 8-15), then both inverses stored (the batched factorization's
+// grouped kernel)
+__device__ __forceinline__ void getrf_block(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt,
+                                            uint16_t* __restrict__ linv, int64_t ldl, uint16_t* __restrict__ uinvT,
+                                            int64_t ldu, uint32_t* status) {
+  extern __shared__ float sm[];
+  float* a = sm;
+  float* x = sm + kB * kP;
+  float* y = sm + 2 * kB * kP;
+  float* urow = sm + 3 * kB * kP; // [2][kPW] pivot row of the current panel step
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool vec = block_vec(b, D, ldd);
+  load_block(a, D, ldd, b, fmt, vec, tid, kGetrfThreads);
+  __syncthreads();
+  lu_block(a, urow, b, status);
+  round_block(a, D, ldd, b, fmt, vec, x, y, tid, kGetrfThreads);
+  __syncthreads();
+  if (warp < 8) inv_lower<256, 2>(x, a, b, tid, warp, lane);
+  else inv_upper<256, 3>(y, a, b, tid - 256, warp - 8, lane);
+  __syncthreads();
+  store_inverse(x, false, b, fmt, linv, ldl, tid, kGetrfThreads);
+  store_inverse(y, true, b, fmt, uinvT, ldu, tid, kGetrfThreads);
+}
+
+// The single-system factorization splits the block's work over two kernels:
+// the LU (one CTA), then its two inverses side by side (CTA 0: L^{-1}, CTA 1:
+// U^{-1}, all kGetrfThreads threads each), from the stored factors.  The
+// same operations per entry as getrf_block, so the same bits.
+constexpr size_t kLuSmem = sizeof(float) * (kB * kP + 2 * kPW + 8);
+constexpr size_t kInvSmem = sizeof(float) * 2 * kB * kP;
+
 __global__ void __launch_bounds__(kGetrfThreads)
-getrf_base_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_t* __restrict__ linv,
-                  int64_t ldl, uint16_t* __restrict__ uinvT, int64_t ldu, uint32_t* status) {
-  pdl_wait();      // may start while the previous kernel of the stream finishes
+getrf_lu_kernel(int b, uint16_t* __restrict__ D, int64_t ldd, int fmt, uint32_t* status) {
+  extern __shared__ float sm[];
+  float* a = sm;
+  float* urow = sm + kB * kP;
+  pdl_wait();
   pdl_trigger();
-  getrf_block(b, D, ldd, fmt, linv, ldl, uinvT, ldu, status);
+  const int tid = threadIdx.x;
+  const bool vec = block_vec(b, D, ldd);
+  load_block(a, D, ldd, b, fmt, vec, tid, kGetrfThreads);
+  __syncthreads();
+  lu_block(a, urow, b, status);
+  round_block(a, D, ldd, b, fmt, vec, nullptr, nullptr, tid, kGetrfThreads);
+}
+
+__global__ void __launch_bounds__(kGetrfThreads)
+getrf_inv_kernel(int b, const uint16_t* __restrict__ D, int64_t ldd, int fmt, uint16_t* __restrict__ linv,
+                 int64_t ldl, uint16_t* __restrict__ uinvT, int64_t ldu) {
+  extern __shared__ float sm[];
+  float* a = sm;
+  float* m = sm + kB * kP;
+  pdl_wait();      // the LU kernel has stored the factors
+  pdl_trigger();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool upper = blockIdx.x == 1;
+  load_block(a, D, ldd, b, fmt, block_vec(b, D, ldd), tid, kGetrfThreads);
+  __syncthreads();
+  init_inverse(m, a, b, upper, tid, kGetrfThreads);
+  __syncthreads();
+  if (upper) inv_upper<kGetrfThreads, 1>(m, a, b, tid, warp, lane);
+  else inv_lower<kGetrfThreads, 1>(m, a, b, tid, warp, lane);
+  __syncthreads();
+  if (upper) store_inverse(m, true, b, fmt, uinvT, ldu, tid, kGetrfThreads);
+  else store_inverse(m, false, b, fmt, linv, ldl, tid, kGetrfThreads);
 }
 
 // Grouped diagonal blocks: CTA t factors task t's block (batched
@@ -1059,12 +1138,14 @@ struct Factorizer {
     check(engine == 1 ? gemm_simt(g, st) : gemm_tc(g, st));
   }
 
+  // LU of the diagonal sub-block at (k, k), then its inverses (two CTAs)
   void getrf_base(int64_t k, int b, int slot) {
     void* tok = prof_begin(st);
-    check(launch_pdl(getrf_base_kernel, dim3(1), dim3(kGetrfThreads), kGetrfSmem, st, b, at(k, k), ld, fmt,
-                     aop(slot) + slot * kB, NB, bop(slot) + slot * kB, NB, w.status));
+    check(launch_pdl(getrf_lu_kernel, dim3(1), dim3(kGetrfThreads), kLuSmem, st, b, at(k, k), ld, fmt, w.status));
+    check(launch_pdl(getrf_inv_kernel, dim3(2), dim3(kGetrfThreads), kInvSmem, st, b, (const uint16_t*)at(k, k), ld,
+                     fmt, aop(slot) + slot * kB, NB, bop(slot) + slot * kB, NB));
     prof_end(tok, kProfGetrf, (double)b * b * b * 2.0, st);
-    count_launches(1);
+    count_launches(2);
   }
 
   void pack(int64_t rows, int cols, const uint16_t* src, uint16_t* dst, int64_t ldd) {
@@ -1720,7 +1801,9 @@ hpmxp_status factor(int64_t n, const double* A, int64_t lda, int prec, int nb, v
   cudaGetDevice(&dev);
   if (attr_dev.load() != dev) {
     cudaError_t e =
-        cudaFuncSetAttribute(getrf_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGetrfSmem);
+        cudaFuncSetAttribute(getrf_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(getrf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvSmem);
     if (e != cudaSuccess) return status_from_cuda(e);
     attr_dev.store(dev);
   }
