@@ -396,6 +396,10 @@ __global__ void __launch_bounds__(256) chain_blocks_kernel(int64_t n, const uint
 
 // words of one published value
 template <class T> constexpr int kWords = sizeof(T) / 4;
+// threads of the preconditioner's CTAs: each 128 x 128 product is split over
+// kPrecondThreads / 128 column groups (512 threads for fp32 measured no faster
+// than 256: the step is bound by the hand-off, not the products)
+template <class T> constexpr int kPrecondThreads = 256;
 
 __device__ inline unsigned long long tag_word(uint32_t bits, int epoch) {
   return (unsigned long long)bits | ((unsigned long long)(unsigned)epoch << 32);
@@ -409,7 +413,7 @@ template <int N>
 __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <class T, int K>
-__global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
+__global__ void __launch_bounds__(kPrecondThreads<T>) precond_kernel(int64_t n, const uint16_t* __restrict__ LU, int64_t ld,
                                                       int fmt, const T* __restrict__ dinv,
                                                       const double* __restrict__ pch,
                                                       const double* __restrict__ v, int64_t ldv,
@@ -420,6 +424,9 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
                                                       const double* __restrict__ cs) {
   constexpr bool kInvInSmem = sizeof(T) == 4;   // the fp32 inverse (64 KB) is staged; the fp64 one stays in L2
   constexpr int W = kWords<T>;
+  constexpr int NT = kPrecondThreads<T>;   // threads: NT / 128 groups of 128 rows ...
+  constexpr int HG = NT / kTB32;
+  constexpr int HC = kTB32 / HG;           // ... each multiplying HC of a tile's columns
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int nb = (int)cdiv<int64_t>(n, kTB32);
   const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x;
@@ -429,14 +436,14 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
   T* acc = reinterpret_cast<T*>(kInvInSmem ? (unsigned char*)(ti + kTB32 * kTB32) : (unsigned char*)ti);
   T* zc = acc + (size_t)nown * kTB32 * K;                         // [128][K] block c
   T* zs = zc + kTB32 * K;                                         // [128][K] block being solved
-  T* part = zs + kTB32 * K;                                       // [2][128][K]
-  T* ys = part + 2 * kTB32 * K;                                   // [128][K] y of the next block (fp64)
+  T* part = zs + kTB32 * K;                                       // [HG][128][K]
+  T* ys = part + HG * kTB32 * K;                                  // [128][K] y of the next block (fp64)
   __shared__ int abort_flag;
   if (tid == 0) abort_flag = 0;
   unsigned long long* fpub = pub;
   unsigned long long* bpub = pub + (size_t)nb * kTB32 * K * W;
   for (int o = 0; o < nown; ++o)
-    for (int t = tid; t < kTB32 * K; t += 256) {
+    for (int t = tid; t < kTB32 * K; t += NT) {
       const int ii = t % kTB32, r = t / kTB32;
       const int64_t i = (int64_t)(me + o * G) * kTB32 + ii;
       // balanced factors (LU of diag(rs) A diag(cs)): M^{-1} v = diag(cs) U^{-1} L^{-1} diag(rs) v;
@@ -452,8 +459,8 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     uint16_t* dst = tl + (size_t)slot * kTB32 * kTB32;
     const int64_t i0 = (int64_t)rb * kTB32, j0 = (int64_t)cb * kTB32;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int chunk = tid + q * 256;            // 2048 chunks of 8 rows
+    for (int q = 0; q < 2048 / NT; ++q) {
+      const int chunk = tid + q * NT;             // 2048 chunks of 8 rows
       const int jj = chunk >> 4, ii = (chunk & 15) * 8;
       const int64_t i = i0 + ii, j = j0 + jj;
       int bytes = 0;
@@ -463,21 +470,21 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     }
   };
   auto inv_block = [&](int which, int cb) { return dinv + ((int64_t)which * nb + cb) * kTB32 * kTB32; };
-  // fp64: the 64 inverse entries a thread multiplies, M(ii, h*64 .. h*64+63),
+  // fp64: the HC inverse entries a thread multiplies, M(ii, h*HC .. h*HC+HC-1),
   // loaded into registers when the block becomes next; used by its solve
-  T invr[kInvInSmem ? 1 : 64];
+  T invr[kInvInSmem ? 1 : HC];
   auto fetch_inv = [&](int which, int cb) {
     const T* src = inv_block(which, cb);
     if constexpr (kInvInSmem) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int chunk = tid + q * 256;          // 4096 chunks of 4 floats
+      for (int q = 0; q < 4096 / NT; ++q) {
+        const int chunk = tid + q * NT;           // 4096 chunks of 4 floats
         cp_async16((uint32_t)__cvta_generic_to_shared(ti + chunk * 4), src + chunk * 4, 16);
       }
     } else {
       const int ii = tid % kTB32, h = tid / kTB32;
 #pragma unroll
-      for (int q = 0; q < 64; ++q) invr[q] = __ldcg(src + (h * 64 + q) * kTB32 + ii);
+      for (int q = 0; q < HC; ++q) invr[q] = __ldcg(src + (h * HC + q) * kTB32 + ii);
     }
   };
   // fp64: the chain block P (which 0) / Q (which 1) of block cb into the same registers
@@ -486,7 +493,7 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
       const double* src = pch + ((int64_t)which * nb + cb) * kTB32 * kTB32;
       const int ii = tid % kTB32, h = tid / kTB32;
 #pragma unroll
-      for (int q = 0; q < 64; ++q) invr[q] = __ldcg(src + (h * 64 + q) * kTB32 + ii);
+      for (int q = 0; q < HC; ++q) invr[q] = __ldcg(src + (h * HC + q) * kTB32 + ii);
     }
   };
   // out[i][r] (-)= sum_j M(i, j) w[j][r]; M a 16-bit tile (T16) or the inverse (Tinv, fp32 in
@@ -498,14 +505,14 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     for (int r = 0; r < K; ++r) s[r] = (T)0;
     if (T16) {
 #pragma unroll 8
-      for (int jj = h * 64; jj < h * 64 + 64; ++jj) {
+      for (int jj = h * HC; jj < h * HC + HC; ++jj) {
         const T tv = (T)u16_to_f32(T16[jj * kTB32 + ii], fmt);
 #pragma unroll
         for (int r = 0; r < K; ++r) s[r] = fma_t<T>(tv, w[jj * K + r], s[r]);
       }
     } else {
 #pragma unroll 16
-      for (int jj = h * 64; jj < h * 64 + 64; ++jj) {
+      for (int jj = h * HC; jj < h * HC + HC; ++jj) {
         const T tv = Tinv[jj * kTB32 + ii];
 #pragma unroll
         for (int r = 0; r < K; ++r) s[r] = fma_t<T>(tv, w[jj * K + r], s[r]);
@@ -514,8 +521,10 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
 #pragma unroll
     for (int r = 0; r < K; ++r) part[(h * kTB32 + ii) * K + r] = s[r];
     __syncthreads();
-    for (int t = tid; t < kTB32 * K; t += 256) {
-      const T tot = part[t] + part[kTB32 * K + t];
+    for (int t = tid; t < kTB32 * K; t += NT) {
+      T tot = part[t];
+#pragma unroll
+      for (int g = 1; g < HG; ++g) tot += part[g * kTB32 * K + t];
       out[t] = subtract ? out[t] - tot : tot;
     }
     __syncthreads();
@@ -531,7 +540,7 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
   auto receive = [&](const unsigned long long* src, int c, T* dst) {
     const unsigned long long* w = src + (size_t)c * kTB32 * K * W;
     const unsigned long long t0 = global_ns();
-    for (int t = tid; t < kTB32 * K; t += 256) {
+    for (int t = tid; t < kTB32 * K; t += NT) {
       uint32_t bits[W];
 #pragma unroll
       for (int h = 0; h < W; ++h) {
@@ -553,21 +562,23 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     __syncthreads();
   };
   // fp64: out = M w (or from - M w) with M in the invr registers (thread: row ii,
-  // columns h*64 .. h*64+63), the two column halves summed through `part`
+  // columns h*HC .. h*HC+HC-1), the column groups summed in order through `part`
   auto reg_product = [&](const T* w, T* out, const T* from) {
     const int ii = tid % kTB32, h = tid / kTB32;
     T sr[K];
 #pragma unroll
     for (int r = 0; r < K; ++r) sr[r] = (T)0;
 #pragma unroll
-    for (int q = 0; q < 64; ++q)
+    for (int q = 0; q < HC; ++q)
 #pragma unroll
-      for (int r = 0; r < K; ++r) sr[r] = fma_t<T>(invr[kInvInSmem ? 0 : q], w[(h * 64 + q) * K + r], sr[r]);
+      for (int r = 0; r < K; ++r) sr[r] = fma_t<T>(invr[kInvInSmem ? 0 : q], w[(h * HC + q) * K + r], sr[r]);
 #pragma unroll
     for (int r = 0; r < K; ++r) part[(h * kTB32 + ii) * K + r] = sr[r];
     __syncthreads();
-    for (int t = tid; t < kTB32 * K; t += 256) {
-      const T tot = part[t] + part[kTB32 * K + t];
+    for (int t = tid; t < kTB32 * K; t += NT) {
+      T tot = part[t];
+#pragma unroll
+      for (int g = 1; g < HG; ++g) tot += part[g * kTB32 * K + t];
       out[t] = from ? from[t] - tot : tot;
     }
     __syncthreads();
@@ -581,7 +592,7 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
       else reg_product(a, zs, nullptr);
     }
     unsigned long long* wd = dst + (size_t)c * kTB32 * K * W;
-    for (int t = tid; t < kTB32 * K; t += 256) {
+    for (int t = tid; t < kTB32 * K; t += NT) {
       a[t] = zs[t];
       if constexpr (W == 1) {
         asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(wd + t), "l"(tag_word(__float_as_uint(zs[t]), epoch))
@@ -666,7 +677,7 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     const int npre = prefetch_updates(c, true, skip);
     cp_async_commit();
     if (c % G == me) {
-      for (int t = tid; t < kTB32 * K; t += 256) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
+      for (int t = tid; t < kTB32 * K; t += NT) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
     } else {
       receive(fpub, c, zc);
       if (abort_flag) break;
@@ -709,7 +720,7 @@ __global__ void __launch_bounds__(256) precond_kernel(int64_t n, const uint16_t*
     const int npre = prefetch_updates(c, false, skip);
     cp_async_commit();
     if (c % G == me) {
-      for (int t = tid; t < kTB32 * K; t += 256) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
+      for (int t = tid; t < kTB32 * K; t += NT) zc[t] = acc[(size_t)(c / G) * kTB32 * K + t];
     } else {
       receive(bpub, c, zc);
       if (abort_flag) break;
@@ -1073,8 +1084,9 @@ size_t precond_smem(int64_t n, int K, int G) {
   const int nb = (int)cdiv<int64_t>(n, kTB32);
   const int nown = cdiv(nb, G);
   const size_t inv = sizeof(T) == 4 ? sizeof(float) * kTB32 * kTB32 : 0;
+  const size_t groups = kPrecondThreads<T> / kTB32;
   return sizeof(uint16_t) * 3 * kTB32 * kTB32 + inv +
-         sizeof(T) * ((size_t)nown * kTB32 * K + 2 * kTB32 * K + 2 * kTB32 * K + kTB32 * K) + 64;
+         sizeof(T) * ((size_t)nown * kTB32 * K + 2 * kTB32 * K + groups * kTB32 * K + kTB32 * K) + 64;
 }
 
 template <class T, int K>
@@ -1092,7 +1104,7 @@ cudaError_t precond_launch_k(int64_t n, const uint16_t* LU, int64_t ld, int fmt,
   unsigned long long ns = wb.ns;
   void* args[] = {&n,  (void*)&LU, &ld,     &fmt,   (void*)&dinv, (void*)&pch, (void*)&v,  &ldv, &z,
                   &ldz, &pub,      &epoch, &status, &polls,      &ns,         (void*)&rs, (void*)&cs};
-  return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(256), args, smem, st);
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(kPrecondThreads<T>), args, smem, st);
 }
 
 template <class T>
