@@ -563,6 +563,14 @@ def main():
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": measured_gemm_traffic(n, nb, args.prec, schedule["gemm_tile"]),
                 "algorithmic_bytes_per_launch": g["bytes"] / max(g["launches"], 1),
+                # the same figure per role: the Schur updates carry the flops, the panel products
+                # (substitution chains of 128-row products) are latency-bound; launches on the
+                # look-ahead streams overlap, so their event durations include waiting for SMs
+                "by_role": {role: {"launches": prof[kind]["launches"], "ms_per_solve": prof[kind]["ms"],
+                                   "tflop_per_solve": prof[kind]["work"] / 1e12,
+                                   "achieved_tflops": (prof[kind]["work"] / (prof[kind]["ms"] / 1e3) / 1e12
+                                                       if prof[kind]["ms"] else None)}
+                            for role, kind in (("schur_updates", "gemm_update"), ("panel_products", "gemm_panel"))},
                 "whole_solve": {"t_roof_ms": t_roof * 1e3, "t_meas_ms": t_step * 1e3, "frac": t_roof / t_step,
                                 "what": "T_roof = 2/3 n^3 / tensor peak + 10 n^2 (iters + 1) bytes / HBM peak"},
                 "per_kind_ms_per_solve": {k: v["ms"] for k, v in prof.items()},
