@@ -800,6 +800,40 @@ __global__ void __launch_bounds__(256) mgs_kernel(int64_t n, int K, int m, int j
   if (threadIdx.x == 0) *counter = 0;
 }
 
+// The whole modified Gram-Schmidt step j in one CTA, for systems small enough
+// that one SM streams w and the basis faster than j + 2 launches would start:
+// for i = 0 .. j, H(i, j) = <w, v_i> then w -= H(i, j) v_i, and hn = ||w||.
+// Every entry of w sees the same operations as in mgs_kernel; the dot products
+// are summed by this CTA's fixed tree instead of across CTAs.
+constexpr int kFusedMgsThreads = 1024;
+constexpr int64_t kFusedMgsMaxElems = 16384;   // n * K at most
+__global__ void __launch_bounds__(kFusedMgsThreads) mgs_fused_kernel(int64_t n, int K, int m, int j, double* W,
+                                                                     int64_t ldw, const double* V, int64_t ldv_col,
+                                                                     int64_t ldv_rhs, RhsState* st) {
+  __shared__ double sh[kFusedMgsThreads];
+  for (int r = 0; r < K; ++r) {
+    if (!st[r].cycle_active) continue;   // the same value for every thread
+    double* w = W + r * ldw;
+    double hprev = 0.0;
+    for (int i = 0; i <= j + 1; ++i) {
+      const double* vprev = i > 0 ? V + r * ldv_rhs + (int64_t)(i - 1) * ldv_col : nullptr;
+      const double* vi = i <= j ? V + r * ldv_rhs + (int64_t)i * ldv_col : nullptr;
+      double part = 0.0;
+      for (int64_t t = threadIdx.x; t < n; t += kFusedMgsThreads) {
+        double wt = w[t];
+        if (vprev) { wt = __fma_rn(-hprev, vprev[t], wt); w[t] = wt; }
+        part = vi ? __fma_rn(wt, vi[t], part) : __fma_rn(wt, wt, part);
+      }
+      const double s = block_sum(part, sh);   // ends with a barrier: w's updates are visible
+      if (threadIdx.x == 0) {
+        if (i <= j) st[r].H[i + j * (m + 1)] = s;
+        else st[r].hn = sqrt(s);
+      }
+      hprev = s;
+    }
+  }
+}
+
 // ||z||_2 for cycle start (beta), into st[r].beta, for rhs with outer_active.
 __global__ void __launch_bounds__(256) norm2_kernel(int64_t n, int K, const double* Z, int64_t ldz, RhsState* st,
                                                     double* partials, unsigned int* counter) {
@@ -1173,6 +1207,18 @@ struct Solver {
   cudaError_t read_brief() {
     return read_to_host(brief, w.brief, sizeof(Brief) * K, st);
   }
+  // modified Gram-Schmidt of Arnoldi step j: one CTA for small systems, else
+  // one launch per projection
+  void mgs(int j) {
+    if (n * K <= kFusedMgsMaxElems) {
+      mgs_fused_kernel<<<1, kFusedMgsThreads, 0, st>>>(n, K, m, j, w.w, n, w.V, n, ldv_rhs(), w.st);
+      count_launches(1);
+      return;
+    }
+    for (int i = 0; i <= j + 1; ++i)
+      mgs_kernel<<<kRedBlocks, 256, 0, st>>>(n, K, m, j, i, w.w, n, w.V, n, ldv_rhs(), w.st, w.partials, w.counter);
+    count_launches(j + 2);
+  }
   bool any(int Brief::*f) const {
     for (int r = 0; r < K; ++r)
       if (brief[r].*f) return true;
@@ -1249,11 +1295,9 @@ struct Solver {
                           prm.matvec_fp32 ? 3 : 0, 0, w, st)) != cudaSuccess)
           return e;
         if ((e = precond(w.tmp, n, w.w, n)) != cudaSuccess) return e;
-        for (int i = 0; i <= j + 1; ++i)
-          mgs_kernel<<<kRedBlocks, 256, 0, st>>>(n, K, m, j, i, w.w, n, w.V, n, ldv_rhs(), w.st, w.partials,
-                                                 w.counter);
+        mgs(j);
         givens_kernel<<<1, 32, 0, st>>>(sp, j, w.st, w.brief);
-        count_launches(j + 4);
+        count_launches(2);
         scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, w.w, n, w.V + (int64_t)(j + 1) * n,
                                                                        ldv_rhs(), w.st, 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1488,14 +1532,12 @@ hpmxp_status solve_ir_batched(const hpmxp_problem* probs, int count, int prec, c
         e = residual(s.n, s.K, s.A, s.lda, s.w.V + (int64_t)j * s.n, s.ldv_rhs(), nullptr, 0, s.w.tmp, s.n,
                      s.prm.matvec_fp32 ? 3 : 0, 0, s.w, st);
         if (e == cudaSuccess) e = s.precond(s.w.tmp, s.n, s.w.w, s.n);
-        for (int i = 0; i <= j + 1; ++i)
-          mgs_kernel<<<kRedBlocks, 256, 0, st>>>(s.n, s.K, s.m, j, i, s.w.w, s.n, s.w.V, s.n, s.ldv_rhs(), s.w.st,
-                                                 s.w.partials, s.w.counter);
+        s.mgs(j);
         givens_kernel<<<1, 32, 0, st>>>(sp, j, s.w.st, s.w.brief);
         scale_kernel<<<(unsigned)cdiv<int64_t>(s.n, 256), 256, 0, st>>>(s.n, s.K, s.w.w, s.n,
                                                                          s.w.V + (int64_t)(j + 1) * s.n,
                                                                          s.ldv_rhs(), s.w.st, 1);
-        count_launches(j + 4);
+        count_launches(2);
       }
       if (e == cudaSuccess) e = cudaGetLastError();
       if (e == cudaSuccess)
