@@ -800,16 +800,19 @@ __global__ void __launch_bounds__(256) mgs_kernel(int64_t n, int K, int m, int j
   if (threadIdx.x == 0) *counter = 0;
 }
 
-// The whole modified Gram-Schmidt step j in one CTA, for systems small enough
-// that one SM streams w and the basis faster than j + 2 launches would start:
-// for i = 0 .. j, H(i, j) = <w, v_i> then w -= H(i, j) v_i, and hn = ||w||.
-// Every entry of w sees the same operations as in mgs_kernel; the dot products
-// are summed by this CTA's fixed tree instead of across CTAs.
+// The tail of Arnoldi step j in one CTA, for systems small enough that one SM
+// streams w and the basis faster than j + 4 launches would start: modified
+// Gram-Schmidt (for i = 0 .. j, H(i, j) = <w, v_i> then w -= H(i, j) v_i, and
+// hn = ||w||), the Givens update, and v_{j+1} = w / hn.  Every entry of w sees
+// the same operations as in mgs_kernel; the dot products are summed by this
+// CTA's fixed tree instead of across CTAs.
+__device__ void givens_rhs(const SolveParams& sp, int j, RhsState* st, Brief* brief, int r);
 constexpr int kFusedMgsThreads = 1024;
 constexpr int64_t kFusedMgsMaxElems = 16384;   // n * K at most
-__global__ void __launch_bounds__(kFusedMgsThreads) mgs_fused_kernel(int64_t n, int K, int m, int j, double* W,
-                                                                     int64_t ldw, const double* V, int64_t ldv_col,
-                                                                     int64_t ldv_rhs, RhsState* st) {
+__global__ void __launch_bounds__(kFusedMgsThreads) arnoldi_tail_kernel(SolveParams sp, int64_t n, int K, int m,
+                                                                        int j, double* W, int64_t ldw, double* V,
+                                                                        int64_t ldv_col, int64_t ldv_rhs,
+                                                                        RhsState* st, Brief* brief) {
   __shared__ double sh[kFusedMgsThreads];
   for (int r = 0; r < K; ++r) {
     if (!st[r].cycle_active) continue;   // the same value for every thread
@@ -831,6 +834,16 @@ __global__ void __launch_bounds__(kFusedMgsThreads) mgs_fused_kernel(int64_t n, 
       }
       hprev = s;
     }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < K) givens_rhs(sp, j, st, brief, threadIdx.x);
+  __syncthreads();
+  for (int r = 0; r < K; ++r) {
+    if (!st[r].cycle_active) continue;
+    const double hn = st[r].hn;
+    const double* w = W + r * ldw;
+    double* v = V + r * ldv_rhs + (int64_t)(j + 1) * ldv_col;
+    for (int64_t t = threadIdx.x; t < n; t += kFusedMgsThreads) v[t] = w[t] / hn;
   }
 }
 
@@ -929,9 +942,8 @@ __global__ void cycle_start_kernel(SolveParams sp, RhsState* st, Brief* brief) {
 }
 
 // Givens update of column j (after MGS filled H(0..j, j) and hn).
-__global__ void givens_kernel(SolveParams sp, int j, RhsState* st, Brief* brief) {
-  const int r = threadIdx.x;
-  if (r >= sp.n_rhs) return;
+// Givens update of right-hand side r after Arnoldi step j (thread r)
+__device__ void givens_rhs(const SolveParams& sp, int j, RhsState* st, Brief* brief, int r) {
   RhsState& s = st[r];
   if (s.cycle_active) {
     const int ld = sp.m + 1;
@@ -962,6 +974,9 @@ __global__ void givens_kernel(SolveParams sp, int j, RhsState* st, Brief* brief)
   }
   brief[r].cycle_active = s.cycle_active; brief[r].outer_active = s.outer_active;
   brief[r].iters = s.iters; brief[r].status = s.status;
+}
+__global__ void givens_kernel(SolveParams sp, int j, RhsState* st, Brief* brief) {
+  if ((int)threadIdx.x < sp.n_rhs) givens_rhs(sp, j, st, brief, threadIdx.x);
 }
 
 // y = H(0:k, 0:k)^{-1} g(0:k) by back substitution.
@@ -1207,17 +1222,22 @@ struct Solver {
   cudaError_t read_brief() {
     return read_to_host(brief, w.brief, sizeof(Brief) * K, st);
   }
-  // modified Gram-Schmidt of Arnoldi step j: one CTA for small systems, else
-  // one launch per projection
-  void mgs(int j) {
+  // Arnoldi step j after w = M^{-1} A v_j: modified Gram-Schmidt, the Givens
+  // update (into the brief) and v_{j+1}; one CTA for small systems, else one
+  // launch per projection, then the rotation and the scaling
+  void arnoldi_tail(int j) {
+    const SolveParams sp{K, m, prm.max_iters, prm.inner_tol, prm.theta, prm.accept, n};
     if (n * K <= kFusedMgsMaxElems) {
-      mgs_fused_kernel<<<1, kFusedMgsThreads, 0, st>>>(n, K, m, j, w.w, n, w.V, n, ldv_rhs(), w.st);
+      arnoldi_tail_kernel<<<1, kFusedMgsThreads, 0, st>>>(sp, n, K, m, j, w.w, n, w.V, n, ldv_rhs(), w.st, w.brief);
       count_launches(1);
       return;
     }
     for (int i = 0; i <= j + 1; ++i)
       mgs_kernel<<<kRedBlocks, 256, 0, st>>>(n, K, m, j, i, w.w, n, w.V, n, ldv_rhs(), w.st, w.partials, w.counter);
-    count_launches(j + 2);
+    givens_kernel<<<1, 32, 0, st>>>(sp, j, w.st, w.brief);
+    scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, w.w, n, w.V + (int64_t)(j + 1) * n, ldv_rhs(),
+                                                                   w.st, 1);
+    count_launches(j + 4);
   }
   bool any(int Brief::*f) const {
     for (int r = 0; r < K; ++r)
@@ -1295,11 +1315,7 @@ struct Solver {
                           prm.matvec_fp32 ? 3 : 0, 0, w, st)) != cudaSuccess)
           return e;
         if ((e = precond(w.tmp, n, w.w, n)) != cudaSuccess) return e;
-        mgs(j);
-        givens_kernel<<<1, 32, 0, st>>>(sp, j, w.st, w.brief);
-        count_launches(2);
-        scale_kernel<<<(unsigned)cdiv<int64_t>(n, 256), 256, 0, st>>>(n, K, w.w, n, w.V + (int64_t)(j + 1) * n,
-                                                                       ldv_rhs(), w.st, 1);
+        arnoldi_tail(j);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = read_brief()) != cudaSuccess) return e;
       }
@@ -1532,12 +1548,7 @@ hpmxp_status solve_ir_batched(const hpmxp_problem* probs, int count, int prec, c
         e = residual(s.n, s.K, s.A, s.lda, s.w.V + (int64_t)j * s.n, s.ldv_rhs(), nullptr, 0, s.w.tmp, s.n,
                      s.prm.matvec_fp32 ? 3 : 0, 0, s.w, st);
         if (e == cudaSuccess) e = s.precond(s.w.tmp, s.n, s.w.w, s.n);
-        s.mgs(j);
-        givens_kernel<<<1, 32, 0, st>>>(sp, j, s.w.st, s.w.brief);
-        scale_kernel<<<(unsigned)cdiv<int64_t>(s.n, 256), 256, 0, st>>>(s.n, s.K, s.w.w, s.n,
-                                                                         s.w.V + (int64_t)(j + 1) * s.n,
-                                                                         s.ldv_rhs(), s.w.st, 1);
-        count_launches(2);
+        s.arnoldi_tail(j);
       }
       if (e == cudaSuccess) e = cudaGetLastError();
       if (e == cudaSuccess)
