@@ -653,6 +653,22 @@ __global__ void __launch_bounds__(kPrecondThreads<T>) precond_kernel(int64_t n, 
     }
   };
 
+  // fp32: once a CTA has solved block b, the tile and inverse that its next
+  // block b' = b +- G will take on the chain are fetched at the end of that
+  // iteration (into slot 0 and the inverse buffer, unused until then), so they
+  // have landed when z_{b'-+1} arrives; `early` names b'
+  int early = -1;
+  auto fetch_early = [&](int nx, int which, bool forward) {
+    if constexpr (kInvInSmem) {
+      if (nx >= 0 && nx < nb) {
+        fetch_tile(0, nx, forward ? nx - 1 : nx + 1);
+        fetch_inv(which, nx);
+        cp_async_commit();
+        early = nx;
+      }
+    }
+  };
+
   // ---------------- forward: L y = v ----------------
   if (me == 0) { fetch_inv(0, 0); cp_async_commit(); ready(); solve(0, 0, false, fpub); }
   for (int c = 0; c < nb && !abort_flag; ++c) {
@@ -664,8 +680,10 @@ __global__ void __launch_bounds__(kPrecondThreads<T>) precond_kernel(int64_t n, 
     const int skip = next_mine ? (c + 1) / G : -1;
     if (next_mine) {
       if constexpr (kInvInSmem) {
-        fetch_tile(0, c + 1, c);
-        fetch_inv(0, c + 1);
+        if (early != c + 1) {
+          fetch_tile(0, c + 1, c);
+          fetch_inv(0, c + 1);
+        }
       } else {
         // fp64: y = Linv_{c+1} acc_{c+1} before z_c is awaited (acc_{c+1} has every
         // term but z_c's), then the chain block P_{c+1} into the registers
@@ -693,8 +711,10 @@ __global__ void __launch_bounds__(kPrecondThreads<T>) precond_kernel(int64_t n, 
       }
     }
     stream_updates(c, true, skip, npre);
+    if (next_mine) fetch_early(c + 1 + G, 0, true);
   }
   ready();
+  early = -1;
 
   // ---------------- backward: U z = y ----------------
   if ((nb - 1) % G == me && !abort_flag) {
@@ -709,8 +729,10 @@ __global__ void __launch_bounds__(kPrecondThreads<T>) precond_kernel(int64_t n, 
     const int skip = next_mine ? (c - 1) / G : -1;
     if (next_mine) {
       if constexpr (kInvInSmem) {
-        fetch_tile(0, c - 1, c);
-        fetch_inv(1, c - 1);
+        if (early != c - 1) {
+          fetch_tile(0, c - 1, c);
+          fetch_inv(1, c - 1);
+        }
       } else {
         fetch_inv(1, c - 1);
         reg_product(acc + (size_t)skip * kTB32 * K, ys, nullptr);
@@ -736,6 +758,7 @@ __global__ void __launch_bounds__(kPrecondThreads<T>) precond_kernel(int64_t n, 
       }
     }
     stream_updates(c, false, skip, npre);
+    if (next_mine) fetch_early(c - 1 - G, 1, false);
   }
   ready();
 }
