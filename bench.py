@@ -66,7 +66,7 @@ def parse():
                     help="1: balance and scale A (hpmxp_balance) inside every timed solve")
     ap.add_argument("--serving-requests", type=int, default=600,
                     help="requests of the serving sub-record at 1000/s (a third of them at 100/s); 0: skip")
-    ap.add_argument("--serving-batch", type=int, default=64, help="serving: requests per batch in batch mode")
+    ap.add_argument("--serving-batch", type=int, default=192, help="serving: requests per batch in batch mode")
     ap.add_argument("--serving-batch-workers", type=int, default=2, help="serving: workers in batch mode")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--rate", type=float, default=1000.0, help="serving: Poisson arrival rate, requests/s")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the timed stream")
     ap.add_argument("--workers", type=int, default=12, help="serving: executor worker streams")
-    ap.add_argument("--arena-gb", type=float, default=16.0, help="serving: executor arena (admission budget)")
+    ap.add_argument("--arena-gb", type=float, default=64.0, help="serving: executor arena (admission budget)")
     ap.add_argument("--serial-requests", type=int, default=300,
                     help="serving: requests of the one-at-a-time comparison (0: skip)")
     return ap.parse_args()
