@@ -621,21 +621,33 @@ def main():
         A2 = api.ColMajor(torch.empty_like(A.storage), n, n)
         b2 = api.ColMajor(torch.empty_like(b.storage), n, 1)
         steps = max(1, min(args.steps, 5))
+
+        def e2e_step(ev):
+            ev[0].record()
+            A2.storage.copy_(A_h, non_blocking=True)
+            b2.storage.copy_(b_h, non_blocking=True)
+            ev[1].record()
+            solver(A2, b2)
+            ev[2].record()
+            x_h.copy_(solver.x.storage, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps + 1)]
+        e2e_step(evs[0])   # untimed warm-up of the host path
         barrier(ws)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(steps):
-            A2.storage.copy_(A_h, non_blocking=True)
-            b2.storage.copy_(b_h, non_blocking=True)
-            solver(A2, b2)
-            x_h.copy_(solver.x.storage, non_blocking=True)
-            torch.cuda.synchronize(dev)
+        for k in range(steps):
+            e2e_step(evs[k + 1])
         t_e2e = (time.perf_counter() - t0) / steps
+        h2d_ms = sum(e[0].elapsed_time(e[1]) for e in evs[1:]) / steps
+        solve_ms = sum(e[1].elapsed_time(e[2]) for e in evs[1:]) / steps
         barrier(ws)
         t_e2e = allmax(t_e2e, ws, dev)
         e2e = {"value": ws * hpl_ops(n) / t_e2e / 1e12, "unit": "TFLOP/s", "ms_per_step": t_e2e * 1e3,
                "h2d_bytes_per_step": int(A_h.numel() * 8 + b_h.numel() * 8),
-               "d2h_bytes_per_step": int(x_h.numel() * 8)}
+               "d2h_bytes_per_step": int(x_h.numel() * 8), "steps": steps, "warmup": 1,
+               "h2d_ms_per_step": h2d_ms, "solve_ms_per_step": solve_ms}
         del A_h, b_h, x_h, A2, b2
     del A, b, solver
     torch.cuda.empty_cache()
