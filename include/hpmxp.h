@@ -405,6 +405,13 @@ int hpmxp_prof_read(int kind, double* total_ms, double* total_work, long long* l
  * kinds 0 and 7: operands once, C read and / or written once; 0 for the
  * others), for comparison with the bytes a profiler measures. */
 int hpmxp_prof_read_bytes(int kind, double* total_bytes);
+/* Execution time the kernels of a kind measured themselves since the last
+ * reset (the GEMM kinds 0 and 7: the global timer from the first CTA's start
+ * after its stream dependency to the last CTA's end, summed over launches),
+ * and how many launches recorded one.  Beside streams that run concurrently
+ * this excludes the time a launch waits for SMs, which the event time of
+ * hpmxp_prof_read includes.  Returns HPMXP_EINVAL for a bad kind. */
+int hpmxp_prof_read_device(int kind, double* total_ms, long long* launches);
 int hpmxp_prof_timeline(double* out, int max_spans);
 
 #ifdef __cplusplus

@@ -118,6 +118,7 @@ def load():
             "hpmxp_set_tuning": ([ctypes.POINTER(Tuning)], i32),
             "hpmxp_get_tuning": ([ctypes.POINTER(Tuning)], None),
             "hpmxp_prof_enable": ([i32], None),
+            "hpmxp_prof_read_device": ([i32, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)], i32),
             "hpmxp_prof_reset": ([], None),
             "hpmxp_prof_read": ([i32, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)], i32),
             "hpmxp_prof_read_bytes": ([i32, ctypes.POINTER(d)], i32),
@@ -292,6 +293,15 @@ PROF_GEMM, PROF_GEMV, PROF_PRECOND, PROF_GETRF, PROF_GEMV32, PROF_CAST, PROF_PAN
     PROF_BALANCE = range(9)
 PROF_NAMES = {0: "gemm_update", 1: "gemv", 2: "precond", 3: "getrf", 4: "gemv32", 5: "cast", 6: "panel",
               7: "gemm_panel", 8: "balance"}
+
+
+def hpmxp_prof_read_device(kind: int) -> dict:
+    """Execution time the kernels of a kind measured on the device (GEMM kinds)."""
+    ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+    st = load().hpmxp_prof_read_device(kind, ctypes.byref(ms), ctypes.byref(cnt))
+    if st != OK:
+        raise HpmxpError("hpmxp_prof_read_device", st)
+    return dict(ms=ms.value, launches=cnt.value)
 
 
 def hpmxp_prof_read(kind: int) -> dict:

@@ -235,6 +235,10 @@ struct TcParams {
   uint32_t* status;
   long long wait_polls;            // bound of the pipeline waits (the drain waits keep the defaults)
   unsigned long long wait_ns;
+  // measurement: [0] the earliest CTA start after the stream dependency, [1]
+  // all-ones minus the latest CTA end (global timer, ns; both kept by
+  // atomicMin from all-ones), NULL when not measured
+  unsigned long long* span;
 };
 
 // Two floats rounded to nearest even into one 32-bit word of 16-bit values (lo
@@ -345,6 +349,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   // no global memory is touched before it has completed
   pdl_wait();
   pdl_trigger();
+  if (p.span && threadIdx.x == 0) atomicMin(p.span, global_ns());
 
   if (warp == 0) {
     if (lane == 0) {
@@ -581,6 +586,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     tc_fence_after();
     tmem_dealloc(tmem, p.ncols);
   }
+  if (p.span && threadIdx.x == 0) atomicMin(p.span + 1, ~global_ns());
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -696,6 +702,7 @@ cudaError_t gemm_tc_tiles(const GemmArgs& g, cudaStream_t st) {
   const double bytes = ((double)g.M + (double)g.N) * (double)g.K * esz +
                        (p.has_c ? mn * CB * (g.mode == kEpiSub ? 2.0 : 1.0) : 0.0) + (g.R ? mn * 2.0 : 0.0);
   void* tok = prof_begin(st);
+  p.span = prof_device_span(tok);
   const cudaError_t e =
       launch_pdl(gemm_tc_kernel<TI, CB>, dim3(grid), dim3(kThreads), Cfg::kSmem, st, ta, tb, tc, p,
                  (const GemmGroupItem*)nullptr, 0);
@@ -764,6 +771,7 @@ cudaError_t gemm_tc_grouped(const GemmArgs& g, const GemmGroupItem* dev_items, i
   CUtensorMap none;
   memset(&none, 0, sizeof(none));   // the items' maps are used instead
   void* tok = prof_begin(st);
+  p.span = prof_device_span(tok);
   const cudaError_t e = launch_pdl(gemm_tc_kernel<128, 2>, dim3(grid), dim3(kThreads), Cfg::kSmem, st, none, none,
                                    none, p, dev_items, nitems);
   prof_end(tok, g.mode == kEpiSub ? kProfGemm : kProfGemmStore, flops, st, bytes);

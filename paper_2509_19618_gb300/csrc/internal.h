@@ -217,6 +217,9 @@ void* prof_begin(cudaStream_t st);
 // work: the kind's unit (flops or bytes, see hpmxp.h); bytes: algorithmic DRAM
 // bytes of the launch where the kind records them (the GEMM kinds)
 void prof_end(void* token, int kind, double work, cudaStream_t st, double bytes = 0.0);
+// device execution span slot for the launch between prof_begin(token) and
+// prof_end (kernels that record their own span); NULL when not measuring
+unsigned long long* prof_device_span(void* token);
 
 cudaError_t host_wait(cudaStream_t st);   // waits for `st` (spinning unless HPMXP_BLOCKING_WAIT=1)
 cudaError_t read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t st);   // + host_wait

@@ -64,6 +64,7 @@ struct Span {
   cudaEvent_t a, b;
   int kind;
   double work, bytes;
+  int slot;                           // device span slot (-1: none)
 };
 
 std::mutex g_mu;
@@ -78,6 +79,17 @@ constexpr size_t kMaxTimeline = size_t(1) << 20;
 double g_ms[kProfKinds], g_work[kProfKinds], g_bytes[kProfKinds];
 long long g_count[kProfKinds];
 std::vector<cudaEvent_t> g_pool;
+// Device spans of the kernels that record their own execution (first CTA start
+// to last CTA end on the global timer): a ring of slot pairs on one device,
+// all-ones when unused; token -> slot for the launch between prof_begin and
+// prof_end.
+constexpr int kSpanSlots = 1 << 16;
+unsigned long long* g_span_dev = nullptr;
+int g_span_device = -1;
+int g_span_next = 0;
+std::vector<std::pair<void*, int>> g_span_of;
+double g_dev_ms[kProfKinds];
+long long g_dev_count[kProfKinds];
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -91,6 +103,14 @@ cudaEvent_t take_event() {
 }
 
 void resolve_locked() {
+  std::vector<unsigned long long> spans;
+  for (const Span& s : g_open)
+    if (s.slot >= 0 && spans.empty()) {
+      spans.resize(2 * (size_t)g_span_next);
+      if (cudaMemcpy(spans.data(), g_span_dev, sizeof(unsigned long long) * spans.size(), cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+        spans.clear();
+    }
   for (Span& s : g_open) {
     float ms = 0.0f;
     if (cudaEventSynchronize(s.b) == cudaSuccess && cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
@@ -101,6 +121,13 @@ void resolve_locked() {
       float t0 = 0.0f;
       if (g_origin && g_timeline.size() < kMaxTimeline && cudaEventElapsedTime(&t0, g_origin, s.a) == cudaSuccess)
         g_timeline.push_back(Interval{s.kind, (double)t0, (double)t0 + ms});
+      if (s.slot >= 0 && 2 * (size_t)s.slot + 1 < spans.size()) {
+        const unsigned long long t_start = spans[2 * (size_t)s.slot], t_end = ~spans[2 * (size_t)s.slot + 1];
+        if (t_start != ~0ull && t_end != 0ull && t_end >= t_start) {
+          g_dev_ms[s.kind] += (double)(t_end - t_start) * 1e-6;
+          g_dev_count[s.kind] += 1;
+        }
+      }
     }
     if (s.a != g_origin) g_pool.push_back(s.a);
     g_pool.push_back(s.b);
@@ -184,12 +211,41 @@ void* prof_begin(cudaStream_t st) {
   return (void*)a;
 }
 
+unsigned long long* prof_device_span(void* token) {
+  if (!token) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (!g_span_dev) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(unsigned long long) * 2 * kSpanSlots) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0xFF, sizeof(unsigned long long) * 2 * kSpanSlots) != cudaSuccess) {
+      cudaFree(p);
+      return nullptr;
+    }
+    g_span_dev = (unsigned long long*)p;
+    g_span_device = dev;
+    g_span_next = 0;
+  }
+  if (dev != g_span_device || g_span_next >= kSpanSlots) return nullptr;
+  const int slot = g_span_next++;
+  g_span_of.emplace_back(token, slot);
+  return g_span_dev + 2 * (size_t)slot;
+}
+
 void prof_end(void* token, int kind, double work, cudaStream_t st, double bytes) {
   if (!token) return;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t b = take_event();
   cudaEventRecord(b, st);
-  g_open.push_back(Span{(cudaEvent_t)token, b, kind, work, bytes});
+  int slot = -1;
+  for (size_t i = g_span_of.size(); i-- > 0;)
+    if (g_span_of[i].first == token) {
+      slot = g_span_of[i].second;
+      g_span_of.erase(g_span_of.begin() + (long)i);
+      break;
+    }
+  g_open.push_back(Span{(cudaEvent_t)token, b, kind, work, bytes, slot});
   if (g_open.size() > 4096) resolve_locked();
 }
 
@@ -221,10 +277,30 @@ void hpmxp_prof_enable(int on) { g_enabled.store(on ? 1 : 0); }
 void hpmxp_prof_reset(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   resolve_locked();
-  for (int k = 0; k < kProfKinds; ++k) { g_ms[k] = 0.0; g_work[k] = 0.0; g_bytes[k] = 0.0; g_count[k] = 0; }
+  for (int k = 0; k < kProfKinds; ++k) {
+    g_ms[k] = 0.0; g_work[k] = 0.0; g_bytes[k] = 0.0; g_count[k] = 0;
+    g_dev_ms[k] = 0.0; g_dev_count[k] = 0;
+  }
+  // every recorded kernel has completed (resolve_locked waited for its end event)
+  if (g_span_dev && g_span_next > 0) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev == g_span_device)
+      cudaMemset(g_span_dev, 0xFF, sizeof(unsigned long long) * 2 * (size_t)g_span_next);
+    g_span_next = 0;
+  }
+  g_span_of.clear();
   if (g_origin) g_pool.push_back(g_origin);
   g_origin = nullptr;
   g_timeline.clear();
+}
+
+int hpmxp_prof_read_device(int kind, double* ms, long long* count) {
+  if (kind < 0 || kind >= kProfKinds) return HPMXP_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  resolve_locked();
+  if (ms) *ms = g_dev_ms[kind];
+  if (count) *count = g_dev_count[kind];
+  return HPMXP_OK;
 }
 
 int hpmxp_prof_timeline(double* out, int max_spans) {
