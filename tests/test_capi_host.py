@@ -112,3 +112,10 @@ def test_autotune_search_space():
     assert {c.gemm_tile for c in autotune.candidates(32768, capi.FP8_E4M3, sms)} == {0}
     # nb larger than the matrix is skipped (below 128 the smallest depth stays)
     assert {c.nb for c in autotune.candidates(200, capi.BF16, sms)} == {128}
+
+
+def test_prof_read_device_on_host(lib):
+    # nothing recorded: zeros, no device access; a bad kind is refused
+    assert capi.hpmxp_prof_read_device(capi.PROF_GEMM) == dict(ms=0.0, launches=0)
+    with pytest.raises(capi.HpmxpError):
+        capi.hpmxp_prof_read_device(-1)
