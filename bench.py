@@ -71,6 +71,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
+    ap.add_argument("--cpu-ladder", default="",
+                    help="comma-separated n: time the CPU oracle alone at each (all cores, then one core up to "
+                         "--cpu-ladder-single-max) and print one JSON line; no GPU work")
+    ap.add_argument("--cpu-ladder-single-max", type=int, default=4096)
     ap.add_argument("--workload", default="solve", choices=["solve", "serving"],
                     help="solve: one large system (default); serving: a stream of small systems")
     ap.add_argument("--rate", type=float, default=1000.0, help="serving: Poisson arrival rate, requests/s")
@@ -216,6 +220,25 @@ def cpu_baseline(args, nb: int) -> dict:
             "sample": f"one oracle solve (factor + GMRES-IR) of the same generated system at n={n} "
                       f"(the full n is out of reach on the host), {dt:.2f} s, status {rc}, iters {info['iters']}",
             "single_thread": single}
+
+
+def run_cpu_ladder(args):
+    """The oracle's own rate at several sizes on the host's cores: the ladder the
+    one-sample cpu_baseline stands for, timed once per size (factor + GMRES-IR)."""
+    import oracle
+    cores = oracle.num_threads()
+    nb = args.nb or 128
+    rows = []
+    for n in [int(v) for v in args.cpu_ladder.split(",") if v]:
+        for threads in ([cores, 1] if n <= args.cpu_ladder_single_max else [cores]):
+            oracle.set_num_threads(threads)
+            dt, info, rc = oracle_solve_timed(n, args.seed, args.prec, min(nb, 512))
+            rows.append({"n": n, "threads": threads, "seconds": dt, "tflops": hpl_ops(n) / dt / 1e12,
+                         "status": rc, "iters": info["iters"]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    oracle.set_num_threads(cores)
+    print(json.dumps({"kind": "oracle ladder", "cpu_model": oracle.cpu_model(), "cores": cores, "nb": nb,
+                      "prec": args.prec, "rows": rows}), flush=True)
 
 
 SERVING_METRIC = "served systems/s (n log-uniform in [256, 8192], 1-8 rhs, Poisson arrivals), scaled residual < 16"
@@ -462,6 +485,9 @@ def main():
         IR_KW.update(theta=args.theta)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.cpu_ladder:
+        run_cpu_ladder(args)
         return
     if args.workload == "serving":
         run_serving(args)
