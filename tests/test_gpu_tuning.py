@@ -78,3 +78,19 @@ def test_sm_budget_keeps_results_bit_identical(budget):
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
     assert outs[0][2] == outs[1][2]
+
+
+@pytest.mark.parametrize("prec", [capi.BF16, capi.FP16, capi.FP8_E4M3])
+def test_lookahead_with_balancing_bit_identical(prec):
+    """The four-stream look-ahead (forced on at this order) and the plain
+    schedule give the same factors of the balanced matrix."""
+    n, nb = 2600, 512
+    A, _ = api.generate(n, seed=31, device=DEV)
+    scales = api.balance(A, prec)
+    outs = []
+    for overlap in (0, 128):   # 0: the built-in threshold (8192) keeps this order plain
+        assert capi.hpmxp_set_tuning(0, 0, overlap) == capi.OK
+        LU = api.factor(A, prec, nb, scales=scales)
+        torch.cuda.synchronize(DEV)
+        outs.append(LU.view().float().cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
