@@ -408,12 +408,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         tc_commit(acc_full(ab));
       }
-      if (!ok) {
-        atomicOr(p.status, kErrTimeout);
-        // the MMAs issued before the wait ran out complete before TMEM is freed
-        tc_commit(mma_drain);
-        if (!mbar_wait(mma_drain, 0)) atomicOr(p.status, kErrTimeout);
-      }
+      if (!ok) atomicOr(p.status, kErrTimeout);
+      // every MMA issued has completed before TMEM is freed, also when an
+      // epilogue group gave up before the last accumulator was written
+      tc_commit(mma_drain);
+      if (!mbar_wait(mma_drain, 0)) atomicOr(p.status, kErrTimeout);
     }
   } else {
     // epilogue: group g = (warp - 2) / 4 owns rows i0 + (TI/2) g .. + TI/2 - 1 of the

@@ -207,6 +207,75 @@ def test_gemm_fp8(eng):
     assert np.all(np.abs(got - want) <= 2.0**-7 * np.abs(want) + 1e-2 * np.abs(C0 - want).max() * 2.0**-8 + 0.5)
 
 
+def _fp8_case(M, N, K, seed):
+    g = np.random.default_rng(seed)
+    qa = g.integers(0, 0x7e, size=(M, K), dtype=np.uint8) | (g.integers(0, 2, size=(M, K), dtype=np.uint8) << 7)
+    qb = g.integers(0, 0x7e, size=(N, K), dtype=np.uint8) | (g.integers(0, 2, size=(N, K), dtype=np.uint8) << 7)
+    nk = K // 128
+    sa = g.uniform(0.5, 2, (-(-M // 128), nk)).astype(np.float32)
+    sb = g.uniform(0.5, 2, (-(-N // 128), nk)).astype(np.float32)
+    C0 = _bf16(g.uniform(-4000, 4000, (M, N)))
+    return qa, qb, sa, sb, C0
+
+
+def _fp8_decode(c):
+    # E4M3: 1 sign, 4 exponent (bias 7), 3 mantissa bits; codes below 0x7f are finite
+    s = np.where(c >> 7, -1.0, 1.0)
+    e = (c >> 3) & 15
+    m = (c & 7).astype(np.float64)
+    return s * np.where(e == 0, m / 8 * 2.0**-6, (1 + m / 8) * np.exp2(e.astype(np.float64) - 7))
+
+
+def _fp8_gemm(qa, qb, sa, sb, C0, eng):
+    M, K = qa.shape
+    N = qb.shape[0]
+    tA, tB = torch.from_numpy(qa).to(DEV), torch.from_numpy(qb).to(DEV)
+    tsa, tsb = torch.from_numpy(sa).to(DEV), torch.from_numpy(sb).to(DEV)
+    C = api.ColMajor.from_tensor(torch.from_numpy(C0), DEV, dtype=torch.bfloat16)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    st = capi.hpmxp_test_gemm(M, N, K, tA.data_ptr(), K, tB.data_ptr(), K, C.ptr, C.ld, None, 0, 0, 1.0, 0, 1,
+                              tsa.data_ptr(), sa.shape[1], tsb.data_ptr(), sb.shape[1], eng, status.data_ptr(),
+                              api.stream_handle())
+    assert st == capi.OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    return to_np(C)
+
+
+def _fp8_want(qa, qb, sa, sb, C0):
+    M, K = qa.shape
+    N = qb.shape[0]
+    A, B = _fp8_decode(qa), _fp8_decode(qb)
+    want = C0.copy()
+    for gk in range(K // 128):
+        sl = slice(128 * gk, 128 * gk + 128)
+        sc = sa[np.arange(M) // 128, gk][:, None].astype(np.float64) * sb[np.arange(N) // 128, gk][None, :]
+        want -= (A[:, sl] @ B[:, sl].T) * sc
+    return want
+
+
+@pytest.mark.parametrize("M,N,K,budget", [(1024, 1000, 512, 3), (640, 520, 384, 5), (1200, 900, 512, 0),
+                                          (384, 256, 128, 1)])
+def test_gemm_fp8_slices_reused_across_tiles(M, N, K, budget):
+    # several tiles per CTA (a small SM budget): the E4M3 accumulator (one
+    # TMEM slice per 128-deep K slice) is rewritten by the next tile's MMAs as
+    # soon as the epilogue has read it, so a missing wait would mix two
+    # tiles' sums
+    qa, qb, sa, sb, C0 = _fp8_case(M, N, K, 50 + K)
+    old = capi.hpmxp_get_tuning()
+    try:
+        assert capi.hpmxp_set_tuning(old["gemm_tile"], old["reserve_sms"], old["overlap_min"], budget) == capi.OK
+        got = _fp8_gemm(qa, qb, sa, sb, C0, 0)
+    finally:
+        assert capi.hpmxp_set_tuning(**old) == capi.OK
+    full_grid = _fp8_gemm(qa, qb, sa, sb, C0, 0)
+    assert np.array_equal(got, full_grid)   # each tile's arithmetic does not depend on its CTA
+    want = _fp8_want(qa, qb, sa, sb, C0)
+    assert np.all(np.abs(got - want) <= 2.0**-7 * np.abs(want) + 1e-2 * np.abs(C0 - want).max() * 2.0**-8 + 0.5)
+    simt = _fp8_gemm(qa, qb, sa, sb, C0, 1)
+    assert np.all(np.abs(got - simt) <= 2.0**-7 * np.abs(simt) + 0.5)
+
+
 # ---------------------------------------------------------------------------
 # factorization
 # ---------------------------------------------------------------------------

@@ -97,6 +97,39 @@ def test_gemm_wait_runs_out_then_recovers(M, N, K):
     assert np.all(np.abs(got - want) <= ulp + 1e-5 * np.abs(A).sum(1)[:, None].max())
 
 
+def test_gemm_fp8_wait_runs_out_then_recovers():
+    # E4M3 operands, four 128-deep slices: the per-slice accumulator waits
+    M, N, K = 1024, 1024, 512
+    g = np.random.default_rng(5)
+    codes = lambda r, c: (g.integers(0, 0x60, size=(r, c), dtype=np.uint8)  # noqa: E731
+                          | (g.integers(0, 2, size=(r, c), dtype=np.uint8) << 7))
+    qa, qb = codes(M, K), codes(N, K)
+    sa = np.ones((M // 128, K // 128), np.float32)
+    sb = np.ones((N // 128, K // 128), np.float32)
+    C0 = oracle.round_to(g.uniform(-64, 64, (M, N)), oracle.BF16)
+    tA, tB = torch.from_numpy(qa).to(DEV), torch.from_numpy(qb).to(DEV)
+    tsa, tsb = torch.from_numpy(sa).to(DEV), torch.from_numpy(sb).to(DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+
+    def run(eng):
+        C = api.ColMajor.from_tensor(torch.from_numpy(C0), DEV, dtype=torch.bfloat16)
+        status.zero_()
+        st = capi.hpmxp_test_gemm(M, N, K, tA.data_ptr(), K, tB.data_ptr(), K, C.ptr, C.ld, None, 0, 0, 1.0, 0, 1,
+                                  tsa.data_ptr(), K // 128, tsb.data_ptr(), K // 128, eng, status.data_ptr(),
+                                  api.stream_handle())
+        torch.cuda.synchronize()
+        return st, int(status.item()), C.view().float().double().cpu().numpy()
+
+    with short_budget():
+        st, word, _ = run(0)
+    assert st == capi.OK and word == 1        # the timeout bit, nothing else
+    st, word, got = run(0)
+    assert st == capi.OK and word == 0
+    st, word, simt = run(1)
+    assert st == capi.OK and word == 0
+    assert np.all(np.abs(got - simt) <= 2.0**-7 * np.abs(simt) + 0.5)
+
+
 def test_solve_reports_timeout_then_recovers():
     n = 2048
     A, b = api.generate(n, seed=11, device=DEV)
