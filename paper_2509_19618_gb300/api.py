@@ -57,6 +57,60 @@ class ColMajor:
         return m
 
 
+class HostBuffer:
+    """Page-locked host memory for a caller that keeps its inputs on the host.
+
+    An anonymous mapping advised for transparent huge pages (512 MiB on an Arm
+    kernel with 64 KiB base pages, 2 MiB on x86-64), filled once so its pages
+    exist, then registered with CUDA.  With huge pages a multi-GB copy needs a
+    few address translations instead of one per base page.  Where the kernel
+    refuses the advice the buffer is still pinned, on base pages.
+    ``tensor`` is a CPU tensor of the given shape over the mapping; ``close()``
+    (or garbage collection) unregisters and unmaps it.
+    """
+
+    def __init__(self, shape, dtype=torch.float64):
+        import mmap
+        self.shape = tuple(int(d) for d in shape)
+        numel = int(np.prod(self.shape)) if self.shape else 1
+        self.nbytes = max(numel * torch.empty((), dtype=dtype).element_size(), 1)
+        self._map = mmap.mmap(-1, self.nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+        self.huge_pages = False
+        if hasattr(mmap, "MADV_HUGEPAGE"):
+            try:
+                self._map.madvise(mmap.MADV_HUGEPAGE)
+                self.huge_pages = True
+            except OSError:
+                pass
+        flat = torch.frombuffer(self._map, dtype=dtype, count=numel)
+        flat.zero_()
+        self.tensor = flat.view(self.shape)
+        err = torch.cuda.cudart().cudaHostRegister(flat.data_ptr(), self.nbytes, 0)
+        if int(err) != 0:
+            self.tensor = None
+            self._map.close()
+            raise RuntimeError(f"cudaHostRegister failed ({err}) for {self.nbytes} bytes")
+        self._registered = True
+
+    def close(self):
+        if getattr(self, "_registered", False):
+            torch.cuda.cudart().cudaHostUnregister(self.tensor.data_ptr())
+            self._registered = False
+        self.tensor = None
+        if getattr(self, "_map", None) is not None:
+            try:
+                self._map.close()
+            except BufferError:   # a view of the tensor is still alive: the mapping goes with it
+                pass
+            self._map = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
