@@ -73,7 +73,9 @@ class HostBuffer:
         import mmap
         self.shape = tuple(int(d) for d in shape)
         numel = int(np.prod(self.shape)) if self.shape else 1
-        self.nbytes = max(numel * torch.empty((), dtype=dtype).element_size(), 1)
+        if numel <= 0:
+            raise ValueError(f"HostBuffer of shape {self.shape} holds no elements")
+        self.nbytes = numel * torch.empty((), dtype=dtype).element_size()
         self._map = mmap.mmap(-1, self.nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
         self.huge_pages = False
         if hasattr(mmap, "MADV_HUGEPAGE"):

@@ -42,6 +42,14 @@ def test_host_buffer_registers_whole_mapping_and_unregisters(monkeypatch):
     assert len(rt.calls) == 2
 
 
+def test_host_buffer_rejects_empty_shape(monkeypatch):
+    rt = _FakeRuntime()
+    monkeypatch.setattr(torch.cuda, "cudart", lambda: rt)
+    with pytest.raises(ValueError):
+        api.HostBuffer((0, 5))
+    assert rt.calls == []
+
+
 def test_host_buffer_register_failure_raises(monkeypatch):
     monkeypatch.setattr(torch.cuda, "cudart", lambda: _FakeRuntime(fail=True))
     with pytest.raises(RuntimeError):
