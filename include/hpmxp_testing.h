@@ -64,6 +64,16 @@ hpmxp_status hpmxp_test_set_wait_budget(long long polls, unsigned long long ns);
  * that kernels initialise every shared variable they read. */
 hpmxp_status hpmxp_test_fill_smem(uint32_t pattern, void* stream);
 
+/* The fp64 value of each 16-bit factor entry as the fp64 preconditioner
+ * decodes it (section "Algorithmic Framework": the low-precision factors
+ * applied in 64-bit arithmetic).  The decoding is exact and assembles the
+ * fp64 bit pattern from the 16-bit fields with integer operations.
+ *   codes  device, count 16-bit codes (BF16 or FP16 bit patterns)
+ *   out    device, count doubles
+ *   fmt    HPMXP_BF16 or HPMXP_FP16; anything else HPMXP_EINVAL
+ * One kernel on `stream`; count == 0 launches nothing. */
+hpmxp_status hpmxp_test_decode16(const uint16_t* codes, double* out, int64_t count, int fmt, void* stream);
+
 /* Host-only check of the request executor's arena allocator (no device
  * memory is touched).  ops[i] > 0: allocate that many bytes, result[i] = the
  * 256-byte aligned offset or -1 when no free block fits (first fit);

@@ -126,6 +126,7 @@ def load():
             "hpmxp_test_precond": ([i64, P, i64, i32, P, i64, P, i64, i64, i32, P, sz, P], i32),
             "hpmxp_test_arena": ([sz, ctypes.POINTER(i64), i32, ctypes.POINTER(i64)], i32),
             "hpmxp_test_fill_smem": ([ctypes.c_uint32, P], i32),
+            "hpmxp_test_decode16": ([P, P, i64, i32, P], i32),
             "hpmxp_test_set_wait_budget": ([ctypes.c_longlong, ctypes.c_ulonglong], i32),
             "hpmxp_request_footprint": ([ctypes.POINTER(Request)], sz),
             "hpmxp_executor_create": ([i32, i32, P, sz, ctypes.POINTER(P)], i32),
@@ -328,6 +329,10 @@ def hpmxp_test_precond(*args):
 
 def hpmxp_test_fill_smem(pattern: int, stream) -> int:
     return _call("hpmxp_test_fill_smem", pattern, stream)
+
+
+def hpmxp_test_decode16(codes, out, count: int, fmt: int, stream) -> int:
+    return _call("hpmxp_test_decode16", codes, out, count, fmt, stream)
 
 
 def hpmxp_test_set_wait_budget(polls: int, ns: int) -> int:

@@ -305,4 +305,9 @@ hpmxp_status hpmxp_test_fill_smem(uint32_t pattern, void* stream) {
   return status_from_cuda(fill_smem(pattern, (cudaStream_t)stream));
 }
 
+hpmxp_status hpmxp_test_decode16(const uint16_t* codes, double* out, int64_t count, int fmt, void* stream) {
+  if (count < 0 || (count > 0 && (!codes || !out)) || (fmt != HPMXP_BF16 && fmt != HPMXP_FP16)) return HPMXP_EINVAL;
+  return status_from_cuda(decode16(codes, out, count, fmt, (cudaStream_t)stream));
+}
+
 }  // extern "C"

@@ -71,6 +71,34 @@ __device__ inline float u16_to_f32(uint16_t h, int fmt) {
   if (fmt == kBF16) return __uint_as_float((uint32_t)h << 16);
   return __half2float(__ushort_as_half(h));
 }
+// The same value as an fp64, its bit pattern assembled with integer
+// operations from the IEEE 754 fields (sign; exponent rebased from bias 127
+// (BF16) or 15 (FP16) to 1023; fraction moved to the top of the 52-bit
+// field; subnormals normalised by their leading one; Inf / NaN kept).  The
+// conversion is exact, so the result equals (double)u16_to_f32(h, fmt); it
+// keeps the conversion off GB300's narrow fp64 unit, which then does the
+// FMAs only.
+__device__ inline double u16_to_f64(uint16_t h, int fmt) {
+  const uint32_t sgn = (uint32_t)(h & 0x8000u) << 16;
+  const int fbits = fmt == kBF16 ? 7 : 10;                 // fraction bits
+  const uint32_t emax = fmt == kBF16 ? 0xffu : 0x1fu;     // exponent field all ones
+  const uint32_t bias_shift = fmt == kBF16 ? 896u : 1008u; // 1023 - 127, 1023 - 15
+  const uint32_t e = ((uint32_t)h >> fbits) & emax, m = (uint32_t)h & ((1u << fbits) - 1u);
+  uint32_t hi;
+  if (e == emax) {
+    hi = sgn | 0x7ff00000u | (m << (20 - fbits));
+  } else if (e != 0) {
+    hi = sgn | ((e + bias_shift) << 20) | (m << (20 - fbits));
+  } else if (m == 0) {
+    hi = sgn;
+  } else {
+    // subnormal m 2^(1 - bias - fbits) = 2^(p + 1 - bias - fbits) (1 + f), p = the leading one's bit
+    const int p = 31 - __clz(m);
+    const uint32_t f = (m << (fbits - p)) & ((1u << fbits) - 1u);
+    hi = sgn | (((uint32_t)(p + 1 - fbits) + bias_shift) << 20) | (f << (20 - fbits));
+  }
+  return __hiloint2double((int)hi, 0);
+}
 __device__ inline uint16_t f32_to_u16(float v, int fmt) {
   if (fmt == kBF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
   return __half_as_ushort(__float2half_rn(v));
@@ -166,6 +194,7 @@ size_t solve_batched_ws_bytes(const hpmxp_problem* probs, int count, int restart
 size_t solve_ws_bytes(int64_t n, int64_t nrhs, int restart);
 size_t solve_a32_bytes(int64_t n);   // optional fp32 copy of A after the solve workspace
 cudaError_t fill_smem(uint32_t pattern, cudaStream_t st);   // test support
+cudaError_t decode16(const uint16_t* codes, double* out, int64_t count, int fmt, cudaStream_t st);   // test support
 size_t residual_ws_bytes(int64_t n, int64_t nrhs);
 hpmxp_status precond_apply(int64_t n, const void* LU, int64_t ldlu, int fmt, const double* v, int64_t ldv,
                            double* z, int64_t ldz, int64_t nrhs, int fp32, void* ws, cudaStream_t st,

@@ -311,6 +311,10 @@ constexpr int kTB32 = 128;
 template <class T> __device__ inline T fma_t(T a, T b, T c);
 template <> __device__ inline float fma_t<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 template <> __device__ inline double fma_t<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+// a 16-bit factor entry as T (exact either way; the fp64 one built with integer operations)
+template <class T> __device__ inline T u16_to(uint16_t h, int fmt);
+template <> __device__ inline float u16_to<float>(uint16_t h, int fmt) { return u16_to_f32(h, fmt); }
+template <> __device__ inline double u16_to<double>(uint16_t h, int fmt) { return u16_to_f64(h, fmt); }
 
 // Inverse of diagonal block c (c < nb) of the unit-lower L (which == 0) or of
 // U (which == 1) in T arithmetic, from the 16-bit factors: one thread per
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__(kPrecondThreads<T>) precond_kernel(int64_t n, 
     if (T16) {
 #pragma unroll 8
       for (int jj = h * HC; jj < h * HC + HC; ++jj) {
-        const T tv = (T)u16_to_f32(T16[jj * kTB32 + ii], fmt);
+        const T tv = u16_to<T>(T16[jj * kTB32 + ii], fmt);
 #pragma unroll
         for (int r = 0; r < K; ++r) s[r] = fma_t<T>(tv, w[jj * K + r], s[r]);
       }
@@ -1361,6 +1365,20 @@ __global__ void fill_smem_kernel(uint32_t pattern, uint32_t words) {
   for (uint32_t t = threadIdx.x; t < words; t += blockDim.x) sw[t] = pattern;
   __syncthreads();
   if (sw[(threadIdx.x * 7u) % words] != pattern) asm volatile("" ::: "memory");
+}
+
+// Test support: the fp64 decoding of 16-bit factor entries, one per thread.
+__global__ void decode16_kernel(const uint16_t* __restrict__ codes, double* __restrict__ out, int64_t count,
+                                int fmt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = u16_to_f64(codes[i], fmt);
+}
+
+cudaError_t decode16(const uint16_t* codes, double* out, int64_t count, int fmt, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  decode16_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(codes, out, count, fmt);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t fill_smem(uint32_t pattern, cudaStream_t st) {

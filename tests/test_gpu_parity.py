@@ -276,6 +276,30 @@ def test_gemm_fp8_slices_reused_across_tiles(M, N, K, budget):
     assert np.all(np.abs(got - simt) <= 2.0**-7 * np.abs(simt) + 0.5)
 
 
+@pytest.mark.parametrize("fmt", [capi.BF16, capi.FP16])
+def test_decode16_to_fp64_exhaustive(fmt):
+    # every 16-bit code: the fp64 preconditioner's integer-built decoding equals
+    # the exact conversion (numpy: float16 -> float64; BF16 = the upper half of
+    # a float32), bit for bit; NaN codes decode to NaN
+    codes = np.arange(65536, dtype=np.uint16)
+    with np.errstate(invalid="ignore"):   # signalling NaN codes
+        if fmt == capi.BF16:
+            want = (codes.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        else:
+            want = codes.view(np.float16).astype(np.float64)
+    d_codes = torch.from_numpy(codes.view(np.int16).copy()).to(DEV)
+    out = torch.full((65536,), 7.0, dtype=torch.float64, device=DEV)
+    st = capi.hpmxp_test_decode16(d_codes.data_ptr(), out.data_ptr(), 65536, fmt, api.stream_handle())
+    assert st == capi.OK
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.uint64), want[~nan].view(np.uint64))
+    assert capi.hpmxp_test_decode16(d_codes.data_ptr(), out.data_ptr(), 4, capi.FP8_E4M3,
+                                    api.stream_handle()) == capi.EINVAL
+
+
 # ---------------------------------------------------------------------------
 # factorization
 # ---------------------------------------------------------------------------
